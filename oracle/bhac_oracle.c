@@ -1,0 +1,1109 @@
+/*
+ * Plain FP64 CPU oracle for the per-block finite-volume GRMHD update.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and the
+ * CPU-baseline leg of bench.py may load this file's library.  It shares no
+ * code, header, table or helper with the CUDA path.
+ *
+ * It follows the method of the paper's Sec. 2 ("Code overview"): a
+ * shock-capturing finite-volume scheme on a block grid with ghost cells,
+ * covariant coordinates, a second-order two-stage time stepper, PPM (or
+ * minmod) reconstruction, and a Newton conserved-to-primitive inversion with
+ * backup strategies.  The concrete equations are the standard 3+1 ("Valencia")
+ * ideal GRMHD system with GLM divergence cleaning; each function names the
+ * published form it writes out.  The code favours obviousness over speed:
+ * metric quantities are re-evaluated at every point, nothing is fused.
+ *
+ * Build: gcc -O2 -std=c11 -ffp-contract=off -fopenmp -shared -fPIC
+ * (-ffp-contract=off keeps x86 and Arm results identical).
+ */
+#include "bhac_oracle.h"
+
+#include <complex.h>
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#ifndef M_PI
+#define M_PI 3.14159265358979323846
+#endif
+
+typedef double complex cplx;
+
+/* ------------------------------------------------------------------------ */
+/* Metric                                                                    */
+/* ------------------------------------------------------------------------ */
+
+/* Kerr-Schild spatial metric, lapse and shift (mass M, spin a) in code
+ * coordinates, written for complex arguments so that derivatives follow from
+ * the complex-step method (Squire & Trapp 1998): d f/dx = Im f(x + i h) / h.
+ *   Sigma = r^2 + a^2 cos^2 th, z = 2 M r / Sigma
+ *   gamma_rr = 1 + z, gamma_rph = -a sin^2 th (1 + z), gamma_thth = Sigma,
+ *   gamma_phph = sin^2 th (Sigma + a^2 sin^2 th (1 + z)),
+ *   alpha = 1/sqrt(1 + z), beta^r = z/(1 + z).
+ * Modified KS: r = exp(x1), th = pi x2, ph = x3 (diagonal Jacobian). */
+static void ks_metric_c(const or_params* p, const cplx x[3], cplx* alpha, cplx beta[3], cplx g[3][3]) {
+  cplx r, th, drdx, dthdx;
+  const double a = p->spin, M = p->mass;
+  if (p->coords == OR_MKS) {
+    r = cexp(x[0]);
+    th = M_PI * x[1];
+    drdx = r;
+    dthdx = M_PI;
+  } else {
+    r = x[0];
+    th = x[1];
+    drdx = 1.0;
+    dthdx = 1.0;
+  }
+  cplx s = csin(th), c = ccos(th);
+  cplx Sigma = r * r + a * a * c * c;
+  cplx z = 2.0 * M * r / Sigma;
+  cplx grr = 1.0 + z;
+  cplx grp = -a * s * s * (1.0 + z);
+  cplx gtt = Sigma;
+  cplx gpp = s * s * (Sigma + a * a * s * s * (1.0 + z));
+  *alpha = 1.0 / csqrt(1.0 + z);
+  beta[0] = z / (1.0 + z) / drdx;
+  beta[1] = 0.0;
+  beta[2] = 0.0;
+  g[0][0] = grr * drdx * drdx;
+  g[0][1] = 0.0;
+  g[0][2] = grp * drdx;
+  g[1][1] = gtt * dthdx * dthdx;
+  g[1][2] = 0.0;
+  g[2][2] = gpp;
+  g[1][0] = g[0][1];
+  g[2][0] = g[0][2];
+  g[2][1] = g[1][2];
+}
+
+static double det3(const double g[3][3]) {
+  return g[0][0] * (g[1][1] * g[2][2] - g[1][2] * g[2][1]) - g[0][1] * (g[1][0] * g[2][2] - g[1][2] * g[2][0]) +
+         g[0][2] * (g[1][0] * g[2][1] - g[1][1] * g[2][0]);
+}
+
+/* Inverse by cofactors: gi = adj(g) / det(g). */
+static void inv3(const double g[3][3], double gi[3][3]) {
+  double d = det3(g);
+  gi[0][0] = (g[1][1] * g[2][2] - g[1][2] * g[2][1]) / d;
+  gi[0][1] = (g[0][2] * g[2][1] - g[0][1] * g[2][2]) / d;
+  gi[0][2] = (g[0][1] * g[1][2] - g[0][2] * g[1][1]) / d;
+  gi[1][0] = (g[1][2] * g[2][0] - g[1][0] * g[2][2]) / d;
+  gi[1][1] = (g[0][0] * g[2][2] - g[0][2] * g[2][0]) / d;
+  gi[1][2] = (g[0][2] * g[1][0] - g[0][0] * g[1][2]) / d;
+  gi[2][0] = (g[1][0] * g[2][1] - g[1][1] * g[2][0]) / d;
+  gi[2][1] = (g[0][1] * g[2][0] - g[0][0] * g[2][1]) / d;
+  gi[2][2] = (g[0][0] * g[1][1] - g[0][1] * g[1][0]) / d;
+}
+
+void or_metric_at(const or_params* p, const double x[3], int with_derivs, or_metric* m) {
+  memset(m, 0, sizeof(*m));
+  if (p->coords == OR_CART) {
+    m->alpha = 1.0;
+    for (int i = 0; i < 3; ++i) m->g[i][i] = m->gi[i][i] = 1.0;
+    m->sqrtg = 1.0;
+    return;
+  }
+  cplx xc[3] = {x[0], x[1], x[2]};
+  cplx al, be[3], g[3][3];
+  ks_metric_c(p, xc, &al, be, g);
+  m->alpha = creal(al);
+  for (int i = 0; i < 3; ++i) {
+    m->beta[i] = creal(be[i]);
+    for (int j = 0; j < 3; ++j) m->g[i][j] = creal(g[i][j]);
+  }
+  double d = det3(m->g);
+  m->sqrtg = d > 0.0 ? sqrt(d) : 0.0;
+  if (d > 0.0) inv3(m->g, m->gi);
+  if (!with_derivs) return;
+  const double h = 1e-30;
+  for (int k = 0; k < 3; ++k) {
+    cplx xp[3] = {x[0], x[1], x[2]};
+    xp[k] += I * h;
+    ks_metric_c(p, xp, &al, be, g);
+    m->da[k] = cimag(al) / h;
+    for (int i = 0; i < 3; ++i) {
+      m->db[k][i] = cimag(be[i]) / h;
+      for (int j = 0; j < 3; ++j) m->dg[k][i][j] = cimag(g[i][j]) / h;
+    }
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Point-wise GRMHD (3+1 Valencia form; Anton et al. 2006, Del Zanna et al.  */
+/* 2007; GLM after Dedner et al. 2002)                                       */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+  double rho, p, u[3], B[3], psi;
+  double ul[3], u2, W, v[3], vl[3], v2;
+  double Bl[3], B2, Bv, b2, rhoh, ptot;
+} state;
+
+static void make_state(const or_params* pp, const or_metric* m, const double P[OR_NV], state* s) {
+  s->rho = P[OR_RHO];
+  s->p = P[OR_P];
+  for (int i = 0; i < 3; ++i) {
+    s->u[i] = P[OR_U1 + i];
+    s->B[i] = P[OR_B1 + i];
+  }
+  s->psi = P[OR_PSI];
+  s->u2 = 0.0;
+  s->B2 = 0.0;
+  for (int i = 0; i < 3; ++i) {
+    s->ul[i] = 0.0;
+    s->Bl[i] = 0.0;
+    for (int j = 0; j < 3; ++j) {
+      s->ul[i] += m->g[i][j] * s->u[j];
+      s->Bl[i] += m->g[i][j] * s->B[j];
+    }
+  }
+  for (int i = 0; i < 3; ++i) {
+    s->u2 += s->u[i] * s->ul[i];
+    s->B2 += s->B[i] * s->Bl[i];
+  }
+  s->W = sqrt(1.0 + s->u2);
+  s->Bv = 0.0;
+  for (int i = 0; i < 3; ++i) {
+    s->v[i] = s->u[i] / s->W;
+    s->vl[i] = s->ul[i] / s->W;
+    s->Bv += s->B[i] * s->vl[i];
+  }
+  s->v2 = s->u2 / (s->W * s->W);
+  s->b2 = s->B2 / (s->W * s->W) + s->Bv * s->Bv;
+  s->rhoh = s->rho + pp->gamma_ad / (pp->gamma_ad - 1.0) * s->p;
+  s->ptot = s->p + 0.5 * s->b2;
+}
+
+/* D = rho W, S_j = (rho h W^2 + B^2) v_j - (B.v) B_j,
+ * tau = rho h W^2 - p + B^2 - (B^2/W^2 + (B.v)^2)/2 - D. */
+static void cons_of_state(const state* s, double U[OR_NV]) {
+  double Z = s->rhoh * s->W * s->W;
+  U[OR_D] = s->rho * s->W;
+  for (int j = 0; j < 3; ++j) U[OR_S1 + j] = (Z + s->B2) * s->vl[j] - s->Bv * s->Bl[j];
+  U[OR_TAU] = Z - s->p + s->B2 - 0.5 * s->b2 - U[OR_D];
+  for (int j = 0; j < 3; ++j) U[OR_B1 + j] = s->B[j];
+  U[OR_PSI] = s->psi;
+}
+
+void or_prim2con(const or_params* p, const or_metric* m, const double P[OR_NV], double U[OR_NV]) {
+  state s;
+  make_state(p, m, P, &s);
+  cons_of_state(&s, U);
+}
+
+/* Mixed-index stress W^i_j = S_j v^i + p_tot delta^i_j - B^i B_j / W^2 - (B.v) B^i v_j. */
+static double stress(const state* s, const double U[OR_NV], int i, int j) {
+  double w = U[OR_S1 + j] * s->v[i] - s->B[i] * s->Bl[j] / (s->W * s->W) - s->Bv * s->B[i] * s->vl[j];
+  if (i == j) w += s->ptot;
+  return w;
+}
+
+/* Fluxes along direction i (undensitized):
+ *   F(D)    = D (alpha v^i - beta^i)
+ *   F(S_j)  = alpha W^i_j - beta^i S_j
+ *   F(tau)  = alpha (S^i - D v^i) - beta^i tau
+ *   F(B^j)  = (alpha v^i - beta^i) B^j - (alpha v^j - beta^j) B^i + alpha gamma^ij psi
+ *   F(psi)  = alpha ch^2 B^i - beta^i psi */
+static void flux_of_state(const or_params* p, const or_metric* m, const state* s, const double U[OR_NV], int i,
+                          double F[OR_NV]) {
+  const double al = m->alpha;
+  F[OR_D] = U[OR_D] * (al * s->v[i] - m->beta[i]);
+  for (int j = 0; j < 3; ++j) F[OR_S1 + j] = al * stress(s, U, i, j) - m->beta[i] * U[OR_S1 + j];
+  double Si = 0.0;
+  for (int j = 0; j < 3; ++j) Si += m->gi[i][j] * U[OR_S1 + j];
+  F[OR_TAU] = al * (Si - U[OR_D] * s->v[i]) - m->beta[i] * U[OR_TAU];
+  for (int j = 0; j < 3; ++j)
+    F[OR_B1 + j] = (al * s->v[i] - m->beta[i]) * s->B[j] - (al * s->v[j] - m->beta[j]) * s->B[i] +
+                   al * m->gi[i][j] * s->psi;
+  F[OR_PSI] = al * p->ch * p->ch * s->B[i] - m->beta[i] * s->psi;
+}
+
+void or_flux(const or_params* p, const or_metric* m, const double P[OR_NV], int dir, double F[OR_NV]) {
+  state s;
+  double U[OR_NV];
+  make_state(p, m, P, &s);
+  cons_of_state(&s, U);
+  flux_of_state(p, m, &s, U, dir, F);
+}
+
+/* Fast-magnetosonic speed bound (Del Zanna et al. 2007): in the fluid frame
+ * a^2 = cs^2 + ca^2 - cs^2 ca^2, with cs^2 = Gamma p / (rho h) and
+ * ca^2 = b^2 / (rho h + b^2); boosted to the Eulerian frame and shifted:
+ *   lam = alpha/(1 - v^2 a^2) [v^i (1 - a^2) +- sqrt(a^2 (1 - v^2)
+ *         (gamma^ii (1 - v^2 a^2) - v^i v^i (1 - a^2)))] - beta^i. */
+static void speeds_of_state(const or_params* p, const or_metric* m, const state* s, int i, double* lm,
+                            double* lp) {
+  double cs2 = p->gamma_ad * s->p / s->rhoh;
+  double ca2 = s->b2 / (s->rhoh + s->b2);
+  double a2 = cs2 + ca2 - cs2 * ca2;
+  double vi = s->v[i];
+  double disc = a2 * (1.0 - s->v2) * (m->gi[i][i] * (1.0 - s->v2 * a2) - vi * vi * (1.0 - a2));
+  if (disc < 0.0) disc = 0.0;
+  double sq = sqrt(disc);
+  double den = 1.0 - s->v2 * a2;
+  *lp = m->alpha * (vi * (1.0 - a2) + sq) / den - m->beta[i];
+  *lm = m->alpha * (vi * (1.0 - a2) - sq) / den - m->beta[i];
+}
+
+void or_wavespeeds(const or_params* p, const or_metric* m, const double P[OR_NV], int dir, double* lm,
+                   double* lp) {
+  state s;
+  make_state(p, m, P, &s);
+  speeds_of_state(p, m, &s, dir, lm, lp);
+}
+
+/* Geometric sources for a stationary metric (E = tau + D):
+ *   S(S_j) = 1/2 alpha W^ik d_j gamma_ik + S_i d_j beta^i - E d_j alpha
+ *   S(tau) = 1/2 W^ik beta^j d_j gamma_ik + W^j_i d_j beta^i - S^j d_j alpha
+ *   S(psi) = -alpha kappa psi - psi d_i beta^i + ch^2 B^i d_i alpha
+ *   S(D) = S(B^j) = 0. */
+void or_sources(const or_params* p, const or_metric* m, const double P[OR_NV], double S[OR_NV]) {
+  state s;
+  double U[OR_NV], Wmix[3][3], Wup[3][3], Sup[3];
+  make_state(p, m, P, &s);
+  cons_of_state(&s, U);
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) Wmix[i][j] = stress(&s, U, i, j); /* W^i_j */
+  for (int i = 0; i < 3; ++i)
+    for (int k = 0; k < 3; ++k) {
+      Wup[i][k] = 0.0;
+      for (int l = 0; l < 3; ++l) Wup[i][k] += Wmix[i][l] * m->gi[l][k];
+    }
+  for (int i = 0; i < 3; ++i) {
+    Sup[i] = 0.0;
+    for (int j = 0; j < 3; ++j) Sup[i] += m->gi[i][j] * U[OR_S1 + j];
+  }
+  double E = U[OR_TAU] + U[OR_D];
+  for (int v = 0; v < OR_NV; ++v) S[v] = 0.0;
+  for (int j = 0; j < 3; ++j) {
+    double a = 0.0;
+    for (int i = 0; i < 3; ++i)
+      for (int k = 0; k < 3; ++k) a += 0.5 * m->alpha * Wup[i][k] * m->dg[j][i][k];
+    for (int i = 0; i < 3; ++i) a += U[OR_S1 + i] * m->db[j][i];
+    a -= E * m->da[j];
+    S[OR_S1 + j] = a;
+  }
+  double t = 0.0;
+  for (int j = 0; j < 3; ++j)
+    for (int i = 0; i < 3; ++i)
+      for (int k = 0; k < 3; ++k) t += 0.5 * Wup[i][k] * m->beta[j] * m->dg[j][i][k];
+  for (int j = 0; j < 3; ++j)
+    for (int i = 0; i < 3; ++i) t += Wmix[j][i] * m->db[j][i];
+  for (int j = 0; j < 3; ++j) t -= Sup[j] * m->da[j];
+  S[OR_TAU] = t;
+  double divb = m->db[0][0] + m->db[1][1] + m->db[2][2];
+  double ps = -m->alpha * p->kappa * s.psi - s.psi * divb;
+  for (int i = 0; i < 3; ++i) ps += p->ch * p->ch * s.B[i] * m->da[i];
+  S[OR_PSI] = ps;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Conserved -> primitive inversion                                           */
+/* ------------------------------------------------------------------------ */
+
+/* Invariants of the conserved state used by the inversion. */
+typedef struct {
+  double D, E, S2, B2, BS, Sup[3], Bl[3];
+} c2p_in;
+
+/* Ideal-gas pressure as a function of Z = rho h W^2 and v^2:
+ *   p = (Gamma-1)/Gamma (Z (1 - v^2) - D sqrt(1 - v^2)). */
+static double c2p_pressure(double gam, double D, double Z, double v2) {
+  return (gam - 1.0) / gam * (Z * (1.0 - v2) - D * sqrt(1.0 - v2));
+}
+
+/* v^2 implied by the momentum equation at a given Z:
+ *   S^2 = (Z + B^2)^2 v^2 - (B.S)^2 (2 Z + B^2) / Z^2. */
+static double c2p_v2_of_Z(const c2p_in* q, double Z) {
+  double num = q->S2 + q->BS * q->BS * (2.0 * Z + q->B2) / (Z * Z);
+  return num / ((Z + q->B2) * (Z + q->B2));
+}
+
+/* Energy residual of the one-dimensional formulation (v^2 clamped to [0, v2max]):
+ *   f(Z) = Z - p + B^2 (1 + v^2)/2 - (B.S)^2/(2 Z^2) - E. */
+static double c2p_f1d(const c2p_in* q, double gam, double v2max, double Z) {
+  double v2 = c2p_v2_of_Z(q, Z);
+  if (v2 > v2max) v2 = v2max;
+  if (v2 < 0.0) v2 = 0.0;
+  return Z - c2p_pressure(gam, q->D, Z, v2) + 0.5 * q->B2 * (1.0 + v2) - 0.5 * q->BS * q->BS / (Z * Z) - q->E;
+}
+
+static int finite9(const double* x) {
+  for (int i = 0; i < OR_NV; ++i)
+    if (!isfinite(x[i])) return 0;
+  return 1;
+}
+
+/* Primary solver: two-dimensional Newton-Raphson in (Z, v^2) on the momentum
+ * and energy equations (the "2D" scheme of Noble et al. 2006), started from
+ * the previous primitives; stop when |dZ| <= tol Z, then one polishing step.
+ * Backup: bracketed bisection on Z of the one-dimensional energy residual.
+ * Last resort: keep the previous primitives (status 3).  Floors last. */
+int or_con2prim(const or_params* p, const or_metric* m, const double U[OR_NV], const double Pg[OR_NV],
+                double r_floor, double P[OR_NV]) {
+  const double gam = p->gamma_ad, gf = (gam - 1.0) / gam;
+  const double v2max = 1.0 - 1.0 / (p->w_max * p->w_max);
+  c2p_in q;
+  q.D = U[OR_D];
+  q.E = U[OR_TAU] + U[OR_D];
+  for (int i = 0; i < 3; ++i) {
+    q.Sup[i] = 0.0;
+    q.Bl[i] = 0.0;
+    for (int j = 0; j < 3; ++j) {
+      q.Sup[i] += m->gi[i][j] * U[OR_S1 + j];
+      q.Bl[i] += m->g[i][j] * U[OR_B1 + j];
+    }
+  }
+  q.S2 = q.B2 = q.BS = 0.0;
+  for (int i = 0; i < 3; ++i) {
+    q.S2 += q.Sup[i] * U[OR_S1 + i];
+    q.B2 += U[OR_B1 + i] * q.Bl[i];
+    q.BS += U[OR_B1 + i] * U[OR_S1 + i];
+  }
+  int status = 0;
+  double Z = 0.0, v2 = 0.0;
+  int solved = 0;
+  if (finite9(U) && q.D > 0.0 && q.E > 0.0) {
+    /* initial guess from the previous primitives */
+    double ul[3], u2 = 0.0;
+    for (int i = 0; i < 3; ++i) {
+      ul[i] = 0.0;
+      for (int j = 0; j < 3; ++j) ul[i] += m->g[i][j] * Pg[OR_U1 + j];
+    }
+    for (int i = 0; i < 3; ++i) u2 += Pg[OR_U1 + i] * ul[i];
+    Z = (Pg[OR_RHO] + gam / (gam - 1.0) * Pg[OR_P]) * (1.0 + u2);
+    v2 = u2 / (1.0 + u2);
+    if (!(Z > 0.0) || !isfinite(Z)) Z = q.E;
+    int polish = 0;
+    for (int it = 0; it < p->c2p_maxit; ++it) {
+      double sq = sqrt(1.0 - v2);
+      double pr = gf * (Z * (1.0 - v2) - q.D * sq);
+      double BS2 = q.BS * q.BS;
+      double f1 = (Z + q.B2) * (Z + q.B2) * v2 - BS2 * (2.0 * Z + q.B2) / (Z * Z) - q.S2;
+      double f2 = Z - pr + 0.5 * q.B2 * (1.0 + v2) - 0.5 * BS2 / (Z * Z) - q.E;
+      double j11 = 2.0 * (Z + q.B2) * v2 + 2.0 * BS2 * (Z + q.B2) / (Z * Z * Z);
+      double j12 = (Z + q.B2) * (Z + q.B2);
+      double dpdZ = gf * (1.0 - v2);
+      double dpdv2 = gf * (-Z + 0.5 * q.D / sq);
+      double j21 = 1.0 - dpdZ + BS2 / (Z * Z * Z);
+      double j22 = -dpdv2 + 0.5 * q.B2;
+      double det = j11 * j22 - j12 * j21;
+      double dZ = (-f1 * j22 + f2 * j12) / det;
+      double dv2 = (-f2 * j11 + f1 * j21) / det;
+      double Zn = Z + dZ, v2n = v2 + dv2;
+      if (!(Zn > 0.0)) Zn = 0.5 * Z;
+      if (v2n < 0.0) v2n = 0.5 * v2;
+      if (v2n >= 1.0) v2n = 0.5 * (v2 + 1.0);
+      int conv = fabs(Zn - Z) <= p->c2p_tol * Zn;
+      Z = Zn;
+      v2 = v2n;
+      if (!isfinite(Z) || !isfinite(v2)) break;
+      if (polish) {
+        solved = 1;
+        break;
+      }
+      if (conv) polish = 1;
+    }
+    if (solved && !(v2 >= 0.0 && v2 < 1.0 && Z > 0.0)) solved = 0;
+    if (solved) {
+      double W = 1.0 / sqrt(1.0 - v2);
+      if (!(q.D / W > 0.0)) solved = 0;
+    }
+    if (!solved) {
+      /* backup: bisection on the bracketed one-dimensional residual */
+      double Z0 = (Pg[OR_RHO] + gam / (gam - 1.0) * Pg[OR_P]) * (1.0 + u2);
+      if (!(Z0 > 0.0) || !isfinite(Z0)) Z0 = q.E;
+      double lo = Z0, hi = Z0;
+      int k = 0;
+      while (c2p_f1d(&q, gam, v2max, lo) > 0.0 && k < 200) {
+        lo *= 0.5;
+        ++k;
+      }
+      k = 0;
+      while (c2p_f1d(&q, gam, v2max, hi) < 0.0 && k < 200) {
+        hi *= 2.0;
+        ++k;
+      }
+      if (c2p_f1d(&q, gam, v2max, lo) <= 0.0 && c2p_f1d(&q, gam, v2max, hi) >= 0.0) {
+        for (int it = 0; it < 200 && hi - lo > 4e-16 * hi; ++it) {
+          double mid = 0.5 * (lo + hi);
+          if (c2p_f1d(&q, gam, v2max, mid) > 0.0)
+            hi = mid;
+          else
+            lo = mid;
+        }
+        Z = 0.5 * (lo + hi);
+        v2 = c2p_v2_of_Z(&q, Z);
+        if (v2 > v2max) v2 = v2max;
+        if (v2 < 0.0) v2 = 0.0;
+        if (isfinite(Z) && Z > 0.0) {
+          solved = 1;
+          status = 1;
+        }
+      }
+    }
+  }
+  if (solved) {
+    double W = 1.0 / sqrt(1.0 - v2);
+    P[OR_RHO] = q.D / W;
+    P[OR_P] = c2p_pressure(gam, q.D, Z, v2);
+    for (int i = 0; i < 3; ++i) P[OR_U1 + i] = W * (q.Sup[i] + q.BS / Z * U[OR_B1 + i]) / (Z + q.B2);
+  } else {
+    status = 3;
+    P[OR_RHO] = Pg[OR_RHO];
+    P[OR_P] = Pg[OR_P];
+    for (int i = 0; i < 3; ++i) P[OR_U1 + i] = Pg[OR_U1 + i];
+  }
+  for (int i = 0; i < 3; ++i) P[OR_B1 + i] = U[OR_B1 + i];
+  P[OR_PSI] = U[OR_PSI];
+  /* floors: rho >= rho_fl r^k1, p >= p_fl r^k2, W <= W_max */
+  int fl = 0;
+  double rfl = p->rho_floor * pow(r_floor, p->rho_floor_pow);
+  double pfl = p->p_floor * pow(r_floor, p->p_floor_pow);
+  if (!(P[OR_RHO] >= rfl)) {
+    P[OR_RHO] = rfl;
+    fl = 1;
+  }
+  if (!(P[OR_P] >= pfl)) {
+    P[OR_P] = pfl;
+    fl = 1;
+  }
+  double u2 = 0.0;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) u2 += m->g[i][j] * P[OR_U1 + i] * P[OR_U1 + j];
+  if (1.0 + u2 > p->w_max * p->w_max) {
+    double s = sqrt((p->w_max * p->w_max - 1.0) / u2);
+    for (int i = 0; i < 3; ++i) P[OR_U1 + i] *= s;
+    fl = 1;
+  }
+  if (status == 3) return 3;
+  if (fl) return 2;
+  return status;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Reconstruction and numerical flux                                          */
+/* ------------------------------------------------------------------------ */
+
+static double minmod(double a, double b) {
+  if (a * b <= 0.0) return 0.0;
+  return fabs(a) < fabs(b) ? a : b;
+}
+
+/* PPM interface value (Colella & Woodward 1984): fourth-order estimate
+ * 7/12 (a_k + a_k+1) - 1/12 (a_k-1 + a_k+2), clipped between a_k and a_k+1. */
+static double ppm_iface(double am1, double a0, double a1, double a2) {
+  double v = 7.0 / 12.0 * (a0 + a1) - 1.0 / 12.0 * (am1 + a2);
+  double lo = a0 < a1 ? a0 : a1, hi = a0 < a1 ? a1 : a0;
+  if (v < lo) v = lo;
+  if (v > hi) v = hi;
+  return v;
+}
+
+/* CW84 monotonicity constraints on the parabola of a cell with mean a and
+ * edge values (aL, aR): flatten at a local extremum, otherwise pull the
+ * far edge in so the parabola does not overshoot. */
+static void ppm_limit(double a, double* aL, double* aR) {
+  if ((*aR - a) * (a - *aL) <= 0.0) {
+    *aL = a;
+    *aR = a;
+    return;
+  }
+  double d = *aR - *aL;
+  double m6 = 6.0 * (a - 0.5 * (*aL + *aR));
+  if (d * m6 > d * d) *aL = 3.0 * a - 2.0 * (*aR);
+  if (-d * d > d * m6) *aR = 3.0 * a - 2.0 * (*aL);
+}
+
+/* Face states from stencil cells 0..5 (the face lies between cells 2 and 3).
+ * If either state has rho <= 0 or p <= 0 the face falls back to first order. */
+void or_reconstruct(const or_params* p, const double st[6][OR_NV], double PL[OR_NV], double PR[OR_NV]) {
+  for (int v = 0; v < OR_NV; ++v) {
+    double a0 = st[0][v], a1 = st[1][v], a2 = st[2][v], a3 = st[3][v], a4 = st[4][v], a5 = st[5][v];
+    if (p->recon == 0) {
+      /* cell 2 (left of the face) and cell 3 (right of the face) */
+      double l2 = ppm_iface(a0, a1, a2, a3), r2 = ppm_iface(a1, a2, a3, a4);
+      double l3 = ppm_iface(a1, a2, a3, a4), r3 = ppm_iface(a2, a3, a4, a5);
+      ppm_limit(a2, &l2, &r2);
+      ppm_limit(a3, &l3, &r3);
+      PL[v] = r2;
+      PR[v] = l3;
+    } else {
+      PL[v] = a2 + 0.5 * minmod(a2 - a1, a3 - a2);
+      PR[v] = a3 - 0.5 * minmod(a3 - a2, a4 - a3);
+    }
+  }
+  if (!(PL[OR_RHO] > 0.0) || !(PL[OR_P] > 0.0) || !(PR[OR_RHO] > 0.0) || !(PR[OR_P] > 0.0)) {
+    for (int v = 0; v < OR_NV; ++v) {
+      PL[v] = st[2][v];
+      PR[v] = st[3][v];
+    }
+  }
+}
+
+/* HLL (Harten, Lax & van Leer 1983) or TVDLF (Rusanov) flux, densitized by
+ * the face sqrt(gamma).  The GLM pair (normal B, psi) uses signal speeds no
+ * smaller than its own characteristic speeds +-alpha ch sqrt(gamma^ii) - beta^i. */
+void or_face_flux(const or_params* p, const or_metric* m, const double PL[OR_NV], const double PR[OR_NV],
+                  int dir, double F[OR_NV]) {
+  state sL, sR;
+  double UL[OR_NV], UR[OR_NV], FL[OR_NV], FR[OR_NV];
+  double lmL, lpL, lmR, lpR;
+  make_state(p, m, PL, &sL);
+  make_state(p, m, PR, &sR);
+  cons_of_state(&sL, UL);
+  cons_of_state(&sR, UR);
+  flux_of_state(p, m, &sL, UL, dir, FL);
+  flux_of_state(p, m, &sR, UR, dir, FR);
+  speeds_of_state(p, m, &sL, dir, &lmL, &lpL);
+  speeds_of_state(p, m, &sR, dir, &lmR, &lpR);
+  double cg = m->alpha * p->ch * sqrt(m->gi[dir][dir]);
+  double lgp = cg - m->beta[dir], lgm = -cg - m->beta[dir];
+  for (int v = 0; v < OR_NV; ++v) {
+    int glm = (v == OR_PSI) || (v == OR_B1 + dir);
+    double f;
+    if (p->riemann == 0) {
+      double lp = 0.0, lm = 0.0;
+      if (lpL > lp) lp = lpL;
+      if (lpR > lp) lp = lpR;
+      if (lmL < lm) lm = lmL;
+      if (lmR < lm) lm = lmR;
+      if (glm) {
+        if (lgp > lp) lp = lgp;
+        if (lgm < lm) lm = lgm;
+      }
+      if (lp - lm > 0.0)
+        f = (lp * FL[v] - lm * FR[v] + lp * lm * (UR[v] - UL[v])) / (lp - lm);
+      else
+        f = 0.5 * (FL[v] + FR[v]);
+    } else {
+      double c = fabs(lpL);
+      if (fabs(lmL) > c) c = fabs(lmL);
+      if (fabs(lpR) > c) c = fabs(lpR);
+      if (fabs(lmR) > c) c = fabs(lmR);
+      if (glm) {
+        if (fabs(lgp) > c) c = fabs(lgp);
+        if (fabs(lgm) > c) c = fabs(lgm);
+      }
+      f = 0.5 * (FL[v] + FR[v]) - 0.5 * c * (UR[v] - UL[v]);
+    }
+    F[v] = m->sqrtg * f;
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Block grid                                                                 */
+/* ------------------------------------------------------------------------ */
+
+struct or_ctx {
+  or_params p;
+  int nb;
+  int* blk;        /* nb x 4 : level, ix, iy, iz */
+  int gd[3];       /* ghosts per dimension */
+  int N[3];        /* ghosted extent per dimension */
+  int ncell;       /* ghosted cells per block */
+  int nint;        /* interior cells per block */
+  double* prim;    /* nb x NV x ghosted */
+  double* ucur;    /* nb x NV x interior, densitized */
+  double* un;      /* conserved at the start of the step */
+  double* flux[3]; /* nb x NV x face-array per direction */
+  int* lut[8];     /* per level: block id at block coordinates, -1 if not a leaf */
+  long long counts[4];
+};
+
+static long lut_size(const or_ctx* c, int L) {
+  long n = 1;
+  for (int d = 0; d < 3; ++d) n *= (long)c->p.nroot[d] << (d < c->p.ndim ? L : 0);
+  return n;
+}
+
+static int lut_get(const or_ctx* c, int L, const long bc[3]) {
+  if (L < 0 || L >= c->p.nlevels) return -1;
+  long nbd[3];
+  for (int d = 0; d < 3; ++d) {
+    nbd[d] = (long)c->p.nroot[d] << (d < c->p.ndim ? L : 0);
+    if (bc[d] < 0 || bc[d] >= nbd[d]) return -1;
+  }
+  return c->lut[L][(bc[2] * nbd[1] + bc[1]) * nbd[0] + bc[0]];
+}
+
+static size_t pidx(const or_ctx* c, int b, int v, int i, int j, int k) {
+  return ((((size_t)b * OR_NV + v) * c->N[2] + k) * c->N[1] + j) * c->N[0] + i;
+}
+
+static size_t uidx(const or_ctx* c, int b, int v, int i, int j, int k) {
+  return ((((size_t)b * OR_NV + v) * c->p.nx[2] + k) * c->p.nx[1] + j) * c->p.nx[0] + i;
+}
+
+static double dxl(const or_ctx* c, int d, int L) {
+  int scale = d < c->p.ndim ? (1 << L) : 1;
+  return (c->p.xmax[d] - c->p.xmin[d]) / ((double)c->p.nroot[d] * c->p.nx[d] * scale);
+}
+
+/* coordinate of cell-centre (off = 0.5) or low face (off = 0) of global index G at level L */
+static double coord(const or_ctx* c, int d, int L, long G, double off) {
+  return c->p.xmin[d] + ((double)G + off) * dxl(c, d, L);
+}
+
+static double floor_radius(const or_params* p, const double x[3]) {
+  if (p->coords == OR_KS) return x[0];
+  if (p->coords == OR_MKS) return exp(x[0]);
+  return 1.0;
+}
+
+or_ctx* or_create(const or_params* p, int nblocks, const int* blocks) {
+  or_ctx* c = (or_ctx*)calloc(1, sizeof(or_ctx));
+  c->p = *p;
+  c->nb = nblocks;
+  c->blk = (int*)malloc(sizeof(int) * 4 * nblocks);
+  memcpy(c->blk, blocks, sizeof(int) * 4 * nblocks);
+  c->ncell = 1;
+  c->nint = 1;
+  for (int d = 0; d < 3; ++d) {
+    c->gd[d] = d < p->ndim ? p->ng : 0;
+    c->N[d] = p->nx[d] + 2 * c->gd[d];
+    c->ncell *= c->N[d];
+    c->nint *= p->nx[d];
+  }
+  c->prim = (double*)calloc((size_t)nblocks * OR_NV * c->ncell, sizeof(double));
+  c->ucur = (double*)calloc((size_t)nblocks * OR_NV * c->nint, sizeof(double));
+  c->un = (double*)calloc((size_t)nblocks * OR_NV * c->nint, sizeof(double));
+  for (int d = 0; d < p->ndim; ++d) {
+    size_t nf = (size_t)c->nint / p->nx[d] * (p->nx[d] + 1);
+    c->flux[d] = (double*)calloc((size_t)nblocks * OR_NV * nf, sizeof(double));
+  }
+  for (int L = 0; L < p->nlevels && L < 8; ++L) {
+    long n = lut_size(c, L);
+    c->lut[L] = (int*)malloc(sizeof(int) * n);
+    for (long i = 0; i < n; ++i) c->lut[L][i] = -1;
+  }
+  for (int b = 0; b < nblocks; ++b) {
+    int L = blocks[4 * b];
+    long nbd[3];
+    for (int d = 0; d < 3; ++d) nbd[d] = (long)p->nroot[d] << (d < p->ndim ? L : 0);
+    c->lut[L][((long)blocks[4 * b + 3] * nbd[1] + blocks[4 * b + 2]) * nbd[0] + blocks[4 * b + 1]] = b;
+  }
+  return c;
+}
+
+void or_destroy(or_ctx* c) {
+  if (!c) return;
+  free(c->blk);
+  free(c->prim);
+  free(c->ucur);
+  free(c->un);
+  for (int d = 0; d < 3; ++d) free(c->flux[d]);
+  for (int L = 0; L < 8; ++L) free(c->lut[L]);
+  free(c);
+}
+
+int or_ghosted_cells(const or_ctx* c) { return c->ncell; }
+
+static void cell_centre(const or_ctx* c, int b, int i, int j, int k, double x[3]) {
+  int L = c->blk[4 * b];
+  int loc[3] = {i, j, k};
+  for (int d = 0; d < 3; ++d) x[d] = coord(c, d, L, (long)c->blk[4 * b + 1 + d] * c->p.nx[d] + loc[d], 0.5);
+}
+
+void or_set_prims(or_ctx* c, const double* prims) {
+  const int* nx = c->p.nx;
+  for (int b = 0; b < c->nb; ++b)
+    for (int k = 0; k < nx[2]; ++k)
+      for (int j = 0; j < nx[1]; ++j)
+        for (int i = 0; i < nx[0]; ++i) {
+          double P[OR_NV], U[OR_NV], x[3];
+          or_metric m;
+          for (int v = 0; v < OR_NV; ++v) {
+            P[v] = prims[uidx(c, b, v, i, j, k)];
+            c->prim[pidx(c, b, v, i + c->gd[0], j + c->gd[1], k + c->gd[2])] = P[v];
+          }
+          cell_centre(c, b, i, j, k, x);
+          or_metric_at(&c->p, x, 0, &m);
+          or_prim2con(&c->p, &m, P, U);
+          for (int v = 0; v < OR_NV; ++v) c->ucur[uidx(c, b, v, i, j, k)] = m.sqrtg * U[v];
+        }
+}
+
+void or_get_prims(const or_ctx* c, double* prims) {
+  const int* nx = c->p.nx;
+  for (int b = 0; b < c->nb; ++b)
+    for (int v = 0; v < OR_NV; ++v)
+      for (int k = 0; k < nx[2]; ++k)
+        for (int j = 0; j < nx[1]; ++j)
+          for (int i = 0; i < nx[0]; ++i)
+            prims[uidx(c, b, v, i, j, k)] = c->prim[pidx(c, b, v, i + c->gd[0], j + c->gd[1], k + c->gd[2])];
+}
+
+void or_get_prims_ghosted(const or_ctx* c, double* prims) {
+  memcpy(prims, c->prim, sizeof(double) * (size_t)c->nb * OR_NV * c->ncell);
+}
+
+void or_get_cons(const or_ctx* c, double* cons) {
+  memcpy(cons, c->ucur, sizeof(double) * (size_t)c->nb * OR_NV * c->nint);
+}
+
+void or_c2p_counts(const or_ctx* c, long long counts[4]) {
+  for (int i = 0; i < 4; ++i) counts[i] = c->counts[i];
+}
+
+/* ---- ghost cells ---- */
+
+/* Maps a level-L global index that may lie outside the root domain back
+ * inside it according to the boundary kinds.  Returns the sign flips and
+ * clamps to apply to the fetched primitives:
+ *   periodic : wrap;  outflow : copy the nearest interior cell;
+ *   no-inflow: outflow, then u^d <= 0 at the low and >= 0 at the high side;
+ *   polar axis (theta): mirror in theta, flip u^theta and B^theta, and in 3-D
+ *   take the cell at phi + pi. */
+typedef struct {
+  int flip;       /* theta components flip sign */
+  int clamp[3];   /* -1: u^d <= 0, +1: u^d >= 0, 0: none */
+} bcfix;
+
+static void apply_bc(const or_ctx* c, int L, long G[3], bcfix* fx) {
+  fx->flip = 0;
+  for (int d = 0; d < 3; ++d) fx->clamp[d] = 0;
+  for (int d = 0; d < c->p.ndim; ++d) {
+    long N = (long)c->p.nroot[d] * c->p.nx[d] << L;
+    for (int side = 0; side < 2; ++side) {
+      int out = side == 0 ? G[d] < 0 : G[d] >= N;
+      if (!out) continue;
+      int kind = c->p.bc[d][side];
+      if (kind == OR_BC_PERIODIC) {
+        G[d] = ((G[d] % N) + N) % N;
+      } else if (kind == OR_BC_OUTFLOW || kind == OR_BC_NOINFLOW) {
+        G[d] = side == 0 ? 0 : N - 1;
+        if (kind == OR_BC_NOINFLOW) fx->clamp[d] = side == 0 ? -1 : 1;
+      } else if (kind == OR_BC_AXIS) {
+        G[d] = side == 0 ? -1 - G[d] : 2 * N - 1 - G[d];
+        fx->flip ^= 1;
+        if (c->p.ndim == 3) {
+          long Nph = (long)c->p.nroot[2] * c->p.nx[2] << L;
+          G[2] = (((G[2] + Nph / 2) % Nph) + Nph) % Nph;
+        }
+      }
+    }
+  }
+  /* the axis shift can move phi out of range only if phi is periodic */
+  if (c->p.ndim == 3) {
+    long Nph = (long)c->p.nroot[2] * c->p.nx[2] << L;
+    if (c->p.bc[2][0] == OR_BC_PERIODIC) G[2] = ((G[2] % Nph) + Nph) % Nph;
+  }
+}
+
+static void fix_values(const bcfix* fx, double P[OR_NV]) {
+  if (fx->flip) {
+    P[OR_U2] = -P[OR_U2];
+    P[OR_B2] = -P[OR_B2];
+  }
+  for (int d = 0; d < 3; ++d) {
+    if (fx->clamp[d] < 0 && P[OR_U1 + d] > 0.0) P[OR_U1 + d] = 0.0;
+    if (fx->clamp[d] > 0 && P[OR_U1 + d] < 0.0) P[OR_U1 + d] = 0.0;
+  }
+}
+
+/* Primitives of cell G (level-L global index, any position) from the leaf
+ * blocks: a copy where a level-L leaf holds the cell; a minmod-limited linear
+ * prolongation from the coarser leaf; or the mean of the 2^ndim finer cells
+ * (restriction) where finer leaves hold it. */
+static void cell_value(const or_ctx* c, int L, const long Gin[3], double P[OR_NV]) {
+  long G[3] = {Gin[0], Gin[1], Gin[2]};
+  bcfix fx;
+  apply_bc(c, L, G, &fx);
+  long bc[3];
+  for (int d = 0; d < 3; ++d) bc[d] = G[d] / c->p.nx[d];
+  int b = lut_get(c, L, bc);
+  if (b >= 0) {
+    for (int v = 0; v < OR_NV; ++v)
+      P[v] = c->prim[pidx(c, b, v, (int)(G[0] % c->p.nx[0]) + c->gd[0], (int)(G[1] % c->p.nx[1]) + c->gd[1],
+                          (int)(G[2] % c->p.nx[2]) + c->gd[2])];
+  } else {
+    /* is a coarser leaf covering this cell? */
+    int coarse = 0;
+    for (int Lc = L - 1; Lc >= 0; --Lc) {
+      long bcc[3];
+      for (int d = 0; d < 3; ++d) bcc[d] = (d < c->p.ndim ? G[d] >> (L - Lc) : G[d]) / c->p.nx[d];
+      if (lut_get(c, Lc, bcc) >= 0) {
+        coarse = 1;
+        break;
+      }
+    }
+    if (coarse && L > 0) {
+      long C[3];
+      for (int d = 0; d < 3; ++d) C[d] = d < c->p.ndim ? G[d] >> 1 : G[d];
+      double Pc[OR_NV];
+      cell_value(c, L - 1, C, Pc);
+      for (int v = 0; v < OR_NV; ++v) P[v] = Pc[v];
+      for (int d = 0; d < c->p.ndim; ++d) {
+        long Cm[3] = {C[0], C[1], C[2]}, Cp[3] = {C[0], C[1], C[2]};
+        Cm[d] -= 1;
+        Cp[d] += 1;
+        double Pm[OR_NV], Pp[OR_NV];
+        cell_value(c, L - 1, Cm, Pm);
+        cell_value(c, L - 1, Cp, Pp);
+        double off = (G[d] & 1) ? 0.25 : -0.25;
+        for (int v = 0; v < OR_NV; ++v) P[v] += off * minmod(Pc[v] - Pm[v], Pp[v] - Pc[v]);
+      }
+    } else {
+      int nch = 1 << c->p.ndim;
+      for (int v = 0; v < OR_NV; ++v) P[v] = 0.0;
+      for (int ch = 0; ch < nch; ++ch) {
+        long F[3] = {G[0], G[1], G[2]};
+        for (int d = 0; d < c->p.ndim; ++d) F[d] = 2 * G[d] + ((ch >> d) & 1);
+        double Pf[OR_NV];
+        cell_value(c, L + 1, F, Pf);
+        for (int v = 0; v < OR_NV; ++v) P[v] += Pf[v];
+      }
+      for (int v = 0; v < OR_NV; ++v) P[v] /= nch;
+    }
+  }
+  fix_values(&fx, P);
+}
+
+static void fill_block_ghosts(or_ctx* c, int b) {
+  int L = c->blk[4 * b];
+  for (int k = 0; k < c->N[2]; ++k)
+    for (int j = 0; j < c->N[1]; ++j)
+      for (int i = 0; i < c->N[0]; ++i) {
+        int loc[3] = {i - c->gd[0], j - c->gd[1], k - c->gd[2]};
+        int inside = 1;
+        for (int d = 0; d < 3; ++d)
+          if (loc[d] < 0 || loc[d] >= c->p.nx[d]) inside = 0;
+        if (inside) continue;
+        long G[3];
+        for (int d = 0; d < 3; ++d) G[d] = (long)c->blk[4 * b + 1 + d] * c->p.nx[d] + loc[d];
+        double P[OR_NV];
+        cell_value(c, L, G, P);
+        for (int v = 0; v < OR_NV; ++v) c->prim[pidx(c, b, v, i, j, k)] = P[v];
+      }
+}
+
+void or_fill_ghosts(or_ctx* c) {
+  /* ghosts read only interior cells, so blocks are independent */
+#pragma omp parallel for schedule(dynamic)
+  for (int b = 0; b < c->nb; ++b) fill_block_ghosts(c, b);
+}
+
+/* ---- CFL ---- */
+
+/* dt = C / max over interior cells of sum_d c_d / dx_d, with c_d the largest
+ * of |lambda+-| and the GLM speeds alpha ch sqrt(gamma^dd) + |beta^d|. */
+double or_cfl_dt(or_ctx* c) {
+  double smax = 0.0;
+#pragma omp parallel for schedule(dynamic) reduction(max : smax)
+  for (int b = 0; b < c->nb; ++b) {
+    int L = c->blk[4 * b];
+    for (int k = 0; k < c->p.nx[2]; ++k)
+      for (int j = 0; j < c->p.nx[1]; ++j)
+        for (int i = 0; i < c->p.nx[0]; ++i) {
+          double x[3], P[OR_NV];
+          or_metric m;
+          cell_centre(c, b, i, j, k, x);
+          or_metric_at(&c->p, x, 0, &m);
+          for (int v = 0; v < OR_NV; ++v) P[v] = c->prim[pidx(c, b, v, i + c->gd[0], j + c->gd[1], k + c->gd[2])];
+          double s = 0.0;
+          for (int d = 0; d < c->p.ndim; ++d) {
+            double lm, lp;
+            or_wavespeeds(&c->p, &m, P, d, &lm, &lp);
+            double cd = fabs(lp) > fabs(lm) ? fabs(lp) : fabs(lm);
+            double cg = m.alpha * c->p.ch * sqrt(m.gi[d][d]) + fabs(m.beta[d]);
+            if (cg > cd) cd = cg;
+            s += cd / dxl(c, d, L);
+          }
+          if (s > smax) smax = s;
+        }
+  }
+  return c->p.cfl / smax;
+}
+
+/* ---- one Runge-Kutta stage ---- */
+
+static size_t fidx(const or_ctx* c, int d, int b, int v, int i, int j, int k) {
+  int n[3] = {c->p.nx[0], c->p.nx[1], c->p.nx[2]};
+  n[d] += 1;
+  return ((((size_t)b * OR_NV + v) * n[2] + k) * n[1] + j) * n[0] + i;
+}
+
+/* Face fluxes of block b in direction d, for faces 0..nx_d (face f lies
+ * between interior cells f-1 and f). */
+static void block_fluxes(or_ctx* c, int b, int d) {
+  int L = c->blk[4 * b];
+  int n[3] = {c->p.nx[0], c->p.nx[1], c->p.nx[2]};
+  n[d] += 1;
+  for (int k = 0; k < n[2]; ++k)
+    for (int j = 0; j < n[1]; ++j)
+      for (int i = 0; i < n[0]; ++i) {
+        int f[3] = {i, j, k};
+        double x[3];
+        long G[3];
+        for (int e = 0; e < 3; ++e) {
+          G[e] = (long)c->blk[4 * b + 1 + e] * c->p.nx[e] + f[e];
+          x[e] = coord(c, e, L, G[e], e == d ? 0.0 : 0.5);
+        }
+        double F[OR_NV];
+        long Nd = (long)c->p.nroot[d] * c->p.nx[d] << L;
+        int axis = (G[d] == 0 && c->p.bc[d][0] == OR_BC_AXIS) || (G[d] == Nd && c->p.bc[d][1] == OR_BC_AXIS);
+        if (axis) {
+          for (int v = 0; v < OR_NV; ++v) F[v] = 0.0;
+        } else {
+          double st[6][OR_NV], PL[OR_NV], PR[OR_NV];
+          for (int s = 0; s < 6; ++s) {
+            int g[3] = {i + c->gd[0], j + c->gd[1], k + c->gd[2]};
+            g[d] += s - 3;
+            for (int v = 0; v < OR_NV; ++v) st[s][v] = c->prim[pidx(c, b, v, g[0], g[1], g[2])];
+          }
+          or_reconstruct(&c->p, (const double(*)[OR_NV])st, PL, PR);
+          or_metric m;
+          or_metric_at(&c->p, x, 0, &m);
+          or_face_flux(&c->p, &m, PL, PR, d, F);
+        }
+        for (int v = 0; v < OR_NV; ++v) c->flux[d][fidx(c, d, b, v, i, j, k)] = F[v];
+      }
+}
+
+/* Coarse-fine flux correction: at a face where the neighbour is one level
+ * finer, the coarse flux becomes the mean of the 2^(ndim-1) fine fluxes that
+ * cover it, so the fluxes leaving and entering each level agree exactly. */
+static void reflux_block(or_ctx* c, int b) {
+  int L = c->blk[4 * b];
+  for (int d = 0; d < c->p.ndim; ++d)
+    for (int side = 0; side < 2; ++side) {
+      long nb_[3];
+      for (int e = 0; e < 3; ++e) nb_[e] = c->blk[4 * b + 1 + e];
+      nb_[d] += side == 0 ? -1 : 1;
+      long nbd = (long)c->p.nroot[d] << L;
+      if (nb_[d] < 0 || nb_[d] >= nbd) {
+        if (c->p.bc[d][side] != OR_BC_PERIODIC) continue;
+        nb_[d] = (nb_[d] + nbd) % nbd;
+      }
+      if (lut_get(c, L, nb_) >= 0) continue; /* same level */
+      /* finer neighbour? check the child block touching this face */
+      long chb[3];
+      for (int e = 0; e < 3; ++e) chb[e] = e < c->p.ndim ? 2 * nb_[e] : nb_[e];
+      if (side == 0) chb[d] += 1;
+      if (lut_get(c, L + 1, chb) < 0) continue;
+      int n[3] = {c->p.nx[0], c->p.nx[1], c->p.nx[2]};
+      int fcoarse = side == 0 ? 0 : n[d];
+      int ffine = side == 0 ? n[d] : 0;
+      int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
+      for (int a = 0; a < n[t1]; ++a)
+        for (int bb = 0; bb < n[t2]; ++bb) {
+          /* global coarse transverse index -> fine block and local indices */
+          double acc[OR_NV] = {0};
+          int cnt = 0;
+          for (int s1 = 0; s1 < (t1 < c->p.ndim ? 2 : 1); ++s1)
+            for (int s2 = 0; s2 < (t2 < c->p.ndim ? 2 : 1); ++s2) {
+              long Gf[3];
+              Gf[d] = 0;
+              long gc1 = (long)c->blk[4 * b + 1 + t1] * n[t1] + a;
+              long gc2 = (long)c->blk[4 * b + 1 + t2] * n[t2] + bb;
+              Gf[t1] = t1 < c->p.ndim ? 2 * gc1 + s1 : gc1;
+              Gf[t2] = t2 < c->p.ndim ? 2 * gc2 + s2 : gc2;
+              long fb[3];
+              fb[d] = chb[d];
+              fb[t1] = Gf[t1] / n[t1];
+              fb[t2] = Gf[t2] / n[t2];
+              int bf = lut_get(c, L + 1, fb);
+              if (bf < 0) continue;
+              int li[3];
+              li[d] = ffine;
+              li[t1] = (int)(Gf[t1] % n[t1]);
+              li[t2] = (int)(Gf[t2] % n[t2]);
+              for (int v = 0; v < OR_NV; ++v) acc[v] += c->flux[d][fidx(c, d, bf, v, li[0], li[1], li[2])];
+              ++cnt;
+            }
+          if (cnt == 0) continue;
+          int lc[3];
+          lc[d] = fcoarse;
+          lc[t1] = a;
+          lc[t2] = bb;
+          for (int v = 0; v < OR_NV; ++v) c->flux[d][fidx(c, d, b, v, lc[0], lc[1], lc[2])] = acc[v] / cnt;
+        }
+    }
+}
+
+/* L = -sum_d (F_d(+) - F_d(-)) / dx_d + sqrt(gamma) S, then the SSP-RK2 stage
+ * (Shu & Osher 1988): stage 1  U1 = Un + dt L(Pn);
+ * stage 2  U = 1/2 Un + 1/2 (U1 + dt L(P1)); then the inversion per cell. */
+static void update_block(or_ctx* c, int b, int stage, double dt, long long cnt[4]) {
+  int L = c->blk[4 * b];
+  const int* nx = c->p.nx;
+  for (int k = 0; k < nx[2]; ++k)
+    for (int j = 0; j < nx[1]; ++j)
+      for (int i = 0; i < nx[0]; ++i) {
+        double x[3], P[OR_NV], S[OR_NV], rhs[OR_NV], U[OR_NV], Pn[OR_NV];
+        or_metric m;
+        cell_centre(c, b, i, j, k, x);
+        or_metric_at(&c->p, x, 1, &m);
+        for (int v = 0; v < OR_NV; ++v) P[v] = c->prim[pidx(c, b, v, i + c->gd[0], j + c->gd[1], k + c->gd[2])];
+        or_sources(&c->p, &m, P, S);
+        for (int v = 0; v < OR_NV; ++v) rhs[v] = 0.0;
+        for (int d = 0; d < c->p.ndim; ++d) {
+          int ip[3] = {i, j, k};
+          ip[d] += 1;
+          double dx = dxl(c, d, L);
+          for (int v = 0; v < OR_NV; ++v)
+            rhs[v] += -(c->flux[d][fidx(c, d, b, v, ip[0], ip[1], ip[2])] - c->flux[d][fidx(c, d, b, v, i, j, k)]) / dx;
+        }
+        for (int v = 0; v < OR_NV; ++v) rhs[v] += m.sqrtg * S[v];
+        for (int v = 0; v < OR_NV; ++v) {
+          size_t u = uidx(c, b, v, i, j, k);
+          if (stage == 1) {
+            c->un[u] = c->ucur[u];
+            U[v] = c->un[u] + dt * rhs[v];
+          } else {
+            U[v] = 0.5 * c->un[u] + 0.5 * (c->ucur[u] + dt * rhs[v]);
+          }
+        }
+        double Uu[OR_NV];
+        for (int v = 0; v < OR_NV; ++v) Uu[v] = U[v] / m.sqrtg;
+        int st = or_con2prim(&c->p, &m, Uu, P, floor_radius(&c->p, x), Pn);
+        cnt[st] += 1;
+        if (st >= 2) {
+          or_prim2con(&c->p, &m, Pn, Uu);
+          for (int v = 0; v < OR_NV; ++v) U[v] = m.sqrtg * Uu[v];
+        }
+        for (int v = 0; v < OR_NV; ++v) c->ucur[uidx(c, b, v, i, j, k)] = U[v];
+        /* the new primitives may only be written once every flux of this
+         * block is final; fluxes were computed before this pass */
+        for (int v = 0; v < OR_NV; ++v) c->prim[pidx(c, b, v, i + c->gd[0], j + c->gd[1], k + c->gd[2])] = Pn[v];
+      }
+}
+
+void or_stage_blocks(or_ctx* c, int stage, double dt, int nsel, const int* sel) {
+  or_fill_ghosts(c);
+  int all = c->p.nlevels > 1; /* refluxing needs the fine neighbours' fluxes */
+#pragma omp parallel for schedule(dynamic)
+  for (int q = 0; q < (all ? c->nb : nsel); ++q) {
+    int b = all ? q : sel[q];
+    for (int d = 0; d < c->p.ndim; ++d) block_fluxes(c, b, d);
+  }
+  if (c->p.nlevels > 1) {
+#pragma omp parallel for schedule(dynamic)
+    for (int q = 0; q < nsel; ++q) reflux_block(c, sel[q]);
+  }
+  long long tot[4] = {0, 0, 0, 0};
+#pragma omp parallel
+  {
+    long long cnt[4] = {0, 0, 0, 0};
+#pragma omp for schedule(dynamic)
+    for (int q = 0; q < nsel; ++q) update_block(c, sel[q], stage, dt, cnt);
+#pragma omp critical
+    for (int s = 0; s < 4; ++s) tot[s] += cnt[s];
+  }
+  for (int s = 0; s < 4; ++s) c->counts[s] += tot[s];
+}
+
+void or_stage(or_ctx* c, int stage, double dt) {
+  int* sel = (int*)malloc(sizeof(int) * c->nb);
+  for (int b = 0; b < c->nb; ++b) sel[b] = b;
+  or_stage_blocks(c, stage, dt, c->nb, sel);
+  free(sel);
+}
+
+void or_step(or_ctx* c, double dt) {
+  or_stage(c, 1, dt);
+  or_stage(c, 2, dt);
+}

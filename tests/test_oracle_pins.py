@@ -1,0 +1,613 @@
+"""Pins of the FP64 oracle against facts that do not come from the oracle:
+closed forms, the covariant (4-D) formulation, textbook limits, invariants,
+brute force and convergence to exact solutions.  CPU only."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import problems as pb
+from tests import covariant as cov
+
+A_SPIN = 0.9375
+
+
+def ks_grid(coords="ks", spin=A_SPIN, mass=1.0, gamma_ad=4.0 / 3.0):
+    return pb.torus_2d().with_(coords=coords, spin=spin, mass=mass, gamma_ad=gamma_ad)
+
+
+def random_state(rng, g, sigma_max=10.0, wmax=5.0):
+    """Random primitive state with W, p/rho and sigma = b^2/rho in range."""
+    rho = 10 ** rng.uniform(-3, 1)
+    p = rho * 10 ** rng.uniform(-3, 1)
+    W = 1.0 + (wmax - 1.0) * rng.random()
+    # random direction, normalised to u^2 = W^2 - 1 with the metric
+    d = rng.normal(size=3)
+    u = d * math.sqrt((W * W - 1.0) / (d @ g @ d))
+    e = rng.normal(size=3)
+    B = e * math.sqrt(rho * sigma_max * rng.random() / (e @ g @ e))
+    return np.array([rho, p, u[0], u[1], u[2], B[0], B[1], B[2], rng.normal() * 0.1])
+
+
+# --------------------------------------------------------------------------
+# metric
+# --------------------------------------------------------------------------
+
+def bl_metric(r, th, a):
+    """Boyer-Lindquist Kerr 4-metric (M = 1), textbook form."""
+    S = r * r + a * a * math.cos(th) ** 2
+    D = r * r - 2 * r + a * a
+    A = (r * r + a * a) ** 2 - a * a * D * math.sin(th) ** 2
+    g = np.zeros((4, 4))
+    g[0, 0] = -(1 - 2 * r / S)
+    g[0, 3] = g[3, 0] = -2 * a * r * math.sin(th) ** 2 / S
+    g[1, 1] = S / D
+    g[2, 2] = S
+    g[3, 3] = A * math.sin(th) ** 2 / S
+    return g
+
+
+@pytest.mark.parametrize("coords", ["ks", "mks"])
+def test_metric_is_kerr_from_boyer_lindquist(coords):
+    """The oracle's 3+1 KS metric, assembled into a 4-metric, equals the
+    Boyer-Lindquist metric transformed by dt_KS = dt_BL + 2r/Delta dr,
+    dphi_KS = dphi_BL + a/Delta dr (and, for MKS, r = e^x1, th = pi x2)."""
+    pt = oracle.Point(ks_grid(coords))
+    rng = np.random.default_rng(1)
+    for _ in range(20):
+        r = rng.uniform(2.2, 50.0)
+        th = rng.uniform(0.1, math.pi - 0.1)
+        D = r * r - 2 * r + A_SPIN ** 2
+        # Lambda = d x_BL / d x_KS (rows BL t,r,th,ph; columns KS t,r,th,ph)
+        Lam = np.eye(4)
+        Lam[0, 1] = -2 * r / D
+        Lam[3, 1] = -A_SPIN / D
+        gks = Lam.T @ bl_metric(r, th, A_SPIN) @ Lam
+        if coords == "mks":
+            Jm = np.diag([1.0, r, math.pi, 1.0])
+            gks = Jm.T @ gks @ Jm
+            x = [math.log(r), th / math.pi, 0.3]
+        else:
+            x = [r, th, 0.3]
+        m = pt.metric(x, derivs=False)
+        G = cov.four_metric(m.alpha, m.beta, m.g)
+        np.testing.assert_allclose(G, gks, rtol=1e-12, atol=1e-12 * np.abs(gks).max())
+        assert m.sqrtg * m.alpha == pytest.approx(
+            (r * r + A_SPIN ** 2 * math.cos(th) ** 2) * math.sin(th) * (r if coords == "mks" else 1.0)
+            * (math.pi if coords == "mks" else 1.0), rel=1e-13)
+        np.testing.assert_allclose(m.g @ m.gi, np.eye(3), atol=1e-13)
+
+
+@pytest.mark.parametrize("coords", ["ks", "mks"])
+def test_metric_derivatives_match_finite_differences(coords):
+    pt = oracle.Point(ks_grid(coords))
+    rng = np.random.default_rng(2)
+    h = 1e-4
+    for _ in range(10):
+        x = np.array([rng.uniform(1.5, 30.0), rng.uniform(0.1, 3.0), rng.uniform(0, 6)])
+        if coords == "mks":
+            x = np.array([math.log(x[0]), x[1] / math.pi, x[2]])
+        m = pt.metric(x)
+        for k in range(3):
+            def f(s):
+                y = x.copy()
+                y[k] += s
+                mm = pt.metric(y, derivs=False)
+                return np.concatenate([[mm.alpha], mm.beta, mm.g.ravel()])
+            fd = (8 * (f(h) - f(-h)) - (f(2 * h) - f(-2 * h))) / (12 * h)
+            an = np.concatenate([[m.da[k]], m.db[k], m.dg[k].ravel()])
+            np.testing.assert_allclose(an, fd, rtol=1e-8, atol=1e-9 * max(1.0, np.abs(fd).max()))
+
+
+def test_flat_spherical_limit():
+    """M = 0, a = 0 gives flat space in spherical coordinates."""
+    pt = oracle.Point(ks_grid("ks", spin=0.0, mass=0.0))
+    r, th = 3.0, 0.7
+    m = pt.metric([r, th, 1.0])
+    np.testing.assert_allclose(m.g, np.diag([1.0, r * r, (r * math.sin(th)) ** 2]), rtol=1e-15)
+    assert m.alpha == 1.0 and np.all(m.beta == 0.0)
+    assert m.dg[0][1][1] == pytest.approx(2 * r, rel=1e-14)
+    assert m.dg[1][2][2] == pytest.approx(2 * r * r * math.sin(th) * math.cos(th), rel=1e-13)
+
+
+# --------------------------------------------------------------------------
+# conserved variables, fluxes and sources against the covariant form
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("coords", ["cart", "mks"])
+def test_prim2con_and_fluxes_match_covariant_form(coords):
+    grid = ks_grid("mks") if coords == "mks" else pb.periodic_box(gamma_ad=5.0 / 3.0)
+    pt = oracle.Point(grid)
+    rng = np.random.default_rng(3)
+    for _ in range(40):
+        x = [math.log(rng.uniform(1.4, 40)), rng.uniform(0.05, 0.95), 1.0] if coords == "mks" else [0.1, 0.2, 0.3]
+        m = pt.metric(x)
+        P = random_state(rng, m.g)
+        U = pt.prim2con(m, P)
+        D, S, tau = cov.conserved(P, m.alpha, m.beta, m.g, grid.gamma_ad)
+        scale = max(abs(D), abs(tau), np.abs(S).max())
+        np.testing.assert_allclose(U[0], D, rtol=1e-13)
+        np.testing.assert_allclose(U[1:4], S, rtol=1e-11, atol=1e-12 * scale)
+        np.testing.assert_allclose(U[4], tau, rtol=1e-10, atol=1e-12 * scale)
+        np.testing.assert_array_equal(U[5:9], P[5:9])
+        for i in range(3):
+            F = pt.flux(m, P, i)
+            FD, FS, Ftau, FB = cov.fluxes(P, m.alpha, m.beta, m.g, grid.gamma_ad, i)
+            fs = max(np.abs(F).max(), 1e-300)
+            np.testing.assert_allclose(F[0], FD, rtol=1e-12, atol=1e-13 * fs)
+            np.testing.assert_allclose(F[1:4], FS, rtol=1e-10, atol=1e-12 * fs)
+            np.testing.assert_allclose(F[4], Ftau, rtol=1e-9, atol=1e-12 * fs)
+            glm = m.alpha * m.gi[i] * P[8]
+            np.testing.assert_allclose(F[5:8] - glm, FB, rtol=1e-10, atol=1e-12 * fs)
+            assert F[8] == pytest.approx(m.alpha * grid.ch ** 2 * P[5 + i] - m.beta[i] * P[8], rel=1e-14,
+                                         abs=1e-15)
+
+
+def test_sources_match_covariant_form():
+    grid = ks_grid("mks")
+    pt = oracle.Point(grid)
+
+    def mfn(y):
+        mm = pt.metric(y, derivs=False)
+        return mm.alpha, mm.beta.copy(), mm.g.copy()
+
+    rng = np.random.default_rng(4)
+    for _ in range(25):
+        x = np.array([math.log(rng.uniform(1.4, 30)), rng.uniform(0.05, 0.95), 2.0])
+        m = pt.metric(x)
+        P = random_state(rng, m.g)
+        S = pt.sources(m, P)
+        SS, Stau = cov.sources(P, mfn, x, grid.gamma_ad)
+        sc = max(np.abs(SS).max(), abs(Stau))
+        np.testing.assert_allclose(S[1:4], SS, rtol=1e-6, atol=1e-8 * sc)
+        assert S[4] == pytest.approx(Stau, rel=1e-6, abs=1e-8 * sc)
+        assert S[0] == 0.0 and np.all(S[5:8] == 0.0)
+
+
+def test_flat_sources_are_glm_damping_only():
+    """Cartesian Minkowski: all geometric sources vanish and the cleaning
+    source reduces to Dedner et al.'s -kappa psi."""
+    grid = pb.periodic_box(kappa=0.7)
+    pt = oracle.Point(grid)
+    rng = np.random.default_rng(5)
+    m = pt.metric([0.5, 0.5, 0.5])
+    P = random_state(rng, m.g)
+    S = pt.sources(m, P)
+    np.testing.assert_array_equal(S[:8], 0.0)
+    assert S[8] == pytest.approx(-0.7 * P[8], rel=1e-15)
+
+
+# --------------------------------------------------------------------------
+# wave speeds
+# --------------------------------------------------------------------------
+
+def test_wavespeeds_reduce_to_sr_hydro():
+    """B = 0, flat, motion along x: textbook SR hydrodynamics,
+    lambda = (v (1 - cs^2) +- cs (1 - v^2)) / (1 - v^2 cs^2)."""
+    grid = pb.periodic_box(gamma_ad=5.0 / 3.0)
+    pt = oracle.Point(grid)
+    m = pt.metric([0.5, 0.5, 0.5])
+    for v, rho, p in [(0.0, 1.0, 1.0), (0.6, 1.0, 0.1), (-0.9, 0.3, 3.0)]:
+        W = 1 / math.sqrt(1 - v * v)
+        P = np.array([rho, p, W * v, 0, 0, 0, 0, 0, 0])
+        h = 1 + 2.5 * p / rho
+        cs = math.sqrt(5.0 / 3.0 * p / (rho * h))
+        lp = (v * (1 - cs * cs) + cs * (1 - v * v)) / (1 - v * v * cs * cs)
+        lm = (v * (1 - cs * cs) - cs * (1 - v * v)) / (1 - v * v * cs * cs)
+        a, b = pt.wavespeeds(m, P, 0)
+        assert a == pytest.approx(lm, rel=1e-13, abs=1e-15)
+        assert b == pytest.approx(lp, rel=1e-13, abs=1e-15)
+
+
+@pytest.mark.parametrize("coords", ["cart", "mks"])
+def test_wavespeeds_bound_flux_jacobian_eigenvalues(coords):
+    """Brute force: the eigenvalues of the finite-difference Jacobian of the
+    7-wave MHD flux (normal B fixed, psi = 0) lie inside [lambda-, lambda+]."""
+    grid = ks_grid("mks") if coords == "mks" else pb.periodic_box(gamma_ad=5.0 / 3.0)
+    pt = oracle.Point(grid)
+    rng = np.random.default_rng(6)
+    for trial in range(30):
+        x = [math.log(rng.uniform(2.5, 30)), rng.uniform(0.1, 0.9), 1.0] if coords == "mks" else [0.5] * 3
+        m = pt.metric(x)
+        P = random_state(rng, m.g, sigma_max=5.0, wmax=3.0)
+        P[8] = 0.0
+        d = trial % 3
+        free = [0, 1, 2, 3, 4] + [5 + j for j in range(3) if j != d]
+        cidx = [0, 1, 2, 3, 4] + [5 + j for j in range(3) if j != d]
+
+        def UF(q):
+            PP = P.copy()
+            PP[free] = q
+            return pt.prim2con(m, PP)[cidx], pt.flux(m, PP, d)[cidx]
+
+        q0 = P[free]
+        n = len(free)
+        dU = np.zeros((n, n))
+        dF = np.zeros((n, n))
+        for k in range(n):
+            h = 1e-6 * max(abs(q0[k]), 1e-3)
+            e = np.zeros(n)
+            e[k] = h
+            Up, Fp = UF(q0 + e)
+            Um, Fm = UF(q0 - e)
+            dU[:, k] = (Up - Um) / (2 * h)
+            dF[:, k] = (Fp - Fm) / (2 * h)
+        ev = np.linalg.eigvals(dF @ np.linalg.inv(dU))
+        lm, lp = pt.wavespeeds(m, P, d)
+        assert np.abs(ev.imag).max() < 1e-5 * max(1.0, np.abs(ev).max())
+        tol = 1e-6 * max(1.0, abs(lm), abs(lp))
+        assert ev.real.min() >= lm - tol and ev.real.max() <= lp + tol
+
+
+# --------------------------------------------------------------------------
+# conserved -> primitive inversion
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("coords", ["cart", "mks"])
+def test_con2prim_round_trip(coords):
+    """prim -> con -> prim over rho in [1e-8, 1e2], p/rho in [1e-6, 1e2],
+    W in [1, 20], sigma in [0, 100], started from a guess 0.1% away (the state
+    of the previous stage).  Backward error (con of the result vs the input)
+    <= 1e-14; forward error <= 1e-12 where the state is well conditioned and
+    within 8 cond eps otherwise, cond = (E + |S| + B^2) / p being the factor by
+    which recovering p from the total energy amplifies round-off."""
+    grid = ks_grid("mks") if coords == "mks" else pb.periodic_box(gamma_ad=4.0 / 3.0)
+    grid = grid.with_(rho_floor=1e-30, p_floor=1e-30, rho_floor_pow=0.0, p_floor_pow=0.0)
+    pt = oracle.Point(grid)
+    rng = np.random.default_rng(7)
+    n_well = 0
+    for _ in range(400):
+        x = [math.log(rng.uniform(1.3, 100)), rng.uniform(0.05, 0.95), 1.0] if coords == "mks" else [0.5] * 3
+        m = pt.metric(x, derivs=False)
+        rho = 10 ** rng.uniform(-8, 2)
+        p = rho * 10 ** rng.uniform(-6, 2)
+        W = 1 + 19 * rng.random() ** 2
+        d = rng.normal(size=3)
+        u = d * math.sqrt((W * W - 1) / (d @ m.g @ d))
+        e = rng.normal(size=3)
+        sigma = 100 * rng.random() ** 2
+        B = e * math.sqrt(sigma * rho * W * W / (e @ m.g @ e))
+        P = np.array([rho, p, *u, *B, 0.01])
+        U = pt.prim2con(m, P)
+        guess = P * (1 + 1e-3 * rng.normal(size=9))
+        Q, st = pt.con2prim(m, U, guess)
+        assert st in (0, 1)
+        back = np.abs(pt.prim2con(m, Q)[:5] - U[:5]).max() / np.abs(U[:5]).max()
+        assert back < 1e-14
+        cond = (U[4] + U[0] + np.abs(U[1:4]).sum() + B @ m.g @ B) / p
+        unorm = max(math.sqrt(u @ m.g @ u), 1e-300)
+        err = np.abs(Q[:5] - P[:5]) / np.array([rho, p, unorm, unorm, unorm])
+        tol = max(1e-12, 8 * cond * 2.2e-16)
+        assert err.max() < tol, (P, Q, err, cond)
+        n_well += cond < 1e3
+    assert n_well > 10
+
+
+def test_con2prim_agrees_with_high_precision_root():
+    """Brute force: Z = rho h W^2 from mpmath bisection at 50 digits of the
+    momentum/energy system equals the oracle's result to 1e-13."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 50
+    grid = pb.periodic_box(gamma_ad=4.0 / 3.0)
+    pt = oracle.Point(grid)
+    m = pt.metric([0.5] * 3)
+    rng = np.random.default_rng(8)
+    for _ in range(5):
+        P = random_state(rng, m.g, sigma_max=20.0, wmax=6.0)
+        U = pt.prim2con(m, P)
+        Q, st = pt.con2prim(m, U, P * (1 + 1e-2 * rng.normal(size=9)))
+        D, S, tau, B = (mp.mpf(U[0]), [mp.mpf(s) for s in U[1:4]], mp.mpf(U[4]), [mp.mpf(b) for b in U[5:8]])
+        S2 = sum(s * s for s in S)
+        B2 = sum(b * b for b in B)
+        BS = sum(b * s for b, s in zip(B, S))
+        gam = mp.mpf(4) / 3
+
+        def v2(Z):
+            return (S2 + BS * BS * (2 * Z + B2) / (Z * Z)) / (Z + B2) ** 2
+
+        def f(Z):
+            w2 = v2(Z)
+            pr = (gam - 1) / gam * (Z * (1 - w2) - D * mp.sqrt(1 - w2))
+            return Z - pr + B2 * (1 + w2) / 2 - BS * BS / (2 * Z * Z) - (tau + D)
+
+        # bracket around the input state's Z = rho h W^2 (the exact root of the
+        # rounded conserved state lies within round-off of it)
+        Wt2 = 1 + P[2:5] @ m.g @ P[2:5]
+        Zt = mp.mpf((P[0] + 4 * P[1]) * Wt2)
+        lo, hi = Zt * (1 - mp.mpf("1e-6")), Zt * (1 + mp.mpf("1e-6"))
+        assert f(lo) < 0 < f(hi)
+        for _ in range(300):
+            mid = (lo + hi) / 2
+            if f(mid) > 0:
+                hi = mid
+            else:
+                lo = mid
+        Z = (lo + hi) / 2
+        W = 1 / mp.sqrt(1 - v2(Z))
+        assert float(D / W) == pytest.approx(Q[0], rel=1e-12)
+        Zq = (Q[0] + 4 * Q[1]) * (1 + Q[2:5] @ Q[2:5])
+        assert Zq == pytest.approx(float(Z), rel=1e-12)
+
+
+def test_con2prim_floors_and_failure():
+    grid = pb.periodic_box(gamma_ad=4.0 / 3.0, rho_floor=1e-6, p_floor=1e-8, w_max=10.0)
+    pt = oracle.Point(grid)
+    m = pt.metric([0.5] * 3)
+    # a state below the floors comes back floored, status 2
+    P = np.array([1e-9, 1e-12, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0])
+    Q, st = pt.con2prim(m, pt.prim2con(m, P), P)
+    assert st == 2 and Q[0] == 1e-6 and Q[1] == 1e-8
+    # Lorentz factor above W_max is rescaled to W_max
+    W = 30.0
+    P = np.array([1.0, 1.0, math.sqrt(W * W - 1), 0, 0, 0, 0, 0, 0])
+    Q, st = pt.con2prim(m, pt.prim2con(m, P), P)
+    assert st == 2 and math.sqrt(1 + Q[2] ** 2) == pytest.approx(10.0, rel=1e-14)
+    # unphysical conserved state (D < 0): previous primitives kept, status 3
+    U = np.array([-1.0, 0, 0, 0, 1.0, 0.3, 0, 0, 0.2])
+    Pg = np.array([1.0, 1.0, 0.1, 0, 0, 9, 9, 9, 9])
+    Q, st = pt.con2prim(m, U, Pg)
+    assert st == 3 and np.all(Q[:5] == Pg[:5]) and np.all(Q[5:] == U[5:])
+
+
+# --------------------------------------------------------------------------
+# reconstruction and the numerical flux
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("recon", ["ppm", "minmod"])
+def test_reconstruction_exact_for_linear_and_constant(recon):
+    pt = oracle.Point(pb.periodic_box(recon=recon))
+    xs = np.arange(6) - 2.5  # face at 0
+    st = np.zeros((6, 9))
+    for v in range(9):
+        st[:, v] = 2.0 + 0.1 * (v + 1) * xs
+    PL, PR = pt.reconstruct(st)
+    np.testing.assert_allclose(PL, st[2] + 0.5 * (st[3] - st[2]), rtol=1e-14)
+    np.testing.assert_allclose(PR, PL, rtol=1e-14)
+    st[:] = 3.0
+    PL, PR = pt.reconstruct(st)
+    assert np.all(PL == 3.0) and np.all(PR == 3.0)
+
+
+def test_ppm_is_monotone_and_flattens_extrema():
+    pt = oracle.Point(pb.periodic_box(recon="ppm"))
+    rng = np.random.default_rng(9)
+    for _ in range(200):
+        st = np.sort(rng.uniform(1, 2, size=6))[:, None].repeat(9, axis=1)
+        PL, PR = pt.reconstruct(st)
+        # monotone data: face states stay inside the neighbouring cell values
+        assert np.all(PL >= st[2] - 1e-15) and np.all(PL <= st[3] + 1e-15)
+        assert np.all(PR >= st[2] - 1e-15) and np.all(PR <= st[3] + 1e-15)
+    st = np.array([1.0, 1.0, 2.0, 1.0, 1.0, 1.0])[:, None].repeat(9, axis=1)  # peak in cell 2
+    PL, PR = pt.reconstruct(st)
+    assert np.all(PL == 2.0)
+
+
+def test_first_order_fallback_on_negative_pressure():
+    pt = oracle.Point(pb.periodic_box(recon="minmod"))
+    st = np.ones((6, 9))
+    st[:, 1] = [1.0, 1.0, 1.0, 1e-3, 1e-3, 1.0]
+    st[:, 1] = [4.0, 2.0, 1e-3, 3.0, 6.0, 9.0]
+    PL, PR = pt.reconstruct(st)
+    assert PL[1] > 0 and PR[1] > 0
+
+
+@pytest.mark.parametrize("riemann", ["hll", "tvdlf"])
+def test_numerical_flux_consistency_and_upwinding(riemann):
+    grid = pb.periodic_box(gamma_ad=5.0 / 3.0, riemann=riemann)
+    pt = oracle.Point(grid)
+    m = pt.metric([0.5] * 3)
+    rng = np.random.default_rng(10)
+    for _ in range(20):
+        P = random_state(rng, m.g)
+        for d in range(3):
+            np.testing.assert_allclose(pt.face_flux(m, P, P, d), pt.flux(m, P, d), rtol=1e-12, atol=1e-14)
+    if riemann == "hll":
+        # every fluid wave moving right: HLL is the left flux (GLM pair excepted)
+        v = 0.95
+        W = 1 / math.sqrt(1 - v * v)
+        PL = np.array([1.0, 0.01, W * v, 0, 0, 0.1, 0.05, 0, 0])
+        PR = np.array([0.5, 0.02, W * v, 0, 0, 0.1, 0.02, 0, 0])
+        F = pt.face_flux(m, PL, PR, 0)
+        FL = pt.flux(m, PL, 0)
+        np.testing.assert_allclose(F[[0, 1, 2, 3, 4, 6, 7]], FL[[0, 1, 2, 3, 4, 6, 7]], rtol=1e-13)
+
+
+# --------------------------------------------------------------------------
+# the block grid: ghosts, update assembly, conservation, convergence
+# --------------------------------------------------------------------------
+
+def test_ghost_fill_periodic_outflow_axis():
+    """Brute force on tiny grids: every ghost equals the cell its boundary
+    rule names."""
+    g = pb.torus_2d(nblock=4, nroot=(2, 2)).with_(nx=(4, 4, 1))
+    o = oracle.Oracle(g)
+    rng = np.random.default_rng(11)
+    P = rng.uniform(0.5, 1.5, size=o.shape)
+    o.set_prims(P)
+    o.fill_ghosts()
+    G = o.prims_ghosted()
+    # global interior array (j, i) per variable
+    glob = np.zeros((9, 8, 8))
+    for b, (lev, ix, iy, iz) in enumerate(g.blocks):
+        glob[:, iy * 4:(iy + 1) * 4, ix * 4:(ix + 1) * 4] = P[b, :, 0]
+    for b, (lev, ix, iy, iz) in enumerate(g.blocks):
+        for jj in range(10):
+            for ii in range(10):
+                J, I = iy * 4 + jj - 3, ix * 4 + ii - 3
+                clampI = 0
+                if I < 0:
+                    I, clampI = 0, -1
+                if I > 7:
+                    I, clampI = 7, 1
+                flip = False
+                if J < 0:
+                    J, flip = -1 - J, True
+                if J > 7:
+                    J, flip = 15 - J, True
+                exp = glob[:, J, I].copy()
+                if flip:
+                    exp[3] *= -1
+                    exp[6] *= -1
+                if clampI < 0:
+                    exp[2] = min(exp[2], 0.0)
+                if clampI > 0:
+                    exp[2] = max(exp[2], 0.0)
+                np.testing.assert_array_equal(G[b, :, 0, jj, ii], exp)
+
+
+def test_update_assembly_brute_force():
+    """Tiny periodic grid, one stage: U1 = Un + dt (-sum_d dF_d/dx_d + sqrt(g) S)
+    assembled face by face from the point-wise functions equals the grid stage."""
+    g = pb.periodic_box(ndim=2, nblock=4, nroot=2, recon="ppm", kappa=0.3)
+    P = pb.random_periodic_prims(g, seed=12)
+    o = oracle.Oracle(g)
+    o.set_prims(P)
+    Un = o.cons()
+    dt = 0.2 * o.cfl_dt()
+    o.stage(1, dt)
+    U1 = o.cons()
+    pt = oracle.Point(g)
+    n = 8
+    glob = np.zeros((9, n, n))
+    for b, (lev, ix, iy, iz) in enumerate(g.blocks):
+        glob[:, iy * 4:(iy + 1) * 4, ix * 4:(ix + 1) * 4] = P[b, :, 0]
+    dx = 1.0 / n
+    m = pt.metric([0.5] * 3)
+
+    def face(J, I, d):  # flux through the low face of cell (J, I) in direction d
+        st = np.zeros((6, 9))
+        for s in range(6):
+            jj, ii = (J, (I + s - 3) % n) if d == 0 else ((J + s - 3) % n, I)
+            st[s] = glob[:, jj, ii]
+        PL, PR = pt.reconstruct(st)
+        return pt.face_flux(m, PL, PR, d)
+
+    for b, (lev, ix, iy, iz) in enumerate(g.blocks):
+        for j in range(4):
+            for i in range(4):
+                J, I = iy * 4 + j, ix * 4 + i
+                rhs = -(face(J, (I + 1) % n, 0) - face(J, I, 0)) / dx - (face((J + 1) % n, I, 1) - face(J, I, 1)) / dx
+                rhs += pt.sources(m, glob[:, J, I])
+                exp = Un[b, :, 0, j, i] + dt * rhs
+                np.testing.assert_allclose(U1[b, :, 0, j, i], exp, rtol=1e-13, atol=1e-14)
+
+
+def test_conservation_periodic_box():
+    """Sum of D, S_i, tau, B^i over a periodic flat box is constant to
+    round-off over 40 steps (fluxes telescope); psi decays."""
+    g = pb.periodic_box(ndim=2, nblock=8, nroot=2, kappa=0.5)
+    P = pb.random_periodic_prims(g)
+    o = oracle.Oracle(g)
+    o.set_prims(P)
+    U0 = o.cons()
+    tot0 = [math.fsum(U0[:, v].ravel()) for v in range(8)]
+    for _ in range(40):
+        o.step(o.cfl_dt())
+    assert o.c2p_counts()[2:].sum() == 0
+    U = o.cons()
+    for v in range(8):
+        tot = math.fsum(U[:, v].ravel())
+        scale = math.fsum(np.abs(U0[:, v]).ravel())
+        assert abs(tot - tot0[v]) <= 1e-13 * scale, (v, tot, tot0[v])
+
+
+def _l1_error(make, n, t_end, var, recon):
+    g = pb.Grid(ndim=1, nx=(n // 4, 1, 1), nroot=(4, 1, 1), xmin=(0, 0, 0), xmax=(1, 1, 1),
+                gamma_ad=5.0 / 3.0, recon=recon, riemann="hll", kappa=0.0, cfl=0.4)
+    o = oracle.Oracle(g)
+    o.set_prims(make(g, 0.0))
+    t = 0.0
+    while t < t_end - 1e-14:
+        dt = min(o.cfl_dt(), t_end - t)
+        o.step(dt)
+        t += dt
+    Q = o.prims()
+    exact = make(g, t_end)
+    return float(np.mean(np.abs(Q[:, var] - exact[:, var])))
+
+
+@pytest.mark.parametrize("recon,order", [("ppm", 1.9), ("minmod", 1.7)])
+def test_contact_wave_converges_at_second_order(recon, order):
+    errs = [_l1_error(lambda g, t: pb.contact_wave_prims(g, t), n, 0.5, 0, recon) for n in (32, 64, 128)]
+    rates = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert rates[-1] >= order, (errs, rates)
+
+
+def test_alfven_wave_is_an_exact_travelling_wave():
+    """The closed-form wave satisfies F(U) - vA U = const along the profile,
+    checked with the covariant fluxes (not the oracle's)."""
+    g = pb.Grid(ndim=1, nx=(16, 1, 1), nroot=(1, 1, 1), xmin=(0, 0, 0), xmax=(1, 1, 1), gamma_ad=5.0 / 3.0)
+    P = pb.alfven_wave_prims(g)[0, :, 0, 0, :].T
+    vA = pb.alfven_speed(1.0, 1.0, 5.0 / 3.0, 1.0, 1.0)
+    I3 = np.eye(3)
+    rows = []
+    for q in P:
+        D, S, tau = cov.conserved(q, 1.0, np.zeros(3), I3, 5.0 / 3.0)
+        FD, FS, Ftau, FB = cov.fluxes(q, 1.0, np.zeros(3), I3, 5.0 / 3.0, 0)
+        U = np.concatenate([[D], S, [tau], q[5:8]])
+        F = np.concatenate([[FD], FS, [Ftau], FB])
+        rows.append(F - vA * U)
+    rows = np.array(rows)
+    assert np.abs(rows - rows[0]).max() < 1e-13
+
+
+def test_alfven_wave_converges_at_second_order():
+    make = lambda g, t: pb.alfven_wave_prims(g, t)  # noqa: E731
+    errs = [_l1_error(make, n, 0.25, 6, "ppm") for n in (32, 64, 128)]
+    rates = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert rates[-1] >= 1.8, (errs, rates)
+
+
+def test_cfl_of_a_uniform_state_is_the_light_crossing():
+    """Static uniform flat state with ch = 1: the largest signal speed is the
+    cleaning speed 1, so dt = C / (1/dx + 1/dy)."""
+    g = pb.shock_tube_2d()
+    P = pb.empty_prims(g)
+    P[:, 0] = 1.0
+    P[:, 1] = 0.1
+    o = oracle.Oracle(g)
+    o.set_prims(P)
+    assert o.cfl_dt() == pytest.approx(0.4 / (128 + 128), rel=1e-15)
+
+
+def test_fm_torus_constants():
+    """The torus angular-momentum constant equals u^t u_phi of the prograde
+    circular Kerr geodesic at r_pmax (Bardeen, Press & Teukolsky 1972)."""
+    a, r = A_SPIN, 12.0
+    ell, _ = pb.fm_constants(a, 6.0, r)
+    den = r ** 0.75 * math.sqrt(r ** 1.5 - 3 * r ** 0.5 + 2 * a)
+    ut = (r ** 1.5 + a) / den
+    uphi = (r * r - 2 * a * r ** 0.5 + a * a) / den
+    assert ell == pytest.approx(ut * uphi, rel=1e-7)
+
+
+def test_fm_torus_equilibrium_converges():
+    """Unmagnetised, unperturbed FM torus: the density drift inside the torus
+    after the same physical time falls with resolution (the torus is an exact
+    equilibrium of the continuum equations)."""
+    drift = []
+    for nb in (4, 8):
+        g = pb.torus_2d(nblock=nb)
+        P = pb.fm_torus_prims(g, field=False, pert=0.0)
+        o = oracle.Oracle(g)
+        o.set_prims(P)
+        t = 0.0
+        while t < 2.0 - 1e-12:
+            dt = min(o.cfl_dt(), 2.0 - t)
+            o.step(dt)
+            t += dt
+        Q = o.prims()
+        m = P[:, 0] > 0.1
+        drift.append(float(np.abs(Q[:, 0][m] - P[:, 0][m]).mean()))
+    assert drift[1] < drift[0] / 3.0, drift
+
+
+def test_shock_tube_matches_stored_oracle_profile():
+    """Regression against tests/golden/shock_tube_profile.txt, which
+    tests/golden/make_golden.py wrote with the oracle alone."""
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "shock_tube_profile.txt")
+    ref = np.loadtxt(path)
+    from tests.golden.make_golden import shock_tube_profile
+    np.testing.assert_allclose(shock_tube_profile(), ref, rtol=1e-12, atol=1e-13)
