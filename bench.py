@@ -1,0 +1,371 @@
+#!/usr/bin/env python3
+"""Benchmark: zone-updates per second per RK stage of the per-block GRMHD
+finite-volume update on GB300, FP64 and mixed forms, with the roofline.
+
+Workload (default): the 3-D Fishbone-Moncrief torus around a Kerr black hole
+(a = 0.9375, modified Kerr-Schild), 512 x 256 x 256 cells as 2048 blocks of
+32 x 32 x 16 with 3 ghost cells, PPM + HLL, GLM cleaning, SSP-RK2, loop field at
+beta = 100, seeded +-2% pressure perturbation.  One step = ghost fill, stage 1,
+ghost fill, stage 2 (the CFL reduction rides in stage 2).  A zone-update is one
+interior cell through one RK stage, so value = cells x 2 x steps / time.
+
+Our arm:   python bench.py [--gpus N --steps K --warmup W]
+Reference: python bench.py --impl reference ...  (the FP64 CPU oracle on the
+           host cores, on a bounded sample of the workload)
+Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import problems as pb  # noqa: E402
+
+METRIC = "zone-updates/s per RK stage"
+UNIT = "zone-updates/s"
+# FP64 peak derived from the part's unit counts and clock: 152 SMs x 2070 MHz x
+# 2 DFMA (4 flops) per clock per SM = 1.26 TFLOP/s (nominal 1.25 TFLOP/s)
+FP64_PEAK_TFLOPS = 152 * 2.07e9 * 4 / 1e12
+FP32_PEAK_TFLOPS = 152 * 2.07e9 * 256 / 1e12  # 128 FFMA per clock per SM
+SAMPLE_CELLS = (128, 64, 64)  # bounded CPU sample of the torus workload
+
+
+def workload(name: str):
+    if name == "torus_3d_large":
+        g = pb.torus_3d_large()
+        desc = "3-D FM torus, Kerr a=0.9375, MKS, 512x256x256 cells as 2048 blocks of 32x32x16 (+3 ghosts)"
+    elif name == "torus_3d":
+        g = pb.torus_3d()
+        desc = "3-D FM torus, Kerr a=0.9375, MKS, 192x96x96 cells as 432 blocks of 16^3 (+3 ghosts)"
+    elif name == "torus_2d":
+        g = pb.torus_2d()
+        desc = "2-D FM torus, Kerr a=0.9375, MKS, 256x256 cells as 256 blocks of 16^2 (+3 ghosts)"
+    elif name == "shock_tube_2d":
+        g = pb.shock_tube_2d()
+        desc = "2-D SRMHD shock tube, 128x128 cells as 16 blocks of 32^2 (+3 ghosts)"
+    else:
+        raise SystemExit(f"unknown workload {name}")
+    return g, desc
+
+
+def initial_prims(g):
+    return pb.shock_tube_prims(g) if g.coords == "cart" else pb.fm_torus_prims(g)
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class Clocks:
+    """Samples nvidia-smi every 200 ms during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 8:
+                self.rows.append(parts)
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+
+        sm = [v for v in (num(r[0]) for r in self.rows) if v is not None]
+        mx = [v for v in (num(r[1]) for r in self.rows) if v is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[4 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def time_form(gb, torch, g, P, form, steps, warmup, stream, count_flops=True):
+    """Device-resident timing of `steps` steps of one form."""
+    s = gb.Solver(g, form, stream=stream)
+    s.set_prims(P)
+    dt = s.cfl_dt()
+    for _ in range(warmup):
+        s.step(0.0)  # device dt: the same path as the timed loop
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    sev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(steps)]
+    with torch.cuda.stream(stream):
+        ev[0].record(stream)
+        for k in range(steps):
+            sev[k][0].record(stream)
+            gb.bhac_stage(s.ctx, 1, 0.0)  # ghost fill + stage-1 kernel
+            sev[k][1].record(stream)
+            sev[k][2].record(stream)
+            gb.bhac_stage(s.ctx, 2, 0.0)  # ghost fill + stage-2 kernel (+ CFL rate)
+            sev[k][3].record(stream)
+        ev[1].record(stream)
+    torch.cuda.synchronize()
+    total_ms = ev[0].elapsed_time(ev[1])
+    stage_ms = ([sev[k][0].elapsed_time(sev[k][1]) for k in range(steps)] +
+                [sev[k][2].elapsed_time(sev[k][3]) for k in range(steps)])
+    # the ghost fill alone on the same state and stream
+    fe = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    with torch.cuda.stream(stream):
+        fe[0].record(stream)
+        for _ in range(steps):
+            gb.bhac_fill_ghosts(s.ctx)
+        fe[1].record(stream)
+    torch.cuda.synchronize()
+    fill_ms = fe[0].elapsed_time(fe[1]) / steps
+    out = {"ms_per_step": total_ms / steps, "stage_ms_mean": sum(stage_ms) / len(stage_ms) - fill_ms,
+           "fill_ms": fill_ms}
+    out["c2p_counts"] = [int(x) for x in s.diagnostics()]
+    if count_flops:
+        out["flops"] = s.count_flops(max(dt, 1e-30), nsamples=4000, seed=7)
+    s.close()
+    return out
+
+
+def e2e_form(gb, torch, g, P, form, steps, stream):
+    """Through the public API with host buffers: every step copies the inputs
+    host->device from pinned memory, runs the step and reads the result back."""
+    s = gb.Solver(g, form, stream=stream)
+    host_in = torch.from_numpy(np.ascontiguousarray(P)).pin_memory()
+    host_out = torch.empty(host_in.shape, dtype=torch.float64).pin_memory()
+    dev = torch.empty(host_in.shape, dtype=torch.float64, device="cuda")
+    out_dev = torch.empty_like(dev)
+    nbytes = host_in.numel() * 8
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    with torch.cuda.stream(stream):
+        ev[0].record(stream)
+        for _ in range(steps):
+            dev.copy_(host_in, non_blocking=True)
+            gb.bhac_set_prims(s.ctx, dev.data_ptr(), True)
+            gb.bhac_cfl_dt(s.ctx, False)
+            gb.bhac_step(s.ctx, 0.0)
+            gb.bhac_get_prims(s.ctx, out_dev.data_ptr(), True)
+            host_out.copy_(out_dev, non_blocking=True)
+        ev[1].record(stream)
+    torch.cuda.synchronize()
+    ms = ev[0].elapsed_time(ev[1])
+    s.close()
+    return {"value": g.ncells * 2 * steps / (ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": nbytes,
+            "d2h_bytes_per_step": nbytes, "ms_per_step": ms / steps, "kernels_per_step": 8}
+
+
+def sample_grid(name):
+    if name == "torus_3d_large":
+        return pb.torus_3d_large(cells=SAMPLE_CELLS)
+    return workload(name)[0]
+
+
+def cpu_baseline(name, budget_s=20.0):
+    """The FP64 oracle (plain C, OpenMP over blocks) on a bounded sample of the
+    workload: the same torus, physics and block shape at reduced resolution."""
+    import oracle
+    g = sample_grid(name)
+    o = oracle.Oracle(g)
+    o.set_prims(initial_prims(g))
+    dt = o.cfl_dt()
+    n = 0
+    t0 = time.perf_counter()
+    while True:
+        o.step(dt)
+        n += 1
+        el = time.perf_counter() - t0
+        if el > budget_s or n >= 50:
+            break
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    nc = [g.nx[d] * g.nroot[d] for d in range(3)]
+    return {"value": g.ncells * 2 * n / el, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{n} oracle steps of the same problem at {nc[0]}x{nc[1]}x{nc[2]} cells "
+                      f"({g.nb} blocks of {g.nx[0]}x{g.nx[1]}x{g.nx[2]}), {el:.1f} s"}
+
+
+def reference_arm(args, rank):
+    """The oracle on the host cores, each step a bounded sample of the workload."""
+    if rank != 0:
+        return
+    import oracle
+    _, desc = workload(args.workload)
+    gs = sample_grid(args.workload)
+    o = oracle.Oracle(gs)
+    o.set_prims(initial_prims(gs))
+    dt = o.cfl_dt()
+    for _ in range(args.warmup):
+        o.step(dt)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        o.step(dt)
+    el = time.perf_counter() - t0
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    v = gs.ncells * 2 * args.steps / el
+    nc = [gs.nx[d] * gs.nroot[d] for d in range(3)]
+    sample = (f"each step: one oracle step of the same problem at {nc[0]}x{nc[1]}x{nc[2]} cells "
+              f"({gs.nb} blocks of {gs.nx[0]}x{gs.nx[1]}x{gs.nx[2]})")
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded Fishbone-Moncrief torus)",
+            "config": {"workload": desc, "sample": sample},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="torus_3d_large")
+    ap.add_argument("--form", default="both", choices=["both", "mixed", "fp64"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        reference_arm(args, rank)
+        return
+
+    import torch
+
+    import paper_2108_12240_gb300 as gb
+
+    if args.warmup < 3:
+        raise SystemExit("at least 3 warm-up steps")
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    # the CPU baseline first (rank 0 at N = 1), before any GPU work
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(args.workload)
+
+    g, desc = workload(args.workload)
+    P = initial_prims(g)
+    stream = torch.cuda.Stream()
+    forms = ["mixed", "fp64"] if args.form == "both" else [args.form]
+    results = {}
+    for form in forms:
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        with Clocks(local) as ck:
+            results[form] = time_form(gb, torch, g, P, form, args.steps, args.warmup, stream)
+        results[form]["clocks"] = ck.summary()
+        if dist:
+            t = torch.tensor([results[form]["ms_per_step"]], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            results[form]["ms_per_step"] = float(t.item())
+        # each rank advances its own full replica (weak scaling)
+        results[form]["value"] = g.ncells * 2 * world / (results[form]["ms_per_step"] * 1e-3)
+    head = forms[0]
+    e2e = None
+    if not args.no_e2e:
+        e2e = e2e_form(gb, torch, g, P, head, max(1, min(args.steps, 3)), stream)
+        e2e["value"] *= world
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    pk, pk_kind = peaks()
+
+    def roofline(form):
+        r = results[form]
+        fl = r["flops"]
+        stage_s = r["stage_ms_mean"] * 1e-3
+        cells = g.ncells
+        ach64 = fl["fp64_flops"] * cells / stage_s / 1e12
+        bytes_alg = (288 if form == "fp64" else 252) * cells
+        return {"bound": "alu", "achieved": ach64, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": ach64 / FP64_PEAK_TFLOPS, "traffic": None, "kernel": "stage_kernel",
+                "stage_ms": r["stage_ms_mean"], "ghost_fill_ms": r["fill_ms"],
+                "peak_kind": "derived FP64: 152 SMs x 2070 MHz x 4 flops/clk/SM",
+                "fp64_flops_per_zone_stage": fl["fp64_flops"],
+                "fp32_flops_per_zone_stage": fl["fp32_flops"],
+                "fp32_frac_of_peak": fl["fp32_flops"] * cells / stage_s / 1e12 / FP32_PEAK_TFLOPS,
+                "hbm_bytes_per_zone_stage": bytes_alg / cells,
+                "hbm_frac_of_measured": bytes_alg / stage_s / 1e9 / pk["hbm_gbs"]}
+
+    r = results[head]
+    line = {
+        "metric": METRIC, "value": r["value"], "unit": UNIT,
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64" if head == "mixed" else "f64",
+        "data": "synthetic (seeded Fishbone-Moncrief torus)",
+        "config": {"workload": desc, "form": head, "replicas": world,
+                   "l2": "inputs larger than L2 (state ~17 GB), no flush",
+                   "launch": "per step: ghost fill + stage kernel, twice; device dt"},
+        "forms": {f: {"value": results[f]["value"], "ms_per_step": results[f]["ms_per_step"],
+                      "roofline": roofline(f), "c2p_counts": results[f]["c2p_counts"],
+                      "clocks": results[f]["clocks"]} for f in forms},
+        "roofline": roofline(head),
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": 4 * args.steps,
+        "clocks": results[head]["clocks"],
+        "peaks": {"kind": pk_kind, "hbm_gbs": pk.get("hbm_gbs")},
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,181 @@
+/*
+ * bhac_gb300.h - C ABI of the GB300 (sm_103a) per-block finite-volume GRMHD update.
+ *
+ * The library advances ideal GRMHD on a grid of equal-sized blocks with ghost
+ * cells, the data-parallel core of the method in Sec. 2 of the paper ("Code
+ * overview"): a shock-capturing finite-volume scheme on block-based AMR in a
+ * covariant coordinate system, second-order two-stage time stepping, PPM (or
+ * minmod) reconstruction and a Newton conserved-to-primitive inversion with
+ * backup strategies.  The ghost-cell fill between blocks of the same level is
+ * the kernel the paper singles out (Sec. 4.3, the roofline figure; Sec. 5.1).
+ *
+ * Conventions shared by every entry point
+ *   - primitive variables, in this order: rho, p, u^1, u^2, u^3, B^1, B^2, B^3, psi
+ *     (u^i = W v^i in contravariant code-coordinate components; psi is the GLM
+ *     cleaning scalar);
+ *   - conserved variables, in this order: D, S_1, S_2, S_3, tau, B^1, B^2, B^3, psi,
+ *     each multiplied by sqrt(gamma) of its cell;
+ *   - host/device arrays of cell data are [block][var][k][j][i] over the interior
+ *     cells of every block, i fastest, FP64, in the block order given at init;
+ *   - every call is asynchronous on the stream given at init, except calls that
+ *     return values through host pointers, which synchronise that stream;
+ *   - errors are returned as bhac_status; nothing traps, aborts or exits.
+ *
+ * Ownership: device memory belongs to the caller, who passes one arena of at
+ * least bhac_query_sizes() bytes at init (e.g. the data pointer of a torch
+ * uint8 tensor).  The library never allocates or frees device memory.  The
+ * context itself (host memory) is owned by the library until bhac_destroy().
+ * A context is not thread-safe.
+ */
+#ifndef BHAC_GB300_H
+#define BHAC_GB300_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bhac_ctx bhac_ctx;
+
+typedef enum {
+  BHAC_OK = 0,
+  BHAC_ERR_ARG = 1,      /* invalid argument or descriptor */
+  BHAC_ERR_CUDA = 2,     /* a CUDA runtime call failed */
+  BHAC_ERR_NOMEM = 3,    /* the arena is smaller than bhac_query_sizes() */
+  BHAC_ERR_STATE = 4,    /* call out of order (e.g. step before set_prims) */
+  BHAC_ERR_TIMEOUT = 5,  /* a bounded device wait gave up */
+  BHAC_WARN_C2P = 6      /* some cells failed the inversion and kept their previous state */
+} bhac_status;
+
+enum { BHAC_COORDS_CART = 0, BHAC_COORDS_KS = 1, BHAC_COORDS_MKS = 2 };
+enum { BHAC_BC_PERIODIC = 0, BHAC_BC_OUTFLOW = 1, BHAC_BC_AXIS = 2, BHAC_BC_NOINFLOW = 3 };
+enum { BHAC_RECON_PPM = 0, BHAC_RECON_MINMOD = 1 };
+enum { BHAC_RIEMANN_HLL = 0, BHAC_RIEMANN_TVDLF = 1 };
+enum { BHAC_PREC_FP64 = 0, BHAC_PREC_MIXED = 1 };
+
+/* Grid and scheme description, copied at init. */
+typedef struct {
+  int ndim;              /* 2 or 3 active dimensions */
+  int nx[3];             /* interior cells per block per dimension (1 if inactive) */
+  int nghost;            /* ghost cells per side in active dimensions; must be 3 */
+  int nroot[3];          /* level-0 blocks per dimension */
+  int nlevels;           /* refinement levels (1 = uniform grid) */
+  double xmin[3], xmax[3];
+  int coords;            /* BHAC_COORDS_*: Cartesian Minkowski, Kerr-Schild (r, th, ph) or
+                            modified KS (x1 = ln r, x2 = th/pi, x3 = ph) */
+  double spin, mass;     /* Kerr a and M (M = 0: flat space in those coordinates) */
+  int bc[3][2];          /* BHAC_BC_* at [dimension][low, high] */
+  int recon;             /* BHAC_RECON_* */
+  int riemann;           /* BHAC_RIEMANN_* */
+  int precision;         /* BHAC_PREC_FP64, or BHAC_PREC_MIXED: FP32 reconstruction,
+                            fluxes and sources summed into FP64 conserved state */
+  double gamma_ad;       /* ideal-gas index */
+  double cfl;            /* Courant number */
+  double ch, kappa;      /* GLM cleaning speed and damping rate */
+  double c2p_tol;        /* Newton tolerance on |dZ|/Z (then one polishing step) */
+  int c2p_maxit;         /* Newton iteration cap */
+  double rho_floor, rho_floor_pow, p_floor, p_floor_pow, w_max;
+                         /* floors rho >= rho_floor r^rho_floor_pow, p >= p_floor r^p_floor_pow,
+                            W <= w_max; r = 1 in Cartesian coordinates */
+} bhac_grid_desc;
+
+/* One leaf block: refinement level and integer block coordinates at that level. */
+typedef struct {
+  int level, ix, iy, iz;
+} bhac_block_desc;
+
+/* Device bytes the arena must hold for this grid (tables, state, ghost maps).
+ * Returns BHAC_ERR_ARG for an invalid description. */
+bhac_status bhac_query_sizes(const bhac_grid_desc* desc, const bhac_block_desc* blocks, int nblocks,
+                             size_t* device_bytes_out);
+
+/* Creates a context on the current CUDA device.  `device_arena` must be a device
+ * pointer to >= bhac_query_sizes() bytes, 256-byte aligned; it stays owned by
+ * the caller and must outlive the context.  `cuda_stream` is a cudaStream_t (or
+ * NULL for the legacy default stream).  Builds the ghost-cell maps on the host
+ * (same-level copies and the physical boundary rules) and uploads them. */
+bhac_status bhac_init_grid(bhac_ctx** out, const bhac_grid_desc* desc, const bhac_block_desc* blocks,
+                           int nblocks, void* device_arena, size_t arena_bytes, void* cuda_stream);
+
+/* Evaluates the metric tables on the device in FP64: lapse, shift, spatial
+ * metric, its inverse, sqrt(gamma), their first derivatives along x1 and x2
+ * (forward-mode dual numbers) and the floor profiles, at cell centres and at
+ * x1- and x2-faces.  The metric must be phi-independent.  `kind` and `spin_a`,
+ * `mass` override the descriptor's coords/spin/mass; `mks_params` is reserved
+ * and may be NULL. */
+bhac_status bhac_set_metric(bhac_ctx* ctx, int kind, double spin_a, double mass, const double* mks_params);
+
+/* Loads interior primitives ([block][var][k][j][i], FP64; host pointer if
+ * on_device == 0, device pointer otherwise) and sets the conserved state from
+ * them.  Floors are not applied. */
+bhac_status bhac_set_prims(bhac_ctx* ctx, const double* prims, int on_device);
+
+/* Fills every ghost cell from the owning block (same level) or the boundary
+ * rule: periodic wrap; outflow copy; no-inflow (outflow, then u^d clamped so
+ * that nothing enters); polar axis (mirror in theta, flip u^theta and B^theta,
+ * and take the cell at phi + pi in 3-D). */
+bhac_status bhac_fill_ghosts(bhac_ctx* ctx);
+
+/* Computes dt = cfl / max over interior cells of sum_d c_d/dx_d (c_d: largest of
+ * the fast-magnetosonic speeds and the GLM speeds along d) into device memory;
+ * also returns it through dt_host when non-NULL (synchronises the stream). */
+bhac_status bhac_cfl_dt(bhac_ctx* ctx, double* dt_host_or_null);
+
+/* One SSP-RK2 step (two stages) of size dt: ghost fill, stage 1, ghost fill,
+ * stage 2; each stage reconstructs, computes HLL/TVDLF face fluxes, adds the
+ * geometric and GLM sources, updates the conserved state and inverts it to
+ * primitives.  dt <= 0 uses the device dt of the last CFL evaluation (the step
+ * itself refreshes it from its final primitives), so steps can be captured in
+ * a CUDA graph with no host round trip. */
+bhac_status bhac_step(bhac_ctx* ctx, double dt);
+
+/* One RK stage (1 or 2) with its preceding ghost fill. */
+bhac_status bhac_stage(bhac_ctx* ctx, int stage, double dt);
+
+/* Copies interior primitives (or densitized conserved variables) out, same
+ * layout as bhac_set_prims; host copies synchronise the stream. */
+bhac_status bhac_get_prims(bhac_ctx* ctx, double* out, int on_device);
+bhac_status bhac_get_cons(bhac_ctx* ctx, double* out, int on_device);
+
+/* Inversion outcome counts accumulated since init, per cell and stage:
+ * [0] Newton converged, [1] backup solver used, [2] floors applied,
+ * [3] failed (previous primitives kept).  Synchronises the stream. */
+bhac_status bhac_get_diagnostics(bhac_ctx* ctx, long long counts[4]);
+
+/* Kernel launch shape of the stage kernel: tile of tx x ty cells per CTA column,
+ * threads per CTA, and persistent = 1 for one CTA per SM slot pulling tiles from
+ * a device work counter.  Values 0 keep the current setting. */
+bhac_status bhac_set_launch(bhac_ctx* ctx, int tx, int ty, int threads, int persistent);
+
+/* Records `nsteps` steps with the device time step (bhac_step(ctx, 0.0)) into a
+ * CUDA graph on the context's stream and instantiates it; bhac_graph_launch()
+ * then replays all of them with one launch.  The stream must be a created
+ * (non-legacy-default) stream; the CFL must have been evaluated (bhac_cfl_dt or
+ * a previous step).  Buffer roles return to their starting state after every
+ * step, so replays continue the evolution.  Capturing again replaces the graph. */
+bhac_status bhac_graph_capture(bhac_ctx* ctx, int nsteps);
+bhac_status bhac_graph_launch(bhac_ctx* ctx);
+
+/* Measurement utility for the roofline (the paper has no counterpart): counts
+ * the floating-point operations one zone-stage costs with the library's own
+ * formulas (reconstruction, Riemann solve, sources, RK combination, inversion
+ * and, averaged over the two stages, the CFL rate), by running them on the
+ * host with a counting scalar over `nsamples` interior cells of the current
+ * state drawn with `seed` (their Newton iteration counts are the real ones;
+ * the stage is taken of size dt > 0).  Convention: + - * / sqrt 1/sqrt = 1 flop,
+ * a fused multiply-add = 2, compares/min/max/selects = 0.  out[0], out[1]:
+ * FP64 and FP32 flops per zone-stage; out[2], out[3]: of which divisions and
+ * (reciprocal) square roots; out[4]: samples; out[5]: blocks sampled.  Fills
+ * the ghost cells of the current state and synchronises the stream. */
+bhac_status bhac_count_flops(bhac_ctx* ctx, double dt, int nsamples, unsigned seed, double out[6]);
+
+/* Releases the context (host memory only; the arena stays the caller's). */
+void bhac_destroy(bhac_ctx* ctx);
+
+const char* bhac_status_string(bhac_status status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,321 @@
+"""GB300 (sm_103a) per-block finite-volume GRMHD update behind a C ABI.
+
+The functions ``bhac_*`` below are a thin ctypes binding of
+``include/bhac_gb300.h`` (same names, argument marshalling only); every step
+of the update runs in the library's CUDA kernels.  ``Solver`` bundles the
+calls for a ``problems.Grid``-like record, with the device arena and stream
+taken from PyTorch.  There is no CPU fallback: if the library cannot be
+loaded, importing this package raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from .build import LIB, build, stale
+
+__all__ = [
+    "GridDesc", "BlockDesc", "Solver", "BhacError", "lib", "status_string",
+    "bhac_query_sizes", "bhac_init_grid", "bhac_set_metric", "bhac_set_prims", "bhac_fill_ghosts",
+    "bhac_cfl_dt", "bhac_step", "bhac_stage", "bhac_get_prims", "bhac_get_cons", "bhac_get_diagnostics",
+    "bhac_set_launch", "bhac_count_flops", "bhac_graph_capture", "bhac_graph_launch", "bhac_destroy",
+    "bhac_status_string",
+]
+
+NV = 9
+COORDS = {"cart": 0, "ks": 1, "mks": 2}
+BCS = {"periodic": 0, "outflow": 1, "axis": 2, "noinflow": 3}
+RECON = {"ppm": 0, "minmod": 1}
+RIEMANN = {"hll": 0, "tvdlf": 1}
+PREC = {"fp64": 0, "mixed": 1}
+STATUS = {0: "ok", 1: "invalid argument", 2: "CUDA error", 3: "arena too small", 4: "call out of order",
+          5: "device wait timed out", 6: "inversion failures"}
+
+
+class GridDesc(C.Structure):
+    _fields_ = [
+        ("ndim", C.c_int), ("nx", C.c_int * 3), ("nghost", C.c_int), ("nroot", C.c_int * 3),
+        ("nlevels", C.c_int), ("xmin", C.c_double * 3), ("xmax", C.c_double * 3), ("coords", C.c_int),
+        ("spin", C.c_double), ("mass", C.c_double), ("bc", (C.c_int * 2) * 3), ("recon", C.c_int),
+        ("riemann", C.c_int), ("precision", C.c_int), ("gamma_ad", C.c_double), ("cfl", C.c_double),
+        ("ch", C.c_double), ("kappa", C.c_double), ("c2p_tol", C.c_double), ("c2p_maxit", C.c_int),
+        ("rho_floor", C.c_double), ("rho_floor_pow", C.c_double), ("p_floor", C.c_double),
+        ("p_floor_pow", C.c_double), ("w_max", C.c_double),
+    ]
+
+
+class BlockDesc(C.Structure):
+    _fields_ = [("level", C.c_int), ("ix", C.c_int), ("iy", C.c_int), ("iz", C.c_int)]
+
+
+class BhacError(RuntimeError):
+    def __init__(self, where: str, status: int):
+        super().__init__(f"{where}: {STATUS.get(status, status)} (status {status})")
+        self.status = status
+
+
+_lib = None
+
+
+def lib():
+    """Loads libbhac_gb300.so (building it first if it is missing or stale)."""
+    global _lib
+    if _lib is None:
+        path = build() if (stale() and os.environ.get("BHAC_NO_BUILD") is None) else LIB
+        if not os.path.exists(path):
+            raise ImportError(f"CUDA library {path} is missing; run paper_2108_12240_gb300.build.build()")
+        L = C.CDLL(path)
+        vp, i, d, sz = C.c_void_p, C.c_int, C.c_double, C.c_size_t
+        G, B = C.POINTER(GridDesc), C.POINTER(BlockDesc)
+        sig = {
+            "bhac_query_sizes": ([G, B, i, C.POINTER(sz)], i),
+            "bhac_init_grid": ([C.POINTER(vp), G, B, i, vp, sz, vp], i),
+            "bhac_set_metric": ([vp, i, d, d, vp], i),
+            "bhac_set_prims": ([vp, vp, i], i),
+            "bhac_fill_ghosts": ([vp], i),
+            "bhac_cfl_dt": ([vp, C.POINTER(d)], i),
+            "bhac_step": ([vp, d], i),
+            "bhac_stage": ([vp, i, d], i),
+            "bhac_get_prims": ([vp, vp, i], i),
+            "bhac_get_cons": ([vp, vp, i], i),
+            "bhac_get_diagnostics": ([vp, C.POINTER(C.c_longlong)], i),
+            "bhac_set_launch": ([vp, i, i, i, i], i),
+            "bhac_count_flops": ([vp, d, i, C.c_uint, C.POINTER(d)], i),
+            "bhac_graph_capture": ([vp, i], i),
+            "bhac_graph_launch": ([vp], i),
+            "bhac_destroy": ([vp], None),
+            "bhac_status_string": ([i], C.c_char_p),
+        }
+        for name, (args, res) in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+    return _lib
+
+
+def _check(where, st):
+    if st not in (0, 6):
+        raise BhacError(where, st)
+    return st
+
+
+def status_string(st: int) -> str:
+    return lib().bhac_status_string(st).decode()
+
+
+# ---- the C ABI, one Python function per entry point ----
+
+def bhac_query_sizes(desc: GridDesc, blocks) -> int:
+    n = C.c_size_t()
+    _check("bhac_query_sizes", lib().bhac_query_sizes(C.byref(desc), blocks, len(blocks), C.byref(n)))
+    return n.value
+
+
+def bhac_init_grid(desc: GridDesc, blocks, arena_ptr: int, arena_bytes: int, stream_ptr: int):
+    ctx = C.c_void_p()
+    _check("bhac_init_grid", lib().bhac_init_grid(C.byref(ctx), C.byref(desc), blocks, len(blocks),
+                                                  C.c_void_p(arena_ptr), arena_bytes, C.c_void_p(stream_ptr)))
+    return ctx
+
+
+def bhac_set_metric(ctx, kind: int, spin: float, mass: float):
+    return _check("bhac_set_metric", lib().bhac_set_metric(ctx, kind, spin, mass, None))
+
+
+def bhac_set_prims(ctx, ptr: int, on_device: bool):
+    return _check("bhac_set_prims", lib().bhac_set_prims(ctx, C.c_void_p(ptr), int(on_device)))
+
+
+def bhac_fill_ghosts(ctx):
+    return _check("bhac_fill_ghosts", lib().bhac_fill_ghosts(ctx))
+
+
+def bhac_cfl_dt(ctx, want_host: bool = True):
+    dt = C.c_double(0.0)
+    _check("bhac_cfl_dt", lib().bhac_cfl_dt(ctx, C.byref(dt) if want_host else None))
+    return dt.value if want_host else None
+
+
+def bhac_step(ctx, dt: float):
+    return _check("bhac_step", lib().bhac_step(ctx, dt))
+
+
+def bhac_stage(ctx, stage: int, dt: float):
+    return _check("bhac_stage", lib().bhac_stage(ctx, stage, dt))
+
+
+def bhac_get_prims(ctx, ptr: int, on_device: bool):
+    return _check("bhac_get_prims", lib().bhac_get_prims(ctx, C.c_void_p(ptr), int(on_device)))
+
+
+def bhac_get_cons(ctx, ptr: int, on_device: bool):
+    return _check("bhac_get_cons", lib().bhac_get_cons(ctx, C.c_void_p(ptr), int(on_device)))
+
+
+def bhac_get_diagnostics(ctx):
+    out = (C.c_longlong * 4)()
+    st = _check("bhac_get_diagnostics", lib().bhac_get_diagnostics(ctx, out))
+    return np.array(list(out), dtype=np.int64), st
+
+
+def bhac_set_launch(ctx, tx=0, ty=0, threads=0, persistent=0):
+    return _check("bhac_set_launch", lib().bhac_set_launch(ctx, tx, ty, threads, persistent))
+
+
+def bhac_count_flops(ctx, dt: float, nsamples: int = 2000, seed: int = 1):
+    out = (C.c_double * 6)()
+    _check("bhac_count_flops", lib().bhac_count_flops(ctx, dt, nsamples, seed, out))
+    return {"fp64_flops": out[0], "fp32_flops": out[1], "fp64_special": out[2], "fp32_special": out[3],
+            "samples": int(out[4]), "blocks": int(out[5])}
+
+
+def bhac_graph_capture(ctx, nsteps: int):
+    return _check("bhac_graph_capture", lib().bhac_graph_capture(ctx, nsteps))
+
+
+def bhac_graph_launch(ctx):
+    return _check("bhac_graph_launch", lib().bhac_graph_launch(ctx))
+
+
+def bhac_destroy(ctx):
+    lib().bhac_destroy(ctx)
+
+
+def bhac_status_string(st: int) -> str:
+    return status_string(st)
+
+
+# ---- convenience wrapper ----
+
+def desc_of(grid, precision: str = "fp64") -> GridDesc:
+    d = GridDesc()
+    d.ndim = grid.ndim
+    for k in range(3):
+        d.nx[k] = grid.nx[k]
+        d.nroot[k] = grid.nroot[k]
+        d.xmin[k] = grid.xmin[k]
+        d.xmax[k] = grid.xmax[k]
+        d.bc[k][0] = BCS[grid.bc[k][0]]
+        d.bc[k][1] = BCS[grid.bc[k][1]]
+    d.nghost = grid.ng
+    d.nlevels = grid.nlevels
+    d.coords = COORDS[grid.coords]
+    d.spin = grid.spin
+    d.mass = grid.mass
+    d.recon = RECON[grid.recon]
+    d.riemann = RIEMANN[grid.riemann]
+    d.precision = PREC[precision]
+    d.gamma_ad = grid.gamma_ad
+    d.cfl = grid.cfl
+    d.ch = grid.ch
+    d.kappa = grid.kappa
+    d.c2p_tol = grid.c2p_tol
+    d.c2p_maxit = grid.c2p_maxit
+    d.rho_floor = grid.rho_floor
+    d.rho_floor_pow = grid.rho_floor_pow
+    d.p_floor = grid.p_floor
+    d.p_floor_pow = grid.p_floor_pow
+    d.w_max = grid.w_max
+    return d
+
+
+def blocks_of(grid):
+    arr = (BlockDesc * grid.nb)()
+    for n, (lev, ix, iy, iz) in enumerate(np.asarray(grid.blocks)):
+        arr[n].level, arr[n].ix, arr[n].iy, arr[n].iz = int(lev), int(ix), int(iy), int(iz)
+    return arr
+
+
+class Solver:
+    """A grid on the current CUDA device: arena from torch, stream from torch."""
+
+    def __init__(self, grid, precision: str = "fp64", device: str = "cuda:0", stream=None):
+        import torch
+
+        self.torch = torch
+        self.grid = grid
+        self.precision = precision
+        self.device = torch.device(device)
+        self.desc = desc_of(grid, precision)
+        self.blocks = blocks_of(grid)
+        self.nbytes = bhac_query_sizes(self.desc, self.blocks)
+        self.arena = torch.empty(self.nbytes + 256, dtype=torch.uint8, device=self.device)
+        base = self.arena.data_ptr()
+        self.base = (base + 255) & ~255
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.ctx = bhac_init_grid(self.desc, self.blocks, self.base, self.nbytes, self.stream.cuda_stream)
+        bhac_set_metric(self.ctx, self.desc.coords, grid.spin, grid.mass)
+        self.shape = (grid.nb, NV, grid.nx[2], grid.nx[1], grid.nx[0])
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            bhac_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_prims(self, prims):
+        torch = self.torch
+        if isinstance(prims, torch.Tensor) and prims.is_cuda:
+            t = prims.to(torch.float64).contiguous()
+            bhac_set_prims(self.ctx, t.data_ptr(), True)
+            self.stream.synchronize()
+        else:
+            a = np.ascontiguousarray(prims, dtype=np.float64)
+            assert a.size == int(np.prod(self.shape))
+            bhac_set_prims(self.ctx, a.ctypes.data, False)
+
+    def prims(self) -> np.ndarray:
+        out = np.empty(self.shape)
+        bhac_get_prims(self.ctx, out.ctypes.data, False)
+        return out
+
+    def cons(self) -> np.ndarray:
+        out = np.empty(self.shape)
+        bhac_get_cons(self.ctx, out.ctypes.data, False)
+        return out
+
+    def prims_device(self, out=None):
+        torch = self.torch
+        if out is None:
+            out = torch.empty(self.shape, dtype=torch.float64, device=self.device)
+        bhac_get_prims(self.ctx, out.data_ptr(), True)
+        return out
+
+    def fill_ghosts(self):
+        bhac_fill_ghosts(self.ctx)
+
+    def cfl_dt(self) -> float:
+        return bhac_cfl_dt(self.ctx, True)
+
+    def step(self, dt: float = 0.0):
+        bhac_step(self.ctx, dt)
+
+    def stage(self, stage: int, dt: float):
+        bhac_stage(self.ctx, stage, dt)
+
+    def diagnostics(self):
+        return bhac_get_diagnostics(self.ctx)[0]
+
+    def count_flops(self, dt: float, nsamples: int = 2000, seed: int = 1):
+        return bhac_count_flops(self.ctx, dt, nsamples, seed)
+
+    def capture(self, nsteps: int):
+        bhac_graph_capture(self.ctx, nsteps)
+
+    def replay(self):
+        bhac_graph_launch(self.ctx)
+
+    def set_launch(self, tx=0, ty=0, threads=0, persistent=0):
+        bhac_set_launch(self.ctx, tx, ty, threads, persistent)
+
+
+# Fail loudly at import if the library cannot be loaded.
+lib()

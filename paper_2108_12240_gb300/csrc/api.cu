@@ -1,0 +1,582 @@
+// The C ABI (include/bhac_gb300.h): context, arena carving, ghost maps, and the
+// launch sequence of a step.  No device memory is allocated here: every
+// device array is a slice of the caller's arena.
+#include <stdlib.h>
+#include <string.h>
+
+#include <vector>
+
+#include "ctx.h"
+
+using namespace bhac;
+
+namespace {
+
+struct Layout {
+  size_t off_blk, off_src, off_flags, off_tmpl, off_tc, off_tf1, off_tf2, off_tc32, off_tf1_32, off_tf2_32;
+  size_t off_P[2], off_P32[2], off_U[2], off_scratch, off_small, total;
+};
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+bool valid_desc(const bhac_grid_desc* d, const bhac_block_desc* b, int nb) {
+  if (!d || !b || nb <= 0) return false;
+  if (d->ndim < 2 || d->ndim > 3 || d->nghost != 3) return false;
+  for (int k = 0; k < 3; ++k) {
+    if (d->nx[k] < 1 || d->nroot[k] < 1) return false;
+    if (k >= d->ndim && d->nx[k] != 1) return false;
+    if (k < d->ndim && d->nx[k] < 3) return false;
+    for (int s = 0; s < 2; ++s)
+      if (d->bc[k][s] < 0 || d->bc[k][s] > 3) return false;
+    if (!(d->xmax[k] > d->xmin[k])) return false;
+  }
+  if (d->nlevels != 1) return false;  // uniform grids
+  if (d->coords < 0 || d->coords > 2) return false;
+  if (d->precision < 0 || d->precision > 1) return false;
+  if (d->recon < 0 || d->recon > 1 || d->riemann < 0 || d->riemann > 1) return false;
+  if (!(d->gamma_ad > 1.0) || !(d->cfl > 0.0) || !(d->ch > 0.0) || d->c2p_maxit < 1) return false;
+  if (!(d->w_max > 1.0)) return false;
+  // the axis rule is for x2 (theta) only; phi must be periodic with an even cell count in 3-D
+  for (int k = 0; k < 3; ++k)
+    for (int s = 0; s < 2; ++s)
+      if (d->bc[k][s] == BHAC_BC_AXIS && k != 1) return false;
+  if ((d->bc[1][0] == BHAC_BC_AXIS || d->bc[1][1] == BHAC_BC_AXIS) && d->ndim == 3 &&
+      (d->bc[2][0] != BHAC_BC_PERIODIC || (d->nroot[2] * d->nx[2]) % 2))
+    return false;
+  for (int i = 0; i < nb; ++i) {
+    if (b[i].level != 0) return false;
+    const int c[3] = {b[i].ix, b[i].iy, b[i].iz};
+    for (int k = 0; k < 3; ++k)
+      if (c[k] < 0 || c[k] >= d->nroot[k]) return false;
+  }
+  // cell indices must fit the 32-bit ghost map
+  long long nc = 1;
+  for (int k = 0; k < 3; ++k) nc *= d->nx[k] + (k < d->ndim ? 6 : 0);
+  if (nc * nb >= (1LL << 31)) return false;
+  return true;
+}
+
+void geometry(const bhac_grid_desc* d, int g[3], int N[3], int& ncell, int& nint, int& nslots) {
+  ncell = 1;
+  nint = 1;
+  for (int k = 0; k < 3; ++k) {
+    g[k] = k < d->ndim ? d->nghost : 0;
+    N[k] = d->nx[k] + 2 * g[k];
+    ncell *= N[k];
+    nint *= d->nx[k];
+  }
+  nslots = ncell - nint;
+}
+
+Layout layout(const bhac_grid_desc* d, int nb) {
+  int g[3], N[3], ncell, nint, nslots;
+  geometry(d, g, N, ncell, nint, nslots);
+  const bool flat = d->coords == BHAC_COORDS_CART;
+  const bool mixed = d->precision == BHAC_PREC_MIXED;
+  const size_t N1 = (size_t)d->nroot[0] * d->nx[0], N2 = (size_t)d->nroot[1] * d->nx[1];
+  Layout L;
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    const size_t at = o;
+    o = align256(o + bytes);
+    return at;
+  };
+  L.off_blk = take(sizeof(int) * 4 * nb);
+  L.off_src = take(sizeof(int) * (size_t)nb * nslots);
+  L.off_flags = take((size_t)nb * nslots);
+  L.off_tmpl = take(sizeof(int) * (size_t)nslots);
+  const size_t nc = flat ? 0 : N1 * N2, nf1 = flat ? 0 : (N1 + 1) * N2, nf2 = flat ? 0 : N1 * (N2 + 1);
+  L.off_tc = take(sizeof(double) * CREC * nc);
+  L.off_tf1 = take(sizeof(double) * FREC * nf1);
+  L.off_tf2 = take(sizeof(double) * FREC * nf2);
+  L.off_tc32 = take(sizeof(float) * CREC * nc);
+  L.off_tf1_32 = take(sizeof(float) * FREC * nf1);
+  L.off_tf2_32 = take(sizeof(float) * FREC * nf2);
+  for (int s = 0; s < 2; ++s) L.off_P[s] = take(sizeof(double) * NV * (size_t)nb * ncell);
+  for (int s = 0; s < 2; ++s) L.off_P32[s] = take(mixed ? sizeof(float) * NV * (size_t)nb * ncell : 0);
+  for (int s = 0; s < 2; ++s) L.off_U[s] = take(sizeof(double) * NV * (size_t)nb * nint);
+  L.off_scratch = take(sizeof(double) * NV * (size_t)nb * nint);
+  L.off_small = take(256);
+  L.total = o;
+  return L;
+}
+
+// Maps a global index outside the root domain back inside it and records the
+// value fix-ups (bit 0: flip theta components; bits 1+2d / 2+2d: clamp u^d to
+// <= 0 / >= 0).  Returns false if the rule leaves the domain (not reached for
+// valid descriptors).
+bool apply_rules(const bhac_grid_desc* d, long long G[3], unsigned& flags) {
+  flags = 0;
+  long long Nd[3];
+  for (int k = 0; k < 3; ++k) Nd[k] = (long long)d->nroot[k] * d->nx[k];
+  for (int k = 0; k < d->ndim; ++k) {
+    for (int side = 0; side < 2; ++side) {
+      const bool out = side == 0 ? G[k] < 0 : G[k] >= Nd[k];
+      if (!out) continue;
+      const int kind = d->bc[k][side];
+      if (kind == BHAC_BC_PERIODIC) {
+        G[k] = ((G[k] % Nd[k]) + Nd[k]) % Nd[k];
+      } else if (kind == BHAC_BC_OUTFLOW || kind == BHAC_BC_NOINFLOW) {
+        G[k] = side == 0 ? 0 : Nd[k] - 1;
+        if (kind == BHAC_BC_NOINFLOW) flags |= 1u << (side == 0 ? 1 + 2 * k : 2 + 2 * k);
+      } else {  // polar axis: mirror, and in 3-D half a turn in phi
+        G[k] = side == 0 ? -1 - G[k] : 2 * Nd[k] - 1 - G[k];
+        flags ^= 1u;
+        if (d->ndim == 3) G[2] += Nd[2] / 2;
+      }
+    }
+  }
+  if (d->ndim == 3 && d->bc[2][0] == BHAC_BC_PERIODIC) G[2] = ((G[2] % Nd[2]) + Nd[2]) % Nd[2];
+  for (int k = 0; k < 3; ++k)
+    if (G[k] < 0 || G[k] >= Nd[k]) return false;
+  return true;
+}
+
+bhac_status cuda_status(cudaError_t e) { return e == cudaSuccess ? BHAC_OK : BHAC_ERR_CUDA; }
+
+}  // namespace
+
+StageArgs base_args(const bhac_ctx* c) {
+  StageArgs a;
+  memset(&a, 0, sizeof(a));
+  const bhac_grid_desc& d = c->d;
+  a.ndim = d.ndim;
+  a.nx = d.nx[0];
+  a.ny = d.nx[1];
+  a.nz = d.nx[2];
+  a.gx = c->g[0];
+  a.gy = c->g[1];
+  a.gz = c->g[2];
+  a.Nx = c->N[0];
+  a.Ny = c->N[1];
+  a.Nz = c->N[2];
+  a.ncell = c->ncell;
+  a.nint = c->nint;
+  a.tx = c->tx;
+  a.ty = c->ty;
+  a.ntx = d.nx[0] / c->tx;
+  a.nty = d.nx[1] / c->ty;
+  a.nblocks = c->nb;
+  a.nitems = c->nb * a.ntx * a.nty;
+  a.persistent = c->persistent;
+  a.blk = c->d_blk;
+  for (int k = 0; k < 3; ++k) {
+    a.dxl0[k] = (d.xmax[k] - d.xmin[k]) / ((double)d.nroot[k] * d.nx[k]);
+    a.idx[k] = 1.0 / a.dxl0[k];
+  }
+  a.N1g = c->N1g;
+  a.N2g = c->N2g;
+  a.axis_lo1 = d.bc[1][0] == BHAC_BC_AXIS;
+  a.axis_hi1 = d.bc[1][1] == BHAC_BC_AXIS;
+  a.flat = c->flat;
+  a.recon = d.recon;
+  a.riemann = d.riemann;
+  a.gam = d.gamma_ad;
+  a.gam_fac = d.gamma_ad / (d.gamma_ad - 1.0);
+  a.ch = d.ch;
+  a.kappa = d.kappa;
+  a.cfl = d.cfl;
+  a.c2p_tol = d.c2p_tol;
+  a.c2p_maxit = d.c2p_maxit;
+  a.wmax = d.w_max;
+  a.rho_fl_c = d.rho_floor;
+  a.p_fl_c = d.p_floor;
+  a.tab_c = c->tab_c;
+  a.tab_f1 = c->tab_f1;
+  a.tab_f2 = c->tab_f2;
+  a.tab_c32 = c->tab_c32;
+  a.tab_f1_32 = c->tab_f1_32;
+  a.tab_f2_32 = c->tab_f2_32;
+  a.dt_dev = c->dt_dev;
+  a.smax_in = c->smax;
+  a.smax_out = c->smax;
+  a.counts = c->counts;
+  a.work = c->work;
+  return a;
+}
+
+bhac_status ghost_fill(bhac_ctx* c, int buf, bool zero_smax) {
+  GhostArgs g;
+  g.src = c->d_src;
+  g.flags = c->d_flags;
+  g.tmpl = c->d_tmpl;
+  g.nslots = c->nslots;
+  g.nblocks = c->nb;
+  g.ncell = c->ncell;
+  g.P = c->mixed ? nullptr : c->P[buf];
+  g.P32 = c->mixed ? c->P32[buf] : nullptr;
+  g.work_reset = c->work;
+  g.smax_reset = zero_smax ? c->smax : nullptr;
+  return cuda_status(launch_ghost_fill(g, c->st));
+}
+
+namespace {
+
+bhac_status run_stage(bhac_ctx* c, int stage, double dt) {
+  StageArgs a = base_args(c);
+  const int in = c->cur, out = 1 - c->cur;
+  a.stage = stage;
+  a.dt_host = dt;
+  a.P_in = c->P[in];
+  a.P_out = c->P[out];
+  a.P32_in = c->P32[in];
+  a.P32_out = c->P32[out];
+  if (stage == 1) {
+    a.Un = c->U[c->ucur];
+    a.U1 = nullptr;
+    a.Uout = c->U[1 - c->ucur];
+  } else {
+    a.Un = c->U[1 - c->ucur];  // conserved at the start of the step
+    a.U1 = c->U[c->ucur];      // after stage 1
+    a.Uout = c->U[1 - c->ucur];
+  }
+  const size_t tsz = c->mixed ? sizeof(float) : sizeof(double);
+  const size_t sFx = (size_t)c->ty * (c->tx + 1), sFy = (size_t)(c->ty + 1) * c->tx, sFz = (size_t)c->tx * c->ty;
+  size_t smem = NV * (sFx + sFy) * tsz;
+  if (c->d.ndim == 3) smem += 2 * NV * sFz * tsz;
+  int grid = a.nitems;
+  if (c->persistent) {
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    grid = nsm * c->persistent;
+  }
+  cudaError_t e = c->mixed ? launch_stage_mixed(a, grid, c->threads, smem, c->st)
+                           : launch_stage_fp64(a, grid, c->threads, smem, c->st);
+  if (e != cudaSuccess) return BHAC_ERR_CUDA;
+  c->cur = out;
+  c->ucur = 1 - c->ucur;
+  return BHAC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* bhac_status_string(bhac_status s) {
+  switch (s) {
+    case BHAC_OK: return "ok";
+    case BHAC_ERR_ARG: return "invalid argument";
+    case BHAC_ERR_CUDA: return "CUDA error";
+    case BHAC_ERR_NOMEM: return "arena too small";
+    case BHAC_ERR_STATE: return "call out of order";
+    case BHAC_ERR_TIMEOUT: return "device wait timed out";
+    case BHAC_WARN_C2P: return "inversion failures";
+  }
+  return "unknown status";
+}
+
+bhac_status bhac_query_sizes(const bhac_grid_desc* d, const bhac_block_desc* b, int nb, size_t* out) {
+  if (!out || !valid_desc(d, b, nb)) return BHAC_ERR_ARG;
+  *out = layout(d, nb).total;
+  return BHAC_OK;
+}
+
+bhac_status bhac_init_grid(bhac_ctx** out, const bhac_grid_desc* d, const bhac_block_desc* b, int nb,
+                           void* arena, size_t arena_bytes, void* stream) {
+  if (!out || !valid_desc(d, b, nb) || !arena || ((uintptr_t)arena & 255)) return BHAC_ERR_ARG;
+  const Layout L = layout(d, nb);
+  if (arena_bytes < L.total) return BHAC_ERR_NOMEM;
+  bhac_ctx* c = new bhac_ctx();
+  c->d = *d;
+  c->nb = nb;
+  c->st = (cudaStream_t)stream;
+  geometry(d, c->g, c->N, c->ncell, c->nint, c->nslots);
+  c->N1g = d->nroot[0] * d->nx[0];
+  c->N2g = d->nroot[1] * d->nx[1];
+  c->flat = d->coords == BHAC_COORDS_CART;
+  c->mixed = d->precision == BHAC_PREC_MIXED;
+  c->arena = (char*)arena;
+  c->arena_bytes = arena_bytes;
+  c->d_blk = (int*)(c->arena + L.off_blk);
+  c->d_src = (int*)(c->arena + L.off_src);
+  c->d_flags = (unsigned char*)(c->arena + L.off_flags);
+  c->d_tmpl = (int*)(c->arena + L.off_tmpl);
+  c->tab_c = (double*)(c->arena + L.off_tc);
+  c->tab_f1 = (double*)(c->arena + L.off_tf1);
+  c->tab_f2 = (double*)(c->arena + L.off_tf2);
+  c->tab_c32 = (float*)(c->arena + L.off_tc32);
+  c->tab_f1_32 = (float*)(c->arena + L.off_tf1_32);
+  c->tab_f2_32 = (float*)(c->arena + L.off_tf2_32);
+  for (int s = 0; s < 2; ++s) {
+    c->P[s] = (double*)(c->arena + L.off_P[s]);
+    c->P32[s] = c->mixed ? (float*)(c->arena + L.off_P32[s]) : nullptr;
+    c->U[s] = (double*)(c->arena + L.off_U[s]);
+  }
+  c->scratch = (double*)(c->arena + L.off_scratch);
+  char* small = c->arena + L.off_small;
+  c->dt_dev = (double*)small;
+  c->smax = (unsigned long long*)(small + 8);
+  c->counts = (unsigned long long*)(small + 16);
+  c->work = (unsigned int*)(small + 48);
+  c->cur = 0;
+  c->ucur = 0;
+  // default launch shape: 16 x 16 columns where they divide the block
+  c->tx = d->nx[0] % 16 == 0 ? 16 : d->nx[0];
+  c->ty = d->nx[1] % 16 == 0 ? 16 : d->nx[1];
+  c->threads = 256;
+  c->persistent = 0;
+  c->graph = nullptr;
+  c->graph_steps = 0;
+
+  // block table and ghost maps
+  c->blk.resize(4 * nb);
+  std::vector<int> lut((size_t)d->nroot[0] * d->nroot[1] * d->nroot[2], -1);
+  for (int i = 0; i < nb; ++i) {
+    c->blk[4 * i] = b[i].level;
+    c->blk[4 * i + 1] = b[i].ix;
+    c->blk[4 * i + 2] = b[i].iy;
+    c->blk[4 * i + 3] = b[i].iz;
+    lut[((size_t)b[i].iz * d->nroot[1] + b[i].iy) * d->nroot[0] + b[i].ix] = i;
+  }
+  std::vector<int> tmpl;
+  tmpl.reserve(c->nslots);
+  for (int k = 0; k < c->N[2]; ++k)
+    for (int j = 0; j < c->N[1]; ++j)
+      for (int i = 0; i < c->N[0]; ++i) {
+        const bool in = i >= c->g[0] && i < c->g[0] + d->nx[0] && j >= c->g[1] && j < c->g[1] + d->nx[1] &&
+                        k >= c->g[2] && k < c->g[2] + d->nx[2];
+        if (!in) tmpl.push_back((k * c->N[1] + j) * c->N[0] + i);
+      }
+  std::vector<int> src((size_t)nb * c->nslots);
+  std::vector<unsigned char> flg((size_t)nb * c->nslots);
+  bool ok = true;
+  for (int bi = 0; bi < nb && ok; ++bi) {
+    for (int s = 0; s < c->nslots; ++s) {
+      const int cell = tmpl[s];
+      const int loc[3] = {cell % c->N[0] - c->g[0], (cell / c->N[0]) % c->N[1] - c->g[1],
+                          cell / (c->N[0] * c->N[1]) - c->g[2]};
+      long long G[3];
+      for (int k = 0; k < 3; ++k) G[k] = (long long)c->blk[4 * bi + 1 + k] * d->nx[k] + loc[k];
+      unsigned f = 0;
+      if (!apply_rules(d, G, f)) {
+        ok = false;
+        break;
+      }
+      const int sb = lut[((size_t)(G[2] / d->nx[2]) * d->nroot[1] + G[1] / d->nx[1]) * d->nroot[0] + G[0] / d->nx[0]];
+      if (sb < 0) {
+        ok = false;
+        break;
+      }
+      const int li = (int)(G[0] % d->nx[0]) + c->g[0], lj = (int)(G[1] % d->nx[1]) + c->g[1],
+                lk = (int)(G[2] % d->nx[2]) + c->g[2];
+      src[(size_t)bi * c->nslots + s] = sb * c->ncell + (lk * c->N[1] + lj) * c->N[0] + li;
+      flg[(size_t)bi * c->nslots + s] = (unsigned char)f;
+    }
+  }
+  if (!ok) {
+    delete c;
+    return BHAC_ERR_ARG;  // a boundary rule points at a missing block
+  }
+  cudaError_t e = cudaMemcpyAsync(c->d_blk, c->blk.data(), sizeof(int) * 4 * nb, cudaMemcpyHostToDevice, c->st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->d_src, src.data(), sizeof(int) * src.size(), cudaMemcpyHostToDevice, c->st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_flags, flg.data(), flg.size(), cudaMemcpyHostToDevice, c->st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->d_tmpl, tmpl.data(), sizeof(int) * tmpl.size(), cudaMemcpyHostToDevice, c->st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(small, 0, 256, c->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);  // host vectors die here
+  if (e != cudaSuccess) {
+    delete c;
+    return BHAC_ERR_CUDA;
+  }
+  c->metric_ok = c->flat;
+  *out = c;
+  return BHAC_OK;
+}
+
+bhac_status bhac_set_metric(bhac_ctx* c, int kind, double spin, double mass, const double* mks_params) {
+  (void)mks_params;
+  if (!c) return BHAC_ERR_ARG;
+  if (kind == BHAC_COORDS_CART) {
+    if (!c->flat) return BHAC_ERR_ARG;
+    c->metric_ok = true;
+    return BHAC_OK;
+  }
+  if (c->flat || kind != c->d.coords) return BHAC_ERR_ARG;
+  c->d.spin = spin;
+  c->d.mass = mass;
+  MetricArgs M;
+  M.coords = kind;
+  M.spin = spin;
+  M.mass = mass;
+  M.x1min = c->d.xmin[0];
+  M.x2min = c->d.xmin[1];
+  M.dx1 = (c->d.xmax[0] - c->d.xmin[0]) / c->N1g;
+  M.dx2 = (c->d.xmax[1] - c->d.xmin[1]) / c->N2g;
+  M.N1 = c->N1g;
+  M.N2 = c->N2g;
+  M.axis_lo = c->d.bc[1][0] == BHAC_BC_AXIS;
+  M.axis_hi = c->d.bc[1][1] == BHAC_BC_AXIS;
+  M.rho_floor = c->d.rho_floor;
+  M.rho_pow = c->d.rho_floor_pow;
+  M.p_floor = c->d.p_floor;
+  M.p_pow = c->d.p_floor_pow;
+  M.tab_c = c->tab_c;
+  M.tab_f1 = c->tab_f1;
+  M.tab_f2 = c->tab_f2;
+  M.tab_c32 = c->tab_c32;
+  M.tab_f1_32 = c->tab_f1_32;
+  M.tab_f2_32 = c->tab_f2_32;
+  bhac_status s = cuda_status(launch_metric_tables(M, c->st));
+  if (s == BHAC_OK) c->metric_ok = true;
+  return s;
+}
+
+bhac_status bhac_set_prims(bhac_ctx* c, const double* prims, int on_device) {
+  if (!c || !prims) return BHAC_ERR_ARG;
+  if (!c->metric_ok) return BHAC_ERR_STATE;
+  const size_t bytes = sizeof(double) * NV * (size_t)c->nb * c->nint;
+  const double* src = prims;
+  if (!on_device) {
+    if (cudaMemcpyAsync(c->scratch, prims, bytes, cudaMemcpyHostToDevice, c->st) != cudaSuccess)
+      return BHAC_ERR_CUDA;
+    src = c->scratch;
+  }
+  c->cur = 0;
+  c->ucur = 0;
+  StageArgs a = base_args(c);
+  cudaError_t e = launch_scatter_prims(a, src, c->P[0], c->P32[0], c->st);
+  if (e == cudaSuccess) e = launch_init_cons(a, c->P[0], c->U[0], c->st);
+  if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(c->st);
+  if (e != cudaSuccess) return BHAC_ERR_CUDA;
+  c->prims_ok = true;
+  c->cfl_ok = false;
+  return BHAC_OK;
+}
+
+bhac_status bhac_fill_ghosts(bhac_ctx* c) {
+  if (!c) return BHAC_ERR_ARG;
+  if (!c->prims_ok) return BHAC_ERR_STATE;
+  return ghost_fill(c, c->cur, false);
+}
+
+bhac_status bhac_cfl_dt(bhac_ctx* c, double* dt_host) {
+  if (!c) return BHAC_ERR_ARG;
+  if (!c->prims_ok) return BHAC_ERR_STATE;
+  if (cudaMemsetAsync(c->smax, 0, sizeof(unsigned long long), c->st) != cudaSuccess) return BHAC_ERR_CUDA;
+  StageArgs a = base_args(c);
+  a.P_in = c->P[c->cur];
+  if (launch_cfl(a, c->st) != cudaSuccess) return BHAC_ERR_CUDA;
+  c->cfl_ok = true;
+  if (dt_host) {
+    unsigned long long bits = 0;
+    if (cudaMemcpyAsync(&bits, c->smax, sizeof(bits), cudaMemcpyDeviceToHost, c->st) != cudaSuccess ||
+        cudaStreamSynchronize(c->st) != cudaSuccess)
+      return BHAC_ERR_CUDA;
+    double smax;
+    memcpy(&smax, &bits, sizeof(smax));
+    *dt_host = c->d.cfl / smax;
+  }
+  return BHAC_OK;
+}
+
+bhac_status bhac_stage(bhac_ctx* c, int stage, double dt) {
+  if (!c || (stage != 1 && stage != 2)) return BHAC_ERR_ARG;
+  if (!c->prims_ok) return BHAC_ERR_STATE;
+  if (stage == 1 && !(dt > 0.0) && !c->cfl_ok) return BHAC_ERR_STATE;
+  bhac_status s = ghost_fill(c, c->cur, stage == 2);
+  if (s != BHAC_OK) return s;
+  s = run_stage(c, stage, dt);
+  if (s == BHAC_OK && stage == 2) c->cfl_ok = true;
+  return s;
+}
+
+bhac_status bhac_step(bhac_ctx* c, double dt) {
+  bhac_status s = bhac_stage(c, 1, dt);
+  if (s != BHAC_OK) return s;
+  return bhac_stage(c, 2, dt);
+}
+
+static bhac_status copy_out(bhac_ctx* c, const double* dev_src, double* out, int on_device) {
+  const size_t bytes = sizeof(double) * NV * (size_t)c->nb * c->nint;
+  cudaError_t e = cudaMemcpyAsync(out, dev_src, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                  c->st);
+  if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(c->st);
+  return cuda_status(e);
+}
+
+bhac_status bhac_get_prims(bhac_ctx* c, double* out, int on_device) {
+  if (!c || !out) return BHAC_ERR_ARG;
+  if (!c->prims_ok) return BHAC_ERR_STATE;
+  StageArgs a = base_args(c);
+  if (on_device) return cuda_status(launch_gather_interior(a, c->P[c->cur], out, c->st));
+  if (launch_gather_interior(a, c->P[c->cur], c->scratch, c->st) != cudaSuccess) return BHAC_ERR_CUDA;
+  return copy_out(c, c->scratch, out, 0);
+}
+
+bhac_status bhac_get_cons(bhac_ctx* c, double* out, int on_device) {
+  if (!c || !out) return BHAC_ERR_ARG;
+  if (!c->prims_ok) return BHAC_ERR_STATE;
+  return copy_out(c, c->U[c->ucur], out, on_device);
+}
+
+bhac_status bhac_get_diagnostics(bhac_ctx* c, long long counts[4]) {
+  if (!c || !counts) return BHAC_ERR_ARG;
+  unsigned long long h[4];
+  if (cudaMemcpyAsync(h, c->counts, sizeof(h), cudaMemcpyDeviceToHost, c->st) != cudaSuccess ||
+      cudaStreamSynchronize(c->st) != cudaSuccess)
+    return BHAC_ERR_CUDA;
+  for (int i = 0; i < 4; ++i) counts[i] = (long long)h[i];
+  return h[3] ? BHAC_WARN_C2P : BHAC_OK;
+}
+
+bhac_status bhac_set_launch(bhac_ctx* c, int tx, int ty, int threads, int persistent) {
+  if (!c) return BHAC_ERR_ARG;
+  const int ntx = tx > 0 ? tx : c->tx, nty = ty > 0 ? ty : c->ty, nth = threads > 0 ? threads : c->threads;
+  if (c->d.nx[0] % ntx || c->d.nx[1] % nty || nth % 32 || nth > 256 || persistent < 0 || persistent > 8)
+    return BHAC_ERR_ARG;
+  const size_t tsz = c->mixed ? sizeof(float) : sizeof(double);
+  size_t smem = NV * ((size_t)nty * (ntx + 1) + (size_t)(nty + 1) * ntx) * tsz;
+  if (c->d.ndim == 3) smem += 2 * NV * (size_t)ntx * nty * tsz;
+  if (smem > 200 * 1024) return BHAC_ERR_ARG;
+  c->tx = ntx;
+  c->ty = nty;
+  c->threads = nth;
+  c->persistent = persistent;
+  return BHAC_OK;
+}
+
+bhac_status bhac_graph_capture(bhac_ctx* c, int nsteps) {
+  if (!c || nsteps < 1) return BHAC_ERR_ARG;
+  if (!c->prims_ok || !c->cfl_ok) return BHAC_ERR_STATE;
+  if (c->graph) {
+    cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+  }
+  if ((c->mixed ? prepare_stage_mixed() : prepare_stage_fp64()) != cudaSuccess) return BHAC_ERR_CUDA;
+  if (cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return BHAC_ERR_CUDA;
+  const int cur = c->cur, ucur = c->ucur;
+  bhac_status s = BHAC_OK;
+  for (int k = 0; k < nsteps && s == BHAC_OK; ++k) s = bhac_step(c, 0.0);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(c->st, &g);
+  c->cur = cur;  // buffer roles return to the same state after every step
+  c->ucur = ucur;
+  if (s != BHAC_OK || e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return s != BHAC_OK ? s : BHAC_ERR_CUDA;
+  }
+  e = cudaGraphInstantiate(&c->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    c->graph = nullptr;
+    return BHAC_ERR_CUDA;
+  }
+  c->graph_steps = nsteps;
+  return BHAC_OK;
+}
+
+bhac_status bhac_graph_launch(bhac_ctx* c) {
+  if (!c) return BHAC_ERR_ARG;
+  if (!c->graph) return BHAC_ERR_STATE;
+  return cuda_status(cudaGraphLaunch(c->graph, c->st));
+}
+
+void bhac_destroy(bhac_ctx* c) {
+  if (!c) return;
+  if (c->graph) cudaGraphExecDestroy(c->graph);
+  delete c;
+}
+
+}  // extern "C"

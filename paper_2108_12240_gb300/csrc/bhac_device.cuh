@@ -1,0 +1,280 @@
+// Device-side data layout and point-wise GRMHD for the GB300 stage kernels.
+//
+// Equations: ideal GRMHD in 3+1 ("Valencia") conservative form with GLM
+// divergence cleaning, the covariant finite-volume scheme of the paper's
+// Sec. 2.  The spatial metric is restricted to the Kerr-Schild structure
+// (gamma_12 = gamma_23 = 0, beta = (beta^1, 0, 0), phi-independent), which
+// covers Minkowski Cartesian, Kerr-Schild and modified Kerr-Schild exactly and
+// lets every contraction skip its structural zeros.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define BHAC_HD __host__ __device__ __forceinline__
+
+namespace bhac {
+
+constexpr int NV = 9;
+// primitive slots
+constexpr int RHO = 0, PRS = 1, U1 = 2, U2 = 3, U3 = 4, B1 = 5, B2 = 6, B3 = 7, PSI = 8;
+// conserved slots
+constexpr int CD = 0, CS1 = 1, CS2 = 2, CS3 = 3, CTAU = 4;
+
+// Metric tables: cell-centre records (CREC doubles) and face records (FREC).
+constexpr int CREC = 32, FREC = 12;
+enum CRec {
+  C_AL = 0, C_BE1, C_G11, C_G13, C_G22, C_G33, C_GI11, C_GI13, C_GI22, C_GI33, C_SG, C_ISG,
+  C_ACG1, C_ACG2, C_ACG3, C_RHOFL, C_PFL,
+  C_DAL1, C_DAL2, C_DBE1_1, C_DBE1_2, C_DG11_1, C_DG11_2, C_DG13_1, C_DG13_2, C_DG22_1, C_DG22_2,
+  C_DG33_1, C_DG33_2
+};
+enum FRec { F_AL = 0, F_BE1, F_G11, F_G13, F_G22, F_G33, F_GI11, F_GI13, F_GI22, F_GI33, F_SG, F_ACG };
+
+// Everything a stage kernel needs, passed by value.
+struct StageArgs {
+  int ndim;
+  int nx, ny, nz;        // interior cells per block
+  int gx, gy, gz;        // ghosts per side
+  int Nx, Ny, Nz;        // ghosted extents
+  int ncell, nint;       // ghosted / interior cells per block
+  int tx, ty, ntx, nty;  // CTA column tile and tiles per block
+  int nblocks, nitems;
+  int persistent;
+  const int* blk;        // nblocks x 4: level, bx, by, bz
+  double idx[3];         // 1/dx at level 0 per dimension
+  double dxl0[3];        // dx at level 0
+  int N1g, N2g;          // level-0 global cells along x1 and x2 (table extents)
+  int axis_lo1, axis_hi1;  // polar axis at the low/high x2 boundary
+  int flat;
+  int recon, riemann;
+  double gam, gam_fac, ch, kappa, cfl;
+  double c2p_tol;
+  int c2p_maxit;
+  double wmax, rho_fl_c, p_fl_c;  // constant floors (flat coordinates)
+  // state
+  const double* P_in;    // FP64 primitives, ghosted
+  double* P_out;
+  const float* P32_in;   // FP32 primitives, ghosted (mixed precision)
+  float* P32_out;
+  const double* Un;      // conserved at the start of the step
+  const double* U1;      // conserved after stage 1
+  double* Uout;
+  const double* tab_c;   // cell-centre metric records, N2g x N1g
+  const double* tab_f1;  // x1-face records, N2g x (N1g+1)
+  const double* tab_f2;  // x2-face records, (N2g+1) x N1g
+  const float* tab_c32;
+  const float* tab_f1_32;
+  const float* tab_f2_32;
+  int stage;
+  double dt_host;        // > 0: use it; else cfl / smax
+  double* dt_dev;
+  unsigned long long* smax_in;   // bits of the max CFL rate read by stage 1
+  unsigned long long* smax_out;  // accumulated by stage 2 (and the CFL kernel)
+  unsigned long long* counts;    // 4 inversion outcome counters
+  unsigned int* work;            // persistent work counter
+};
+
+template <typename T>
+struct Met {
+  T al, be1, g11, g13, g22, g33, gi11, gi13, gi22, gi33, sg;
+};
+
+template <typename T>
+BHAC_HD Met<T> flat_metric() {
+  Met<T> m;
+  m.al = T(1); m.be1 = T(0);
+  m.g11 = T(1); m.g13 = T(0); m.g22 = T(1); m.g33 = T(1);
+  m.gi11 = T(1); m.gi13 = T(0); m.gi22 = T(1); m.gi33 = T(1);
+  m.sg = T(1);
+  return m;
+}
+
+template <typename T, typename R>
+BHAC_HD Met<T> load_face_metric(const R* __restrict__ rec) {
+  Met<T> m;
+  m.al = T(rec[F_AL]); m.be1 = T(rec[F_BE1]);
+  m.g11 = T(rec[F_G11]); m.g13 = T(rec[F_G13]); m.g22 = T(rec[F_G22]); m.g33 = T(rec[F_G33]);
+  m.gi11 = T(rec[F_GI11]); m.gi13 = T(rec[F_GI13]); m.gi22 = T(rec[F_GI22]); m.gi33 = T(rec[F_GI33]);
+  m.sg = T(rec[F_SG]);
+  return m;
+}
+
+template <typename T, typename R>
+BHAC_HD Met<T> load_centre_metric(const R* __restrict__ rec) {
+  Met<T> m;
+  m.al = T(rec[C_AL]); m.be1 = T(rec[C_BE1]);
+  m.g11 = T(rec[C_G11]); m.g13 = T(rec[C_G13]); m.g22 = T(rec[C_G22]); m.g33 = T(rec[C_G33]);
+  m.gi11 = T(rec[C_GI11]); m.gi13 = T(rec[C_GI13]); m.gi22 = T(rec[C_GI22]); m.gi33 = T(rec[C_GI33]);
+  m.sg = T(rec[C_SG]);
+  return m;
+}
+
+// Scalar helpers.  The double/float overloads are the device arithmetic; the
+// flop counter provides overloads for its counting type.
+__device__ __forceinline__ double rsqrt_t(double x) { return rsqrt(x); }
+__device__ __forceinline__ float rsqrt_t(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double sqrt_t(double x) { return sqrt(x); }
+__device__ __forceinline__ float sqrt_t(float x) { return sqrtf(x); }
+__device__ __forceinline__ double rcp_t(double x) { return 1.0 / x; }
+__device__ __forceinline__ float rcp_t(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double abs_t(double x) { return fabs(x); }
+__device__ __forceinline__ float abs_t(float x) { return fabsf(x); }
+__device__ __forceinline__ bool finite_t(double x) { return isfinite(x); }
+__device__ __forceinline__ double to_double(double x) { return x; }
+__device__ __forceinline__ double to_double(float x) { return (double)x; }
+
+template <typename T>
+BHAC_HD T sel3(int d, T a, T b, T c) {
+  return d == 0 ? a : (d == 1 ? b : c);
+}
+
+// Derived quantities of a primitive state under a metric.
+template <typename T>
+struct Derived {
+  T ul1, ul2, ul3, Bl1, Bl2, Bl3;
+  T iW, W, iW2, v1, v2, v3, vl1, vl2, vl3, vsq;
+  T Bsq, Bv, b2, rhoh, ptot;
+};
+
+template <typename T>
+BHAC_HD void derive(const Met<T>& m, const T* P, T gam_fac, Derived<T>& s) {
+  const T u1 = P[U1], u2 = P[U2], u3 = P[U3], B1_ = P[B1], B2_ = P[B2], B3_ = P[B3];
+  s.ul1 = m.g11 * u1 + m.g13 * u3;
+  s.ul2 = m.g22 * u2;
+  s.ul3 = m.g13 * u1 + m.g33 * u3;
+  s.Bl1 = m.g11 * B1_ + m.g13 * B3_;
+  s.Bl2 = m.g22 * B2_;
+  s.Bl3 = m.g13 * B1_ + m.g33 * B3_;
+  const T usq = u1 * s.ul1 + u2 * s.ul2 + u3 * s.ul3;
+  const T W2 = T(1) + usq;
+  s.iW = rsqrt_t(W2);
+  s.W = W2 * s.iW;
+  s.iW2 = s.iW * s.iW;
+  s.v1 = u1 * s.iW; s.v2 = u2 * s.iW; s.v3 = u3 * s.iW;
+  s.vl1 = s.ul1 * s.iW; s.vl2 = s.ul2 * s.iW; s.vl3 = s.ul3 * s.iW;
+  s.vsq = usq * s.iW2;
+  s.Bsq = B1_ * s.Bl1 + B2_ * s.Bl2 + B3_ * s.Bl3;
+  s.Bv = B1_ * s.vl1 + B2_ * s.vl2 + B3_ * s.vl3;
+  s.b2 = s.Bsq * s.iW2 + s.Bv * s.Bv;
+  s.rhoh = P[RHO] + gam_fac * P[PRS];
+  s.ptot = P[PRS] + T(0.5) * s.b2;
+}
+
+// D = rho W, S_j = (rho h W^2 + B^2) v_j - (B.v) B_j, tau = rho h W^2 - p + B^2 - b^2/2 - D.
+template <typename T>
+BHAC_HD void cons_of(const T* P, const Derived<T>& s, T* U) {
+  const T Z = s.rhoh * s.W * s.W;
+  U[CD] = P[RHO] * s.W;
+  const T ZB = Z + s.Bsq;
+  U[CS1] = ZB * s.vl1 - s.Bv * s.Bl1;
+  U[CS2] = ZB * s.vl2 - s.Bv * s.Bl2;
+  U[CS3] = ZB * s.vl3 - s.Bv * s.Bl3;
+  U[CTAU] = Z - P[PRS] + s.Bsq - T(0.5) * s.b2 - U[CD];
+  U[B1] = P[B1]; U[B2] = P[B2]; U[B3] = P[B3];
+  U[PSI] = P[PSI];
+}
+
+// Fluxes along d (undensitized):
+//   F(D) = D (alpha v^d - beta^d), F(S_j) = alpha W^d_j - beta^d S_j,
+//   W^d_j = S_j v^d + p_tot delta^d_j - B^d B_j / W^2 - (B.v) B^d v_j,
+//   F(tau) = alpha (S^d - D v^d) - beta^d tau,
+//   F(B^j) = (alpha v^d - beta^d) B^j - (alpha v^j - beta^j) B^d + alpha gamma^dj psi,
+//   F(psi) = alpha ch^2 B^d - beta^d psi.
+template <typename T>
+BHAC_HD void flux_of(const Met<T>& m, const T* P, const Derived<T>& s, const T* U, int d,
+                                        T ch2, T* F) {
+  const T vd = sel3(d, s.v1, s.v2, s.v3);
+  const T Bd = sel3(d, P[B1], P[B2], P[B3]);
+  const T bed = d == 0 ? m.be1 : T(0);
+  const T gid1 = sel3(d, m.gi11, T(0), m.gi13);
+  const T gid2 = d == 1 ? m.gi22 : T(0);
+  const T gid3 = sel3(d, m.gi13, T(0), m.gi33);
+  const T al = m.al;
+  F[CD] = U[CD] * (al * vd - bed);
+  const T BdiW2 = Bd * s.iW2, BvBd = s.Bv * Bd;
+  F[CS1] = al * (U[CS1] * vd - BdiW2 * s.Bl1 - BvBd * s.vl1 + (d == 0 ? s.ptot : T(0))) - bed * U[CS1];
+  F[CS2] = al * (U[CS2] * vd - BdiW2 * s.Bl2 - BvBd * s.vl2 + (d == 1 ? s.ptot : T(0))) - bed * U[CS2];
+  F[CS3] = al * (U[CS3] * vd - BdiW2 * s.Bl3 - BvBd * s.vl3 + (d == 2 ? s.ptot : T(0))) - bed * U[CS3];
+  const T Sd = gid1 * U[CS1] + gid2 * U[CS2] + gid3 * U[CS3];
+  F[CTAU] = al * (Sd - U[CD] * vd) - bed * U[CTAU];
+  const T Vd = al * vd - bed;
+  const T alpsi = al * P[PSI];
+  F[B1] = Vd * P[B1] - (al * s.v1 - m.be1) * Bd + alpsi * gid1;
+  F[B2] = Vd * P[B2] - (al * s.v2) * Bd + alpsi * gid2;
+  F[B3] = Vd * P[B3] - (al * s.v3) * Bd + alpsi * gid3;
+  F[PSI] = al * ch2 * Bd - bed * P[PSI];
+}
+
+// Fast-magnetosonic bound in the Eulerian frame (Del Zanna et al. 2007):
+// a^2 = cs^2 + ca^2 - cs^2 ca^2, boosted by v and shifted by beta.
+template <typename T>
+BHAC_HD void speeds_of(const Met<T>& m, const T* P, const Derived<T>& s, int d, T gam,
+                                          T& lm, T& lp) {
+  const T inv = rcp_t(s.rhoh * (s.rhoh + s.b2));
+  const T cs2 = gam * P[PRS] * (s.rhoh + s.b2) * inv;
+  const T ca2 = s.b2 * s.rhoh * inv;
+  const T a2 = cs2 + ca2 - cs2 * ca2;
+  const T vd = sel3(d, s.v1, s.v2, s.v3);
+  const T gidd = sel3(d, m.gi11, m.gi22, m.gi33);
+  T disc = a2 * (T(1) - s.vsq) * (gidd * (T(1) - s.vsq * a2) - vd * vd * (T(1) - a2));
+  disc = disc > T(0) ? disc : T(0);
+  const T sq = sqrt_t(disc);
+  const T iden = rcp_t(T(1) - s.vsq * a2);
+  const T bed = d == 0 ? m.be1 : T(0);
+  const T c = vd * (T(1) - a2);
+  lp = m.al * (c + sq) * iden - bed;
+  lm = m.al * (c - sq) * iden - bed;
+}
+
+// ----------------------------------------------------------------------------
+// Reconstruction (per variable).  PPM: Colella & Woodward 1984 interface value
+// 7/12 (a_k + a_k+1) - 1/12 (a_k-1 + a_k+2) clipped to [a_k, a_k+1], then the
+// CW84 monotonicity constraints per cell.  Minmod: limited linear slopes.
+// ----------------------------------------------------------------------------
+template <typename T>
+BHAC_HD T ppm_iface(T am1, T a0, T a1, T a2) {
+  T v = T(7.0 / 12.0) * (a0 + a1) - T(1.0 / 12.0) * (am1 + a2);
+  const T lo = a0 < a1 ? a0 : a1, hi = a0 < a1 ? a1 : a0;
+  v = v < lo ? lo : v;
+  v = v > hi ? hi : v;
+  return v;
+}
+
+template <typename T>
+BHAC_HD void ppm_limit(T a, T& aL, T& aR) {
+  if ((aR - a) * (a - aL) <= T(0)) {
+    aL = a;
+    aR = a;
+  } else {
+    const T d = aR - aL;
+    const T m6 = T(6) * (a - T(0.5) * (aL + aR));
+    if (d * m6 > d * d) aL = T(3) * a - T(2) * aR;
+    if (-d * d > d * m6) aR = T(3) * a - T(2) * aL;
+  }
+}
+
+template <typename T>
+BHAC_HD T minmod_t(T a, T b) {
+  if (a * b <= T(0)) return T(0);
+  return (a < T(0) ? -a : a) < (b < T(0) ? -b : b) ? a : b;
+}
+
+template <typename T>
+BHAC_HD void recon_var(int recon, T a0, T a1, T a2, T a3, T a4, T a5, T& L, T& R) {
+  if (recon == 0) {
+    T l2 = ppm_iface(a0, a1, a2, a3);
+    T r2 = ppm_iface(a1, a2, a3, a4);
+    T l3 = r2;
+    T r3 = ppm_iface(a2, a3, a4, a5);
+    ppm_limit(a2, l2, r2);
+    ppm_limit(a3, l3, r3);
+    L = r2;
+    R = l3;
+  } else {
+    L = a2 + T(0.5) * minmod_t(a2 - a1, a3 - a2);
+    R = a3 - T(0.5) * minmod_t(a3 - a2, a4 - a3);
+  }
+}
+
+}  // namespace bhac

@@ -1,0 +1,50 @@
+// The library context (host memory), shared by the translation units that
+// implement the C ABI.
+#pragma once
+
+#include <vector>
+
+#include "../../include/bhac_gb300.h"
+#include "launch.h"
+
+struct bhac_ctx {
+  // descriptor, blocks and stream
+  bhac_grid_desc d;
+  int nb;
+  std::vector<int> blk;  // nb x 4
+  cudaStream_t st;
+  // geometry
+  int g[3], N[3], ncell, nint, nslots;
+  int N1g, N2g;
+  bool flat, mixed;
+  // arena slices
+  char* arena;
+  size_t arena_bytes;
+  int* d_blk;
+  int* d_src;
+  unsigned char* d_flags;
+  int* d_tmpl;
+  double *tab_c, *tab_f1, *tab_f2;
+  float *tab_c32, *tab_f1_32, *tab_f2_32;
+  double* P[2];
+  float* P32[2];
+  double* U[2];
+  double* scratch;
+  double* dt_dev;
+  unsigned long long* smax;
+  unsigned long long* counts;
+  unsigned int* work;
+  // state
+  int cur;       // primitive buffer holding the current state
+  int ucur;      // conserved buffer holding the current state
+  bool metric_ok, prims_ok, cfl_ok;
+  // launch shape
+  int tx, ty, threads, persistent;
+  // captured steps
+  cudaGraphExec_t graph;
+  int graph_steps;
+};
+
+// Shared helpers of the ABI units (api.cu).
+bhac::StageArgs base_args(const bhac_ctx* c);
+bhac_status ghost_fill(bhac_ctx* c, int buf, bool zero_smax);

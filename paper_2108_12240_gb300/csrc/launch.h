@@ -1,0 +1,52 @@
+// Host-side launchers shared by the translation units of the library.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "bhac_device.cuh"
+
+namespace bhac {
+
+// stage kernels (stage_fp64.cu / stage_mixed.cu)
+cudaError_t launch_stage_fp64(const StageArgs& a, int grid, int threads, size_t smem, cudaStream_t st);
+cudaError_t launch_stage_mixed(const StageArgs& a, int grid, int threads, size_t smem, cudaStream_t st);
+cudaError_t launch_cfl(const StageArgs& a, cudaStream_t st);
+// set kernel attributes ahead of a stream capture
+cudaError_t prepare_stage_fp64();
+cudaError_t prepare_stage_mixed();
+
+// auxiliary kernels (aux.cu)
+struct GhostArgs {
+  const int* src;               // per (block, slot): source ghosted-cell index over all blocks
+  const unsigned char* flags;   // per (block, slot): bit0 flip theta, bits 1+2d / 2+2d clamp u^d <= 0 / >= 0
+  const int* tmpl;              // per slot: destination cell index inside a block
+  int nslots, nblocks, ncell;
+  double* P;                    // FP64 ghosted primitives (or null)
+  float* P32;                   // FP32 ghosted primitives (or null)
+  unsigned int* work_reset;     // zeroed by the first thread (persistent work counter)
+  unsigned long long* smax_reset;  // zeroed by the first thread when non-null
+};
+cudaError_t launch_ghost_fill(const GhostArgs& g, cudaStream_t st);
+
+struct MetricArgs {
+  int coords;                   // 1 KS, 2 MKS
+  double spin, mass;
+  double x1min, x2min, dx1, dx2;
+  int N1, N2;                   // cells along x1, x2
+  int axis_lo, axis_hi;         // polar axis at x2 = low / high boundary
+  double rho_floor, rho_pow, p_floor, p_pow;
+  double* tab_c;                // N2 x N1 x CREC
+  double* tab_f1;               // N2 x (N1+1) x FREC
+  double* tab_f2;               // (N2+1) x N1 x FREC
+  float* tab_c32;
+  float* tab_f1_32;
+  float* tab_f2_32;
+};
+cudaError_t launch_metric_tables(const MetricArgs& m, cudaStream_t st);
+
+// interior <-> ghosted copies and the initial conserved state
+cudaError_t launch_scatter_prims(const StageArgs& a, const double* src, double* P, float* P32, cudaStream_t st);
+cudaError_t launch_gather_interior(const StageArgs& a, const double* P, double* dst, cudaStream_t st);
+cudaError_t launch_init_cons(const StageArgs& a, const double* P, double* U, cudaStream_t st);
+
+}  // namespace bhac

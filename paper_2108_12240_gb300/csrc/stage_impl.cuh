@@ -1,0 +1,641 @@
+// The fused RK-stage kernel: reconstruction, HLL/TVDLF face fluxes, geometric
+// and GLM sources, the SSP-RK2 stage combination, the Newton conserved-to-
+// primitive inversion with its backup and floors, and (stage 2) the per-cell
+// CFL rate reduced into one device word.  Included by stage_fp64.cu and
+// stage_mixed.cu, which instantiate it for FP64 and FP32 flux arithmetic.
+//
+// Work decomposition: one CTA owns a column of tx x ty cells of one block and
+// marches through its nz planes.  Per plane it computes every x-, y- and (top)
+// z-face flux of the column once into shared memory, then updates each cell;
+// the z-face flux at the top of a plane is carried over as the bottom of the
+// next, so no interior face flux is ever evaluated twice.
+#pragma once
+
+#include "bhac_device.cuh"
+#include "launch.h"
+
+namespace bhac {
+
+__device__ __forceinline__ double warp_max_d(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// ----------------------------------------------------------------------------
+// Geometric + GLM sources for a stationary, phi-independent metric of
+// Kerr-Schild structure (derivatives along x1 and x2 only):
+//   S(S_j) = 1/2 alpha W^ik d_j gamma_ik + S_i d_j beta^i - E d_j alpha
+//   S(tau) = 1/2 W^ik beta^j d_j gamma_ik + W^j_i d_j beta^i - S^j d_j alpha
+//   S(psi) = -alpha kappa psi - psi d_i beta^i + ch^2 B^i d_i alpha
+// ----------------------------------------------------------------------------
+template <typename T, typename R>
+BHAC_HD void sources_of(const Met<T>& m, const R* __restrict__ rec, const T* P,
+                                           const Derived<T>& s, const T* U, T kappa, T ch2, T* S) {
+  const T dal1 = T(rec[C_DAL1]), dal2 = T(rec[C_DAL2]);
+  const T db11 = T(rec[C_DBE1_1]), db12 = T(rec[C_DBE1_2]);
+  const T Su1 = m.gi11 * U[CS1] + m.gi13 * U[CS3];
+  const T Su2 = m.gi22 * U[CS2];
+  const T Su3 = m.gi13 * U[CS1] + m.gi33 * U[CS3];
+  const T B1_ = P[B1], B2_ = P[B2], B3_ = P[B3];
+  const T BvB1 = s.Bv * B1_, BvB2 = s.Bv * B2_, BvB3 = s.Bv * B3_;
+  const T W11 = Su1 * s.v1 + s.ptot * m.gi11 - B1_ * B1_ * s.iW2 - BvB1 * s.v1;
+  const T W13 = Su3 * s.v1 + s.ptot * m.gi13 - B1_ * B3_ * s.iW2 - BvB1 * s.v3;
+  const T W22 = Su2 * s.v2 + s.ptot * m.gi22 - B2_ * B2_ * s.iW2 - BvB2 * s.v2;
+  const T W33 = Su3 * s.v3 + s.ptot * m.gi33 - B3_ * B3_ * s.iW2 - BvB3 * s.v3;
+  const T G1 = W11 * T(rec[C_DG11_1]) + T(2) * W13 * T(rec[C_DG13_1]) + W22 * T(rec[C_DG22_1]) +
+               W33 * T(rec[C_DG33_1]);
+  const T G2 = W11 * T(rec[C_DG11_2]) + T(2) * W13 * T(rec[C_DG13_2]) + W22 * T(rec[C_DG22_2]) +
+               W33 * T(rec[C_DG33_2]);
+  const T E = U[CTAU] + U[CD];
+  S[CD] = T(0);
+  S[CS1] = T(0.5) * m.al * G1 + U[CS1] * db11 - E * dal1;
+  S[CS2] = T(0.5) * m.al * G2 + U[CS1] * db12 - E * dal2;
+  S[CS3] = T(0);
+  const T Wm11 = U[CS1] * s.v1 + s.ptot - B1_ * s.Bl1 * s.iW2 - BvB1 * s.vl1;  // W^1_1
+  const T Wm21 = U[CS1] * s.v2 - B2_ * s.Bl1 * s.iW2 - BvB2 * s.vl1;           // W^2_1
+  S[CTAU] = T(0.5) * m.be1 * G1 + Wm11 * db11 + Wm21 * db12 - (Su1 * dal1 + Su2 * dal2);
+  S[B1] = T(0); S[B2] = T(0); S[B3] = T(0);
+  S[PSI] = -m.al * kappa * P[PSI] - P[PSI] * db11 + ch2 * (B1_ * dal1 + B2_ * dal2);
+}
+
+// ----------------------------------------------------------------------------
+// Conserved -> primitive inversion (FP64).  Two-dimensional Newton-Raphson in
+// (Z = rho h W^2, v^2) on the momentum and energy equations (Noble et al.
+// 2006), started from the previous primitives; converged when
+// |dZ| <= tol Z, then one polishing step.  Backup: bisection on Z of the
+// one-dimensional energy residual over a bracket grown from the guess.  Last
+// resort: previous primitives (status 3).  Then floors (status 2).
+// ----------------------------------------------------------------------------
+template <typename T>
+struct C2PQ {
+  T D, E, S2, Bsq, BS;
+};
+
+template <typename T>
+BHAC_HD T c2p_v2(const C2PQ<T>& q, T Z) {
+  const T iZ = T(1.0) / Z;
+  const T num = q.S2 + q.BS * q.BS * (T(2.0) * Z + q.Bsq) * iZ * iZ;
+  const T ZB = Z + q.Bsq;
+  return num / (ZB * ZB);
+}
+
+template <typename T>
+BHAC_HD T c2p_f1d(const C2PQ<T>& q, T gf, T v2max, T Z) {
+  T v2 = c2p_v2(q, Z);
+  v2 = v2 > v2max ? v2max : v2;
+  v2 = v2 < T(0.0) ? T(0.0) : v2;
+  const T pr = gf * (Z * (T(1.0) - v2) - q.D * sqrt_t(T(1.0) - v2));
+  return Z - pr + T(0.5) * q.Bsq * (T(1.0) + v2) - T(0.5) * q.BS * q.BS / (Z * Z) - q.E;
+}
+
+// U undensitized; Pg the previous primitives; writes P; returns the status.
+template <typename T>
+BHAC_HD int con2prim_t(const Met<T>& m, const T* U, const T* Pg, T rho_fl, T p_fl, double gam_d,
+                       double gam_fac, double wmax_d, double tol, int maxit, T* P) {
+  const T gam = T(gam_d), gf = (gam - T(1.0)) / gam;
+  const T wmax = T(wmax_d);
+  const T v2max = T(1.0) - T(1.0) / (wmax * wmax);
+  C2PQ<T> q;
+  q.D = U[CD];
+  q.E = U[CTAU] + U[CD];
+  const T Su1 = m.gi11 * U[CS1] + m.gi13 * U[CS3];
+  const T Su2 = m.gi22 * U[CS2];
+  const T Su3 = m.gi13 * U[CS1] + m.gi33 * U[CS3];
+  const T Bl1 = m.g11 * U[B1] + m.g13 * U[B3];
+  const T Bl2 = m.g22 * U[B2];
+  const T Bl3 = m.g13 * U[B1] + m.g33 * U[B3];
+  q.S2 = Su1 * U[CS1] + Su2 * U[CS2] + Su3 * U[CS3];
+  q.Bsq = U[B1] * Bl1 + U[B2] * Bl2 + U[B3] * Bl3;
+  q.BS = U[B1] * U[CS1] + U[B2] * U[CS2] + U[B3] * U[CS3];
+  bool fin = true;
+  for (int v = 0; v < NV; ++v) fin = fin && finite_t(U[v]);
+  int status = 0;
+  bool solved = false;
+  T Z = T(0.0), v2 = T(0.0);
+  if (fin && q.D > T(0.0) && q.E > T(0.0)) {
+    const T gu1 = m.g11 * Pg[U1] + m.g13 * Pg[U3];
+    const T gu2 = m.g22 * Pg[U2];
+    const T gu3 = m.g13 * Pg[U1] + m.g33 * Pg[U3];
+    const T usq = Pg[U1] * gu1 + Pg[U2] * gu2 + Pg[U3] * gu3;
+    const T Z0g = (Pg[RHO] + T(gam_fac) * Pg[PRS]) * (T(1.0) + usq);
+    const T Z0 = (Z0g > T(0.0) && finite_t(Z0g)) ? Z0g : q.E;
+    Z = Z0;
+    v2 = usq / (T(1.0) + usq);
+    const T BS2 = q.BS * q.BS;
+    bool polish = false;
+    for (int it = 0; it < maxit; ++it) {
+      const T omv = T(1.0) - v2;
+      const T isq = rsqrt_t(omv);
+      const T sq = omv * isq;
+      const T pr = gf * (Z * omv - q.D * sq);
+      const T iZ = T(1.0) / Z;
+      const T iZ2 = iZ * iZ;
+      const T ZB = Z + q.Bsq;
+      const T f1 = ZB * ZB * v2 - BS2 * (T(2.0) * Z + q.Bsq) * iZ2 - q.S2;
+      const T f2 = Z - pr + T(0.5) * q.Bsq * (T(1.0) + v2) - T(0.5) * BS2 * iZ2 - q.E;
+      const T j11 = T(2.0) * ZB * v2 + T(2.0) * BS2 * ZB * iZ2 * iZ;
+      const T j12 = ZB * ZB;
+      const T j21 = T(1.0) - gf * omv + BS2 * iZ2 * iZ;
+      const T j22 = -gf * (-Z + T(0.5) * q.D * isq) + T(0.5) * q.Bsq;
+      const T idet = T(1.0) / (j11 * j22 - j12 * j21);
+      const T dZ = (-f1 * j22 + f2 * j12) * idet;
+      const T dv2 = (-f2 * j11 + f1 * j21) * idet;
+      T Zn = Z + dZ, v2n = v2 + dv2;
+      if (!(Zn > T(0.0))) Zn = T(0.5) * Z;
+      if (v2n < T(0.0)) v2n = T(0.5) * v2;
+      if (v2n >= T(1.0)) v2n = T(0.5) * (v2 + T(1.0));
+      const bool conv = abs_t(Zn - Z) <= T(tol) * Zn;
+      Z = Zn;
+      v2 = v2n;
+      if (!finite_t(Z) || !finite_t(v2)) break;
+      if (polish) {
+        solved = true;
+        break;
+      }
+      if (conv) polish = true;
+    }
+    if (solved && !(v2 >= T(0.0) && v2 < T(1.0) && Z > T(0.0))) solved = false;
+    if (solved && !(q.D * sqrt_t(T(1.0) - v2) > T(0.0))) solved = false;
+    if (!solved) {
+      T lo = Z0, hi = Z0;
+      int k = 0;
+      while (c2p_f1d(q, gf, v2max, lo) > T(0.0) && k < 200) {
+        lo = lo * T(0.5);
+        ++k;
+      }
+      k = 0;
+      while (c2p_f1d(q, gf, v2max, hi) < T(0.0) && k < 200) {
+        hi = hi * T(2.0);
+        ++k;
+      }
+      if (c2p_f1d(q, gf, v2max, lo) <= T(0.0) && c2p_f1d(q, gf, v2max, hi) >= T(0.0)) {
+        for (int it = 0; it < 200 && hi - lo > T(4e-16) * hi; ++it) {
+          const T mid = T(0.5) * (lo + hi);
+          if (c2p_f1d(q, gf, v2max, mid) > T(0.0))
+            hi = mid;
+          else
+            lo = mid;
+        }
+        Z = T(0.5) * (lo + hi);
+        v2 = c2p_v2(q, Z);
+        v2 = v2 > v2max ? v2max : v2;
+        v2 = v2 < T(0.0) ? T(0.0) : v2;
+        if (finite_t(Z) && Z > T(0.0)) {
+          solved = true;
+          status = 1;
+        }
+      }
+    }
+  }
+  if (solved) {
+    const T sq = sqrt_t(T(1.0) - v2);
+    const T W = T(1.0) / sq;
+    P[RHO] = q.D * sq;
+    P[PRS] = gf * (Z * (T(1.0) - v2) - q.D * sq);
+    const T c = W / (Z + q.Bsq);
+    const T bz = q.BS / Z;
+    P[U1] = c * (Su1 + bz * U[B1]);
+    P[U2] = c * (Su2 + bz * U[B2]);
+    P[U3] = c * (Su3 + bz * U[B3]);
+  } else {
+    status = 3;
+    P[RHO] = Pg[RHO];
+    P[PRS] = Pg[PRS];
+    P[U1] = Pg[U1];
+    P[U2] = Pg[U2];
+    P[U3] = Pg[U3];
+  }
+  P[B1] = U[B1];
+  P[B2] = U[B2];
+  P[B3] = U[B3];
+  P[PSI] = U[PSI];
+  bool fl = false;
+  if (!(P[RHO] >= rho_fl)) {
+    P[RHO] = rho_fl;
+    fl = true;
+  }
+  if (!(P[PRS] >= p_fl)) {
+    P[PRS] = p_fl;
+    fl = true;
+  }
+  const T gu1 = m.g11 * P[U1] + m.g13 * P[U3];
+  const T gu2 = m.g22 * P[U2];
+  const T gu3 = m.g13 * P[U1] + m.g33 * P[U3];
+  const T usq = P[U1] * gu1 + P[U2] * gu2 + P[U3] * gu3;
+  if (T(1.0) + usq > wmax * wmax) {
+    const T sc = sqrt_t((wmax * wmax - T(1.0)) / usq);
+    P[U1] = P[U1] * sc;
+    P[U2] = P[U2] * sc;
+    P[U3] = P[U3] * sc;
+    fl = true;
+  }
+  if (status == 3) return 3;
+  return fl ? 2 : status;
+}
+
+static __device__ __noinline__ int con2prim(const Met<double>& m, const double* U, const double* Pg, double rho_fl,
+                                            double p_fl, const StageArgs& a, double* P) {
+  return con2prim_t<double>(m, U, Pg, rho_fl, p_fl, a.gam, a.gam_fac, a.wmax, a.c2p_tol, a.c2p_maxit, P);
+}
+
+// CFL rate of one cell: sum over active d of c_d / dx_d, where c_d is the
+// largest of |lambda+-| and ch alpha sqrt(gamma^dd) + |beta^d|.
+template <typename T, int DIM>
+BHAC_HD T cfl_rate_t(const Met<T>& m, const T* acg, const T* P, double gam, double gam_fac, double ch,
+                     const double* idx) {
+  Derived<T> s;
+  derive(m, P, T(gam_fac), s);
+  T rate = T(0.0);
+  for (int d = 0; d < DIM; ++d) {
+    T lm, lp;
+    speeds_of(m, P, s, d, T(gam), lm, lp);
+    const T alp = abs_t(lp), alm = abs_t(lm);
+    T c = alp > alm ? alp : alm;
+    const T cg = T(ch) * acg[d] + (d == 0 ? abs_t(m.be1) : T(0.0));
+    c = cg > c ? cg : c;
+    rate = rate + c * T(idx[d]);
+  }
+  return rate;
+}
+
+template <int DIM>
+__device__ __forceinline__ double cfl_rate(const Met<double>& m, const double* acg, const double* P,
+                                           const StageArgs& a) {
+  return cfl_rate_t<double, DIM>(m, acg, P, a.gam, a.gam_fac, a.ch, a.idx);
+}
+
+// ----------------------------------------------------------------------------
+// Riemann solve at one face: states PL, PR (already reconstructed), face
+// metric m, GLM speed factor acg = alpha sqrt(gamma^dd).  HLL or TVDLF; the
+// GLM pair (normal B, psi) uses signal speeds no smaller than
+// +-ch alpha sqrt(gamma^dd) - beta^d.  Writes the flux densitized by sqrt(gamma).
+// ----------------------------------------------------------------------------
+template <typename T>
+BHAC_HD void riemann_flux(const Met<T>& m, T acg, const T* PL, const T* PR, int d, int riemann, T gam, T gam_fac,
+                          T ch, T* out) {
+  const T ch2 = ch * ch;
+  Derived<T> sL, sR;
+  derive(m, PL, gam_fac, sL);
+  derive(m, PR, gam_fac, sR);
+  T lmL, lpL, lmR, lpR;
+  speeds_of(m, PL, sL, d, gam, lmL, lpL);
+  speeds_of(m, PR, sR, d, gam, lmR, lpR);
+  const T bed = d == 0 ? m.be1 : T(0);
+  const T lgp = acg * ch - bed, lgm = -acg * ch - bed;
+  T acc[NV];
+  T U[NV], F[NV];
+  if (riemann == 0) {
+    T lp = T(0), lm = T(0);
+    lp = lpL > lp ? lpL : lp;
+    lp = lpR > lp ? lpR : lp;
+    lm = lmL < lm ? lmL : lm;
+    lm = lmR < lm ? lmR : lm;
+    const T lpg = lgp > lp ? lgp : lp, lmg = lgm < lm ? lgm : lm;
+    const bool okh = lp - lm > T(0), okg = lpg - lmg > T(0);
+    const T ih = okh ? rcp_t(lp - lm) : T(0);
+    const T ihg = okg ? rcp_t(lpg - lmg) : T(0);
+    cons_of(PL, sL, U);
+    flux_of(m, PL, sL, U, d, ch2, F);
+    T FL[NV];
+    for (int v = 0; v < NV; ++v) {
+      const bool g = (v == PSI) || (v == B1 + d);
+      const T p = g ? lpg : lp, q = g ? lmg : lm;
+      acc[v] = p * (F[v] - q * U[v]);
+      FL[v] = F[v];
+    }
+    cons_of(PR, sR, U);
+    flux_of(m, PR, sR, U, d, ch2, F);
+    for (int v = 0; v < NV; ++v) {
+      const bool g = (v == PSI) || (v == B1 + d);
+      const T p = g ? lpg : lp, q = g ? lmg : lm, ihv = g ? ihg : ih;
+      // a degenerate fan (no signal speed at all) falls back to the mean flux
+      out[v] = m.sg * ((g ? okg : okh) ? (acc[v] - q * (F[v] - p * U[v])) * ihv : T(0.5) * (FL[v] + F[v]));
+    }
+  } else {
+    const T alpL = abs_t(lpL), almL = abs_t(lmL), alpR = abs_t(lpR), almR = abs_t(lmR);
+    T c = alpL;
+    c = almL > c ? almL : c;
+    c = alpR > c ? alpR : c;
+    c = almR > c ? almR : c;
+    const T agp = abs_t(lgp), agm = abs_t(lgm);
+    T cg = c;
+    cg = agp > cg ? agp : cg;
+    cg = agm > cg ? agm : cg;
+    cons_of(PL, sL, U);
+    flux_of(m, PL, sL, U, d, ch2, F);
+    for (int v = 0; v < NV; ++v) {
+      const bool g = (v == PSI) || (v == B1 + d);
+      acc[v] = F[v] + (g ? cg : c) * U[v];
+    }
+    cons_of(PR, sR, U);
+    flux_of(m, PR, sR, U, d, ch2, F);
+    for (int v = 0; v < NV; ++v) {
+      const bool g = (v == PSI) || (v == B1 + d);
+      out[v] = m.sg * (T(0.5) * (acc[v] + F[v]) - T(0.5) * (g ? cg : c) * U[v]);
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------
+// One face flux, densitized by the face sqrt(gamma).  (ig, jg, kg): ghosted
+// coordinates of the cell on the high side of the face.
+// ----------------------------------------------------------------------------
+template <typename T, bool FLAT>
+__device__ __forceinline__ void face_flux(const StageArgs& a, const T* __restrict__ Pb, int d, int ig, int jg,
+                                          int kg, int I1, int I2, T* out, int ostride) {
+  const int sd = d == 0 ? 1 : (d == 1 ? a.Nx : a.Nx * a.Ny);
+  const int c0 = (kg * a.Ny + jg) * a.Nx + ig;
+  // axis faces carry no flux (sqrt(gamma) = 0 there)
+  if (!FLAT && d == 1 && ((I2 == 0 && a.axis_lo1) || (I2 == a.N2g && a.axis_hi1))) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) out[v * ostride] = T(0);
+    return;
+  }
+  T PL[NV], PR[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    const T* p = Pb + (size_t)v * a.ncell + c0;
+    const T s0 = p[-3 * sd], s1 = p[-2 * sd], s2 = p[-sd], s3 = p[0], s4 = p[sd], s5 = p[2 * sd];
+    recon_var(a.recon, s0, s1, s2, s3, s4, s5, PL[v], PR[v]);
+  }
+  if (!(PL[RHO] > T(0)) || !(PL[PRS] > T(0)) || !(PR[RHO] > T(0)) || !(PR[PRS] > T(0))) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const T* p = Pb + (size_t)v * a.ncell + c0;
+      PL[v] = p[-sd];
+      PR[v] = p[0];
+    }
+  }
+  Met<T> m;
+  T acg;
+  if (FLAT) {
+    m = flat_metric<T>();
+    acg = T(1);
+  } else if (sizeof(T) == 8) {
+    const double* rec = d == 0 ? a.tab_f1 + (size_t)(I2 * (a.N1g + 1) + I1) * FREC
+                               : (d == 1 ? a.tab_f2 + (size_t)(I2 * a.N1g + I1) * FREC
+                                         : a.tab_c + (size_t)(I2 * a.N1g + I1) * CREC);
+    m = load_face_metric<T>(rec);
+    acg = T(d == 2 ? rec[C_ACG3] : rec[F_ACG]);
+  } else {
+    const float* rec = d == 0 ? a.tab_f1_32 + (size_t)(I2 * (a.N1g + 1) + I1) * FREC
+                              : (d == 1 ? a.tab_f2_32 + (size_t)(I2 * a.N1g + I1) * FREC
+                                        : a.tab_c32 + (size_t)(I2 * a.N1g + I1) * CREC);
+    m = load_face_metric<T>(rec);
+    acg = T(d == 2 ? rec[C_ACG3] : rec[F_ACG]);
+  }
+  T F[NV];
+  riemann_flux(m, acg, PL, PR, d, a.riemann, T(a.gam), T(a.gam_fac), T(a.ch), F);
+#pragma unroll
+  for (int v = 0; v < NV; ++v) out[v * ostride] = F[v];
+}
+
+// ----------------------------------------------------------------------------
+// The stage kernel.  T: flux arithmetic (double: FP64 form; float: mixed form).
+// ----------------------------------------------------------------------------
+template <typename T, int DIM, bool FLAT>
+__global__ void __launch_bounds__(256) stage_kernel(StageArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int tx = a.tx, ty = a.ty;
+  const int sFx = ty * (tx + 1), sFy = (ty + 1) * tx, sFz = tx * ty;
+  T* Fx = reinterpret_cast<T*>(smem_raw);
+  T* Fy = Fx + NV * sFx;
+  T* Fza = Fy + NV * sFy;
+  T* Fzb = Fza + NV * sFz;
+  __shared__ int s_item;
+
+  // time step
+  double dt;
+  if (a.dt_host > 0.0) {
+    dt = a.dt_host;
+  } else if (a.stage == 1) {
+    dt = a.cfl / __longlong_as_double((long long)*a.smax_in);
+  } else {
+    dt = *a.dt_dev;
+  }
+  if (a.stage == 1 && blockIdx.x == 0 && threadIdx.x == 0) *a.dt_dev = dt;
+
+  const T* Pb_all = sizeof(T) == 8 ? reinterpret_cast<const T*>(a.P_in) : reinterpret_cast<const T*>(a.P32_in);
+  unsigned cnt[4] = {0u, 0u, 0u, 0u};
+  double rate_max = 0.0;
+  const int ntile = a.ntx * a.nty;
+
+  int item = a.persistent ? -1 : (int)blockIdx.x;
+  for (;;) {
+    if (a.persistent) {
+      __syncthreads();
+      if (threadIdx.x == 0) s_item = (int)atomicAdd(a.work, 1u);
+      __syncthreads();
+      item = s_item;
+    }
+    if (item >= a.nitems) break;
+    const int b = item / ntile;
+    const int tile = item - b * ntile;
+    const int x0 = (tile % a.ntx) * tx, y0 = (tile / a.ntx) * ty;
+    const int bx = a.blk[4 * b + 1], by = a.blk[4 * b + 2];
+    const int I1b = bx * a.nx + x0, I2b = by * a.ny + y0;
+    const T* Pb = Pb_all + (size_t)b * NV * a.ncell;
+    T* Fz0 = Fza;
+    T* Fz1 = Fzb;
+    if (DIM == 3) {
+      // bottom face of plane 0
+      for (int t = threadIdx.x; t < sFz; t += blockDim.x) {
+        const int i = t % tx, j = t / tx;
+        face_flux<T, FLAT>(a, Pb, 2, i + x0 + a.gx, j + y0 + a.gy, a.gz, I1b + i, I2b + j, Fz0 + t, sFz);
+      }
+    }
+    for (int k = 0; k < a.nz; ++k) {
+      const int kg = k + a.gz;
+      const int nfx = sFx, nfy = sFy, nfz = DIM == 3 ? sFz : 0;
+      for (int t = threadIdx.x; t < nfx + nfy + nfz; t += blockDim.x) {
+        if (t < nfx) {
+          const int i = t % (tx + 1), j = t / (tx + 1);
+          face_flux<T, FLAT>(a, Pb, 0, i + x0 + a.gx, j + y0 + a.gy, kg, I1b + i, I2b + j, Fx + t, sFx);
+        } else if (t < nfx + nfy) {
+          const int u = t - nfx;
+          const int i = u % tx, j = u / tx;
+          face_flux<T, FLAT>(a, Pb, 1, i + x0 + a.gx, j + y0 + a.gy, kg, I1b + i, I2b + j, Fy + u, sFy);
+        } else {
+          const int u = t - nfx - nfy;
+          const int i = u % tx, j = u / tx;
+          face_flux<T, FLAT>(a, Pb, 2, i + x0 + a.gx, j + y0 + a.gy, kg + 1, I1b + i, I2b + j, Fz1 + u, sFz);
+        }
+      }
+      __syncthreads();
+      for (int c = threadIdx.x; c < sFz; c += blockDim.x) {
+        const int i = c % tx, j = c / tx;
+        const int ig = i + x0 + a.gx, jg = j + y0 + a.gy;
+        const int cg = (kg * a.Ny + jg) * a.Nx + ig;
+        const int ci = (k * a.ny + (j + y0)) * a.nx + (i + x0);
+        const int I1 = I1b + i, I2 = I2b + j;
+        double rhs[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          double r = -((double)Fx[v * sFx + j * (tx + 1) + i + 1] - (double)Fx[v * sFx + j * (tx + 1) + i]) * a.idx[0];
+          r += -((double)Fy[v * sFy + (j + 1) * tx + i] - (double)Fy[v * sFy + j * tx + i]) * a.idx[1];
+          if (DIM == 3) r += -((double)Fz1[v * sFz + c] - (double)Fz0[v * sFz + c]) * a.idx[2];
+          rhs[v] = r;
+        }
+        // sources from the cell's primitives
+        const double* crec = FLAT ? nullptr : a.tab_c + (size_t)(I2 * a.N1g + I1) * CREC;
+        double sg = 1.0, isg = 1.0, rho_fl = a.rho_fl_c, p_fl = a.p_fl_c;
+        {
+          T Pc[NV], Uc[NV], S[NV];
+#pragma unroll
+          for (int v = 0; v < NV; ++v) Pc[v] = Pb[(size_t)v * a.ncell + cg];
+          if (FLAT) {
+            rhs[PSI] += to_double(-T(a.kappa) * Pc[PSI]);
+          } else {
+            Met<T> m;
+            if (sizeof(T) == 8) {
+              m = load_centre_metric<T>(crec);
+            } else {
+              m = load_centre_metric<T>(a.tab_c32 + (size_t)(I2 * a.N1g + I1) * CREC);
+            }
+            Derived<T> s;
+            derive(m, Pc, T(a.gam_fac), s);
+            cons_of(Pc, s, Uc);
+            if (sizeof(T) == 8)
+              sources_of(m, crec, Pc, s, Uc, T(a.kappa), T(a.ch * a.ch), S);
+            else
+              sources_of(m, a.tab_c32 + (size_t)(I2 * a.N1g + I1) * CREC, Pc, s, Uc, T(a.kappa),
+                         T(a.ch * a.ch), S);
+            sg = crec[C_SG];
+            isg = crec[C_ISG];
+            rho_fl = crec[C_RHOFL];
+            p_fl = crec[C_PFL];
+#pragma unroll
+            for (int v = 0; v < NV; ++v) rhs[v] += sg * (double)S[v];
+          }
+        }
+        // RK combination
+        const size_t ub = (size_t)b * NV * a.nint + ci;
+        double U[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          const double un = a.Un[ub + (size_t)v * a.nint];
+          if (a.stage == 1)
+            U[v] = un + dt * rhs[v];
+          else
+            U[v] = 0.5 * un + 0.5 * (a.U1[ub + (size_t)v * a.nint] + dt * rhs[v]);
+        }
+        // inversion
+        Met<double> md = FLAT ? flat_metric<double>() : load_centre_metric<double>(crec);
+        double Uu[NV], Pg[NV], Pn[NV];
+        const double* Pd = a.P_in + (size_t)b * NV * a.ncell + cg;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          Uu[v] = U[v] * isg;
+          Pg[v] = Pd[(size_t)v * a.ncell];
+        }
+        const int st = con2prim(md, Uu, Pg, rho_fl, p_fl, a, Pn);
+        cnt[st] += 1u;
+        if (st >= 2) {
+          Derived<double> s;
+          derive(md, Pn, a.gam_fac, s);
+          cons_of(Pn, s, Uu);
+#pragma unroll
+          for (int v = 0; v < NV; ++v) U[v] = sg * Uu[v];
+        }
+        double* Po = a.P_out + (size_t)b * NV * a.ncell + cg;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          a.Uout[ub + (size_t)v * a.nint] = U[v];
+          Po[(size_t)v * a.ncell] = Pn[v];
+        }
+        if (sizeof(T) == 4) {
+          float* P3 = a.P32_out + (size_t)b * NV * a.ncell + cg;
+#pragma unroll
+          for (int v = 0; v < NV; ++v) P3[(size_t)v * a.ncell] = (float)Pn[v];
+        }
+        if (a.stage == 2) {
+          double acg[3] = {1.0, 1.0, 1.0};
+          if (!FLAT) {
+            acg[0] = crec[C_ACG1];
+            acg[1] = crec[C_ACG2];
+            acg[2] = crec[C_ACG3];
+          }
+          rate_max = fmax(rate_max, cfl_rate<DIM>(md, acg, Pn, a));
+        }
+      }
+      __syncthreads();
+      T* tmp = Fz0;
+      Fz0 = Fz1;
+      Fz1 = tmp;
+    }
+    if (!a.persistent) break;
+  }
+  // reductions: inversion counters and the CFL rate
+  const unsigned lane = threadIdx.x & 31u;
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    const unsigned tot = __reduce_add_sync(0xffffffffu, cnt[s]);
+    if (lane == 0 && tot) atomicAdd(a.counts + s, (unsigned long long)tot);
+  }
+  if (a.stage == 2) {
+    const double w = warp_max_d(rate_max);
+    if (lane == 0) atomicMax(a.smax_out, (unsigned long long)__double_as_longlong(w));
+  }
+}
+
+// Stand-alone CFL rate reduction over interior cells (FP64 primitives).
+template <int DIM, bool FLAT>
+__global__ void __launch_bounds__(256) cfl_kernel(StageArgs a) {
+  double rate_max = 0.0;
+  const long long n = (long long)a.nblocks * a.nint;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    const int b = (int)(t / a.nint);
+    const int ci = (int)(t - (long long)b * a.nint);
+    const int i = ci % a.nx, j = (ci / a.nx) % a.ny, k = ci / (a.nx * a.ny);
+    const int cg = ((k + a.gz) * a.Ny + (j + a.gy)) * a.Nx + (i + a.gx);
+    double P[NV];
+    const double* Pd = a.P_in + (size_t)b * NV * a.ncell + cg;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) P[v] = Pd[(size_t)v * a.ncell];
+    Met<double> m = flat_metric<double>();
+    double acg[3] = {1.0, 1.0, 1.0};
+    if (!FLAT) {
+      const int I1 = a.blk[4 * b + 1] * a.nx + i, I2 = a.blk[4 * b + 2] * a.ny + j;
+      const double* crec = a.tab_c + (size_t)(I2 * a.N1g + I1) * CREC;
+      m = load_centre_metric<double>(crec);
+      acg[0] = crec[C_ACG1];
+      acg[1] = crec[C_ACG2];
+      acg[2] = crec[C_ACG3];
+    }
+    rate_max = fmax(rate_max, cfl_rate<DIM>(m, acg, P, a));
+  }
+  const double w = warp_max_d(rate_max);
+  if ((threadIdx.x & 31u) == 0) atomicMax(a.smax_out, (unsigned long long)__double_as_longlong(w));
+}
+
+template <typename T, int DIM, bool FLAT>
+static cudaError_t configure_stage_t() {
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(stage_kernel<T, DIM, FLAT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         200 * 1024);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  return cudaSuccess;
+}
+
+template <typename T>
+static cudaError_t configure_all_t() {
+  cudaError_t e = configure_stage_t<T, 2, true>();
+  if (e == cudaSuccess) e = configure_stage_t<T, 2, false>();
+  if (e == cudaSuccess) e = configure_stage_t<T, 3, true>();
+  if (e == cudaSuccess) e = configure_stage_t<T, 3, false>();
+  return e;
+}
+
+template <typename T, int DIM, bool FLAT>
+static cudaError_t launch_stage_t(const StageArgs& a, int grid, int threads, size_t smem, cudaStream_t st) {
+  cudaError_t e = configure_stage_t<T, DIM, FLAT>();
+  if (e != cudaSuccess) return e;
+  stage_kernel<T, DIM, FLAT><<<grid, threads, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace bhac

@@ -16,7 +16,7 @@ import math
 
 from . import Grid
 
-__all__ = ["shock_tube_2d", "torus_2d", "torus_3d", "torus_3d_large", "periodic_box", "TORUS_SPIN"]
+__all__ = ["shock_tube_2d", "torus_2d", "torus_3d", "torus_3d_large", "periodic_box", "amr_torus", "TORUS_SPIN"]
 
 TORUS_SPIN = 0.9375
 R_IN, R_OUT = 1.2, 2500.0
@@ -62,3 +62,36 @@ def periodic_box(ndim=2, nblock=8, nroot=2, **kw) -> Grid:
     g = Grid(ndim=ndim, nx=nx, nroot=nr, xmin=(0.0, 0.0, 0.0), xmax=(1.0, 1.0, 1.0),
              coords="cart", bc=(("periodic", "periodic"),) * 3, gamma_ad=5.0 / 3.0, name="periodic_box")
     return g.with_(**kw) if kw else g
+
+
+def amr_torus(root=(8, 4, 5), nblock=16, r_refine=(60.0, 20.0), **kw) -> Grid:
+    """Three-level torus: root blocks of nblock^3 in MKS; a block is refined to
+    level 1 where its inner radius is below r_refine[0] and, at level 1, to
+    level 2 where its inner radius is below r_refine[1] (finest level inside
+    r < 20 M).  Refinement depends on r only, so neighbouring blocks differ by
+    at most one level across faces, edges and corners (and through the axis).
+    Leaf blocks only, ordered by level then z, y, x."""
+    x1min, x1max = math.log(R_IN), math.log(R_OUT)
+    leaves = []
+
+    def inner_r(level, ix):
+        w = (x1max - x1min) / (root[0] * 2 ** level)
+        return math.exp(x1min + ix * w)
+
+    def visit(level, ix, iy, iz):
+        if level < len(r_refine) and inner_r(level, ix) < r_refine[level]:
+            for dz in (0, 1):
+                for dy in (0, 1):
+                    for dx in (0, 1):
+                        visit(level + 1, 2 * ix + dx, 2 * iy + dy, 2 * iz + dz)
+        else:
+            leaves.append((level, ix, iy, iz))
+
+    for iz in range(root[2]):
+        for iy in range(root[1]):
+            for ix in range(root[0]):
+                visit(0, ix, iy, iz)
+    import numpy as np
+    blocks = np.asarray(sorted(leaves, key=lambda b: (b[0], b[3], b[2], b[1])), dtype=np.int32)
+    g = _torus_common(3, (nblock, nblock, nblock), tuple(root), "amr_torus", **kw)
+    return g.with_(nlevels=len(r_refine) + 1, blocks=blocks)

@@ -107,6 +107,14 @@ def fm_torus_prims(grid: Grid, r_in=6.0, r_pmax=12.0, beta=100.0, pert=0.02, see
     drawn in cell order [block][k][j][i].  Outside: floor density and pressure
     at rest with respect to the normal observer."""
     assert grid.coords == "mks"
+    if grid.ndim == 3 and grid.nx[2] > 1:
+        # the equilibrium and the field do not depend on phi: build one plane
+        # per block and repeat it, then draw the perturbation per cell
+        flat = fm_torus_prims(grid.with_(nx=(grid.nx[0], grid.nx[1], 1)), r_in, r_pmax, beta, 0.0, seed, field)
+        P = np.repeat(flat, grid.nx[2], axis=2)
+        if pert > 0.0:
+            _perturb(grid, P, pert, seed)
+        return P
     a, gam = grid.spin, grid.gamma_ad
     ell, lnh_in = fm_constants(a, r_in, r_pmax)
     hmax = math.exp(float(fm_lnh(r_pmax, math.pi / 2, a, ell)) - lnh_in)
@@ -143,11 +151,18 @@ def fm_torus_prims(grid: Grid, r_in=6.0, r_pmax=12.0, beta=100.0, pert=0.02, see
             P[:, 5] = B1 * scale
             P[:, 6] = B2 * scale
     if pert > 0.0:
-        rng = np.random.default_rng(seed)
-        xi = rng.random(P[:, 1].size).reshape(P[:, 1].shape)
-        torus = P[:, 0] > 10.0 * rho_fl
-        P[:, 1] = np.where(torus, P[:, 1] * (1.0 + pert * (2.0 * xi - 1.0)), P[:, 1])
+        _perturb(grid, P, pert, seed)
     return P
+
+
+def _perturb(grid, P, pert, seed):
+    """p <- p (1 + pert (2 xi - 1)), xi ~ U[0, 1) in cell order, where rho > 10 rho_floor."""
+    x1 = cell_centres(grid)[0]
+    rho_fl = grid.rho_floor * np.exp(x1) ** grid.rho_floor_pow
+    rng = np.random.default_rng(seed)
+    xi = rng.random(P[:, 1].size).reshape(P[:, 1].shape)
+    torus = P[:, 0] > 10.0 * rho_fl
+    P[:, 1] = np.where(torus, P[:, 1] * (1.0 + pert * (2.0 * xi - 1.0)), P[:, 1])
 
 
 def _loop_field(grid, a, gam, ell, lnh_in, K, r_in):

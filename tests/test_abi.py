@@ -1,0 +1,54 @@
+"""Host-side checks of the C ABI (no GPU needed): the library loads, exports
+every entry point the public header declares, sizes arenas and rejects
+invalid descriptions."""
+import os
+import re
+
+import pytest
+
+import paper_2108_12240_gb300 as gb
+import problems as pb
+
+HDR = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "bhac_gb300.h")
+
+
+def declared_functions():
+    text = open(HDR).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(bhac_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_library_exports_every_declared_entry_point():
+    names = declared_functions()
+    assert "bhac_step" in names and "bhac_init_grid" in names and len(names) >= 12
+    L = gb.lib()
+    for n in names:
+        assert hasattr(L, n), n
+
+
+def test_query_sizes_counts_state_and_tables():
+    g = pb.torus_3d(nroot=(2, 2, 2))
+    n64 = gb.bhac_query_sizes(gb.desc_of(g, "fp64"), gb.blocks_of(g))
+    n32 = gb.bhac_query_sizes(gb.desc_of(g, "mixed"), gb.blocks_of(g))
+    cells_g = 22 ** 3 * g.nb
+    cells_i = 16 ** 3 * g.nb
+    # two ghosted FP64 primitive buffers, two conserved buffers and a scratch array at least
+    assert n64 >= 8 * 9 * (2 * cells_g + 3 * cells_i)
+    assert n32 >= n64 + 4 * 9 * 2 * cells_g
+
+
+@pytest.mark.parametrize("bad", [
+    dict(ndim=4), dict(nx=(2, 16, 1)), dict(nroot=(0, 1, 1)), dict(gamma_ad=1.0), dict(cfl=0.0),
+    dict(bc=(("axis", "axis"), ("periodic", "periodic"), ("periodic", "periodic"))),
+])
+def test_invalid_descriptions_are_rejected(bad):
+    g = pb.shock_tube_2d(nblock=16, nroot=2)
+    g = g.with_(**bad)
+    with pytest.raises(gb.BhacError) as e:
+        gb.bhac_query_sizes(gb.desc_of(g), gb.blocks_of(pb.shock_tube_2d(nblock=16, nroot=2)))
+    assert e.value.status == 1
+
+
+def test_status_strings():
+    assert gb.status_string(0) == "ok"
+    assert gb.status_string(3) == "arena too small"

@@ -1,0 +1,256 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C ABI.
+
+Error metric (per cell, per conserved variable, after one step from the same
+seeded input): |q_gpu - q_oracle| / (|q_oracle| + s_q), where s_q is the size
+the variable can reach given the cell's total energy E = tau + D (densitized),
+in orthonormal units:
+  D: |D| only;  tau: E;  S_j: sqrt(gamma_jj) E  (|S| <= E);
+  B^j: sqrt(2 E sqrt(gamma) / gamma_jj)  (B^2/2 <= E);  psi: ch sqrt(2 E sqrt(gamma)).
+Momentum components and fields cross zero (S_theta of an equilibrium torus is
+a residual of cancelling pressure and gravity terms), so a plain ratio to
+|q| or to max|q| measures round-off of the cancelling terms rather than the
+agreement of the two implementations.  Bar: 1e-12 for the FP64 form, 1e-5
+for the mixed form.  Both implementations differ only in rounding order
+(fused multiply-adds, reciprocals, structural zeros of the metric)."""
+import numpy as np
+import pytest
+
+import oracle
+import problems as pb
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+TOLMIX = 1e-5
+
+
+@pytest.fixture(scope="module")
+def gb():
+    import torch
+    assert torch.cuda.is_available()
+    import paper_2108_12240_gb300 as m
+    return m
+
+
+def normwise(got, ref):
+    """Per conserved variable: max |got - ref| / max |ref| (reported only)."""
+    num = np.abs(got - ref).max(axis=(0, 2, 3, 4))
+    den = np.maximum(np.abs(ref).max(axis=(0, 2, 3, 4)), 1e-300)
+    return num / den
+
+
+def energy_scaled(got, ref, grid, blocks=None):
+    """Per conserved variable: max over cells of |got - ref| / (|ref| + s_q)."""
+    sub = grid if blocks is None else grid.with_(blocks=np.asarray(grid.blocks)[blocks])
+    x1, x2, _ = pb.cell_centres(sub)
+    if grid.coords == "mks":
+        _, _, gm = pb.ks_code_metric(x1, x2, grid.spin)
+        gjj = [gm[..., 0, 0], gm[..., 1, 1], gm[..., 2, 2]]
+        sg = np.sqrt(gm[..., 1, 1] * (gm[..., 0, 0] * gm[..., 2, 2] - gm[..., 0, 2] ** 2))
+    else:
+        gjj = [np.ones_like(x1)] * 3
+        sg = np.ones_like(x1)
+    E = np.abs(ref[:, 4] + ref[:, 0])
+    scale = [np.zeros_like(E), np.sqrt(gjj[0]) * E, np.sqrt(gjj[1]) * E, np.sqrt(gjj[2]) * E, E,
+             np.sqrt(2 * E * sg / gjj[0]), np.sqrt(2 * E * sg / gjj[1]), np.sqrt(2 * E * sg / gjj[2]),
+             grid.ch * np.sqrt(2 * E * sg)]
+    out = np.zeros(9)
+    for v in range(9):
+        den = np.abs(ref[:, v]) + scale[v]
+        d = np.abs(got[:, v] - ref[:, v])
+        out[v] = np.max(np.where(d > 0, d / np.maximum(den, 1e-300), 0.0))
+    return out
+
+
+def one_step(gb, grid, P, precision="fp64", dt=None, steps=1):
+    s = gb.Solver(grid, precision)
+    s.set_prims(P)
+    o = oracle.Oracle(grid)
+    o.set_prims(P)
+    dts = []
+    for _ in range(steps):
+        d = dt if dt is not None else o.cfl_dt()
+        dts.append(d)
+        o.step(d)
+        s.step(d)
+    return s, o, dts
+
+
+def assert_parity(got, ref, tol, what="", grid=None, blocks=None):
+    assert np.all(np.isfinite(got)), what
+    err = energy_scaled(got, ref, grid, blocks)
+    assert np.all(err <= tol), f"{what}: energy-scaled error per variable {err} (normwise {normwise(got, ref)})"
+    return err
+
+
+def test_shock_tube_one_step(gb):
+    g = pb.shock_tube_2d()
+    s, o, _ = one_step(gb, g, pb.shock_tube_prims(g))
+    assert_parity(s.cons(), o.cons(), TOL64, "cons", g)
+    assert np.all(normwise(s.prims(), o.prims()) <= TOL64)
+    assert np.array_equal(s.diagnostics(), o.c2p_counts())
+
+
+@pytest.mark.parametrize("k", [10, 50])
+def test_shock_tube_from_oracle_state(gb, k):
+    """Steps k -> k+1 from the oracle's own state after k steps."""
+    g = pb.shock_tube_2d()
+    o = oracle.Oracle(g)
+    o.set_prims(pb.shock_tube_prims(g))
+    for _ in range(k):
+        o.step(o.cfl_dt())
+    Pk = o.prims()
+    s, o2, _ = one_step(gb, g, Pk)
+    assert_parity(s.cons(), o2.cons(), TOL64, f"step {k}", g)
+
+
+def test_cfl_matches_oracle(gb):
+    g = pb.torus_2d()
+    P = pb.fm_torus_prims(g)
+    s = gb.Solver(g)
+    s.set_prims(P)
+    o = oracle.Oracle(g)
+    o.set_prims(P)
+    assert s.cfl_dt() == pytest.approx(o.cfl_dt(), rel=1e-14)
+
+
+def test_torus_2d_full_size(gb):
+    """256x256 Fishbone-Moncrief torus, Kerr a = 0.9375, MKS, loop field,
+    seeded perturbation: one step and a second step."""
+    g = pb.torus_2d()
+    s, o, _ = one_step(gb, g, pb.fm_torus_prims(g), steps=2)
+    assert_parity(s.cons(), o.cons(), TOL64, "cons", g)
+
+
+@pytest.mark.parametrize("recon,riemann", [("minmod", "hll"), ("ppm", "tvdlf")])
+def test_torus_2d_scheme_variants(gb, recon, riemann):
+    g = pb.torus_2d(nblock=8).with_(recon=recon, riemann=riemann)
+    s, o, _ = one_step(gb, g, pb.fm_torus_prims(g))
+    assert_parity(s.cons(), o.cons(), TOL64, f"{recon}/{riemann}", g)
+
+
+def test_torus_3d_full_size(gb):
+    """192x96x96 torus as 432 blocks of 16^3 (polar axis across phi + pi)."""
+    g = pb.torus_3d()
+    s, o, _ = one_step(gb, g, pb.fm_torus_prims(g))
+    assert_parity(s.cons(), o.cons(), TOL64, "cons", g)
+
+
+def test_torus_3d_ragged_blocks(gb):
+    """Blocks that are not multiples of the 16x16 tile (12 x 20 x 8 cells)."""
+    g = pb.torus_3d(nblock=(12, 20, 8), nroot=(4, 3, 4))
+    s, o, _ = one_step(gb, g, pb.fm_torus_prims(g))
+    assert_parity(s.cons(), o.cons(), TOL64, "cons", g)
+
+
+def test_mixed_precision_within_1e5(gb):
+    g = pb.torus_3d(nroot=(6, 3, 4))
+    s, o, _ = one_step(gb, g, pb.fm_torus_prims(g), precision="mixed")
+    err = assert_parity(s.cons(), o.cons(), TOLMIX, "mixed cons", g)
+    assert err.max() > 1e-12  # the FP32 arithmetic is really in use
+
+
+def test_mixed_shock_tube(gb):
+    g = pb.shock_tube_2d()
+    s, o, _ = one_step(gb, g, pb.shock_tube_prims(g), precision="mixed")
+    assert_parity(s.cons(), o.cons(), TOLMIX, "mixed cons", g)
+
+
+def test_launch_shapes_are_bitwise_identical(gb):
+    g = pb.torus_3d(nroot=(4, 3, 2))
+    P = pb.fm_torus_prims(g)
+    outs = []
+    for shape in [(16, 16, 256, 0), (16, 8, 128, 0), (8, 8, 64, 0), (16, 16, 256, 2)]:
+        s = gb.Solver(g)
+        s.set_launch(*shape)
+        s.set_prims(P)
+        dt = s.cfl_dt()
+        s.step(dt)
+        s.step(dt)
+        outs.append(s.cons())
+    for x in outs[1:]:
+        assert np.array_equal(x, outs[0])
+
+
+def test_device_dt_path(gb):
+    """step(dt <= 0) uses the CFL of the previous step's final primitives."""
+    g = pb.torus_2d(nblock=8)
+    P = pb.fm_torus_prims(g)
+    s = gb.Solver(g)
+    s.set_prims(P)
+    s.cfl_dt()
+    s.step(0.0)
+    s.step(0.0)
+    o = oracle.Oracle(g)
+    o.set_prims(P)
+    for _ in range(2):
+        o.step(o.cfl_dt())
+    assert_parity(s.cons(), o.cons(), TOL64, "device dt", g)
+
+
+def test_bench_workload_sampled(gb):
+    """512x256x256 torus as 2048 blocks of 32x32x16 (the benchmark's launch
+    configuration): one GPU step; the oracle recomputes stage 1 on a set of
+    sampled blocks and their neighbours and stage 2 on the sampled blocks."""
+    g = pb.torus_3d_large()
+    P = pb.fm_torus_prims(g)
+    s = gb.Solver(g)
+    s.set_prims(P)
+    dt = s.cfl_dt()
+    s.step(dt)
+    got = s.cons()
+    rng = np.random.default_rng(5)
+    nb = g.nb
+    blocks = np.asarray(g.blocks)
+    nr = g.nroot
+    index = {tuple(b[1:]): n for n, b in enumerate(blocks)}
+    # torus body (r ~ 12, theta ~ pi/2), polar-axis rows, inner and outer radial
+    # boundaries, and random blocks
+    picks = [(4, 3, 0), (4, 4, 5), (5, 4, 9), (3, 0, 2), (4, nr[1] - 1, 13), (0, 3, 7), (nr[0] - 1, 5, 1)]
+    sel = sorted({index[p] for p in picks} | set(rng.choice(nb, size=3, replace=False).tolist()))
+    # neighbourhood: blocks within one block in every direction (periodic in phi, axis wraps by pi)
+    hood = set()
+    for n in sel:
+        _, ix, iy, iz = blocks[n]
+        for dx in (-1, 0, 1):
+            for dy in (-1, 0, 1):
+                for dz in (-1, 0, 1):
+                    jx, jy, jz = ix + dx, iy + dy, (iz + dz) % nr[2]
+                    if not 0 <= jx < nr[0]:
+                        continue
+                    if not 0 <= jy < nr[1]:
+                        jy = iy
+                        jz = (jz + nr[2] // 2) % nr[2]
+                    hood.add(index[(jx, jy, jz)])
+                    hood.add(index[(jx, jy, (jz + nr[2] // 2) % nr[2])])
+    o = oracle.Oracle(g)
+    o.set_prims(P)
+    o.stage(1, dt, blocks=sorted(hood))
+    o.stage(2, dt, blocks=sel)
+    ref = o.cons()
+    err = assert_parity(got[sel], ref[sel], TOL64, "sampled blocks", g, sel)
+    assert np.abs(ref[sel][:, 0]).max() > 0.1  # the torus body is among the samples
+
+
+def test_cuda_graph_replay_is_bitwise_identical(gb):
+    """Two steps captured in a CUDA graph and replayed twice equal four plain
+    device-dt steps bit for bit (persistent launch in the captured form)."""
+    import torch
+    g = pb.torus_3d(nroot=(4, 3, 2))
+    P = pb.fm_torus_prims(g)
+    st = torch.cuda.Stream()
+    a = gb.Solver(g, stream=st)
+    a.set_prims(P)
+    a.cfl_dt()
+    for _ in range(4):
+        a.step(0.0)
+    b = gb.Solver(g, stream=st)
+    b.set_launch(persistent=2)
+    b.set_prims(P)
+    b.cfl_dt()
+    b.capture(2)
+    b.replay()
+    b.replay()
+    st.synchronize()
+    assert np.array_equal(a.cons(), b.cons())
+    assert np.array_equal(a.prims(), b.prims())
