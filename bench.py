@@ -52,6 +52,11 @@ def workload(name: str):
     elif name == "torus_2d":
         g = pb.torus_2d()
         desc = "2-D FM torus, Kerr a=0.9375, MKS, 256x256 cells as 256 blocks of 16^2 (+3 ghosts)"
+    elif name == "amr_torus":
+        g = pb.amr_torus()
+        lev = np.bincount(g.blocks[:, 0])
+        desc = (f"3-D FM torus, Kerr a=0.9375, MKS, 3 levels of 16^3 blocks ({g.nb} leaves: "
+                f"{lev[0]}/{lev[1]}/{lev[2]} per level, finest inside r < 20 M), one launch per stage")
     elif name == "shock_tube_2d":
         g = pb.shock_tube_2d()
         desc = "2-D SRMHD shock tube, 128x128 cells as 16 blocks of 32^2 (+3 ghosts)"
@@ -200,6 +205,8 @@ def e2e_form(gb, torch, g, P, form, steps, stream):
 def sample_grid(name):
     if name == "torus_3d_large":
         return pb.torus_3d_large(cells=SAMPLE_CELLS)
+    if name == "amr_torus":
+        return pb.amr_torus(root=(4, 2, 2), nblock=8)
     return workload(name)[0]
 
 
