@@ -14,7 +14,9 @@ namespace {
 
 struct Layout {
   size_t off_blk, off_src, off_flags, off_tmpl, off_tc, off_tf1, off_tf2, off_tc32, off_tf1_32, off_tf2_32;
-  size_t off_P[2], off_P32[2], off_U[2], off_scratch, off_small, total;
+  size_t off_P[2], off_P32[2], off_U[2], off_scratch, off_small;
+  size_t off_nodes, off_ops, off_nodeval, off_cf, off_regoff, off_reg, off_rcells, off_rterms, total;
+  long long toff_c[MAXLEV], toff_f1[MAXLEV], toff_f2[MAXLEV];
 };
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -30,7 +32,7 @@ bool valid_desc(const bhac_grid_desc* d, const bhac_block_desc* b, int nb) {
       if (d->bc[k][s] < 0 || d->bc[k][s] > 3) return false;
     if (!(d->xmax[k] > d->xmin[k])) return false;
   }
-  if (d->nlevels != 1) return false;  // uniform grids
+  if (d->nlevels < 1 || d->nlevels > MAXLEV) return false;
   if (d->coords < 0 || d->coords > 2) return false;
   if (d->precision < 0 || d->precision > 1) return false;
   if (d->recon < 0 || d->recon > 1 || d->riemann < 0 || d->riemann > 1) return false;
@@ -44,10 +46,10 @@ bool valid_desc(const bhac_grid_desc* d, const bhac_block_desc* b, int nb) {
       (d->bc[2][0] != BHAC_BC_PERIODIC || (d->nroot[2] * d->nx[2]) % 2))
     return false;
   for (int i = 0; i < nb; ++i) {
-    if (b[i].level != 0) return false;
+    if (b[i].level < 0 || b[i].level >= d->nlevels) return false;
     const int c[3] = {b[i].ix, b[i].iy, b[i].iz};
     for (int k = 0; k < 3; ++k)
-      if (c[k] < 0 || c[k] >= d->nroot[k]) return false;
+      if (c[k] < 0 || c[k] >= (d->nroot[k] << (k < d->ndim ? b[i].level : 0))) return false;
   }
   // cell indices must fit the 32-bit ghost map
   long long nc = 1;
@@ -68,13 +70,24 @@ void geometry(const bhac_grid_desc* d, int g[3], int N[3], int& ncell, int& nint
   nslots = ncell - nint;
 }
 
-Layout layout(const bhac_grid_desc* d, int nb) {
+Layout layout(const bhac_grid_desc* d, int nb, const HostMaps& M) {
   int g[3], N[3], ncell, nint, nslots;
   geometry(d, g, N, ncell, nint, nslots);
   const bool flat = d->coords == BHAC_COORDS_CART;
   const bool mixed = d->precision == BHAC_PREC_MIXED;
-  const size_t N1 = (size_t)d->nroot[0] * d->nx[0], N2 = (size_t)d->nroot[1] * d->nx[1];
   Layout L;
+  long long nc = 0, nf1 = 0, nf2 = 0;
+  for (int l = 0; l < MAXLEV; ++l) {
+    L.toff_c[l] = nc;
+    L.toff_f1[l] = nf1;
+    L.toff_f2[l] = nf2;
+    if (l < d->nlevels && !flat) {
+      const long long N1 = (long long)d->nroot[0] * d->nx[0] << l, N2 = (long long)d->nroot[1] * d->nx[1] << l;
+      nc += N1 * N2;
+      nf1 += (N1 + 1) * N2;
+      nf2 += N1 * (N2 + 1);
+    }
+  }
   size_t o = 0;
   auto take = [&](size_t bytes) {
     const size_t at = o;
@@ -85,7 +98,6 @@ Layout layout(const bhac_grid_desc* d, int nb) {
   L.off_src = take(sizeof(int) * (size_t)nb * nslots);
   L.off_flags = take((size_t)nb * nslots);
   L.off_tmpl = take(sizeof(int) * (size_t)nslots);
-  const size_t nc = flat ? 0 : N1 * N2, nf1 = flat ? 0 : (N1 + 1) * N2, nf2 = flat ? 0 : N1 * (N2 + 1);
   L.off_tc = take(sizeof(double) * CREC * nc);
   L.off_tf1 = take(sizeof(double) * FREC * nf1);
   L.off_tf2 = take(sizeof(double) * FREC * nf2);
@@ -97,39 +109,16 @@ Layout layout(const bhac_grid_desc* d, int nb) {
   for (int s = 0; s < 2; ++s) L.off_U[s] = take(sizeof(double) * NV * (size_t)nb * nint);
   L.off_scratch = take(sizeof(double) * NV * (size_t)nb * nint);
   L.off_small = take(256);
+  L.off_nodes = take(sizeof(GhostNode) * M.nodes.size());
+  L.off_ops = take(sizeof(long long) * M.ops.size());
+  L.off_nodeval = take((mixed ? sizeof(float) : sizeof(double)) * NV * M.nodes.size());
+  L.off_cf = take((size_t)nb);
+  L.off_regoff = take(sizeof(long long) * 6 * (size_t)nb);
+  L.off_reg = take(sizeof(double) * (size_t)M.reg_elems);
+  L.off_rcells = take(sizeof(RefluxCell) * M.rcells.size());
+  L.off_rterms = take(sizeof(RefluxTerm) * M.rterms.size());
   L.total = o;
   return L;
-}
-
-// Maps a global index outside the root domain back inside it and records the
-// value fix-ups (bit 0: flip theta components; bits 1+2d / 2+2d: clamp u^d to
-// <= 0 / >= 0).  Returns false if the rule leaves the domain (not reached for
-// valid descriptors).
-bool apply_rules(const bhac_grid_desc* d, long long G[3], unsigned& flags) {
-  flags = 0;
-  long long Nd[3];
-  for (int k = 0; k < 3; ++k) Nd[k] = (long long)d->nroot[k] * d->nx[k];
-  for (int k = 0; k < d->ndim; ++k) {
-    for (int side = 0; side < 2; ++side) {
-      const bool out = side == 0 ? G[k] < 0 : G[k] >= Nd[k];
-      if (!out) continue;
-      const int kind = d->bc[k][side];
-      if (kind == BHAC_BC_PERIODIC) {
-        G[k] = ((G[k] % Nd[k]) + Nd[k]) % Nd[k];
-      } else if (kind == BHAC_BC_OUTFLOW || kind == BHAC_BC_NOINFLOW) {
-        G[k] = side == 0 ? 0 : Nd[k] - 1;
-        if (kind == BHAC_BC_NOINFLOW) flags |= 1u << (side == 0 ? 1 + 2 * k : 2 + 2 * k);
-      } else {  // polar axis: mirror, and in 3-D half a turn in phi
-        G[k] = side == 0 ? -1 - G[k] : 2 * Nd[k] - 1 - G[k];
-        flags ^= 1u;
-        if (d->ndim == 3) G[2] += Nd[2] / 2;
-      }
-    }
-  }
-  if (d->ndim == 3 && d->bc[2][0] == BHAC_BC_PERIODIC) G[2] = ((G[2] % Nd[2]) + Nd[2]) % Nd[2];
-  for (int k = 0; k < 3; ++k)
-    if (G[k] < 0 || G[k] >= Nd[k]) return false;
-  return true;
 }
 
 bhac_status cuda_status(cudaError_t e) { return e == cudaSuccess ? BHAC_OK : BHAC_ERR_CUDA; }
@@ -192,11 +181,41 @@ StageArgs base_args(const bhac_ctx* c) {
   a.smax_out = c->smax;
   a.counts = c->counts;
   a.work = c->work;
+  a.nlev = c->d.nlevels;
+  for (int l = 0; l < MAXLEV; ++l) {
+    a.toff_c[l] = c->toff_c[l];
+    a.toff_f1[l] = c->toff_f1[l];
+    a.toff_f2[l] = c->toff_f2[l];
+    a.N1l[l] = c->N1g << l;
+    a.N2l[l] = c->N2g << l;
+  }
+  a.cf = c->d_cf;
+  a.regoff = c->d_regoff;
+  a.reg = c->d_reg;
+  a.rcells = c->d_rcells;
+  a.rterms = c->d_rterms;
+  a.nrcells = c->nrcells;
   return a;
 }
 
 bhac_status ghost_fill(bhac_ctx* c, int buf, bool zero_smax) {
+  for (size_t dep = 1; dep < c->depth_start.size(); ++dep) {
+    NodeArgs n;
+    n.nodes = c->d_nodes;
+    n.ops = c->d_ops;
+    n.first = c->depth_start[dep - 1];
+    n.count = c->depth_start[dep] - c->depth_start[dep - 1];
+    n.nnodes = c->nnodes;
+    n.ncell = c->ncell;
+    n.P = c->mixed ? nullptr : c->P[buf];
+    n.P32 = c->mixed ? c->P32[buf] : nullptr;
+    n.out = c->d_node64;
+    n.out32 = c->d_node32;
+    if (launch_ghost_nodes(n, c->st) != cudaSuccess) return BHAC_ERR_CUDA;
+  }
   GhostArgs g;
+  g.node64 = c->d_node64;
+  g.node32 = c->d_node32;
   g.src = c->d_src;
   g.flags = c->d_flags;
   g.tmpl = c->d_tmpl;
@@ -268,14 +287,22 @@ const char* bhac_status_string(bhac_status s) {
 
 bhac_status bhac_query_sizes(const bhac_grid_desc* d, const bhac_block_desc* b, int nb, size_t* out) {
   if (!out || !valid_desc(d, b, nb)) return BHAC_ERR_ARG;
-  *out = layout(d, nb).total;
+  int g[3], N[3], ncell, nint, nslots;
+  geometry(d, g, N, ncell, nint, nslots);
+  const HostMaps M = build_maps(d, b, nb, g, N, ncell);
+  if (!M.ok) return BHAC_ERR_ARG;
+  *out = layout(d, nb, M).total;
   return BHAC_OK;
 }
 
 bhac_status bhac_init_grid(bhac_ctx** out, const bhac_grid_desc* d, const bhac_block_desc* b, int nb,
                            void* arena, size_t arena_bytes, void* stream) {
   if (!out || !valid_desc(d, b, nb) || !arena || ((uintptr_t)arena & 255)) return BHAC_ERR_ARG;
-  const Layout L = layout(d, nb);
+  int g[3], N[3], ncell, nint, nslots;
+  geometry(d, g, N, ncell, nint, nslots);
+  const HostMaps M = build_maps(d, b, nb, g, N, ncell);
+  if (!M.ok) return BHAC_ERR_ARG;  // a boundary rule or a level points at a missing block
+  const Layout L = layout(d, nb, M);
   if (arena_bytes < L.total) return BHAC_ERR_NOMEM;
   bhac_ctx* c = new bhac_ctx();
   c->d = *d;
@@ -298,6 +325,11 @@ bhac_status bhac_init_grid(bhac_ctx** out, const bhac_grid_desc* d, const bhac_b
   c->tab_c32 = (float*)(c->arena + L.off_tc32);
   c->tab_f1_32 = (float*)(c->arena + L.off_tf1_32);
   c->tab_f2_32 = (float*)(c->arena + L.off_tf2_32);
+  for (int l = 0; l < MAXLEV; ++l) {
+    c->toff_c[l] = L.toff_c[l];
+    c->toff_f1[l] = L.toff_f1[l];
+    c->toff_f2[l] = L.toff_f2[l];
+  }
   for (int s = 0; s < 2; ++s) {
     c->P[s] = (double*)(c->arena + L.off_P[s]);
     c->P32[s] = c->mixed ? (float*)(c->arena + L.off_P32[s]) : nullptr;
@@ -309,6 +341,18 @@ bhac_status bhac_init_grid(bhac_ctx** out, const bhac_grid_desc* d, const bhac_b
   c->smax = (unsigned long long*)(small + 8);
   c->counts = (unsigned long long*)(small + 16);
   c->work = (unsigned int*)(small + 48);
+  c->nnodes = (int)M.nodes.size();
+  c->depth_start = M.depth_start;
+  c->d_nodes = (GhostNode*)(c->arena + L.off_nodes);
+  c->d_ops = (long long*)(c->arena + L.off_ops);
+  c->d_node64 = c->mixed ? nullptr : (double*)(c->arena + L.off_nodeval);
+  c->d_node32 = c->mixed ? (float*)(c->arena + L.off_nodeval) : nullptr;
+  c->d_cf = (unsigned char*)(c->arena + L.off_cf);
+  c->d_regoff = (long long*)(c->arena + L.off_regoff);
+  c->d_reg = (double*)(c->arena + L.off_reg);
+  c->d_rcells = (RefluxCell*)(c->arena + L.off_rcells);
+  c->d_rterms = (RefluxTerm*)(c->arena + L.off_rterms);
+  c->nrcells = (int)M.rcells.size();
   c->cur = 0;
   c->ucur = 0;
   // default launch shape: 16 x 16 columns where they divide the block
@@ -318,64 +362,28 @@ bhac_status bhac_init_grid(bhac_ctx** out, const bhac_grid_desc* d, const bhac_b
   c->persistent = 0;
   c->graph = nullptr;
   c->graph_steps = 0;
-
-  // block table and ghost maps
   c->blk.resize(4 * nb);
-  std::vector<int> lut((size_t)d->nroot[0] * d->nroot[1] * d->nroot[2], -1);
   for (int i = 0; i < nb; ++i) {
     c->blk[4 * i] = b[i].level;
     c->blk[4 * i + 1] = b[i].ix;
     c->blk[4 * i + 2] = b[i].iy;
     c->blk[4 * i + 3] = b[i].iz;
-    lut[((size_t)b[i].iz * d->nroot[1] + b[i].iy) * d->nroot[0] + b[i].ix] = i;
   }
-  std::vector<int> tmpl;
-  tmpl.reserve(c->nslots);
-  for (int k = 0; k < c->N[2]; ++k)
-    for (int j = 0; j < c->N[1]; ++j)
-      for (int i = 0; i < c->N[0]; ++i) {
-        const bool in = i >= c->g[0] && i < c->g[0] + d->nx[0] && j >= c->g[1] && j < c->g[1] + d->nx[1] &&
-                        k >= c->g[2] && k < c->g[2] + d->nx[2];
-        if (!in) tmpl.push_back((k * c->N[1] + j) * c->N[0] + i);
-      }
-  std::vector<int> src((size_t)nb * c->nslots);
-  std::vector<unsigned char> flg((size_t)nb * c->nslots);
-  bool ok = true;
-  for (int bi = 0; bi < nb && ok; ++bi) {
-    for (int s = 0; s < c->nslots; ++s) {
-      const int cell = tmpl[s];
-      const int loc[3] = {cell % c->N[0] - c->g[0], (cell / c->N[0]) % c->N[1] - c->g[1],
-                          cell / (c->N[0] * c->N[1]) - c->g[2]};
-      long long G[3];
-      for (int k = 0; k < 3; ++k) G[k] = (long long)c->blk[4 * bi + 1 + k] * d->nx[k] + loc[k];
-      unsigned f = 0;
-      if (!apply_rules(d, G, f)) {
-        ok = false;
-        break;
-      }
-      const int sb = lut[((size_t)(G[2] / d->nx[2]) * d->nroot[1] + G[1] / d->nx[1]) * d->nroot[0] + G[0] / d->nx[0]];
-      if (sb < 0) {
-        ok = false;
-        break;
-      }
-      const int li = (int)(G[0] % d->nx[0]) + c->g[0], lj = (int)(G[1] % d->nx[1]) + c->g[1],
-                lk = (int)(G[2] % d->nx[2]) + c->g[2];
-      src[(size_t)bi * c->nslots + s] = sb * c->ncell + (lk * c->N[1] + lj) * c->N[0] + li;
-      flg[(size_t)bi * c->nslots + s] = (unsigned char)f;
-    }
-  }
-  if (!ok) {
-    delete c;
-    return BHAC_ERR_ARG;  // a boundary rule points at a missing block
-  }
-  cudaError_t e = cudaMemcpyAsync(c->d_blk, c->blk.data(), sizeof(int) * 4 * nb, cudaMemcpyHostToDevice, c->st);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(c->d_src, src.data(), sizeof(int) * src.size(), cudaMemcpyHostToDevice, c->st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_flags, flg.data(), flg.size(), cudaMemcpyHostToDevice, c->st);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(c->d_tmpl, tmpl.data(), sizeof(int) * tmpl.size(), cudaMemcpyHostToDevice, c->st);
+  auto up = [&](void* dst, const void* src, size_t bytes) {
+    return bytes ? cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, c->st) : cudaSuccess;
+  };
+  cudaError_t e = up(c->d_blk, c->blk.data(), sizeof(int) * 4 * nb);
+  if (e == cudaSuccess) e = up(c->d_src, M.src.data(), sizeof(int) * M.src.size());
+  if (e == cudaSuccess) e = up(c->d_flags, M.flags.data(), M.flags.size());
+  if (e == cudaSuccess) e = up(c->d_tmpl, M.tmpl.data(), sizeof(int) * M.tmpl.size());
+  if (e == cudaSuccess) e = up(c->d_nodes, M.nodes.data(), sizeof(GhostNode) * M.nodes.size());
+  if (e == cudaSuccess) e = up(c->d_ops, M.ops.data(), sizeof(long long) * M.ops.size());
+  if (e == cudaSuccess) e = up(c->d_cf, M.cf.data(), M.cf.size());
+  if (e == cudaSuccess) e = up(c->d_regoff, M.regoff.data(), sizeof(long long) * M.regoff.size());
+  if (e == cudaSuccess) e = up(c->d_rcells, M.rcells.data(), sizeof(RefluxCell) * M.rcells.size());
+  if (e == cudaSuccess) e = up(c->d_rterms, M.rterms.data(), sizeof(RefluxTerm) * M.rterms.size());
   if (e == cudaSuccess) e = cudaMemsetAsync(small, 0, 256, c->st);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);  // host vectors die here
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);  // the host maps die here
   if (e != cudaSuccess) {
     delete c;
     return BHAC_ERR_CUDA;
@@ -396,31 +404,33 @@ bhac_status bhac_set_metric(bhac_ctx* c, int kind, double spin, double mass, con
   if (c->flat || kind != c->d.coords) return BHAC_ERR_ARG;
   c->d.spin = spin;
   c->d.mass = mass;
-  MetricArgs M;
-  M.coords = kind;
-  M.spin = spin;
-  M.mass = mass;
-  M.x1min = c->d.xmin[0];
-  M.x2min = c->d.xmin[1];
-  M.dx1 = (c->d.xmax[0] - c->d.xmin[0]) / c->N1g;
-  M.dx2 = (c->d.xmax[1] - c->d.xmin[1]) / c->N2g;
-  M.N1 = c->N1g;
-  M.N2 = c->N2g;
-  M.axis_lo = c->d.bc[1][0] == BHAC_BC_AXIS;
-  M.axis_hi = c->d.bc[1][1] == BHAC_BC_AXIS;
-  M.rho_floor = c->d.rho_floor;
-  M.rho_pow = c->d.rho_floor_pow;
-  M.p_floor = c->d.p_floor;
-  M.p_pow = c->d.p_floor_pow;
-  M.tab_c = c->tab_c;
-  M.tab_f1 = c->tab_f1;
-  M.tab_f2 = c->tab_f2;
-  M.tab_c32 = c->tab_c32;
-  M.tab_f1_32 = c->tab_f1_32;
-  M.tab_f2_32 = c->tab_f2_32;
-  bhac_status s = cuda_status(launch_metric_tables(M, c->st));
-  if (s == BHAC_OK) c->metric_ok = true;
-  return s;
+  for (int l = 0; l < c->d.nlevels; ++l) {
+    MetricArgs M;
+    M.coords = kind;
+    M.spin = spin;
+    M.mass = mass;
+    M.x1min = c->d.xmin[0];
+    M.x2min = c->d.xmin[1];
+    M.N1 = c->N1g << l;
+    M.N2 = c->N2g << l;
+    M.dx1 = (c->d.xmax[0] - c->d.xmin[0]) / M.N1;
+    M.dx2 = (c->d.xmax[1] - c->d.xmin[1]) / M.N2;
+    M.axis_lo = c->d.bc[1][0] == BHAC_BC_AXIS;
+    M.axis_hi = c->d.bc[1][1] == BHAC_BC_AXIS;
+    M.rho_floor = c->d.rho_floor;
+    M.rho_pow = c->d.rho_floor_pow;
+    M.p_floor = c->d.p_floor;
+    M.p_pow = c->d.p_floor_pow;
+    M.tab_c = c->tab_c + c->toff_c[l] * CREC;
+    M.tab_f1 = c->tab_f1 + c->toff_f1[l] * FREC;
+    M.tab_f2 = c->tab_f2 + c->toff_f2[l] * FREC;
+    M.tab_c32 = c->tab_c32 + c->toff_c[l] * CREC;
+    M.tab_f1_32 = c->tab_f1_32 + c->toff_f1[l] * FREC;
+    M.tab_f2_32 = c->tab_f2_32 + c->toff_f2[l] * FREC;
+    if (launch_metric_tables(M, c->st) != cudaSuccess) return BHAC_ERR_CUDA;
+  }
+  c->metric_ok = true;
+  return BHAC_OK;
 }
 
 bhac_status bhac_set_prims(bhac_ctx* c, const double* prims, int on_device) {

@@ -22,11 +22,20 @@ __global__ void __launch_bounds__(256) ghost_fill_kernel(GhostArgs g) {
     const int b = (int)(t / g.nslots);
     const int s = (int)(t - (long long)b * g.nslots);
     const int src = g.src[t];
+    const size_t dout = (size_t)b * NV * g.ncell + g.tmpl[s];
+    if (src < 0) {
+      // value of a cross-level node (already fixed up for the boundary rules)
+      const size_t nn = (size_t)(-src - 1) * NV;
+      if (g.P)
+        for (int q = 0; q < NV; ++q) g.P[dout + (size_t)q * g.ncell] = g.node64[nn + q];
+      if (g.P32)
+        for (int q = 0; q < NV; ++q) g.P32[dout + (size_t)q * g.ncell] = g.node32[nn + q];
+      continue;
+    }
     const unsigned f = g.flags[t];
     const int sb = src / g.ncell;
     const int sc = src - sb * g.ncell;
     const size_t so = (size_t)sb * NV * g.ncell + sc;
-    const size_t dout = (size_t)b * NV * g.ncell + g.tmpl[s];
     if (g.P) {
       double v[NV];
 #pragma unroll
@@ -309,8 +318,9 @@ __global__ void init_cons_kernel(StageArgs a, const double* __restrict__ P, doub
     Met<double> m = flat_metric<double>();
     double sg = 1.0;
     if (!a.flat) {
+      const LevelGeo geo = level_geo(a, a.blk[4 * b]);
       const int I1 = a.blk[4 * b + 1] * a.nx + i, I2 = a.blk[4 * b + 2] * a.ny + j;
-      const double* rec = a.tab_c + (size_t)(I2 * a.N1g + I1) * CREC;
+      const double* rec = geo.tc + (size_t)(I2 * geo.N1 + I1) * CREC;
       m = load_centre_metric<double>(rec);
       sg = rec[C_SG];
     }

@@ -16,6 +16,7 @@
 namespace bhac {
 
 constexpr int NV = 9;
+constexpr int MAXLEV = 4;  // refinement levels supported
 // primitive slots
 constexpr int RHO = 0, PRS = 1, U1 = 2, U2 = 3, U3 = 4, B1 = 5, B2 = 6, B3 = 7, PSI = 8;
 // conserved slots
@@ -73,7 +74,49 @@ struct StageArgs {
   unsigned long long* smax_out;  // accumulated by stage 2 (and the CFL kernel)
   unsigned long long* counts;    // 4 inversion outcome counters
   unsigned int* work;            // persistent work counter
+  // refinement levels: table offsets (records) and extents per level
+  int nlev;
+  long long toff_c[MAXLEV], toff_f1[MAXLEV], toff_f2[MAXLEV];
+  int N1l[MAXLEV], N2l[MAXLEV];
+  // coarse-fine faces: per block, bit 2d+s marks a face bordering finer blocks
+  // (its adjacent cells are finished by the reflux pass); per block x 6 the
+  // element offset of the face's flux register, or -1
+  const unsigned char* cf;
+  const long long* regoff;
+  double* reg;
+  const struct RefluxCell* rcells;
+  const struct RefluxTerm* rterms;
+  int nrcells;
 };
+
+// Geometry of one refinement level as seen by a kernel.
+struct LevelGeo {
+  const double* tc;
+  const double* tf1;
+  const double* tf2;
+  const float* tc32;
+  const float* tf1_32;
+  const float* tf2_32;
+  int N1, N2;
+  double idx[3];
+};
+
+__host__ __device__ __forceinline__ LevelGeo level_geo(const StageArgs& a, int L) {
+  LevelGeo g;
+  g.tc = a.tab_c ? a.tab_c + a.toff_c[L] * CREC : nullptr;
+  g.tf1 = a.tab_f1 ? a.tab_f1 + a.toff_f1[L] * FREC : nullptr;
+  g.tf2 = a.tab_f2 ? a.tab_f2 + a.toff_f2[L] * FREC : nullptr;
+  g.tc32 = a.tab_c32 ? a.tab_c32 + a.toff_c[L] * CREC : nullptr;
+  g.tf1_32 = a.tab_f1_32 ? a.tab_f1_32 + a.toff_f1[L] * FREC : nullptr;
+  g.tf2_32 = a.tab_f2_32 ? a.tab_f2_32 + a.toff_f2[L] * FREC : nullptr;
+  g.N1 = a.N1l[L];
+  g.N2 = a.N2l[L];
+  const double s = (double)(1 << L);
+  g.idx[0] = a.idx[0] * s;
+  g.idx[1] = a.idx[1] * s;
+  g.idx[2] = a.ndim == 3 ? a.idx[2] * s : a.idx[2];
+  return g;
+}
 
 template <typename T>
 struct Met {

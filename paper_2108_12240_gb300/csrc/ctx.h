@@ -5,6 +5,7 @@
 #include <vector>
 
 #include "../../include/bhac_gb300.h"
+#include "amr.h"
 #include "launch.h"
 
 struct bhac_ctx {
@@ -40,6 +41,21 @@ struct bhac_ctx {
   bool metric_ok, prims_ok, cfl_ok;
   // launch shape
   int tx, ty, threads, persistent;
+  // refinement levels: metric-table record offsets per level
+  long long toff_c[bhac::MAXLEV], toff_f1[bhac::MAXLEV], toff_f2[bhac::MAXLEV];
+  // cross-level ghost nodes (evaluated depth by depth) and flux correction
+  int nnodes;
+  std::vector<int> depth_start;
+  bhac::GhostNode* d_nodes;
+  long long* d_ops;
+  double* d_node64;
+  float* d_node32;
+  unsigned char* d_cf;
+  long long* d_regoff;
+  double* d_reg;
+  bhac::RefluxCell* d_rcells;
+  bhac::RefluxTerm* d_rterms;
+  int nrcells;
   // captured steps
   cudaGraphExec_t graph;
   int graph_steps;

@@ -17,12 +17,15 @@ cudaError_t prepare_stage_mixed();
 
 // auxiliary kernels (aux.cu)
 struct GhostArgs {
-  const int* src;               // per (block, slot): source ghosted-cell index over all blocks
+  const int* src;               // per (block, slot): source ghosted-cell index over all blocks,
+                                // or -(node + 1) for a cross-level value
   const unsigned char* flags;   // per (block, slot): bit0 flip theta, bits 1+2d / 2+2d clamp u^d <= 0 / >= 0
   const int* tmpl;              // per slot: destination cell index inside a block
   int nslots, nblocks, ncell;
   double* P;                    // FP64 ghosted primitives (or null)
   float* P32;                   // FP32 ghosted primitives (or null)
+  const double* node64;         // cross-level node values (FP64 form)
+  const float* node32;          // cross-level node values (mixed form)
   unsigned int* work_reset;     // zeroed by the first thread (persistent work counter)
   unsigned long long* smax_reset;  // zeroed by the first thread when non-null
 };

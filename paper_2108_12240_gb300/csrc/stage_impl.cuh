@@ -11,6 +11,7 @@
 // next, so no interior face flux is ever evaluated twice.
 #pragma once
 
+#include "amr.h"
 #include "bhac_device.cuh"
 #include "launch.h"
 
@@ -259,12 +260,6 @@ BHAC_HD T cfl_rate_t(const Met<T>& m, const T* acg, const T* P, double gam, doub
   return rate;
 }
 
-template <int DIM>
-__device__ __forceinline__ double cfl_rate(const Met<double>& m, const double* acg, const double* P,
-                                           const StageArgs& a) {
-  return cfl_rate_t<double, DIM>(m, acg, P, a.gam, a.gam_fac, a.ch, a.idx);
-}
-
 // ----------------------------------------------------------------------------
 // Riemann solve at one face: states PL, PR (already reconstructed), face
 // metric m, GLM speed factor acg = alpha sqrt(gamma^dd).  HLL or TVDLF; the
@@ -339,15 +334,16 @@ BHAC_HD void riemann_flux(const Met<T>& m, T acg, const T* PL, const T* PR, int 
 
 // ----------------------------------------------------------------------------
 // One face flux, densitized by the face sqrt(gamma).  (ig, jg, kg): ghosted
-// coordinates of the cell on the high side of the face.
+// coordinates of the cell on the high side of the face; (I1, I2): level-global
+// table indices of the face.
 // ----------------------------------------------------------------------------
 template <typename T, bool FLAT>
-__device__ __forceinline__ void face_flux(const StageArgs& a, const T* __restrict__ Pb, int d, int ig, int jg,
-                                          int kg, int I1, int I2, T* out, int ostride) {
+__device__ __forceinline__ void face_flux(const StageArgs& a, const LevelGeo& geo, const T* __restrict__ Pb, int d,
+                                          int ig, int jg, int kg, int I1, int I2, T* out, int ostride) {
   const int sd = d == 0 ? 1 : (d == 1 ? a.Nx : a.Nx * a.Ny);
   const int c0 = (kg * a.Ny + jg) * a.Nx + ig;
   // axis faces carry no flux (sqrt(gamma) = 0 there)
-  if (!FLAT && d == 1 && ((I2 == 0 && a.axis_lo1) || (I2 == a.N2g && a.axis_hi1))) {
+  if (!FLAT && d == 1 && ((I2 == 0 && a.axis_lo1) || (I2 == geo.N2 && a.axis_hi1))) {
 #pragma unroll
     for (int v = 0; v < NV; ++v) out[v * ostride] = T(0);
     return;
@@ -373,15 +369,15 @@ __device__ __forceinline__ void face_flux(const StageArgs& a, const T* __restric
     m = flat_metric<T>();
     acg = T(1);
   } else if (sizeof(T) == 8) {
-    const double* rec = d == 0 ? a.tab_f1 + (size_t)(I2 * (a.N1g + 1) + I1) * FREC
-                               : (d == 1 ? a.tab_f2 + (size_t)(I2 * a.N1g + I1) * FREC
-                                         : a.tab_c + (size_t)(I2 * a.N1g + I1) * CREC);
+    const double* rec = d == 0 ? geo.tf1 + (size_t)(I2 * (geo.N1 + 1) + I1) * FREC
+                               : (d == 1 ? geo.tf2 + (size_t)(I2 * geo.N1 + I1) * FREC
+                                         : geo.tc + (size_t)(I2 * geo.N1 + I1) * CREC);
     m = load_face_metric<T>(rec);
     acg = T(d == 2 ? rec[C_ACG3] : rec[F_ACG]);
   } else {
-    const float* rec = d == 0 ? a.tab_f1_32 + (size_t)(I2 * (a.N1g + 1) + I1) * FREC
-                              : (d == 1 ? a.tab_f2_32 + (size_t)(I2 * a.N1g + I1) * FREC
-                                        : a.tab_c32 + (size_t)(I2 * a.N1g + I1) * CREC);
+    const float* rec = d == 0 ? geo.tf1_32 + (size_t)(I2 * (geo.N1 + 1) + I1) * FREC
+                              : (d == 1 ? geo.tf2_32 + (size_t)(I2 * geo.N1 + I1) * FREC
+                                        : geo.tc32 + (size_t)(I2 * geo.N1 + I1) * CREC);
     m = load_face_metric<T>(rec);
     acg = T(d == 2 ? rec[C_ACG3] : rec[F_ACG]);
   }
@@ -391,8 +387,91 @@ __device__ __forceinline__ void face_flux(const StageArgs& a, const T* __restric
   for (int v = 0; v < NV; ++v) out[v * ostride] = F[v];
 }
 
+// Copies a block-boundary face flux into the face's register (faces between
+// refinement levels only).  fc: index of the face cell in the register, over
+// the two transverse dimensions in ascending order.
+template <typename T>
+__device__ __forceinline__ void to_register(const StageArgs& a, int b, int d, int side, int fc, const T* F,
+                                            int stride) {
+  const long long off = a.regoff[b * 6 + 2 * d + side];
+  if (off < 0) return;
+  const int ncf = d == 0 ? a.ny * a.nz : (d == 1 ? a.nx * a.nz : a.nx * a.ny);
+#pragma unroll
+  for (int v = 0; v < NV; ++v) a.reg[off + (long long)v * ncf + fc] = to_double(F[v * stride]);
+}
+
+// Inversion, floors, outputs, counters and (stage 2) the CFL rate of a cell
+// whose stage conserved state U (densitized) is final.
+template <typename T, int DIM, bool FLAT>
+__device__ __forceinline__ void finish_cell(const StageArgs& a, const LevelGeo& geo, int b, int ci, int cg, int I1,
+                                            int I2, double U[NV], unsigned cnt[4], double& rate_max) {
+  const double* crec = FLAT ? nullptr : geo.tc + (size_t)(I2 * geo.N1 + I1) * CREC;
+  const double sg = FLAT ? 1.0 : crec[C_SG];
+  const double isg = FLAT ? 1.0 : crec[C_ISG];
+  const double rho_fl = FLAT ? a.rho_fl_c : crec[C_RHOFL];
+  const double p_fl = FLAT ? a.p_fl_c : crec[C_PFL];
+  Met<double> md = FLAT ? flat_metric<double>() : load_centre_metric<double>(crec);
+  double Uu[NV], Pg[NV], Pn[NV];
+  const double* Pd = a.P_in + (size_t)b * NV * a.ncell + cg;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    Uu[v] = U[v] * isg;
+    Pg[v] = Pd[(size_t)v * a.ncell];
+  }
+  const int st = con2prim(md, Uu, Pg, rho_fl, p_fl, a, Pn);
+  cnt[st] += 1u;
+  if (st >= 2) {
+    Derived<double> s;
+    derive(md, Pn, a.gam_fac, s);
+    cons_of(Pn, s, Uu);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) U[v] = sg * Uu[v];
+  }
+  const size_t ub = (size_t)b * NV * a.nint + ci;
+  double* Po = a.P_out + (size_t)b * NV * a.ncell + cg;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    a.Uout[ub + (size_t)v * a.nint] = U[v];
+    Po[(size_t)v * a.ncell] = Pn[v];
+  }
+  if (sizeof(T) == 4) {
+    float* P3 = a.P32_out + (size_t)b * NV * a.ncell + cg;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) P3[(size_t)v * a.ncell] = (float)Pn[v];
+  }
+  if (a.stage == 2) {
+    double acg[3] = {1.0, 1.0, 1.0};
+    if (!FLAT) {
+      acg[0] = crec[C_ACG1];
+      acg[1] = crec[C_ACG2];
+      acg[2] = crec[C_ACG3];
+    }
+    rate_max = fmax(rate_max, cfl_rate_t<double, DIM>(md, acg, Pn, a.gam, a.gam_fac, a.ch, geo.idx));
+  }
+}
+
+__device__ __forceinline__ double stage_dt(const StageArgs& a) {
+  if (a.dt_host > 0.0) return a.dt_host;
+  if (a.stage == 1) return a.cfl / __longlong_as_double((long long)*a.smax_in);
+  return *a.dt_dev;
+}
+
+__device__ __forceinline__ void reduce_outputs(const StageArgs& a, const unsigned cnt[4], double rate_max) {
+  const unsigned lane = threadIdx.x & 31u;
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    const unsigned tot = __reduce_add_sync(0xffffffffu, cnt[s]);
+    if (lane == 0 && tot) atomicAdd(a.counts + s, (unsigned long long)tot);
+  }
+  if (a.stage == 2) {
+    const double w = warp_max_d(rate_max);
+    if (lane == 0) atomicMax(a.smax_out, (unsigned long long)__double_as_longlong(w));
+  }
+}
+
 // ----------------------------------------------------------------------------
 // The stage kernel.  T: flux arithmetic (double: FP64 form; float: mixed form).
+// Every block of every level is an item of the same launch.
 // ----------------------------------------------------------------------------
 template <typename T, int DIM, bool FLAT>
 __global__ void __launch_bounds__(256) stage_kernel(StageArgs a) {
@@ -405,15 +484,7 @@ __global__ void __launch_bounds__(256) stage_kernel(StageArgs a) {
   T* Fzb = Fza + NV * sFz;
   __shared__ int s_item;
 
-  // time step
-  double dt;
-  if (a.dt_host > 0.0) {
-    dt = a.dt_host;
-  } else if (a.stage == 1) {
-    dt = a.cfl / __longlong_as_double((long long)*a.smax_in);
-  } else {
-    dt = *a.dt_dev;
-  }
+  const double dt = stage_dt(a);
   if (a.stage == 1 && blockIdx.x == 0 && threadIdx.x == 0) *a.dt_dev = dt;
 
   const T* Pb_all = sizeof(T) == 8 ? reinterpret_cast<const T*>(a.P_in) : reinterpret_cast<const T*>(a.P32_in);
@@ -433,16 +504,21 @@ __global__ void __launch_bounds__(256) stage_kernel(StageArgs a) {
     const int b = item / ntile;
     const int tile = item - b * ntile;
     const int x0 = (tile % a.ntx) * tx, y0 = (tile / a.ntx) * ty;
+    const int L = a.blk[4 * b];
+    const LevelGeo geo = level_geo(a, L);
     const int bx = a.blk[4 * b + 1], by = a.blk[4 * b + 2];
     const int I1b = bx * a.nx + x0, I2b = by * a.ny + y0;
     const T* Pb = Pb_all + (size_t)b * NV * a.ncell;
+    const unsigned cfb = a.nlev > 1 ? a.cf[b] : 0u;
+    const bool regs = a.nlev > 1;
     T* Fz0 = Fza;
     T* Fz1 = Fzb;
     if (DIM == 3) {
       // bottom face of plane 0
       for (int t = threadIdx.x; t < sFz; t += blockDim.x) {
         const int i = t % tx, j = t / tx;
-        face_flux<T, FLAT>(a, Pb, 2, i + x0 + a.gx, j + y0 + a.gy, a.gz, I1b + i, I2b + j, Fz0 + t, sFz);
+        face_flux<T, FLAT>(a, geo, Pb, 2, i + x0 + a.gx, j + y0 + a.gy, a.gz, I1b + i, I2b + j, Fz0 + t, sFz);
+        if (regs) to_register(a, b, 2, 0, (j + y0) * a.nx + i + x0, Fz0 + t, sFz);
       }
     }
     for (int k = 0; k < a.nz; ++k) {
@@ -451,15 +527,20 @@ __global__ void __launch_bounds__(256) stage_kernel(StageArgs a) {
       for (int t = threadIdx.x; t < nfx + nfy + nfz; t += blockDim.x) {
         if (t < nfx) {
           const int i = t % (tx + 1), j = t / (tx + 1);
-          face_flux<T, FLAT>(a, Pb, 0, i + x0 + a.gx, j + y0 + a.gy, kg, I1b + i, I2b + j, Fx + t, sFx);
+          face_flux<T, FLAT>(a, geo, Pb, 0, i + x0 + a.gx, j + y0 + a.gy, kg, I1b + i, I2b + j, Fx + t, sFx);
+          if (regs && (x0 + i == 0 || x0 + i == a.nx))
+            to_register(a, b, 0, x0 + i == 0 ? 0 : 1, k * a.ny + j + y0, Fx + t, sFx);
         } else if (t < nfx + nfy) {
           const int u = t - nfx;
           const int i = u % tx, j = u / tx;
-          face_flux<T, FLAT>(a, Pb, 1, i + x0 + a.gx, j + y0 + a.gy, kg, I1b + i, I2b + j, Fy + u, sFy);
+          face_flux<T, FLAT>(a, geo, Pb, 1, i + x0 + a.gx, j + y0 + a.gy, kg, I1b + i, I2b + j, Fy + u, sFy);
+          if (regs && (y0 + j == 0 || y0 + j == a.ny))
+            to_register(a, b, 1, y0 + j == 0 ? 0 : 1, k * a.nx + i + x0, Fy + u, sFy);
         } else {
           const int u = t - nfx - nfy;
           const int i = u % tx, j = u / tx;
-          face_flux<T, FLAT>(a, Pb, 2, i + x0 + a.gx, j + y0 + a.gy, kg + 1, I1b + i, I2b + j, Fz1 + u, sFz);
+          face_flux<T, FLAT>(a, geo, Pb, 2, i + x0 + a.gx, j + y0 + a.gy, kg + 1, I1b + i, I2b + j, Fz1 + u, sFz);
+          if (regs && k + 1 == a.nz) to_register(a, b, 2, 1, (j + y0) * a.nx + i + x0, Fz1 + u, sFz);
         }
       }
       __syncthreads();
@@ -472,14 +553,12 @@ __global__ void __launch_bounds__(256) stage_kernel(StageArgs a) {
         double rhs[NV];
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
-          double r = -((double)Fx[v * sFx + j * (tx + 1) + i + 1] - (double)Fx[v * sFx + j * (tx + 1) + i]) * a.idx[0];
-          r += -((double)Fy[v * sFy + (j + 1) * tx + i] - (double)Fy[v * sFy + j * tx + i]) * a.idx[1];
-          if (DIM == 3) r += -((double)Fz1[v * sFz + c] - (double)Fz0[v * sFz + c]) * a.idx[2];
+          double r = -((double)Fx[v * sFx + j * (tx + 1) + i + 1] - (double)Fx[v * sFx + j * (tx + 1) + i]) * geo.idx[0];
+          r += -((double)Fy[v * sFy + (j + 1) * tx + i] - (double)Fy[v * sFy + j * tx + i]) * geo.idx[1];
+          if (DIM == 3) r += -((double)Fz1[v * sFz + c] - (double)Fz0[v * sFz + c]) * geo.idx[2];
           rhs[v] = r;
         }
         // sources from the cell's primitives
-        const double* crec = FLAT ? nullptr : a.tab_c + (size_t)(I2 * a.N1g + I1) * CREC;
-        double sg = 1.0, isg = 1.0, rho_fl = a.rho_fl_c, p_fl = a.p_fl_c;
         {
           T Pc[NV], Uc[NV], S[NV];
 #pragma unroll
@@ -487,11 +566,12 @@ __global__ void __launch_bounds__(256) stage_kernel(StageArgs a) {
           if (FLAT) {
             rhs[PSI] += to_double(-T(a.kappa) * Pc[PSI]);
           } else {
+            const double* crec = geo.tc + (size_t)(I2 * geo.N1 + I1) * CREC;
             Met<T> m;
             if (sizeof(T) == 8) {
               m = load_centre_metric<T>(crec);
             } else {
-              m = load_centre_metric<T>(a.tab_c32 + (size_t)(I2 * a.N1g + I1) * CREC);
+              m = load_centre_metric<T>(geo.tc32 + (size_t)(I2 * geo.N1 + I1) * CREC);
             }
             Derived<T> s;
             derive(m, Pc, T(a.gam_fac), s);
@@ -499,12 +579,9 @@ __global__ void __launch_bounds__(256) stage_kernel(StageArgs a) {
             if (sizeof(T) == 8)
               sources_of(m, crec, Pc, s, Uc, T(a.kappa), T(a.ch * a.ch), S);
             else
-              sources_of(m, a.tab_c32 + (size_t)(I2 * a.N1g + I1) * CREC, Pc, s, Uc, T(a.kappa),
-                         T(a.ch * a.ch), S);
-            sg = crec[C_SG];
-            isg = crec[C_ISG];
-            rho_fl = crec[C_RHOFL];
-            p_fl = crec[C_PFL];
+              sources_of(m, geo.tc32 + (size_t)(I2 * geo.N1 + I1) * CREC, Pc, s, Uc, T(a.kappa), T(a.ch * a.ch),
+                         S);
+            const double sg = crec[C_SG];
 #pragma unroll
             for (int v = 0; v < NV; ++v) rhs[v] += sg * (double)S[v];
           }
@@ -520,43 +597,15 @@ __global__ void __launch_bounds__(256) stage_kernel(StageArgs a) {
           else
             U[v] = 0.5 * un + 0.5 * (a.U1[ub + (size_t)v * a.nint] + dt * rhs[v]);
         }
-        // inversion
-        Met<double> md = FLAT ? flat_metric<double>() : load_centre_metric<double>(crec);
-        double Uu[NV], Pg[NV], Pn[NV];
-        const double* Pd = a.P_in + (size_t)b * NV * a.ncell + cg;
+        // cells next to a face bordering finer blocks are finished by the reflux pass
+        const bool later = cfb && (((cfb & 1u) && x0 + i == 0) || ((cfb & 2u) && x0 + i == a.nx - 1) ||
+                                   ((cfb & 4u) && y0 + j == 0) || ((cfb & 8u) && y0 + j == a.ny - 1) ||
+                                   ((cfb & 16u) && k == 0) || ((cfb & 32u) && k == a.nz - 1));
+        if (later) {
 #pragma unroll
-        for (int v = 0; v < NV; ++v) {
-          Uu[v] = U[v] * isg;
-          Pg[v] = Pd[(size_t)v * a.ncell];
-        }
-        const int st = con2prim(md, Uu, Pg, rho_fl, p_fl, a, Pn);
-        cnt[st] += 1u;
-        if (st >= 2) {
-          Derived<double> s;
-          derive(md, Pn, a.gam_fac, s);
-          cons_of(Pn, s, Uu);
-#pragma unroll
-          for (int v = 0; v < NV; ++v) U[v] = sg * Uu[v];
-        }
-        double* Po = a.P_out + (size_t)b * NV * a.ncell + cg;
-#pragma unroll
-        for (int v = 0; v < NV; ++v) {
-          a.Uout[ub + (size_t)v * a.nint] = U[v];
-          Po[(size_t)v * a.ncell] = Pn[v];
-        }
-        if (sizeof(T) == 4) {
-          float* P3 = a.P32_out + (size_t)b * NV * a.ncell + cg;
-#pragma unroll
-          for (int v = 0; v < NV; ++v) P3[(size_t)v * a.ncell] = (float)Pn[v];
-        }
-        if (a.stage == 2) {
-          double acg[3] = {1.0, 1.0, 1.0};
-          if (!FLAT) {
-            acg[0] = crec[C_ACG1];
-            acg[1] = crec[C_ACG2];
-            acg[2] = crec[C_ACG3];
-          }
-          rate_max = fmax(rate_max, cfl_rate<DIM>(md, acg, Pn, a));
+          for (int v = 0; v < NV; ++v) a.Uout[ub + (size_t)v * a.nint] = U[v];
+        } else {
+          finish_cell<T, DIM, FLAT>(a, geo, b, ci, cg, I1, I2, U, cnt, rate_max);
         }
       }
       __syncthreads();
@@ -566,17 +615,46 @@ __global__ void __launch_bounds__(256) stage_kernel(StageArgs a) {
     }
     if (!a.persistent) break;
   }
-  // reductions: inversion counters and the CFL rate
-  const unsigned lane = threadIdx.x & 31u;
+  reduce_outputs(a, cnt, rate_max);
+}
+
+// Coarse-fine flux correction: each listed coarse cell trades the coarse flux
+// through a face bordering finer blocks for the mean of the fine fluxes that
+// cover it (U += f dt (F_fine - F_coarse) / dx, sign by side, f = 1 in stage 1
+// and 1/2 in stage 2), then is inverted like every other cell.
+template <typename T, int DIM, bool FLAT>
+__global__ void __launch_bounds__(128) reflux_kernel(StageArgs a) {
+  const double dt = stage_dt(a);
+  const double f = a.stage == 1 ? 1.0 : 0.5;
+  unsigned cnt[4] = {0u, 0u, 0u, 0u};
+  double rate_max = 0.0;
+  const int n = a.nrcells;
+  const int nthreads = gridDim.x * blockDim.x;
+  const int rounds = (n + nthreads - 1) / nthreads;
+  for (int r = 0; r < rounds; ++r) {
+    const int t = r * nthreads + blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) continue;
+    const RefluxCell rc = a.rcells[t];
+    const LevelGeo geo = level_geo(a, rc.level);
+    const size_t ub = (size_t)rc.b * NV * a.nint + rc.ci;
+    double U[NV];
 #pragma unroll
-  for (int s = 0; s < 4; ++s) {
-    const unsigned tot = __reduce_add_sync(0xffffffffu, cnt[s]);
-    if (lane == 0 && tot) atomicAdd(a.counts + s, (unsigned long long)tot);
+    for (int v = 0; v < NV; ++v) U[v] = a.Uout[ub + (size_t)v * a.nint];
+    for (int q = 0; q < rc.nterm; ++q) {
+      const RefluxTerm T_ = a.rterms[rc.term0 + q];
+      const double w = f * dt * geo.idx[T_.d] * (double)T_.sign;
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        double acc = 0.0;
+        for (int m = 0; m < T_.nfine; ++m) acc += a.reg[T_.fine[m] + (long long)v * T_.fstride];
+        const double Ff = acc / T_.nfine;
+        const double Fc = a.reg[T_.coarse + (long long)v * T_.cstride];
+        U[v] += w * (Ff - Fc);
+      }
+    }
+    finish_cell<T, DIM, FLAT>(a, geo, rc.b, rc.ci, rc.cg, rc.I1, rc.I2, U, cnt, rate_max);
   }
-  if (a.stage == 2) {
-    const double w = warp_max_d(rate_max);
-    if (lane == 0) atomicMax(a.smax_out, (unsigned long long)__double_as_longlong(w));
-  }
+  reduce_outputs(a, cnt, rate_max);
 }
 
 // Stand-alone CFL rate reduction over interior cells (FP64 primitives).
@@ -589,6 +667,7 @@ __global__ void __launch_bounds__(256) cfl_kernel(StageArgs a) {
     const int ci = (int)(t - (long long)b * a.nint);
     const int i = ci % a.nx, j = (ci / a.nx) % a.ny, k = ci / (a.nx * a.ny);
     const int cg = ((k + a.gz) * a.Ny + (j + a.gy)) * a.Nx + (i + a.gx);
+    const LevelGeo geo = level_geo(a, a.blk[4 * b]);
     double P[NV];
     const double* Pd = a.P_in + (size_t)b * NV * a.ncell + cg;
 #pragma unroll
@@ -597,13 +676,13 @@ __global__ void __launch_bounds__(256) cfl_kernel(StageArgs a) {
     double acg[3] = {1.0, 1.0, 1.0};
     if (!FLAT) {
       const int I1 = a.blk[4 * b + 1] * a.nx + i, I2 = a.blk[4 * b + 2] * a.ny + j;
-      const double* crec = a.tab_c + (size_t)(I2 * a.N1g + I1) * CREC;
+      const double* crec = geo.tc + (size_t)(I2 * geo.N1 + I1) * CREC;
       m = load_centre_metric<double>(crec);
       acg[0] = crec[C_ACG1];
       acg[1] = crec[C_ACG2];
       acg[2] = crec[C_ACG3];
     }
-    rate_max = fmax(rate_max, cfl_rate<DIM>(m, acg, P, a));
+    rate_max = fmax(rate_max, cfl_rate_t<double, DIM>(m, acg, P, a.gam, a.gam_fac, a.ch, geo.idx));
   }
   const double w = warp_max_d(rate_max);
   if ((threadIdx.x & 31u) == 0) atomicMax(a.smax_out, (unsigned long long)__double_as_longlong(w));
@@ -635,6 +714,10 @@ static cudaError_t launch_stage_t(const StageArgs& a, int grid, int threads, siz
   cudaError_t e = configure_stage_t<T, DIM, FLAT>();
   if (e != cudaSuccess) return e;
   stage_kernel<T, DIM, FLAT><<<grid, threads, smem, st>>>(a);
+  e = cudaGetLastError();
+  if (e != cudaSuccess || a.nrcells == 0) return e;
+  int g = (a.nrcells + 127) / 128;
+  reflux_kernel<T, DIM, FLAT><<<g, 128, 0, st>>>(a);
   return cudaGetLastError();
 }
 

@@ -254,3 +254,53 @@ def test_cuda_graph_replay_is_bitwise_identical(gb):
     st.synchronize()
     assert np.array_equal(a.cons(), b.cons())
     assert np.array_equal(a.prims(), b.prims())
+
+
+# ---------------------------------------------------------------------------
+# block grids with several refinement levels
+# ---------------------------------------------------------------------------
+
+def _two_level_box():
+    blocks = [(0, 1, 0, 0), (0, 0, 1, 0), (0, 1, 1, 0)] + [(1, i, j, 0) for j in (0, 1) for i in (0, 1)]
+    return pb.periodic_box(ndim=2, nblock=16, nroot=2).with_(
+        nlevels=2, blocks=np.asarray(blocks, dtype=np.int32), kappa=0.5)
+
+
+def test_two_level_box_prolongation_restriction_reflux(gb):
+    """Flat periodic box with one refined quadrant: cross-level ghost values
+    and the coarse-fine flux correction, two steps."""
+    g = _two_level_box()
+    s, o, _ = one_step(gb, g, pb.random_periodic_prims(g, jump=True), steps=2)
+    assert_parity(s.cons(), o.cons(), TOL64, "two-level cons", g)
+    assert np.array_equal(s.diagnostics(), o.c2p_counts())
+
+
+def test_two_level_box_conserves(gb):
+    g = _two_level_box()
+    s = gb.Solver(g)
+    s.set_prims(pb.random_periodic_prims(g, jump=True))
+    vol = np.array([1.0 / 4 ** lev for lev in g.blocks[:, 0]])[:, None, None, None]
+    U0 = s.cons()
+    t0 = [np.sum(U0[:, v] * vol) for v in range(8)]
+    s.cfl_dt()
+    for _ in range(10):
+        s.step(0.0)
+    U = s.cons()
+    for v in range(8):
+        assert abs(np.sum(U[:, v] * vol) - t0[v]) <= 1e-13 * np.sum(np.abs(U0[:, v] * vol))
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", TOL64), ("mixed", TOLMIX)])
+def test_amr_torus_small(gb, precision, tol):
+    """Three-level torus (levels by radius, 8^3 blocks), one step."""
+    g = pb.amr_torus(root=(4, 2, 2), nblock=8)
+    s, o, _ = one_step(gb, g, pb.fm_torus_prims(g), precision=precision)
+    assert_parity(s.cons(), o.cons(), tol, f"amr torus {precision}", g)
+
+
+def test_amr_torus_full_size(gb):
+    """The batched uneven AMR workload: 4220 leaf blocks of 16^3 on three
+    levels (finest inside r < 20 M), one step, every block compared."""
+    g = pb.amr_torus()
+    s, o, _ = one_step(gb, g, pb.fm_torus_prims(g))
+    assert_parity(s.cons(), o.cons(), TOL64, "amr torus", g)
