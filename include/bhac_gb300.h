@@ -170,6 +170,34 @@ bhac_status bhac_graph_launch(bhac_ctx* ctx);
  * the ghost cells of the current state and synchronises the stream. */
 bhac_status bhac_count_flops(bhac_ctx* ctx, double dt, int nsamples, unsigned seed, double out[6]);
 
+/* Allocation-free CFL time step, for callers that cannot allocate device memory
+ * (no counterpart in the paper: it exists only because of how some callers run).
+ * Such callers include code that runs while another component captures the
+ * stream into a CUDA graph (allocation is not allowed there), hosts whose
+ * device memory is entirely owned by another allocator and that therefore hand
+ * this library no arena, and per-step diagnostics that must never enter an
+ * allocator because cudaMalloc can synchronise the device.
+ *
+ * Computes dt = cfl / max over interior cells of sum_d c_d / dx_d (the same
+ * rate as bhac_cfl_dt) for the FP64 interior primitives `prims` (device pointer,
+ * [block][var][k][j][i] as in bhac_set_prims) of the leaf blocks `blocks`, and
+ * writes it to the device word `dt`; no context, no arena.  The scratch (a copy
+ * of the block table and one partial maximum per block) is a pair of file-scope
+ * device arrays of this library sized for BHAC_STATIC_MAX_BLOCKS blocks (24 bytes
+ * each, 384 KiB in all), held by every GPU that loads the library until the
+ * process exits.  More blocks than that: BHAC_ERR_ARG, nothing launched.
+ *
+ * The first call on a device looks up the arrays' device addresses
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  Every call reuses the same arrays and leaves its
+ * contents there; each call writes every partial it reads, so nothing has to be
+ * cleared between calls.  Calls whose kernels overlap on the GPU (other streams,
+ * other threads) race on the arrays: serialise them.  Asynchronous on `stream`;
+ * the host block table is copied before the call returns. */
+#define BHAC_STATIC_MAX_BLOCKS 16384
+bhac_status bhac_cfl_dt_static(const bhac_grid_desc* desc, const bhac_block_desc* blocks, int nblocks,
+                               const double* prims, double* dt, void* cuda_stream);
+
 /* Releases the context (host memory only; the arena stays the caller's). */
 void bhac_destroy(bhac_ctx* ctx);
 

@@ -20,7 +20,7 @@ __all__ = [
     "GridDesc", "BlockDesc", "Solver", "BhacError", "lib", "status_string",
     "bhac_query_sizes", "bhac_init_grid", "bhac_set_metric", "bhac_set_prims", "bhac_fill_ghosts",
     "bhac_cfl_dt", "bhac_step", "bhac_stage", "bhac_get_prims", "bhac_get_cons", "bhac_get_diagnostics",
-    "bhac_set_launch", "bhac_count_flops", "bhac_graph_capture", "bhac_graph_launch", "bhac_destroy",
+    "bhac_set_launch", "bhac_count_flops", "bhac_graph_capture", "bhac_graph_launch", "bhac_cfl_dt_static", "bhac_destroy",
     "bhac_status_string",
 ]
 
@@ -85,6 +85,7 @@ def lib():
             "bhac_count_flops": ([vp, d, i, C.c_uint, C.POINTER(d)], i),
             "bhac_graph_capture": ([vp, i], i),
             "bhac_graph_launch": ([vp], i),
+            "bhac_cfl_dt_static": ([G, B, i, vp, vp, vp], i),
             "bhac_destroy": ([vp], None),
             "bhac_status_string": ([i], C.c_char_p),
         }
@@ -178,6 +179,12 @@ def bhac_graph_capture(ctx, nsteps: int):
 
 def bhac_graph_launch(ctx):
     return _check("bhac_graph_launch", lib().bhac_graph_launch(ctx))
+
+
+def bhac_cfl_dt_static(desc: GridDesc, blocks, prims_ptr: int, dt_ptr: int, stream_ptr: int):
+    """Allocation-free CFL step: device primitives in, device dt out."""
+    return _check("bhac_cfl_dt_static", lib().bhac_cfl_dt_static(
+        C.byref(desc), blocks, len(blocks), C.c_void_p(prims_ptr), C.c_void_p(dt_ptr), C.c_void_p(stream_ptr)))
 
 
 def bhac_destroy(ctx):
