@@ -46,6 +46,9 @@ def workload(name: str):
     if name == "torus_3d_large":
         g = pb.torus_3d_large()
         desc = "3-D FM torus, Kerr a=0.9375, MKS, 512x256x256 cells as 2048 blocks of 32x32x16 (+3 ghosts)"
+    elif name == "torus_3d_mid":
+        g = pb.torus_3d_large(cells=(256, 128, 128))
+        desc = "3-D FM torus, Kerr a=0.9375, MKS, 256x128x128 cells as 256 blocks of 32x32x16 (+3 ghosts)"
     elif name == "torus_3d":
         g = pb.torus_3d()
         desc = "3-D FM torus, Kerr a=0.9375, MKS, 192x96x96 cells as 432 blocks of 16^3 (+3 ghosts)"
@@ -132,9 +135,34 @@ class Clocks:
                 "reasons": reasons, "samples": len(self.rows)}
 
 
+def aggregate_ms(ms: float, dist, device) -> float:
+    """Slowest rank's time: every rank runs its own replica of the workload
+    (the update has no exchange between GPUs), so the job takes the max."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(cells: int, world: int, ms_per_step: float) -> float:
+    """Zone-updates per second of the whole job: world replicas x cells x 2 stages."""
+    return cells * 2 * world / (ms_per_step * 1e-3)
+
+
+TUNE = True
+
+
 def time_form(gb, torch, g, P, form, steps, warmup, stream, count_flops=True):
     """Device-resident timing of `steps` steps of one form."""
+    from paper_2108_12240_gb300 import autotune
+
     s = gb.Solver(g, form, stream=stream)
+    if TUNE:
+        shape, tried = autotune.tune(s, P)  # launch shape for this grid and form (outside the timed region)
+    else:
+        shape, tried = autotune.cached_or_default(s), {}
     s.set_prims(P)
     dt = s.cfl_dt()
     for _ in range(warmup):
@@ -166,7 +194,10 @@ def time_form(gb, torch, g, P, form, steps, warmup, stream, count_flops=True):
     torch.cuda.synchronize()
     fill_ms = fe[0].elapsed_time(fe[1]) / steps
     out = {"ms_per_step": total_ms / steps, "stage_ms_mean": sum(stage_ms) / len(stage_ms) - fill_ms,
-           "fill_ms": fill_ms}
+           "fill_ms": fill_ms, "launch_shape": {"tx": shape[0], "ty": shape[1], "threads": shape[2],
+                                                 "persistent": shape[3], "min_ctas": shape[4],
+                                                 "producer_warps": shape[5] if len(shape) > 5 else 0,
+                                                 "candidates_timed": len(tried)}}
     out["c2p_counts"] = [int(x) for x in s.diagnostics()]
     if count_flops:
         out["flops"] = s.count_flops(max(dt, 1e-30), nsamples=4000, seed=7)
@@ -264,6 +295,33 @@ def reference_arm(args, rank):
     print(json.dumps(line), flush=True)
 
 
+def sweep_blocks(args):
+    """The 512x256x256 torus in several block shapes (8^3 to 32^3): zone-updates/s
+    and FP64 roofline fraction per shape and form, one JSON line."""
+    import torch
+
+    import paper_2108_12240_gb300 as gb
+
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    rows = []
+    for nb in [(8, 8, 8), (16, 16, 16), (32, 32, 16), (32, 32, 32)]:
+        g = pb.torus_3d_large(nblock=nb)
+        P = initial_prims(g)
+        for form in ("mixed", "fp64"):
+            r = time_form(gb, torch, g, P, form, args.steps, args.warmup, stream)
+            stage_s = r["stage_ms_mean"] * 1e-3
+            ach = r["flops"]["fp64_flops"] * g.ncells / stage_s / 1e12
+            rows.append({"block": "x".join(map(str, nb)), "blocks": g.nb, "form": form,
+                         "zone_updates_per_s": job_value(g.ncells, 1, r["ms_per_step"]),
+                         "stage_ms": r["stage_ms_mean"], "ghost_fill_ms": r["fill_ms"],
+                         "fp64_flops_per_zone_stage": r["flops"]["fp64_flops"],
+                         "fp64_frac": ach / FP64_PEAK_TFLOPS, "launch_shape": r["launch_shape"]})
+            print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+        del P
+    print(json.dumps({"sweep": "block shape", "workload": "512x256x256 torus", "rows": rows}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -274,7 +332,14 @@ def main():
     ap.add_argument("--form", default="both", choices=["both", "mixed", "fp64"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--sweep-blocks", action="store_true", help="block-shape roofline sweep instead of the bench line")
+    ap.add_argument("--no-tune", action="store_true", help="use the cached launch shape (or the default) without timing candidates")
     args = ap.parse_args()
+    global TUNE
+    TUNE = not args.no_tune
+    if args.sweep_blocks:
+        sweep_blocks(args)
+        return
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -314,12 +379,9 @@ def main():
         with Clocks(local) as ck:
             results[form] = time_form(gb, torch, g, P, form, args.steps, args.warmup, stream)
         results[form]["clocks"] = ck.summary()
-        if dist:
-            t = torch.tensor([results[form]["ms_per_step"]], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            results[form]["ms_per_step"] = float(t.item())
+        results[form]["ms_per_step"] = aggregate_ms(results[form]["ms_per_step"], dist, "cuda")
         # each rank advances its own full replica (weak scaling)
-        results[form]["value"] = g.ncells * 2 * world / (results[form]["ms_per_step"] * 1e-3)
+        results[form]["value"] = job_value(g.ncells, world, results[form]["ms_per_step"])
     head = forms[0]
     e2e = None
     if not args.no_e2e:
@@ -358,9 +420,10 @@ def main():
         "data": "synthetic (seeded Fishbone-Moncrief torus)",
         "config": {"workload": desc, "form": head, "replicas": world,
                    "l2": "inputs larger than L2 (state ~17 GB), no flush",
-                   "launch": "per step: ghost fill + stage kernel, twice; device dt"},
+                   "launch": "per step: ghost fill + stage kernel, twice; device dt; shape by autotuner"},
         "forms": {f: {"value": results[f]["value"], "ms_per_step": results[f]["ms_per_step"],
                       "roofline": roofline(f), "c2p_counts": results[f]["c2p_counts"],
+                      "launch_shape": results[f]["launch_shape"],
                       "clocks": results[f]["clocks"]} for f in forms},
         "roofline": roofline(head),
         "cpu_baseline": cpu,

@@ -143,10 +143,18 @@ bhac_status bhac_get_cons(bhac_ctx* ctx, double* out, int on_device);
  * [3] failed (previous primitives kept).  Synchronises the stream. */
 bhac_status bhac_get_diagnostics(bhac_ctx* ctx, long long counts[4]);
 
-/* Kernel launch shape of the stage kernel: tile of tx x ty cells per CTA column,
- * threads per CTA, and persistent = 1 for one CTA per SM slot pulling tiles from
- * a device work counter.  Values 0 keep the current setting. */
-bhac_status bhac_set_launch(bhac_ctx* ctx, int tx, int ty, int threads, int persistent);
+/* Kernel launch shape of the stage kernel: tile of tx x ty cells per CTA column
+ * (must divide the block), threads per CTA (a multiple of 32, at most 256),
+ * persistent = k > 0 for k CTAs per SM pulling (block, tile) items from a device
+ * work counter (0: one CTA per item), and min_ctas = 1 or 2: the register bound
+ * the 3-D kernel is compiled for (2 trades a few spilled registers for two
+ * resident CTAs per SM), and producer_warps = p > 0 (3-D only, p * 32 < threads)
+ * for the warp-specialised form: p warps compute the next plane's face fluxes
+ * while the others update the current plane's cells (0: the phased form).
+ * tx, ty, threads, min_ctas = 0 keep the current setting.  Results do not
+ * depend on the launch shape. */
+bhac_status bhac_set_launch(bhac_ctx* ctx, int tx, int ty, int threads, int persistent, int min_ctas,
+                            int producer_warps);
 
 /* Records `nsteps` steps with the device time step (bhac_step(ctx, 0.0)) into a
  * CUDA graph on the context's stream and instantiates it; bhac_graph_launch()

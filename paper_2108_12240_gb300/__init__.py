@@ -81,7 +81,7 @@ def lib():
             "bhac_get_prims": ([vp, vp, i], i),
             "bhac_get_cons": ([vp, vp, i], i),
             "bhac_get_diagnostics": ([vp, C.POINTER(C.c_longlong)], i),
-            "bhac_set_launch": ([vp, i, i, i, i], i),
+            "bhac_set_launch": ([vp, i, i, i, i, i, i], i),
             "bhac_count_flops": ([vp, d, i, C.c_uint, C.POINTER(d)], i),
             "bhac_graph_capture": ([vp, i], i),
             "bhac_graph_launch": ([vp], i),
@@ -162,8 +162,9 @@ def bhac_get_diagnostics(ctx):
     return np.array(list(out), dtype=np.int64), st
 
 
-def bhac_set_launch(ctx, tx=0, ty=0, threads=0, persistent=0):
-    return _check("bhac_set_launch", lib().bhac_set_launch(ctx, tx, ty, threads, persistent))
+def bhac_set_launch(ctx, tx=0, ty=0, threads=0, persistent=0, min_ctas=0, producer_warps=0):
+    return _check("bhac_set_launch", lib().bhac_set_launch(ctx, tx, ty, threads, persistent, min_ctas,
+                                                           producer_warps))
 
 
 def bhac_count_flops(ctx, dt: float, nsamples: int = 2000, seed: int = 1):
@@ -320,8 +321,8 @@ class Solver:
     def replay(self):
         bhac_graph_launch(self.ctx)
 
-    def set_launch(self, tx=0, ty=0, threads=0, persistent=0):
-        bhac_set_launch(self.ctx, tx, ty, threads, persistent)
+    def set_launch(self, tx=0, ty=0, threads=0, persistent=0, min_ctas=0, producer_warps=0):
+        bhac_set_launch(self.ctx, tx, ty, threads, persistent, min_ctas, producer_warps)
 
 
 # Fail loudly at import if the library cannot be loaded.

@@ -4,6 +4,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "ctx.h"
@@ -13,7 +14,7 @@ using namespace bhac;
 namespace {
 
 struct Layout {
-  size_t off_blk, off_src, off_flags, off_tmpl, off_tc, off_tf1, off_tf2, off_tc32, off_tf1_32, off_tf2_32;
+  size_t off_blk, off_order, off_src, off_flags, off_tmpl, off_tc, off_tf1, off_tf2, off_tc32, off_tf1_32, off_tf2_32;
   size_t off_P[2], off_P32[2], off_U[2], off_scratch, off_small;
   size_t off_nodes, off_ops, off_nodeval, off_cf, off_regoff, off_reg, off_rcells, off_rterms, total;
   long long toff_c[MAXLEV], toff_f1[MAXLEV], toff_f2[MAXLEV];
@@ -95,6 +96,7 @@ Layout layout(const bhac_grid_desc* d, int nb, const HostMaps& M) {
     return at;
   };
   L.off_blk = take(sizeof(int) * 4 * nb);
+  L.off_order = take(sizeof(int) * nb);
   L.off_src = take(sizeof(int) * (size_t)nb * nslots);
   L.off_flags = take((size_t)nb * nslots);
   L.off_tmpl = take(sizeof(int) * (size_t)nslots);
@@ -148,7 +150,10 @@ StageArgs base_args(const bhac_ctx* c) {
   a.nblocks = c->nb;
   a.nitems = c->nb * a.ntx * a.nty;
   a.persistent = c->persistent;
+  a.minb = c->minb;
+  a.pwarps = c->pwarps;
   a.blk = c->d_blk;
+  a.order = c->d_order;
   for (int k = 0; k < 3; ++k) {
     a.dxl0[k] = (d.xmax[k] - d.xmin[k]) / ((double)d.nroot[k] * d.nx[k]);
     a.idx[k] = 1.0 / a.dxl0[k];
@@ -196,6 +201,18 @@ StageArgs base_args(const bhac_ctx* c) {
   a.rterms = c->d_rterms;
   a.nrcells = c->nrcells;
   return a;
+}
+
+// Shared memory of the stage kernel: face fluxes of one plane (x, y and two
+// z-face planes), or in the warp-specialised form two planes of x and y faces
+// and three z-face planes.
+size_t stage_smem(const bhac_ctx* c, int tx, int ty, int pwarps) {
+  const size_t tsz = c->mixed ? sizeof(float) : sizeof(double);
+  const size_t sFx = (size_t)ty * (tx + 1), sFy = (size_t)(ty + 1) * tx, sFz = (size_t)tx * ty;
+  if (c->d.ndim == 3 && pwarps > 0) return NV * (2 * sFx + 2 * sFy + 3 * sFz) * tsz;
+  size_t smem = NV * (sFx + sFy) * tsz;
+  if (c->d.ndim == 3) smem += 2 * NV * sFz * tsz;
+  return smem;
 }
 
 bhac_status ghost_fill(bhac_ctx* c, int buf, bool zero_smax) {
@@ -249,10 +266,7 @@ bhac_status run_stage(bhac_ctx* c, int stage, double dt) {
     a.U1 = c->U[c->ucur];      // after stage 1
     a.Uout = c->U[1 - c->ucur];
   }
-  const size_t tsz = c->mixed ? sizeof(float) : sizeof(double);
-  const size_t sFx = (size_t)c->ty * (c->tx + 1), sFy = (size_t)(c->ty + 1) * c->tx, sFz = (size_t)c->tx * c->ty;
-  size_t smem = NV * (sFx + sFy) * tsz;
-  if (c->d.ndim == 3) smem += 2 * NV * sFz * tsz;
+  const size_t smem = stage_smem(c, c->tx, c->ty, c->pwarps);
   int grid = a.nitems;
   if (c->persistent) {
     int dev = 0, nsm = 0;
@@ -316,6 +330,7 @@ bhac_status bhac_init_grid(bhac_ctx** out, const bhac_grid_desc* d, const bhac_b
   c->arena = (char*)arena;
   c->arena_bytes = arena_bytes;
   c->d_blk = (int*)(c->arena + L.off_blk);
+  c->d_order = (int*)(c->arena + L.off_order);
   c->d_src = (int*)(c->arena + L.off_src);
   c->d_flags = (unsigned char*)(c->arena + L.off_flags);
   c->d_tmpl = (int*)(c->arena + L.off_tmpl);
@@ -356,10 +371,12 @@ bhac_status bhac_init_grid(bhac_ctx** out, const bhac_grid_desc* d, const bhac_b
   c->cur = 0;
   c->ucur = 0;
   // default launch shape: 16 x 16 columns where they divide the block
-  c->tx = d->nx[0] % 16 == 0 ? 16 : d->nx[0];
+  c->tx = d->nx[0] % 32 == 0 ? 32 : (d->nx[0] % 16 == 0 ? 16 : d->nx[0]);
   c->ty = d->nx[1] % 16 == 0 ? 16 : d->nx[1];
   c->threads = 256;
   c->persistent = 0;
+  c->minb = 1;
+  c->pwarps = 0;
   c->graph = nullptr;
   c->graph_steps = 0;
   c->blk.resize(4 * nb);
@@ -369,10 +386,23 @@ bhac_status bhac_init_grid(bhac_ctx** out, const bhac_grid_desc* d, const bhac_b
     c->blk[4 * i + 2] = b[i].iy;
     c->blk[4 * i + 3] = b[i].iz;
   }
+  // visiting order: finest level first, then by x2 and x1 with x3 fastest, so
+  // the CTAs in flight share the phi-independent metric records in L2
+  std::vector<int> order(nb);
+  for (int i = 0; i < nb; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int p, int q) {
+    const int* x = &c->blk[4 * p];
+    const int* y = &c->blk[4 * q];
+    if (x[0] != y[0]) return x[0] > y[0];
+    if (x[2] != y[2]) return x[2] < y[2];
+    if (x[1] != y[1]) return x[1] < y[1];
+    return x[3] < y[3];
+  });
   auto up = [&](void* dst, const void* src, size_t bytes) {
     return bytes ? cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, c->st) : cudaSuccess;
   };
   cudaError_t e = up(c->d_blk, c->blk.data(), sizeof(int) * 4 * nb);
+  if (e == cudaSuccess) e = up(c->d_order, order.data(), sizeof(int) * nb);
   if (e == cudaSuccess) e = up(c->d_src, M.src.data(), sizeof(int) * M.src.size());
   if (e == cudaSuccess) e = up(c->d_flags, M.flags.data(), M.flags.size());
   if (e == cudaSuccess) e = up(c->d_tmpl, M.tmpl.data(), sizeof(int) * M.tmpl.size());
@@ -531,15 +561,18 @@ bhac_status bhac_get_diagnostics(bhac_ctx* c, long long counts[4]) {
   return h[3] ? BHAC_WARN_C2P : BHAC_OK;
 }
 
-bhac_status bhac_set_launch(bhac_ctx* c, int tx, int ty, int threads, int persistent) {
-  if (!c) return BHAC_ERR_ARG;
+bhac_status bhac_set_launch(bhac_ctx* c, int tx, int ty, int threads, int persistent, int min_ctas,
+                            int producer_warps) {
+  if (!c || min_ctas < 0 || min_ctas > 2 || producer_warps < 0) return BHAC_ERR_ARG;
+  if (producer_warps > 0 && (c->d.ndim != 3 || producer_warps * 32 >= (threads > 0 ? threads : c->threads)))
+    return BHAC_ERR_ARG;
   const int ntx = tx > 0 ? tx : c->tx, nty = ty > 0 ? ty : c->ty, nth = threads > 0 ? threads : c->threads;
   if (c->d.nx[0] % ntx || c->d.nx[1] % nty || nth % 32 || nth > 256 || persistent < 0 || persistent > 8)
     return BHAC_ERR_ARG;
-  const size_t tsz = c->mixed ? sizeof(float) : sizeof(double);
-  size_t smem = NV * ((size_t)nty * (ntx + 1) + (size_t)(nty + 1) * ntx) * tsz;
-  if (c->d.ndim == 3) smem += 2 * NV * (size_t)ntx * nty * tsz;
+  const size_t smem = stage_smem(c, ntx, nty, producer_warps);
   if (smem > 200 * 1024) return BHAC_ERR_ARG;
+  if (min_ctas > 0) c->minb = min_ctas;
+  c->pwarps = producer_warps;
   c->tx = ntx;
   c->ty = nty;
   c->threads = nth;

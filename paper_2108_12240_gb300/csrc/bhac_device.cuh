@@ -42,7 +42,10 @@ struct StageArgs {
   int tx, ty, ntx, nty;  // CTA column tile and tiles per block
   int nblocks, nitems;
   int persistent;
+  int minb;              // register bound of the 3-D stage kernel: 1 or 2 CTAs per SM
+  int pwarps;            // 3-D: warps that produce face fluxes while the others update cells (0: phased)
   const int* blk;        // nblocks x 4: level, bx, by, bz
+  const int* order;      // visiting order of the blocks (items run through it)
   double idx[3];         // 1/dx at level 0 per dimension
   double dxl0[3];        // dx at level 0
   int N1g, N2g;          // level-0 global cells along x1 and x2 (table extents)
@@ -250,24 +253,27 @@ BHAC_HD void flux_of(const Met<T>& m, const T* P, const Derived<T>& s, const T* 
 }
 
 // Fast-magnetosonic bound in the Eulerian frame (Del Zanna et al. 2007):
-// a^2 = cs^2 + ca^2 - cs^2 ca^2, boosted by v and shifted by beta.
+// a^2 = cs^2 + ca^2 - cs^2 ca^2, boosted by v and shifted by beta.  With
+// cs^2 = Gamma p / (rho h) and ca^2 = b^2 / (rho h + b^2) this is
+// a^2 = G / E, G = Gamma p + b^2, E = rho h + b^2, so with R = E - v^2 G
+//   lambda = alpha [v^d (E - G) +- sqrt(G (1 - v^2) (gamma^dd R - v^d v^d (E - G)))] / R - beta^d,
+// one reciprocal and one square root per state.
 template <typename T>
-BHAC_HD void speeds_of(const Met<T>& m, const T* P, const Derived<T>& s, int d, T gam,
-                                          T& lm, T& lp) {
-  const T inv = rcp_t(s.rhoh * (s.rhoh + s.b2));
-  const T cs2 = gam * P[PRS] * (s.rhoh + s.b2) * inv;
-  const T ca2 = s.b2 * s.rhoh * inv;
-  const T a2 = cs2 + ca2 - cs2 * ca2;
+BHAC_HD void speeds_of(const Met<T>& m, const T* P, const Derived<T>& s, int d, T gam, T& lm, T& lp) {
+  const T E = s.rhoh + s.b2;
+  const T G = gam * P[PRS] + s.b2;
+  const T R = E - s.vsq * G;
+  const T EG = E - G;
   const T vd = sel3(d, s.v1, s.v2, s.v3);
   const T gidd = sel3(d, m.gi11, m.gi22, m.gi33);
-  T disc = a2 * (T(1) - s.vsq) * (gidd * (T(1) - s.vsq * a2) - vd * vd * (T(1) - a2));
+  T disc = G * (T(1) - s.vsq) * (gidd * R - vd * vd * EG);
   disc = disc > T(0) ? disc : T(0);
   const T sq = sqrt_t(disc);
-  const T iden = rcp_t(T(1) - s.vsq * a2);
+  const T ir = rcp_t(R);
   const T bed = d == 0 ? m.be1 : T(0);
-  const T c = vd * (T(1) - a2);
-  lp = m.al * (c + sq) * iden - bed;
-  lm = m.al * (c - sq) * iden - bed;
+  const T c = vd * EG;
+  lp = m.al * (c + sq) * ir - bed;
+  lm = m.al * (c - sq) * ir - bed;
 }
 
 // ----------------------------------------------------------------------------

@@ -22,6 +22,7 @@ struct bhac_ctx {
   char* arena;
   size_t arena_bytes;
   int* d_blk;
+  int* d_order;
   int* d_src;
   unsigned char* d_flags;
   int* d_tmpl;
@@ -40,7 +41,7 @@ struct bhac_ctx {
   int ucur;      // conserved buffer holding the current state
   bool metric_ok, prims_ok, cfl_ok;
   // launch shape
-  int tx, ty, threads, persistent;
+  int tx, ty, threads, persistent, minb, pwarps;
   // refinement levels: metric-table record offsets per level
   long long toff_c[bhac::MAXLEV], toff_f1[bhac::MAXLEV], toff_f2[bhac::MAXLEV];
   // cross-level ghost nodes (evaluated depth by depth) and flux correction
@@ -64,3 +65,4 @@ struct bhac_ctx {
 // Shared helpers of the ABI units (api.cu).
 bhac::StageArgs base_args(const bhac_ctx* c);
 bhac_status ghost_fill(bhac_ctx* c, int buf, bool zero_smax);
+size_t stage_smem(const bhac_ctx* c, int tx, int ty, int pwarps);

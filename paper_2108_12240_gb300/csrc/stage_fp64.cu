@@ -4,11 +4,7 @@
 namespace bhac {
 
 cudaError_t launch_stage_fp64(const StageArgs& a, int grid, int threads, size_t smem, cudaStream_t st) {
-  if (a.ndim == 3)
-    return a.flat ? launch_stage_t<double, 3, true>(a, grid, threads, smem, st)
-                  : launch_stage_t<double, 3, false>(a, grid, threads, smem, st);
-  return a.flat ? launch_stage_t<double, 2, true>(a, grid, threads, smem, st)
-                : launch_stage_t<double, 2, false>(a, grid, threads, smem, st);
+  return launch_stage_any<double>(a, grid, threads, smem, st);
 }
 
 cudaError_t prepare_stage_fp64() { return configure_all_t<double>(); }

@@ -245,6 +245,13 @@ static __device__ __noinline__ int con2prim(const Met<double>& m, const double* 
 template <typename T, int DIM>
 BHAC_HD T cfl_rate_t(const Met<T>& m, const T* acg, const T* P, double gam, double gam_fac, double ch,
                      const double* idx) {
+  if (ch >= 1.0) {
+    // The fast-magnetosonic bound boosts a comoving speed a < 1 and so never
+    // leaves the light cone: with ch >= 1 the cleaning speed is the largest.
+    T rate = T(0.0);
+    for (int d = 0; d < DIM; ++d) rate = rate + (T(ch) * acg[d] + (d == 0 ? abs_t(m.be1) : T(0.0))) * T(idx[d]);
+    return rate;
+  }
   Derived<T> s;
   derive(m, P, T(gam_fac), s);
   T rate = T(0.0);
@@ -287,9 +294,12 @@ BHAC_HD void riemann_flux(const Met<T>& m, T acg, const T* PL, const T* PR, int 
     lm = lmL < lm ? lmL : lm;
     lm = lmR < lm ? lmR : lm;
     const T lpg = lgp > lp ? lgp : lp, lmg = lgm < lm ? lgm : lm;
-    const bool okh = lp - lm > T(0), okg = lpg - lmg > T(0);
-    const T ih = okh ? rcp_t(lp - lm) : T(0);
-    const T ihg = okg ? rcp_t(lpg - lmg) : T(0);
+    const T wh = lp - lm, wg = lpg - lmg;
+    const bool okh = wh > T(0), okg = wg > T(0);
+    // both fan widths' reciprocals from one division
+    const T r = okh && okg ? rcp_t(wh * wg) : T(0);
+    const T ih = okh ? (okg ? wg * r : rcp_t(wh)) : T(0);
+    const T ihg = okg ? (okh ? wh * r : rcp_t(wg)) : T(0);
     cons_of(PL, sL, U);
     flux_of(m, PL, sL, U, d, ch2, F);
     T FL[NV];
@@ -469,12 +479,88 @@ __device__ __forceinline__ void reduce_outputs(const StageArgs& a, const unsigne
   }
 }
 
+// Divergence of the face fluxes staged in shared memory, sources, RK stage
+// combination and (unless the reflux pass owns the cell) the inversion of cell
+// c of plane k in the tile at (x0, y0) of block b.
+template <typename T, int DIM, bool FLAT>
+__device__ __forceinline__ void cell_update(const StageArgs& a, const LevelGeo& geo, const T* __restrict__ Pb, int b,
+                                            int x0, int y0, int k, int c, const T* Fx, const T* Fy, const T* Fz0,
+                                            const T* Fz1, double dt, unsigned cfb, unsigned cnt[4],
+                                            double& rate_max) {
+  const int tx = a.tx, ty = a.ty;
+  const int sFx = ty * (tx + 1), sFy = (ty + 1) * tx, sFz = tx * ty;
+  const int kg = k + a.gz;
+  const int I1b = a.blk[4 * b + 1] * a.nx + x0, I2b = a.blk[4 * b + 2] * a.ny + y0;
+  const int i = c % tx, j = c / tx;
+  const int ig = i + x0 + a.gx, jg = j + y0 + a.gy;
+  const int cg = (kg * a.Ny + jg) * a.Nx + ig;
+  const int ci = (k * a.ny + (j + y0)) * a.nx + (i + x0);
+  const int I1 = I1b + i, I2 = I2b + j;
+  double rhs[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    double r = -((double)Fx[v * sFx + j * (tx + 1) + i + 1] - (double)Fx[v * sFx + j * (tx + 1) + i]) * geo.idx[0];
+    r += -((double)Fy[v * sFy + (j + 1) * tx + i] - (double)Fy[v * sFy + j * tx + i]) * geo.idx[1];
+    if (DIM == 3) r += -((double)Fz1[v * sFz + c] - (double)Fz0[v * sFz + c]) * geo.idx[2];
+    rhs[v] = r;
+  }
+  // sources from the cell's primitives
+  {
+    T Pc[NV], Uc[NV], S[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) Pc[v] = Pb[(size_t)v * a.ncell + cg];
+    if (FLAT) {
+      rhs[PSI] += to_double(-T(a.kappa) * Pc[PSI]);
+    } else {
+      const double* crec = geo.tc + (size_t)(I2 * geo.N1 + I1) * CREC;
+      Met<T> m;
+      if (sizeof(T) == 8) {
+        m = load_centre_metric<T>(crec);
+      } else {
+        m = load_centre_metric<T>(geo.tc32 + (size_t)(I2 * geo.N1 + I1) * CREC);
+      }
+      Derived<T> s;
+      derive(m, Pc, T(a.gam_fac), s);
+      cons_of(Pc, s, Uc);
+      if (sizeof(T) == 8)
+        sources_of(m, crec, Pc, s, Uc, T(a.kappa), T(a.ch * a.ch), S);
+      else
+        sources_of(m, geo.tc32 + (size_t)(I2 * geo.N1 + I1) * CREC, Pc, s, Uc, T(a.kappa), T(a.ch * a.ch),
+                   S);
+      const double sg = crec[C_SG];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) rhs[v] += sg * (double)S[v];
+    }
+  }
+  // RK combination
+  const size_t ub = (size_t)b * NV * a.nint + ci;
+  double U[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    const double un = a.Un[ub + (size_t)v * a.nint];
+    if (a.stage == 1)
+      U[v] = un + dt * rhs[v];
+    else
+      U[v] = 0.5 * un + 0.5 * (a.U1[ub + (size_t)v * a.nint] + dt * rhs[v]);
+  }
+  // cells next to a face bordering finer blocks are finished by the reflux pass
+  const bool later = cfb && (((cfb & 1u) && x0 + i == 0) || ((cfb & 2u) && x0 + i == a.nx - 1) ||
+                             ((cfb & 4u) && y0 + j == 0) || ((cfb & 8u) && y0 + j == a.ny - 1) ||
+                             ((cfb & 16u) && k == 0) || ((cfb & 32u) && k == a.nz - 1));
+  if (later) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) a.Uout[ub + (size_t)v * a.nint] = U[v];
+  } else {
+    finish_cell<T, DIM, FLAT>(a, geo, b, ci, cg, I1, I2, U, cnt, rate_max);
+  }
+}
+
 // ----------------------------------------------------------------------------
 // The stage kernel.  T: flux arithmetic (double: FP64 form; float: mixed form).
 // Every block of every level is an item of the same launch.
 // ----------------------------------------------------------------------------
-template <typename T, int DIM, bool FLAT>
-__global__ void __launch_bounds__(256) stage_kernel(StageArgs a) {
+template <typename T, int DIM, bool FLAT, int MINB>
+__global__ void __launch_bounds__(256, MINB) stage_kernel(StageArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int tx = a.tx, ty = a.ty;
   const int sFx = ty * (tx + 1), sFy = (ty + 1) * tx, sFz = tx * ty;
@@ -501,8 +587,9 @@ __global__ void __launch_bounds__(256) stage_kernel(StageArgs a) {
       item = s_item;
     }
     if (item >= a.nitems) break;
-    const int b = item / ntile;
-    const int tile = item - b * ntile;
+    const int ord = item / ntile;
+    const int b = a.order[ord];
+    const int tile = item - ord * ntile;
     const int x0 = (tile % a.ntx) * tx, y0 = (tile / a.ntx) * ty;
     const int L = a.blk[4 * b];
     const LevelGeo geo = level_geo(a, L);
@@ -544,74 +631,134 @@ __global__ void __launch_bounds__(256) stage_kernel(StageArgs a) {
         }
       }
       __syncthreads();
-      for (int c = threadIdx.x; c < sFz; c += blockDim.x) {
-        const int i = c % tx, j = c / tx;
-        const int ig = i + x0 + a.gx, jg = j + y0 + a.gy;
-        const int cg = (kg * a.Ny + jg) * a.Nx + ig;
-        const int ci = (k * a.ny + (j + y0)) * a.nx + (i + x0);
-        const int I1 = I1b + i, I2 = I2b + j;
-        double rhs[NV];
-#pragma unroll
-        for (int v = 0; v < NV; ++v) {
-          double r = -((double)Fx[v * sFx + j * (tx + 1) + i + 1] - (double)Fx[v * sFx + j * (tx + 1) + i]) * geo.idx[0];
-          r += -((double)Fy[v * sFy + (j + 1) * tx + i] - (double)Fy[v * sFy + j * tx + i]) * geo.idx[1];
-          if (DIM == 3) r += -((double)Fz1[v * sFz + c] - (double)Fz0[v * sFz + c]) * geo.idx[2];
-          rhs[v] = r;
-        }
-        // sources from the cell's primitives
-        {
-          T Pc[NV], Uc[NV], S[NV];
-#pragma unroll
-          for (int v = 0; v < NV; ++v) Pc[v] = Pb[(size_t)v * a.ncell + cg];
-          if (FLAT) {
-            rhs[PSI] += to_double(-T(a.kappa) * Pc[PSI]);
-          } else {
-            const double* crec = geo.tc + (size_t)(I2 * geo.N1 + I1) * CREC;
-            Met<T> m;
-            if (sizeof(T) == 8) {
-              m = load_centre_metric<T>(crec);
-            } else {
-              m = load_centre_metric<T>(geo.tc32 + (size_t)(I2 * geo.N1 + I1) * CREC);
-            }
-            Derived<T> s;
-            derive(m, Pc, T(a.gam_fac), s);
-            cons_of(Pc, s, Uc);
-            if (sizeof(T) == 8)
-              sources_of(m, crec, Pc, s, Uc, T(a.kappa), T(a.ch * a.ch), S);
-            else
-              sources_of(m, geo.tc32 + (size_t)(I2 * geo.N1 + I1) * CREC, Pc, s, Uc, T(a.kappa), T(a.ch * a.ch),
-                         S);
-            const double sg = crec[C_SG];
-#pragma unroll
-            for (int v = 0; v < NV; ++v) rhs[v] += sg * (double)S[v];
-          }
-        }
-        // RK combination
-        const size_t ub = (size_t)b * NV * a.nint + ci;
-        double U[NV];
-#pragma unroll
-        for (int v = 0; v < NV; ++v) {
-          const double un = a.Un[ub + (size_t)v * a.nint];
-          if (a.stage == 1)
-            U[v] = un + dt * rhs[v];
-          else
-            U[v] = 0.5 * un + 0.5 * (a.U1[ub + (size_t)v * a.nint] + dt * rhs[v]);
-        }
-        // cells next to a face bordering finer blocks are finished by the reflux pass
-        const bool later = cfb && (((cfb & 1u) && x0 + i == 0) || ((cfb & 2u) && x0 + i == a.nx - 1) ||
-                                   ((cfb & 4u) && y0 + j == 0) || ((cfb & 8u) && y0 + j == a.ny - 1) ||
-                                   ((cfb & 16u) && k == 0) || ((cfb & 32u) && k == a.nz - 1));
-        if (later) {
-#pragma unroll
-          for (int v = 0; v < NV; ++v) a.Uout[ub + (size_t)v * a.nint] = U[v];
-        } else {
-          finish_cell<T, DIM, FLAT>(a, geo, b, ci, cg, I1, I2, U, cnt, rate_max);
-        }
-      }
+      for (int c = threadIdx.x; c < sFz; c += blockDim.x)
+        cell_update<T, DIM, FLAT>(a, geo, Pb, b, x0, y0, k, c, Fx, Fy, Fz0, Fz1, dt, cfb, cnt, rate_max);
       __syncthreads();
       T* tmp = Fz0;
       Fz0 = Fz1;
       Fz1 = tmp;
+    }
+    if (!a.persistent) break;
+  }
+  reduce_outputs(a, cnt, rate_max);
+}
+
+// ----------------------------------------------------------------------------
+// Warp-specialised form of the 3-D stage kernel.  The first pwarps warps
+// (producers) compute the face fluxes of plane k+1 while the other warps
+// (consumers) update the cells of plane k, so the FP64 work of the cell
+// updates is not interrupted by the face phase.  Face fluxes are double
+// buffered (x and y faces per plane parity, z faces in three slots: plane k
+// reads faces k and k+1 while plane k+1's producer writes face k+2); named
+// barriers FULL[parity] (producers -> consumers) and EMPTY[parity]
+// (consumers -> producers) hand the buffers over.
+// ----------------------------------------------------------------------------
+// Named barriers (ids 1..4; 0 is __syncthreads).  Producer and consumer roles
+// are whole warps; each warp reconverges before the barrier instruction.
+__device__ __forceinline__ void named_sync(int id, int n) {
+  __syncwarp();
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+__device__ __forceinline__ void named_arrive(int id, int n) {
+  __syncwarp();
+  asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+constexpr int BAR_FULL = 1, BAR_EMPTY = 3;
+
+template <typename T, bool FLAT>
+__device__ __forceinline__ void produce_plane(const StageArgs& a, const LevelGeo& geo, const T* __restrict__ Pb, int b,
+                                              int x0, int y0, int k, bool bottom, T* Fx, T* Fy, T* Fzlo, T* Fzhi,
+                                              int ptid, int nprod) {
+  const int tx = a.tx, ty = a.ty;
+  const int sFx = ty * (tx + 1), sFy = (ty + 1) * tx, sFz = tx * ty;
+  const int I1b = a.blk[4 * b + 1] * a.nx + x0, I2b = a.blk[4 * b + 2] * a.ny + y0;
+  const bool regs = a.nlev > 1;
+  const int kg = k + a.gz;
+  const int nb = bottom ? sFz : 0;
+  const int n = nb + sFx + sFy + sFz;
+  for (int t = ptid; t < n; t += nprod) {
+    if (t < nb) {
+      const int i = t % tx, j = t / tx;
+      face_flux<T, FLAT>(a, geo, Pb, 2, i + x0 + a.gx, j + y0 + a.gy, kg, I1b + i, I2b + j, Fzlo + t, sFz);
+      if (regs) to_register(a, b, 2, 0, (j + y0) * a.nx + i + x0, Fzlo + t, sFz);
+      continue;
+    }
+    const int u0 = t - nb;
+    if (u0 < sFx) {
+      const int i = u0 % (tx + 1), j = u0 / (tx + 1);
+      face_flux<T, FLAT>(a, geo, Pb, 0, i + x0 + a.gx, j + y0 + a.gy, kg, I1b + i, I2b + j, Fx + u0, sFx);
+      if (regs && (x0 + i == 0 || x0 + i == a.nx)) to_register(a, b, 0, x0 + i == 0 ? 0 : 1, k * a.ny + j + y0, Fx + u0, sFx);
+    } else if (u0 < sFx + sFy) {
+      const int u = u0 - sFx;
+      const int i = u % tx, j = u / tx;
+      face_flux<T, FLAT>(a, geo, Pb, 1, i + x0 + a.gx, j + y0 + a.gy, kg, I1b + i, I2b + j, Fy + u, sFy);
+      if (regs && (y0 + j == 0 || y0 + j == a.ny)) to_register(a, b, 1, y0 + j == 0 ? 0 : 1, k * a.nx + i + x0, Fy + u, sFy);
+    } else {
+      const int u = u0 - sFx - sFy;
+      const int i = u % tx, j = u / tx;
+      face_flux<T, FLAT>(a, geo, Pb, 2, i + x0 + a.gx, j + y0 + a.gy, kg + 1, I1b + i, I2b + j, Fzhi + u, sFz);
+      if (regs && k + 1 == a.nz) to_register(a, b, 2, 1, (j + y0) * a.nx + i + x0, Fzhi + u, sFz);
+    }
+  }
+}
+
+template <typename T, bool FLAT, int MINB>
+__global__ void __launch_bounds__(256, MINB) stage_kernel_ws(StageArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int tx = a.tx, ty = a.ty;
+  const int sFx = ty * (tx + 1), sFy = (ty + 1) * tx, sFz = tx * ty;
+  T* base = reinterpret_cast<T*>(smem_raw);
+  T* FxB[2] = {base, base + NV * sFx};
+  T* FyB[2] = {base + 2 * NV * sFx, base + 2 * NV * sFx + NV * sFy};
+  T* FzB[3];
+  for (int q = 0; q < 3; ++q) FzB[q] = base + 2 * NV * (sFx + sFy) + q * NV * sFz;
+  __shared__ int s_item;
+
+  const double dt = stage_dt(a);
+  if (a.stage == 1 && blockIdx.x == 0 && threadIdx.x == 0) *a.dt_dev = dt;
+  const T* Pb_all = sizeof(T) == 8 ? reinterpret_cast<const T*>(a.P_in) : reinterpret_cast<const T*>(a.P32_in);
+  const int nthr = blockDim.x, nprod = a.pwarps * 32, ncons = nthr - nprod;
+  const bool producer = (int)threadIdx.x < nprod;
+  unsigned cnt[4] = {0u, 0u, 0u, 0u};
+  double rate_max = 0.0;
+  const int ntile = a.ntx * a.nty;
+  int item = a.persistent ? -1 : (int)blockIdx.x;
+  for (;;) {
+    if (a.persistent) {
+      __syncthreads();
+      if (threadIdx.x == 0) s_item = (int)atomicAdd(a.work, 1u);
+      __syncthreads();
+      item = s_item;
+    }
+    if (item >= a.nitems) break;
+    const int ord = item / ntile;
+    const int b = a.order[ord];
+    const int tile = item - ord * ntile;
+    const int x0 = (tile % a.ntx) * tx, y0 = (tile / a.ntx) * ty;
+    const LevelGeo geo = level_geo(a, a.blk[4 * b]);
+    const T* Pb = Pb_all + (size_t)b * NV * a.ncell;
+    const unsigned cfb = a.nlev > 1 ? a.cf[b] : 0u;
+    if (producer) {
+      for (int k = 0; k < a.nz; ++k) {
+        const int par = k & 1;
+        if (k >= 2) named_sync(BAR_EMPTY + par, nthr);
+        produce_plane<T, FLAT>(a, geo, Pb, b, x0, y0, k, k == 0, FxB[par], FyB[par], FzB[k % 3], FzB[(k + 1) % 3],
+                               threadIdx.x, nprod);
+        __threadfence_block();
+        named_arrive(BAR_FULL + par, nthr);
+      }
+      // take the consumers' last releases so every barrier starts the next item clean
+      for (int k = a.nz - 2 < 0 ? 0 : a.nz - 2; k < a.nz; ++k) named_sync(BAR_EMPTY + (k & 1), nthr);
+    } else {
+      for (int k = 0; k < a.nz; ++k) {
+        const int par = k & 1;
+        named_sync(BAR_FULL + par, nthr);
+        for (int c = threadIdx.x - nprod; c < sFz; c += ncons)
+          cell_update<T, 3, FLAT>(a, geo, Pb, b, x0, y0, k, c, FxB[par], FyB[par], FzB[k % 3], FzB[(k + 1) % 3], dt,
+                                  cfb, cnt, rate_max);
+        __threadfence_block();
+        named_arrive(BAR_EMPTY + par, nthr);
+      }
     }
     if (!a.persistent) break;
   }
@@ -688,11 +835,23 @@ __global__ void __launch_bounds__(256) cfl_kernel(StageArgs a) {
   if ((threadIdx.x & 31u) == 0) atomicMax(a.smax_out, (unsigned long long)__double_as_longlong(w));
 }
 
-template <typename T, int DIM, bool FLAT>
+template <typename T, int DIM, bool FLAT, int MINB>
 static cudaError_t configure_stage_t() {
   static bool configured = false;
   if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(stage_kernel<T, DIM, FLAT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(stage_kernel<T, DIM, FLAT, MINB>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  return cudaSuccess;
+}
+
+template <typename T, bool FLAT, int MINB>
+static cudaError_t configure_ws_t() {
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(stage_kernel_ws<T, FLAT, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          200 * 1024);
     if (e != cudaSuccess) return e;
     configured = true;
@@ -702,23 +861,52 @@ static cudaError_t configure_stage_t() {
 
 template <typename T>
 static cudaError_t configure_all_t() {
-  cudaError_t e = configure_stage_t<T, 2, true>();
-  if (e == cudaSuccess) e = configure_stage_t<T, 2, false>();
-  if (e == cudaSuccess) e = configure_stage_t<T, 3, true>();
-  if (e == cudaSuccess) e = configure_stage_t<T, 3, false>();
+  cudaError_t e = cudaSuccess;
+  if (e == cudaSuccess) e = configure_stage_t<T, 2, true, 1>();
+  if (e == cudaSuccess) e = configure_stage_t<T, 2, false, 1>();
+  if (e == cudaSuccess) e = configure_stage_t<T, 3, true, 1>();
+  if (e == cudaSuccess) e = configure_stage_t<T, 3, false, 1>();
+  if (e == cudaSuccess) e = configure_stage_t<T, 3, true, 2>();
+  if (e == cudaSuccess) e = configure_stage_t<T, 3, false, 2>();
+  if (e == cudaSuccess) e = configure_ws_t<T, true, 1>();
+  if (e == cudaSuccess) e = configure_ws_t<T, false, 1>();
+  if (e == cudaSuccess) e = configure_ws_t<T, true, 2>();
+  if (e == cudaSuccess) e = configure_ws_t<T, false, 2>();
   return e;
 }
 
-template <typename T, int DIM, bool FLAT>
+template <typename T, int DIM, bool FLAT, int MINB>
 static cudaError_t launch_stage_t(const StageArgs& a, int grid, int threads, size_t smem, cudaStream_t st) {
-  cudaError_t e = configure_stage_t<T, DIM, FLAT>();
-  if (e != cudaSuccess) return e;
-  stage_kernel<T, DIM, FLAT><<<grid, threads, smem, st>>>(a);
+  cudaError_t e;
+  if (DIM == 3 && a.pwarps > 0) {
+    e = configure_ws_t<T, FLAT, MINB>();
+    if (e != cudaSuccess) return e;
+    stage_kernel_ws<T, FLAT, MINB><<<grid, threads, smem, st>>>(a);
+  } else {
+    e = configure_stage_t<T, DIM, FLAT, MINB>();
+    if (e != cudaSuccess) return e;
+    stage_kernel<T, DIM, FLAT, MINB><<<grid, threads, smem, st>>>(a);
+  }
   e = cudaGetLastError();
   if (e != cudaSuccess || a.nrcells == 0) return e;
   int g = (a.nrcells + 127) / 128;
   reflux_kernel<T, DIM, FLAT><<<g, 128, 0, st>>>(a);
   return cudaGetLastError();
+}
+
+// 3-D kernels exist with one or two resident CTAs per SM as the register
+// bound; 2-D grids use the one-CTA form.
+template <typename T>
+static cudaError_t launch_stage_any(const StageArgs& a, int grid, int threads, size_t smem, cudaStream_t st) {
+  if (a.ndim == 3) {
+    if (a.minb == 2)
+      return a.flat ? launch_stage_t<T, 3, true, 2>(a, grid, threads, smem, st)
+                    : launch_stage_t<T, 3, false, 2>(a, grid, threads, smem, st);
+    return a.flat ? launch_stage_t<T, 3, true, 1>(a, grid, threads, smem, st)
+                  : launch_stage_t<T, 3, false, 1>(a, grid, threads, smem, st);
+  }
+  return a.flat ? launch_stage_t<T, 2, true, 1>(a, grid, threads, smem, st)
+                : launch_stage_t<T, 2, false, 1>(a, grid, threads, smem, st);
 }
 
 }  // namespace bhac

@@ -87,7 +87,12 @@ def test_shock_tube_one_step(gb):
     g = pb.shock_tube_2d()
     s, o, _ = one_step(gb, g, pb.shock_tube_prims(g))
     assert_parity(s.cons(), o.cons(), TOL64, "cons", g)
-    assert np.all(normwise(s.prims(), o.prims()) <= TOL64)
+    # primitives normwise too; psi stays exactly 0 in this 1-D problem (div B = 0),
+    # so it is measured against the field magnitude instead
+    gp, rp = s.prims(), o.prims()
+    err = normwise(gp[:, :8], rp[:, :8])
+    assert np.all(err <= TOL64), err
+    assert np.abs(gp[:, 8] - rp[:, 8]).max() <= TOL64 * np.abs(rp[:, 5:8]).max()
     assert np.array_equal(s.diagnostics(), o.c2p_counts())
 
 
@@ -160,7 +165,8 @@ def test_launch_shapes_are_bitwise_identical(gb):
     g = pb.torus_3d(nroot=(4, 3, 2))
     P = pb.fm_torus_prims(g)
     outs = []
-    for shape in [(16, 16, 256, 0), (16, 8, 128, 0), (8, 8, 64, 0), (16, 16, 256, 2)]:
+    for shape in [(16, 16, 256, 0), (16, 8, 128, 0), (8, 8, 64, 0), (16, 16, 256, 2), (16, 16, 256, 0, 2),
+                  (16, 16, 256, 0, 1, 2), (16, 8, 256, 2, 2, 4), (8, 8, 128, 0, 1, 1)]:
         s = gb.Solver(g)
         s.set_launch(*shape)
         s.set_prims(P)
@@ -298,9 +304,59 @@ def test_amr_torus_small(gb, precision, tol):
     assert_parity(s.cons(), o.cons(), tol, f"amr torus {precision}", g)
 
 
+def test_amr_torus_warp_specialised(gb):
+    """The warp-specialised stage kernel (flux registers written by the
+    producer warps) on the three-level torus, bitwise equal to the phased form."""
+    g = pb.amr_torus(root=(4, 2, 2), nblock=8)
+    P = pb.fm_torus_prims(g)
+    outs = []
+    for shape in [(8, 8, 64, 0, 1, 0), (8, 8, 128, 0, 1, 2), (8, 8, 256, 2, 2, 4)]:
+        s = gb.Solver(g)
+        s.set_launch(*shape)
+        s.set_prims(P)
+        s.cfl_dt()
+        s.step(0.0)
+        s.step(0.0)
+        outs.append(s.cons())
+    for x in outs[1:]:
+        assert np.array_equal(x, outs[0])
+
+
 def test_amr_torus_full_size(gb):
     """The batched uneven AMR workload: 4220 leaf blocks of 16^3 on three
     levels (finest inside r < 20 M), one step, every block compared."""
     g = pb.amr_torus()
     s, o, _ = one_step(gb, g, pb.fm_torus_prims(g))
     assert_parity(s.cons(), o.cons(), TOL64, "amr torus", g)
+
+
+def test_mixed_smooth_wave_l1_within_1p1_of_oracle(gb):
+    """Circularly polarised Alfven wave along x (128 x 16 cells, periodic):
+    the mixed form's L1 error against the exact solution at t = 0.25 is within
+    1.1x of the FP64 oracle's."""
+    g = pb.Grid(ndim=2, nx=(32, 16, 1), nroot=(4, 1, 1), xmin=(0, 0, 0), xmax=(1, 0.125, 1),
+                gamma_ad=5.0 / 3.0, recon="ppm", riemann="hll", kappa=0.0, cfl=0.4)
+    P0 = pb.alfven_wave_prims(g, 0.0)
+    s = gb.Solver(g, "mixed")
+    s.set_prims(P0)
+    o = oracle.Oracle(g)
+    o.set_prims(P0)
+    t, t_end = 0.0, 0.25
+    while t < t_end - 1e-14:
+        dt = min(o.cfl_dt(), t_end - t)
+        o.step(dt)
+        s.step(dt)
+        t += dt
+    exact = pb.alfven_wave_prims(g, t_end)
+    e_or = float(np.mean(np.abs(o.prims()[:, 6] - exact[:, 6])))
+    e_mx = float(np.mean(np.abs(s.prims()[:, 6] - exact[:, 6])))
+    assert e_mx <= 1.1 * e_or, (e_mx, e_or)
+
+
+def test_mixed_full_config_2_per_variable(gb):
+    """192x96x96 torus, mixed form vs the FP64 oracle, one step: every
+    conserved variable within 1e-5 (energy-scaled), reported per variable."""
+    g = pb.torus_3d()
+    s, o, _ = one_step(gb, g, pb.fm_torus_prims(g), precision="mixed")
+    err = assert_parity(s.cons(), o.cons(), TOLMIX, "mixed config 2", g)
+    print("mixed vs oracle per conserved variable (D S1 S2 S3 tau B1 B2 B3 psi):", err)

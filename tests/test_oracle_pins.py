@@ -611,3 +611,20 @@ def test_shock_tube_matches_stored_oracle_profile():
     ref = np.loadtxt(path)
     from tests.golden.make_golden import shock_tube_profile
     np.testing.assert_allclose(shock_tube_profile(), ref, rtol=1e-12, atol=1e-13)
+
+
+@pytest.mark.parametrize("coords", ["cart", "mks"])
+def test_fast_speeds_inside_the_light_cone(coords):
+    """|lambda+-| <= alpha sqrt(gamma^dd) + |beta^d| for random states: with
+    ch >= 1 the cleaning speed bounds the CFL rate."""
+    grid = ks_grid("mks") if coords == "mks" else pb.periodic_box(gamma_ad=2.0)
+    pt = oracle.Point(grid)
+    rng = np.random.default_rng(21)
+    for _ in range(500):
+        x = [math.log(rng.uniform(1.25, 2000)), rng.uniform(0.01, 0.99), 1.0] if coords == "mks" else [0.5] * 3
+        m = pt.metric(x, derivs=False)
+        P = random_state(rng, m.g, sigma_max=1e3, wmax=30.0)
+        for d in range(3):
+            lm, lp = pt.wavespeeds(m, P, d)
+            light = m.alpha * math.sqrt(m.gi[d][d]) + abs(m.beta[d])
+            assert max(abs(lm), abs(lp)) <= light * (1 + 1e-13)
