@@ -15,23 +15,27 @@ import json
 import os
 
 DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune.json")
-SMEM_LIMIT = 200 * 1024
+SMEM_LIMIT = 226 * 1024
+# names the stage kernel's shared-memory design; cached shapes of another
+# design are not reused
+KERNEL_TAG = "edge-staged"
 
 
 def smem_bytes(tx: int, ty: int, ndim: int, precision: str, producers: int = 0) -> int:
+    """Dynamic shared memory of the stage kernel (the library's own sizing)."""
     t = 4 if precision == "mixed" else 8
     sfx, sfy, sfz = ty * (tx + 1), (ty + 1) * tx, tx * ty
     if ndim == 3 and producers:
         return 9 * (2 * sfx + 2 * sfy + 3 * sfz) * t
-    n = 9 * (sfx + sfy)
+    n = sfx + sfy + 2 * (tx + 2) * ty + 2 * tx * (ty + 2)
     if ndim == 3:
-        n += 2 * 9 * sfz
-    return n * t
+        n += 3 * sfz
+    return 9 * n * t
 
 
 def candidates(grid, precision: str):
     nx, ny = grid.nx[0], grid.nx[1]
-    tiles = [(tx, ty) for tx in (32, 16, 8) for ty in (16, 8) if nx % tx == 0 and ny % ty == 0]
+    tiles = [(tx, ty) for tx in (32, 16, 8) for ty in (16, 8, 4) if nx % tx == 0 and ny % ty == 0 and tx * ty >= 64]
     if not tiles:
         tiles = [(nx, ny)]
     out = []
@@ -57,7 +61,8 @@ def candidates(grid, precision: str):
 def key_of(grid, precision: str) -> str:
     import torch
     name = torch.cuda.get_device_name() if torch.cuda.is_available() else "cpu"
-    return f"{name}|nx={grid.nx[0]}x{grid.nx[1]}x{grid.nx[2]}|ndim={grid.ndim}|levels={grid.nlevels}|{precision}"
+    return (f"{name}|{KERNEL_TAG}|nx={grid.nx[0]}x{grid.nx[1]}x{grid.nx[2]}|ndim={grid.ndim}"
+            f"|levels={grid.nlevels}|{precision}|{grid.recon}")
 
 
 def load_cache(path: str = DEFAULT_CACHE) -> dict:
@@ -132,6 +137,7 @@ def cached_or_default(solver, cache_path: str = DEFAULT_CACHE):
         solver.set_launch(*shape)
         return shape
     nx, ny = solver.grid.nx[0], solver.grid.nx[1]
-    tx = 32 if nx % 32 == 0 else (16 if nx % 16 == 0 else nx)
-    ty = 16 if ny % 16 == 0 else ny
-    return (tx, ty, 256, 0, 1, 0)
+    for tx, ty in ((32, 16), (16, 16), (16, 8), (8, 8)):
+        if nx % tx == 0 and ny % ty == 0 and smem_bytes(tx, ty, solver.grid.ndim, solver.precision) <= SMEM_LIMIT:
+            return (tx, ty, 256, 0, 1, 0)
+    return (nx, ny, 256, 0, 1, 0)

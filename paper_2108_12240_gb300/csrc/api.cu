@@ -210,9 +210,12 @@ size_t stage_smem(const bhac_ctx* c, int tx, int ty, int pwarps) {
   const size_t tsz = c->mixed ? sizeof(float) : sizeof(double);
   const size_t sFx = (size_t)ty * (tx + 1), sFy = (size_t)(ty + 1) * tx, sFz = (size_t)tx * ty;
   if (c->d.ndim == 3 && pwarps > 0) return NV * (2 * sFx + 2 * sFy + 3 * sFz) * tsz;
-  size_t smem = NV * (sFx + sFy) * tsz;
-  if (c->d.ndim == 3) smem += 2 * NV * sFz * tsz;
-  return smem;
+  // phased form: face fluxes, edges along x and y (tile plus halo), and in
+  // 3-D two z-face planes and the carried z edges
+  const size_t nex = (size_t)(tx + 2) * ty, ney = (size_t)tx * (ty + 2);
+  size_t n = sFx + sFy + 2 * nex + 2 * ney;
+  if (c->d.ndim == 3) n += 3 * sFz;
+  return NV * n * tsz;
 }
 
 bhac_status ghost_fill(bhac_ctx* c, int buf, bool zero_smax) {
@@ -370,10 +373,21 @@ bhac_status bhac_init_grid(bhac_ctx** out, const bhac_grid_desc* d, const bhac_b
   c->nrcells = (int)M.rcells.size();
   c->cur = 0;
   c->ucur = 0;
-  // default launch shape: 16 x 16 columns where they divide the block
-  c->tx = d->nx[0] % 32 == 0 ? 32 : (d->nx[0] % 16 == 0 ? 16 : d->nx[0]);
-  c->ty = d->nx[1] % 16 == 0 ? 16 : d->nx[1];
   c->threads = 256;
+  // default launch shape: the largest of these tiles that divides the block
+  // and fits the shared-memory limit, else the whole block face
+  {
+    static const int tiles[][2] = {{32, 16}, {16, 16}, {16, 8}, {8, 8}};
+    c->tx = d->nx[0];
+    c->ty = d->nx[1];
+    for (const auto& t : tiles) {
+      if (d->nx[0] % t[0] == 0 && d->nx[1] % t[1] == 0 && stage_smem(c, t[0], t[1], 0) <= (size_t)kMaxDynSmem) {
+        c->tx = t[0];
+        c->ty = t[1];
+        break;
+      }
+    }
+  }
   c->persistent = 0;
   c->minb = 1;
   c->pwarps = 0;
@@ -570,7 +584,7 @@ bhac_status bhac_set_launch(bhac_ctx* c, int tx, int ty, int threads, int persis
   if (c->d.nx[0] % ntx || c->d.nx[1] % nty || nth % 32 || nth > 256 || persistent < 0 || persistent > 8)
     return BHAC_ERR_ARG;
   const size_t smem = stage_smem(c, ntx, nty, producer_warps);
-  if (smem > 200 * 1024) return BHAC_ERR_ARG;
+  if (smem > (size_t)kMaxDynSmem) return BHAC_ERR_ARG;
   if (min_ctas > 0) c->minb = min_ctas;
   c->pwarps = producer_warps;
   c->tx = ntx;

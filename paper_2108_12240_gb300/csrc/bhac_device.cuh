@@ -170,6 +170,65 @@ __device__ __forceinline__ bool finite_t(double x) { return isfinite(x); }
 __device__ __forceinline__ double to_double(double x) { return x; }
 __device__ __forceinline__ double to_double(float x) { return (double)x; }
 
+// Ordered selections.  On GB300 an FP64 compare occupies the SM's FP64 unit
+// exactly like an FP64 fused multiply-add (two lanes per clock per SM), while
+// 64-bit integer compares and selects run on the integer pipes at tens of
+// lanes per clock.  The double overloads therefore compare an
+// order-preserving integer image of the operands: okey maps -0 and +0 to 0
+// and every other finite or infinite double so that okey(x) < okey(y)
+// exactly when x < y, so each decision is the IEEE compare's for non-NaN
+// operands.  gt0_t, le0_t and lt_abs_t are exact for NaN too (false, false,
+// false as IEEE); lt_t orders NaN arbitrarily and is used only where the
+// operands are values of a valid state.  The generic templates (float, and
+// the flop counter's counting type) are the plain compares.
+__device__ __forceinline__ long long okey(double x) {
+  const long long b = __double_as_longlong(x);
+  return b < 0 ? (long long)(0x8000000000000000ULL - (unsigned long long)b) : b;
+}
+constexpr unsigned long long kExpAll = 0x7FF0000000000000ULL;  // bits of +inf
+template <typename T>
+BHAC_HD bool lt_t(T a, T b) { return a < b; }
+template <typename T>
+BHAC_HD bool gt0_t(T x) { return x > T(0); }
+template <typename T>
+BHAC_HD bool le0_t(T x) { return x <= T(0); }
+template <typename T>
+BHAC_HD bool lt_abs_t(T a, T b) { return abs_t(a) < abs_t(b); }
+BHAC_HD bool lt_t(double a, double b) {
+#ifdef __CUDA_ARCH__
+  return okey(a) < okey(b);
+#else
+  return a < b;
+#endif
+}
+BHAC_HD bool gt0_t(double x) {
+#ifdef __CUDA_ARCH__
+  // positive finite or +inf: bits in [1, kExpAll]
+  return (unsigned long long)__double_as_longlong(x) - 1ULL < kExpAll;
+#else
+  return x > 0.0;
+#endif
+}
+BHAC_HD bool le0_t(double x) {
+#ifdef __CUDA_ARCH__
+  // +0, or sign bit set and not NaN
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  return b == 0ULL || ((b >> 63) && (b & 0x7FFFFFFFFFFFFFFFULL) <= kExpAll);
+#else
+  return x <= 0.0;
+#endif
+}
+BHAC_HD bool lt_abs_t(double a, double b) {
+#ifdef __CUDA_ARCH__
+  const unsigned long long m = 0x7FFFFFFFFFFFFFFFULL;
+  const unsigned long long x = (unsigned long long)__double_as_longlong(a) & m;
+  const unsigned long long y = (unsigned long long)__double_as_longlong(b) & m;
+  return x < y && y <= kExpAll;
+#else
+  return fabs(a) < fabs(b);
+#endif
+}
+
 template <typename T>
 BHAC_HD T sel3(int d, T a, T b, T c) {
   return d == 0 ? a : (d == 1 ? b : c);
@@ -267,7 +326,7 @@ BHAC_HD void speeds_of(const Met<T>& m, const T* P, const Derived<T>& s, int d, 
   const T vd = sel3(d, s.v1, s.v2, s.v3);
   const T gidd = sel3(d, m.gi11, m.gi22, m.gi33);
   T disc = G * (T(1) - s.vsq) * (gidd * R - vd * vd * EG);
-  disc = disc > T(0) ? disc : T(0);
+  disc = gt0_t(disc) ? disc : T(0);
   const T sq = sqrt_t(disc);
   const T ir = rcp_t(R);
   const T bed = d == 0 ? m.be1 : T(0);
@@ -284,29 +343,47 @@ BHAC_HD void speeds_of(const Met<T>& m, const T* P, const Derived<T>& s, int d, 
 template <typename T>
 BHAC_HD T ppm_iface(T am1, T a0, T a1, T a2) {
   T v = T(7.0 / 12.0) * (a0 + a1) - T(1.0 / 12.0) * (am1 + a2);
-  const T lo = a0 < a1 ? a0 : a1, hi = a0 < a1 ? a1 : a0;
-  v = v < lo ? lo : v;
-  v = v > hi ? hi : v;
+  const bool o = lt_t(a0, a1);
+  const T lo = o ? a0 : a1, hi = o ? a1 : a0;
+  v = lt_t(v, lo) ? lo : v;
+  v = lt_t(hi, v) ? hi : v;
   return v;
 }
 
 template <typename T>
 BHAC_HD void ppm_limit(T a, T& aL, T& aR) {
-  if ((aR - a) * (a - aL) <= T(0)) {
+  if (le0_t((aR - a) * (a - aL))) {
     aL = a;
     aR = a;
   } else {
     const T d = aR - aL;
     const T m6 = T(6) * (a - T(0.5) * (aL + aR));
-    if (d * m6 > d * d) aL = T(3) * a - T(2) * aR;
-    if (-d * d > d * m6) aR = T(3) * a - T(2) * aL;
+    if (lt_t(d * d, d * m6)) aL = T(3) * a - T(2) * aR;
+    if (lt_t(d * m6, -d * d)) aR = T(3) * a - T(2) * aL;
   }
 }
 
 template <typename T>
 BHAC_HD T minmod_t(T a, T b) {
-  if (a * b <= T(0)) return T(0);
-  return (a < T(0) ? -a : a) < (b < T(0) ? -b : b) ? a : b;
+  if (le0_t(a * b)) return T(0);
+  return lt_abs_t(a, b) ? a : b;
+}
+
+// Both edges of one cell from its five-point stencil s_m2..s2 (cells c-2..c+2):
+// aL at the cell's low face, aR at its high face.  The same formulas as
+// recon_var evaluates per face, so a face's states from two cells' edges are
+// bit-identical to recon_var's.
+template <typename T>
+BHAC_HD void recon_edges(int recon, T s_m2, T s_m1, T s0, T s1, T s2, T& aL, T& aR) {
+  if (recon == 0) {
+    aL = ppm_iface(s_m2, s_m1, s0, s1);
+    aR = ppm_iface(s_m1, s0, s1, s2);
+    ppm_limit(s0, aL, aR);
+  } else {
+    const T mm = minmod_t(s0 - s_m1, s1 - s0);
+    aL = s0 - T(0.5) * mm;
+    aR = s0 + T(0.5) * mm;
+  }
 }
 
 template <typename T>

@@ -93,9 +93,19 @@ template <typename T, typename S>
 void load_stencil(const StageArgs& a, const S* Pb, int d, int ig, int jg, int kg, T PL[NV], T PR[NV]) {
   const int sd = d == 0 ? 1 : (d == 1 ? a.Nx : a.Nx * a.Ny);
   const int c0 = (kg * a.Ny + jg) * a.Nx + ig;
+  // the face states are the high edge of the low cell and the low edge of
+  // the high cell; the kernel reconstructs each cell's edges once per
+  // direction, so only the high cell's (the sampled cell's) are counted
+  const bool on = g_on;
   for (int v = 0; v < NV; ++v) {
     const S* p = Pb + (size_t)v * a.ncell + c0;
-    recon_var(a.recon, T(p[-3 * sd]), T(p[-2 * sd]), T(p[-sd]), T(p[0]), T(p[sd]), T(p[2 * sd]), PL[v], PR[v]);
+    T l0, r0, l1, r1;
+    g_on = false;
+    recon_edges(a.recon, T(p[-3 * sd]), T(p[-2 * sd]), T(p[-sd]), T(p[0]), T(p[sd]), l0, r0);
+    g_on = on;
+    recon_edges(a.recon, T(p[-2 * sd]), T(p[-sd]), T(p[0]), T(p[sd]), T(p[2 * sd]), l1, r1);
+    PL[v] = r0;
+    PR[v] = l1;
   }
   if (!(PL[RHO] > T(0)) || !(PL[PRS] > T(0)) || !(PR[RHO] > T(0)) || !(PR[PRS] > T(0))) {
     for (int v = 0; v < NV; ++v) {
@@ -157,13 +167,14 @@ void cell(const StageArgs& a, const HostState& h, int sb, int i, int j, int k, d
                   Fhi[d]);
   }
   g_on = true;
-  // flux divergence in FP64, as the kernel forms it
+  // flux divergence in the flux arithmetic T, as the kernel forms it
+  T rdiv[NV];
   N64 rhs[NV];
   for (int v = 0; v < NV; ++v) {
-    N64 r = -(N64(Fhi[0][v]) - N64(Flo[0][v])) * N64(a.idx[0]);
-    r = r + -(N64(Fhi[1][v]) - N64(Flo[1][v])) * N64(a.idx[1]);
-    if (a.ndim == 3) r = r + -(N64(Fhi[2][v]) - N64(Flo[2][v])) * N64(a.idx[2]);
-    rhs[v] = r;
+    T r = -(T(Fhi[0][v]) - T(Flo[0][v])) * T(a.idx[0]);
+    r = r - (T(Fhi[1][v]) - T(Flo[1][v])) * T(a.idx[1]);
+    if (a.ndim == 3) r = r - (T(Fhi[2][v]) - T(Flo[2][v])) * T(a.idx[2]);
+    rdiv[v] = r;
   }
   const int cg = (kg * a.Ny + jg) * a.Nx + ig;
   T Pc[NV];
@@ -171,7 +182,8 @@ void cell(const StageArgs& a, const HostState& h, int sb, int i, int j, int k, d
   double sg = 1.0, isg = 1.0, rho_fl = a.rho_fl_c, p_fl = a.p_fl_c;
   const double* crec = a.flat ? nullptr : h.tc.data() + (size_t)(I2 * a.N1g + I1) * CREC;
   if (a.flat) {
-    rhs[PSI] = rhs[PSI] + N64(to_double(-T(a.kappa) * Pc[PSI]));
+    rdiv[PSI] = rdiv[PSI] - T(a.kappa) * Pc[PSI];
+    for (int v = 0; v < NV; ++v) rhs[v] = N64(to_double(rdiv[v]));
   } else {
     const R* rec = tc + (size_t)(I2 * a.N1g + I1) * CREC;
     Met<T> m = load_centre_metric<T>(rec);
@@ -184,7 +196,11 @@ void cell(const StageArgs& a, const HostState& h, int sb, int i, int j, int k, d
     isg = crec[C_ISG];
     rho_fl = crec[C_RHOFL];
     p_fl = crec[C_PFL];
-    for (int v = 0; v < NV; ++v) rhs[v] = rhs[v] + N64(sg) * N64(to_double(S_[v]));
+    if (std::is_same<T, N64>::value) {
+      for (int v = 0; v < NV; ++v) rhs[v] = N64(to_double(rdiv[v])) + N64(sg) * N64(to_double(S_[v]));
+    } else {
+      for (int v = 0; v < NV; ++v) rhs[v] = N64(to_double(rdiv[v] + T(sg) * S_[v]));
+    }
   }
   // RK combination (the stage-2 form also uses the stage-1 state; the
   // operation count does not depend on its value)

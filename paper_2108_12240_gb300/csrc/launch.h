@@ -7,6 +7,11 @@
 
 namespace bhac {
 
+// Largest dynamic shared memory a stage kernel may request (bytes): the
+// opt-in per-CTA limit of sm_103a (227 KB) less room for the kernels' static
+// shared memory (the attribute plus the static size must fit the limit).
+constexpr int kMaxDynSmem = 226 * 1024;
+
 // stage kernels (stage_fp64.cu / stage_mixed.cu)
 cudaError_t launch_stage_fp64(const StageArgs& a, int grid, int threads, size_t smem, cudaStream_t st);
 cudaError_t launch_stage_mixed(const StageArgs& a, int grid, int threads, size_t smem, cudaStream_t st);

@@ -289,13 +289,13 @@ BHAC_HD void riemann_flux(const Met<T>& m, T acg, const T* PL, const T* PR, int 
   T U[NV], F[NV];
   if (riemann == 0) {
     T lp = T(0), lm = T(0);
-    lp = lpL > lp ? lpL : lp;
-    lp = lpR > lp ? lpR : lp;
-    lm = lmL < lm ? lmL : lm;
-    lm = lmR < lm ? lmR : lm;
-    const T lpg = lgp > lp ? lgp : lp, lmg = lgm < lm ? lgm : lm;
+    lp = lt_t(lp, lpL) ? lpL : lp;
+    lp = lt_t(lp, lpR) ? lpR : lp;
+    lm = lt_t(lmL, lm) ? lmL : lm;
+    lm = lt_t(lmR, lm) ? lmR : lm;
+    const T lpg = lt_t(lp, lgp) ? lgp : lp, lmg = lt_t(lgm, lm) ? lgm : lm;
     const T wh = lp - lm, wg = lpg - lmg;
-    const bool okh = wh > T(0), okg = wg > T(0);
+    const bool okh = gt0_t(wh), okg = gt0_t(wg);
     // both fan widths' reciprocals from one division
     const T r = okh && okg ? rcp_t(wh * wg) : T(0);
     const T ih = okh ? (okg ? wg * r : rcp_t(wh)) : T(0);
@@ -320,13 +320,13 @@ BHAC_HD void riemann_flux(const Met<T>& m, T acg, const T* PL, const T* PR, int 
   } else {
     const T alpL = abs_t(lpL), almL = abs_t(lmL), alpR = abs_t(lpR), almR = abs_t(lmR);
     T c = alpL;
-    c = almL > c ? almL : c;
-    c = alpR > c ? alpR : c;
-    c = almR > c ? almR : c;
+    c = lt_t(c, almL) ? almL : c;
+    c = lt_t(c, alpR) ? alpR : c;
+    c = lt_t(c, almR) ? almR : c;
     const T agp = abs_t(lgp), agm = abs_t(lgm);
     T cg = c;
-    cg = agp > cg ? agp : cg;
-    cg = agm > cg ? agm : cg;
+    cg = lt_t(cg, agp) ? agp : cg;
+    cg = lt_t(cg, agm) ? agm : cg;
     cons_of(PL, sL, U);
     flux_of(m, PL, sL, U, d, ch2, F);
     for (int v = 0; v < NV; ++v) {
@@ -343,29 +343,22 @@ BHAC_HD void riemann_flux(const Met<T>& m, T acg, const T* PL, const T* PR, int 
 }
 
 // ----------------------------------------------------------------------------
-// One face flux, densitized by the face sqrt(gamma).  (ig, jg, kg): ghosted
+// Face fluxes, densitized by the face sqrt(gamma).  (ig, jg, kg): ghosted
 // coordinates of the cell on the high side of the face; (I1, I2): level-global
 // table indices of the face.
 // ----------------------------------------------------------------------------
-template <typename T, bool FLAT>
-__device__ __forceinline__ void face_flux(const StageArgs& a, const LevelGeo& geo, const T* __restrict__ Pb, int d,
-                                          int ig, int jg, int kg, int I1, int I2, T* out, int ostride) {
-  const int sd = d == 0 ? 1 : (d == 1 ? a.Nx : a.Nx * a.Ny);
-  const int c0 = (kg * a.Ny + jg) * a.Nx + ig;
-  // axis faces carry no flux (sqrt(gamma) = 0 there)
-  if (!FLAT && d == 1 && ((I2 == 0 && a.axis_lo1) || (I2 == geo.N2 && a.axis_hi1))) {
-#pragma unroll
-    for (int v = 0; v < NV; ++v) out[v * ostride] = T(0);
-    return;
-  }
-  T PL[NV], PR[NV];
-#pragma unroll
-  for (int v = 0; v < NV; ++v) {
-    const T* p = Pb + (size_t)v * a.ncell + c0;
-    const T s0 = p[-3 * sd], s1 = p[-2 * sd], s2 = p[-sd], s3 = p[0], s4 = p[sd], s5 = p[2 * sd];
-    recon_var(a.recon, s0, s1, s2, s3, s4, s5, PL[v], PR[v]);
-  }
-  if (!(PL[RHO] > T(0)) || !(PL[PRS] > T(0)) || !(PR[RHO] > T(0)) || !(PR[PRS] > T(0))) {
+// Axis faces carry no flux (sqrt(gamma) = 0 there).
+template <bool FLAT>
+__device__ __forceinline__ bool axis_face(const StageArgs& a, const LevelGeo& geo, int d, int I2) {
+  return !FLAT && d == 1 && ((I2 == 0 && a.axis_lo1) || (I2 == geo.N2 && a.axis_hi1));
+}
+
+// Reconstructed states with a non-positive density or pressure fall back to
+// the two adjacent cell values (first order).  c0: ghosted index of the high cell.
+template <typename T>
+__device__ __forceinline__ void positivity_fallback(const StageArgs& a, const T* __restrict__ Pb, int sd, int c0,
+                                                    T PL[NV], T PR[NV]) {
+  if (!gt0_t(PL[RHO]) || !gt0_t(PL[PRS]) || !gt0_t(PR[RHO]) || !gt0_t(PR[PRS])) {
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
       const T* p = Pb + (size_t)v * a.ncell + c0;
@@ -373,6 +366,12 @@ __device__ __forceinline__ void face_flux(const StageArgs& a, const LevelGeo& ge
       PR[v] = p[0];
     }
   }
+}
+
+// Face metric and Riemann solve of the states PL, PR.
+template <typename T, bool FLAT>
+__device__ __forceinline__ void face_solve(const StageArgs& a, const LevelGeo& geo, int d, int I1, int I2,
+                                           const T PL[NV], const T PR[NV], T* out, int ostride) {
   Met<T> m;
   T acg;
   if (FLAT) {
@@ -395,6 +394,67 @@ __device__ __forceinline__ void face_flux(const StageArgs& a, const LevelGeo& ge
   riemann_flux(m, acg, PL, PR, d, a.riemann, T(a.gam), T(a.gam_fac), T(a.ch), F);
 #pragma unroll
   for (int v = 0; v < NV; ++v) out[v * ostride] = F[v];
+}
+
+// One face flux from the six-point stencil across the face (the
+// warp-specialised kernel's per-face form).
+template <typename T, bool FLAT>
+__device__ __forceinline__ void face_flux(const StageArgs& a, const LevelGeo& geo, const T* __restrict__ Pb, int d,
+                                          int ig, int jg, int kg, int I1, int I2, T* out, int ostride) {
+  const int sd = d == 0 ? 1 : (d == 1 ? a.Nx : a.Nx * a.Ny);
+  const int c0 = (kg * a.Ny + jg) * a.Nx + ig;
+  if (axis_face<FLAT>(a, geo, d, I2)) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) out[v * ostride] = T(0);
+    return;
+  }
+  T PL[NV], PR[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    const T* p = Pb + (size_t)v * a.ncell + c0;
+    const T s0 = p[-3 * sd], s1 = p[-2 * sd], s2 = p[-sd], s3 = p[0], s4 = p[sd], s5 = p[2 * sd];
+    recon_var(a.recon, s0, s1, s2, s3, s4, s5, PL[v], PR[v]);
+  }
+  positivity_fallback(a, Pb, sd, c0, PL, PR);
+  face_solve<T, FLAT>(a, geo, d, I1, I2, PL, PR, out, ostride);
+}
+
+// Both reconstructed edges along d of the cell at ghosted index c, all
+// variables: aL (low face) to L[v * sl], aR (high face) to R[v * sr].
+template <typename T>
+__device__ __forceinline__ void cell_edges(const StageArgs& a, const T* __restrict__ Pb, int sd, int c, T* L, int sl,
+                                           T* R, int sr) {
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    const T* p = Pb + (size_t)v * a.ncell + c;
+    T l, r;
+    recon_edges(a.recon, p[-2 * sd], p[-sd], p[0], p[sd], p[2 * sd], l, r);
+    L[v * sl] = l;
+    R[v * sr] = r;
+  }
+}
+
+// A face flux from the two adjacent cells' edges: the low cell's aR (eL,
+// stride es) and the high cell's aL (eR).
+template <typename T, bool FLAT>
+__device__ __forceinline__ void edge_face(const StageArgs& a, const LevelGeo& geo, const T* __restrict__ Pb, int d,
+                                          int ig, int jg, int kg, int I1, int I2, const T* eL, const T* eR, int es,
+                                          T* out, int ostride) {
+  if (axis_face<FLAT>(a, geo, d, I2)) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) out[v * ostride] = T(0);
+    return;
+  }
+  const int sd = d == 0 ? 1 : (d == 1 ? a.Nx : a.Nx * a.Ny);
+  const int c0 = (kg * a.Ny + jg) * a.Nx + ig;
+  T PL[NV], PR[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    PL[v] = eL[v * es];
+    PR[v] = eR[v * es];
+  }
+  positivity_fallback(a, Pb, sd, c0, PL, PR);
+  face_solve<T, FLAT>(a, geo, d, I1, I2, PL, PR, out, ostride);
 }
 
 // Copies a block-boundary face flux into the face's register (faces between
@@ -496,21 +556,27 @@ __device__ __forceinline__ void cell_update(const StageArgs& a, const LevelGeo& 
   const int cg = (kg * a.Ny + jg) * a.Nx + ig;
   const int ci = (k * a.ny + (j + y0)) * a.nx + (i + x0);
   const int I1 = I1b + i, I2 = I2b + j;
-  double rhs[NV];
+  // flux divergence in the flux arithmetic T (FP32 in the mixed form, whose
+  // face fluxes carry FP32 rounding already), then widened once per variable
+  T rdiv[NV];
+  const T ix = T(geo.idx[0]), iy = T(geo.idx[1]), iz = T(geo.idx[2]);
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
-    double r = -((double)Fx[v * sFx + j * (tx + 1) + i + 1] - (double)Fx[v * sFx + j * (tx + 1) + i]) * geo.idx[0];
-    r += -((double)Fy[v * sFy + (j + 1) * tx + i] - (double)Fy[v * sFy + j * tx + i]) * geo.idx[1];
-    if (DIM == 3) r += -((double)Fz1[v * sFz + c] - (double)Fz0[v * sFz + c]) * geo.idx[2];
-    rhs[v] = r;
+    T r = -(Fx[v * sFx + j * (tx + 1) + i + 1] - Fx[v * sFx + j * (tx + 1) + i]) * ix;
+    r = r - (Fy[v * sFy + (j + 1) * tx + i] - Fy[v * sFy + j * tx + i]) * iy;
+    if (DIM == 3) r = r - (Fz1[v * sFz + c] - Fz0[v * sFz + c]) * iz;
+    rdiv[v] = r;
   }
+  double rhs[NV];
   // sources from the cell's primitives
   {
     T Pc[NV], Uc[NV], S[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) Pc[v] = Pb[(size_t)v * a.ncell + cg];
     if (FLAT) {
-      rhs[PSI] += to_double(-T(a.kappa) * Pc[PSI]);
+      rdiv[PSI] = rdiv[PSI] - T(a.kappa) * Pc[PSI];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) rhs[v] = to_double(rdiv[v]);
     } else {
       const double* crec = geo.tc + (size_t)(I2 * geo.N1 + I1) * CREC;
       Met<T> m;
@@ -527,9 +593,15 @@ __device__ __forceinline__ void cell_update(const StageArgs& a, const LevelGeo& 
       else
         sources_of(m, geo.tc32 + (size_t)(I2 * geo.N1 + I1) * CREC, Pc, s, Uc, T(a.kappa), T(a.ch * a.ch),
                    S);
-      const double sg = crec[C_SG];
+      if (sizeof(T) == 8) {
+        const double sg = crec[C_SG];
 #pragma unroll
-      for (int v = 0; v < NV; ++v) rhs[v] += sg * (double)S[v];
+        for (int v = 0; v < NV; ++v) rhs[v] = to_double(rdiv[v]) + sg * to_double(S[v]);
+      } else {
+        const T sg = T(geo.tc32[(size_t)(I2 * geo.N1 + I1) * CREC + C_SG]);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) rhs[v] = to_double(rdiv[v] + sg * S[v]);
+      }
     }
   }
   // RK combination
@@ -558,16 +630,37 @@ __device__ __forceinline__ void cell_update(const StageArgs& a, const LevelGeo& 
 // ----------------------------------------------------------------------------
 // The stage kernel.  T: flux arithmetic (double: FP64 form; float: mixed form).
 // Every block of every level is an item of the same launch.
+//
+// Per plane k of the CTA's column, three phases separated by CTA barriers:
+//  R  every cell's two reconstructed edges along x (the tile plus one cell on
+//     each x side) and along y (plus one cell on each y side) into shared
+//     memory; in 3-D each z column also reconstructs its cell of plane k+1,
+//     solves the z face between planes k and k+1 from that cell's low edge
+//     and plane k's high edge (kept in shared memory from the previous
+//     plane), and keeps plane k+1's high edge for the next plane;
+//  F  the x and y face fluxes from the edges of the two adjacent cells;
+//  C  the cell updates.
+// Each cell's edges are reconstructed once per direction (up to the one-cell
+// tile halo) instead of once for each of its two faces; the face states are
+// the same numbers as a per-face reconstruction's.
+//
+// Shared memory (T): Fx, Fy, [Fz0, Fz1, EzR in 3-D], ExL, ExR, EyL, EyR.
 // ----------------------------------------------------------------------------
 template <typename T, int DIM, bool FLAT, int MINB>
 __global__ void __launch_bounds__(256, MINB) stage_kernel(StageArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int tx = a.tx, ty = a.ty;
   const int sFx = ty * (tx + 1), sFy = (ty + 1) * tx, sFz = tx * ty;
+  const int nex = (tx + 2) * ty, ney = tx * (ty + 2);
   T* Fx = reinterpret_cast<T*>(smem_raw);
   T* Fy = Fx + NV * sFx;
   T* Fza = Fy + NV * sFy;
-  T* Fzb = Fza + NV * sFz;
+  T* Fzb = Fza + (DIM == 3 ? NV * sFz : 0);
+  T* EzR = Fzb + (DIM == 3 ? NV * sFz : 0);
+  T* ExL = EzR + (DIM == 3 ? NV * sFz : 0);
+  T* ExR = ExL + NV * nex;
+  T* EyL = ExR + NV * nex;
+  T* EyR = EyL + NV * ney;
   __shared__ int s_item;
 
   const double dt = stage_dt(a);
@@ -577,6 +670,8 @@ __global__ void __launch_bounds__(256, MINB) stage_kernel(StageArgs a) {
   unsigned cnt[4] = {0u, 0u, 0u, 0u};
   double rate_max = 0.0;
   const int ntile = a.ntx * a.nty;
+  const int sy = a.Nx, sz = a.Nx * a.Ny;
+  const int nzc = DIM == 3 ? sFz : 0;
 
   int item = a.persistent ? -1 : (int)blockIdx.x;
   for (;;) {
@@ -601,36 +696,73 @@ __global__ void __launch_bounds__(256, MINB) stage_kernel(StageArgs a) {
     T* Fz0 = Fza;
     T* Fz1 = Fzb;
     if (DIM == 3) {
-      // bottom face of plane 0
+      // bottom face of plane 0 from the high edge of plane -1 and the low
+      // edge of plane 0; plane 0's high edge is kept for the face above it
       for (int t = threadIdx.x; t < sFz; t += blockDim.x) {
         const int i = t % tx, j = t / tx;
-        face_flux<T, FLAT>(a, geo, Pb, 2, i + x0 + a.gx, j + y0 + a.gy, a.gz, I1b + i, I2b + j, Fz0 + t, sFz);
+        const int ig = i + x0 + a.gx, jg = j + y0 + a.gy;
+        const int c0 = (a.gz * a.Ny + jg) * a.Nx + ig;
+        T PL[NV], PR[NV], tmp[NV];
+        if (axis_face<FLAT>(a, geo, 2, I2b + j)) {
+#pragma unroll
+          for (int v = 0; v < NV; ++v) Fz0[v * sFz + t] = T(0);
+        } else {
+          cell_edges(a, Pb, sz, c0 - sz, tmp, 1, PL, 1);
+          cell_edges(a, Pb, sz, c0, PR, 1, EzR + t, sFz);
+          positivity_fallback(a, Pb, sz, c0, PL, PR);
+          face_solve<T, FLAT>(a, geo, 2, I1b + i, I2b + j, PL, PR, Fz0 + t, sFz);
+        }
         if (regs) to_register(a, b, 2, 0, (j + y0) * a.nx + i + x0, Fz0 + t, sFz);
       }
     }
     for (int k = 0; k < a.nz; ++k) {
       const int kg = k + a.gz;
-      const int nfx = sFx, nfy = sFy, nfz = DIM == 3 ? sFz : 0;
-      for (int t = threadIdx.x; t < nfx + nfy + nfz; t += blockDim.x) {
-        if (t < nfx) {
-          const int i = t % (tx + 1), j = t / (tx + 1);
-          face_flux<T, FLAT>(a, geo, Pb, 0, i + x0 + a.gx, j + y0 + a.gy, kg, I1b + i, I2b + j, Fx + t, sFx);
-          if (regs && (x0 + i == 0 || x0 + i == a.nx))
-            to_register(a, b, 0, x0 + i == 0 ? 0 : 1, k * a.ny + j + y0, Fx + t, sFx);
-        } else if (t < nfx + nfy) {
-          const int u = t - nfx;
-          const int i = u % tx, j = u / tx;
-          face_flux<T, FLAT>(a, geo, Pb, 1, i + x0 + a.gx, j + y0 + a.gy, kg, I1b + i, I2b + j, Fy + u, sFy);
-          if (regs && (y0 + j == 0 || y0 + j == a.ny))
-            to_register(a, b, 1, y0 + j == 0 ? 0 : 1, k * a.nx + i + x0, Fy + u, sFy);
+      // R: edges (and the z face above plane k)
+      for (int t = threadIdx.x; t < nzc + nex + ney; t += blockDim.x) {
+        if (t < nzc) {
+          const int i = t % tx, j = t / tx;
+          const int ig = i + x0 + a.gx, jg = j + y0 + a.gy;
+          const int c1 = ((kg + 1) * a.Ny + jg) * a.Nx + ig;
+          T PL[NV], PR[NV];
+#pragma unroll
+          for (int v = 0; v < NV; ++v) PL[v] = EzR[v * sFz + t];
+          cell_edges(a, Pb, sz, c1, PR, 1, EzR + t, sFz);
+          positivity_fallback(a, Pb, sz, c1, PL, PR);
+          face_solve<T, FLAT>(a, geo, 2, I1b + i, I2b + j, PL, PR, Fz1 + t, sFz);
+          if (regs && k + 1 == a.nz) to_register(a, b, 2, 1, (j + y0) * a.nx + i + x0, Fz1 + t, sFz);
+        } else if (t < nzc + nex) {
+          const int u = t - nzc;
+          const int i = u % (tx + 2) - 1, j = u / (tx + 2);
+          const int c = (kg * a.Ny + j + y0 + a.gy) * a.Nx + i + x0 + a.gx;
+          cell_edges(a, Pb, 1, c, ExL + u, nex, ExR + u, nex);
         } else {
-          const int u = t - nfx - nfy;
-          const int i = u % tx, j = u / tx;
-          face_flux<T, FLAT>(a, geo, Pb, 2, i + x0 + a.gx, j + y0 + a.gy, kg + 1, I1b + i, I2b + j, Fz1 + u, sFz);
-          if (regs && k + 1 == a.nz) to_register(a, b, 2, 1, (j + y0) * a.nx + i + x0, Fz1 + u, sFz);
+          const int u = t - nzc - nex;
+          const int i = u % tx, j = u / tx - 1;
+          const int c = (kg * a.Ny + j + y0 + a.gy) * a.Nx + i + x0 + a.gx;
+          cell_edges(a, Pb, sy, c, EyL + u, ney, EyR + u, ney);
         }
       }
       __syncthreads();
+      // F: x and y faces
+      for (int t = threadIdx.x; t < sFx + sFy; t += blockDim.x) {
+        if (t < sFx) {
+          const int i = t % (tx + 1), j = t / (tx + 1);
+          const int e = j * (tx + 2) + i;  // edge slot of the low cell
+          edge_face<T, FLAT>(a, geo, Pb, 0, i + x0 + a.gx, j + y0 + a.gy, kg, I1b + i, I2b + j, ExR + e, ExL + e + 1,
+                             nex, Fx + t, sFx);
+          if (regs && (x0 + i == 0 || x0 + i == a.nx))
+            to_register(a, b, 0, x0 + i == 0 ? 0 : 1, k * a.ny + j + y0, Fx + t, sFx);
+        } else {
+          const int u = t - sFx;
+          const int i = u % tx, j = u / tx;
+          edge_face<T, FLAT>(a, geo, Pb, 1, i + x0 + a.gx, j + y0 + a.gy, kg, I1b + i, I2b + j, EyR + u,
+                             EyL + u + tx, ney, Fy + u, sFy);
+          if (regs && (y0 + j == 0 || y0 + j == a.ny))
+            to_register(a, b, 1, y0 + j == 0 ? 0 : 1, k * a.nx + i + x0, Fy + u, sFy);
+        }
+      }
+      __syncthreads();
+      // C: cell updates
       for (int c = threadIdx.x; c < sFz; c += blockDim.x)
         cell_update<T, DIM, FLAT>(a, geo, Pb, b, x0, y0, k, c, Fx, Fy, Fz0, Fz1, dt, cfb, cnt, rate_max);
       __syncthreads();
@@ -835,12 +967,28 @@ __global__ void __launch_bounds__(256) cfl_kernel(StageArgs a) {
   if ((threadIdx.x & 31u) == 0) atomicMax(a.smax_out, (unsigned long long)__double_as_longlong(w));
 }
 
+// Raises a kernel's dynamic shared-memory limit to kMaxDynSmem, or to what
+// the device's opt-in limit leaves beside the kernel's static shared memory
+// if that is less.
+template <typename K>
+static cudaError_t raise_smem_limit(K kernel) {
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, kernel);
+  if (e != cudaSuccess) return e;
+  int dev = 0, optin = 0;
+  e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return e;
+  int lim = optin - (int)fa.sharedSizeBytes;
+  lim = lim < kMaxDynSmem ? lim : kMaxDynSmem;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+}
+
 template <typename T, int DIM, bool FLAT, int MINB>
 static cudaError_t configure_stage_t() {
   static bool configured = false;
   if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(stage_kernel<T, DIM, FLAT, MINB>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaError_t e = raise_smem_limit(stage_kernel<T, DIM, FLAT, MINB>);
     if (e != cudaSuccess) return e;
     configured = true;
   }
@@ -851,8 +999,7 @@ template <typename T, bool FLAT, int MINB>
 static cudaError_t configure_ws_t() {
   static bool configured = false;
   if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(stage_kernel_ws<T, FLAT, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         200 * 1024);
+    cudaError_t e = raise_smem_limit(stage_kernel_ws<T, FLAT, MINB>);
     if (e != cudaSuccess) return e;
     configured = true;
   }
