@@ -178,6 +178,20 @@ bhac_status bhac_graph_launch(bhac_ctx* ctx);
  * the ghost cells of the current state and synchronises the stream. */
 bhac_status bhac_count_flops(bhac_ctx* ctx, double dt, int nsamples, unsigned seed, double out[6]);
 
+/* Self-check utility (the paper has no counterpart).  The stage kernels
+ * replace FP64 compares and FP32<->FP64 conversions by integer bit operations
+ * (GB300 runs those FP64-unit instructions at the cost of an FP64 FMA).  This
+ * runs each replacement beside the hardware instruction on `n` operand pairs
+ * generated on the device from `seed` (random bit patterns; doubles in and
+ * around the float range; round-to-nearest ties; neighbours one ulp apart;
+ * zeros, subnormals, infinities, NaNs) and writes the number of disagreements
+ * per operation to out[8]: [0] a < b on non-NaN pairs, [1] x > 0, [2] x <= 0,
+ * [3] |a| < |b|, [4] IEEE a < b, a <= b, x < 0 with NaN operands included,
+ * [5] isfinite, [6] double -> float (bitwise; NaN as NaN), [7] float -> double.
+ * n in [1, 1<<26].  Synchronous (default stream); the counters are a
+ * file-scope device array, so concurrent calls race on them. */
+bhac_status bhac_check_bit_ops(long long n, unsigned seed, long long out[8]);
+
 /* Allocation-free CFL time step, for callers that cannot allocate device memory
  * (no counterpart in the paper: it exists only because of how some callers run).
  * Such callers include code that runs while another component captures the

@@ -21,7 +21,7 @@ __all__ = [
     "bhac_query_sizes", "bhac_init_grid", "bhac_set_metric", "bhac_set_prims", "bhac_fill_ghosts",
     "bhac_cfl_dt", "bhac_step", "bhac_stage", "bhac_get_prims", "bhac_get_cons", "bhac_get_diagnostics",
     "bhac_set_launch", "bhac_count_flops", "bhac_graph_capture", "bhac_graph_launch", "bhac_cfl_dt_static", "bhac_destroy",
-    "bhac_status_string",
+    "bhac_status_string", "bhac_check_bit_ops",
 ]
 
 NV = 9
@@ -86,6 +86,7 @@ def lib():
             "bhac_graph_capture": ([vp, i], i),
             "bhac_graph_launch": ([vp], i),
             "bhac_cfl_dt_static": ([G, B, i, vp, vp, vp], i),
+            "bhac_check_bit_ops": ([C.c_longlong, C.c_uint, C.POINTER(C.c_longlong)], i),
             "bhac_destroy": ([vp], None),
             "bhac_status_string": ([i], C.c_char_p),
         }
@@ -172,6 +173,14 @@ def bhac_count_flops(ctx, dt: float, nsamples: int = 2000, seed: int = 1):
     _check("bhac_count_flops", lib().bhac_count_flops(ctx, dt, nsamples, seed, out))
     return {"fp64_flops": out[0], "fp32_flops": out[1], "fp64_special": out[2], "fp32_special": out[3],
             "samples": int(out[4]), "blocks": int(out[5])}
+
+
+def bhac_check_bit_ops(n: int, seed: int = 1):
+    """Disagreement counts of the integer-pipe compares and conversions with
+    the hardware instructions (see the header for the eight operations)."""
+    out = (C.c_longlong * 8)()
+    _check("bhac_check_bit_ops", lib().bhac_check_bit_ops(n, seed, out))
+    return list(out)
 
 
 def bhac_graph_capture(ctx, nsteps: int):

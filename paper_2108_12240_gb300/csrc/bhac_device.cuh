@@ -166,9 +166,45 @@ __device__ __forceinline__ double rcp_t(double x) { return 1.0 / x; }
 __device__ __forceinline__ float rcp_t(float x) { return __frcp_rn(x); }
 __device__ __forceinline__ double abs_t(double x) { return fabs(x); }
 __device__ __forceinline__ float abs_t(float x) { return fabsf(x); }
-__device__ __forceinline__ bool finite_t(double x) { return isfinite(x); }
+// exponent field not all ones (integer test, off the FP64 unit)
+__device__ __forceinline__ bool finite_t(double x) {
+  return ((unsigned)__double2hiint(x) & 0x7FF00000u) != 0x7FF00000u;
+}
+// FP32 <-> FP64 conversions by integer bit operations.  The FP64 unit
+// executes conversion instructions at the cost of an FP64 FMA; rearranging
+// the bits on the integer pipes gives the same IEEE results.  Widening is
+// exact: a normal float's exponent is rebiased (+896) and its 23-bit
+// significand placed at the top of the 52-bit one; narrowing rounds the
+// 52-bit significand to 23 bits to nearest, ties to even (round bit = bit 28
+// of the low word, sticky = bits 0..27), a carry out of the significand
+// incrementing the exponent and reaching +-inf past the largest float.
+// Zeros are handled in place; subnormal, overflowing, infinite and NaN
+// operands take the hardware conversion.
+__device__ __forceinline__ double widen_f32(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned e = (u >> 23) & 0xFFu;
+  if (e - 1u < 254u) {
+    const unsigned hi = (u & 0x80000000u) | ((e + 896u) << 20) | ((u >> 3) & 0xFFFFFu);
+    return __hiloint2double((int)hi, (int)(u << 29));
+  }
+  if ((u & 0x7FFFFFFFu) == 0u) return __hiloint2double((int)(u & 0x80000000u), 0);
+  return (double)f;
+}
+__device__ __forceinline__ float narrow_f64(double x) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const unsigned E = (hi >> 20) & 0x7FFu;
+  if (E - 897u < 254u) {  // the float exponent E - 896 is in [1, 254]
+    unsigned r = (hi & 0x80000000u) | ((E - 896u) << 23) | ((hi & 0xFFFFFu) << 3) | (lo >> 29);
+    const unsigned rb = (lo >> 28) & 1u;
+    const unsigned sticky = (lo & 0x0FFFFFFFu) != 0u ? 1u : 0u;
+    r += rb & (sticky | (r & 1u));
+    return __uint_as_float(r);
+  }
+  if (((hi & 0x7FFFFFFFu) | lo) == 0u) return __uint_as_float(hi & 0x80000000u);
+  return __double2float_rn(x);
+}
 __device__ __forceinline__ double to_double(double x) { return x; }
-__device__ __forceinline__ double to_double(float x) { return (double)x; }
+__device__ __forceinline__ double to_double(float x) { return widen_f32(x); }
 
 // Ordered selections.  On GB300 an FP64 compare occupies the SM's FP64 unit
 // exactly like an FP64 fused multiply-add (two lanes per clock per SM), while
@@ -218,6 +254,41 @@ BHAC_HD bool le0_t(double x) {
   return x <= 0.0;
 #endif
 }
+// IEEE compares of doubles (false when either operand is NaN), for the FP64
+// inversion, whose failure handling relies on NaN comparing false.
+__device__ __forceinline__ bool isnan_bits(double x) {
+  return ((unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFULL) > kExpAll;
+}
+template <typename T>
+BHAC_HD bool lt_x(T a, T b) { return a < b; }
+template <typename T>
+BHAC_HD bool le_x(T a, T b) { return a <= b; }
+template <typename T>
+BHAC_HD bool lt0_x(T x) { return x < T(0); }
+BHAC_HD bool lt_x(double a, double b) {
+#ifdef __CUDA_ARCH__
+  return okey(a) < okey(b) && !isnan_bits(a) && !isnan_bits(b);
+#else
+  return a < b;
+#endif
+}
+BHAC_HD bool le_x(double a, double b) {
+#ifdef __CUDA_ARCH__
+  return okey(a) <= okey(b) && !isnan_bits(a) && !isnan_bits(b);
+#else
+  return a <= b;
+#endif
+}
+BHAC_HD bool lt0_x(double x) {
+#ifdef __CUDA_ARCH__
+  // sign bit set, magnitude in (0, +inf]
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  return (b >> 63) && (b & 0x7FFFFFFFFFFFFFFFULL) - 1ULL < kExpAll;
+#else
+  return x < 0.0;
+#endif
+}
+
 BHAC_HD bool lt_abs_t(double a, double b) {
 #ifdef __CUDA_ARCH__
   const unsigned long long m = 0x7FFFFFFFFFFFFFFFULL;

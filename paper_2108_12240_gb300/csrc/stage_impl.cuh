@@ -114,13 +114,13 @@ BHAC_HD int con2prim_t(const Met<T>& m, const T* U, const T* Pg, T rho_fl, T p_f
   int status = 0;
   bool solved = false;
   T Z = T(0.0), v2 = T(0.0);
-  if (fin && q.D > T(0.0) && q.E > T(0.0)) {
+  if (fin && gt0_t(q.D) && gt0_t(q.E)) {
     const T gu1 = m.g11 * Pg[U1] + m.g13 * Pg[U3];
     const T gu2 = m.g22 * Pg[U2];
     const T gu3 = m.g13 * Pg[U1] + m.g33 * Pg[U3];
     const T usq = Pg[U1] * gu1 + Pg[U2] * gu2 + Pg[U3] * gu3;
     const T Z0g = (Pg[RHO] + T(gam_fac) * Pg[PRS]) * (T(1.0) + usq);
-    const T Z0 = (Z0g > T(0.0) && finite_t(Z0g)) ? Z0g : q.E;
+    const T Z0 = (gt0_t(Z0g) && finite_t(Z0g)) ? Z0g : q.E;
     Z = Z0;
     v2 = usq / (T(1.0) + usq);
     const T BS2 = q.BS * q.BS;
@@ -143,10 +143,10 @@ BHAC_HD int con2prim_t(const Met<T>& m, const T* U, const T* Pg, T rho_fl, T p_f
       const T dZ = (-f1 * j22 + f2 * j12) * idet;
       const T dv2 = (-f2 * j11 + f1 * j21) * idet;
       T Zn = Z + dZ, v2n = v2 + dv2;
-      if (!(Zn > T(0.0))) Zn = T(0.5) * Z;
-      if (v2n < T(0.0)) v2n = T(0.5) * v2;
-      if (v2n >= T(1.0)) v2n = T(0.5) * (v2 + T(1.0));
-      const bool conv = abs_t(Zn - Z) <= T(tol) * Zn;
+      if (!gt0_t(Zn)) Zn = T(0.5) * Z;
+      if (lt0_x(v2n)) v2n = T(0.5) * v2;
+      if (le_x(T(1.0), v2n)) v2n = T(0.5) * (v2 + T(1.0));
+      const bool conv = le_x(abs_t(Zn - Z), T(tol) * Zn);
       Z = Zn;
       v2 = v2n;
       if (!finite_t(Z) || !finite_t(v2)) break;
@@ -156,8 +156,8 @@ BHAC_HD int con2prim_t(const Met<T>& m, const T* U, const T* Pg, T rho_fl, T p_f
       }
       if (conv) polish = true;
     }
-    if (solved && !(v2 >= T(0.0) && v2 < T(1.0) && Z > T(0.0))) solved = false;
-    if (solved && !(q.D * sqrt_t(T(1.0) - v2) > T(0.0))) solved = false;
+    if (solved && !(le_x(T(0.0), v2) && lt_x(v2, T(1.0)) && gt0_t(Z))) solved = false;
+    if (solved && !gt0_t(q.D * sqrt_t(T(1.0) - v2))) solved = false;
     if (!solved) {
       T lo = Z0, hi = Z0;
       int k = 0;
@@ -212,11 +212,11 @@ BHAC_HD int con2prim_t(const Met<T>& m, const T* U, const T* Pg, T rho_fl, T p_f
   P[B3] = U[B3];
   P[PSI] = U[PSI];
   bool fl = false;
-  if (!(P[RHO] >= rho_fl)) {
+  if (!le_x(rho_fl, P[RHO])) {
     P[RHO] = rho_fl;
     fl = true;
   }
-  if (!(P[PRS] >= p_fl)) {
+  if (!le_x(p_fl, P[PRS])) {
     P[PRS] = p_fl;
     fl = true;
   }
@@ -224,7 +224,7 @@ BHAC_HD int con2prim_t(const Met<T>& m, const T* U, const T* Pg, T rho_fl, T p_f
   const T gu2 = m.g22 * P[U2];
   const T gu3 = m.g13 * P[U1] + m.g33 * P[U3];
   const T usq = P[U1] * gu1 + P[U2] * gu2 + P[U3] * gu3;
-  if (T(1.0) + usq > wmax * wmax) {
+  if (lt_x(wmax * wmax, T(1.0) + usq)) {
     const T sc = sqrt_t((wmax * wmax - T(1.0)) / usq);
     P[U1] = P[U1] * sc;
     P[U2] = P[U2] * sc;
@@ -507,7 +507,7 @@ __device__ __forceinline__ void finish_cell(const StageArgs& a, const LevelGeo& 
   if (sizeof(T) == 4) {
     float* P3 = a.P32_out + (size_t)b * NV * a.ncell + cg;
 #pragma unroll
-    for (int v = 0; v < NV; ++v) P3[(size_t)v * a.ncell] = (float)Pn[v];
+    for (int v = 0; v < NV; ++v) P3[(size_t)v * a.ncell] = narrow_f64(Pn[v]);
   }
   if (a.stage == 2) {
     double acg[3] = {1.0, 1.0, 1.0};

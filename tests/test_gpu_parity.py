@@ -389,3 +389,12 @@ def test_mixed_full_config_2_per_variable(gb):
     s, o, _ = one_step(gb, g, pb.fm_torus_prims(g), precision="mixed")
     err = assert_parity(s.cons(), o.cons(), TOLMIX, "mixed config 2", g)
     print("mixed vs oracle per conserved variable (D S1 S2 S3 tau B1 B2 B3 psi):", err)
+
+
+def test_integer_pipe_compares_and_conversions_match_hardware(gb):
+    """The stage kernels' integer-bit replacements of FP64 compares and of
+    FP32 <-> FP64 conversions agree with the hardware instructions on 2^24
+    generated operand pairs (ties, zeros, subnormals, overflow edge, NaN)."""
+    bad = gb.bhac_check_bit_ops(1 << 24, seed=12345)
+    assert bad == [0] * 8, bad
+
