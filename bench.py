@@ -205,32 +205,106 @@ def time_form(gb, torch, g, P, form, steps, warmup, stream, count_flops=True):
     return out
 
 
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic_stage_kernel_torus_3d_large.txt")
+
+
+def kernel_fingerprint() -> str:
+    """sha256 over the CUDA sources and the public header (sorted by name)."""
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2108_12240_gb300", "csrc")
+    files = sorted(f for f in os.listdir(csrc) if f.endswith((".cu", ".cuh", ".h")))
+    for f in files + ["../../include/bhac_gb300.h"]:
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(f.encode() + b"\0" + fh.read())
+    return h.hexdigest()
+
+
+def shape_key(ls) -> str:
+    """Launch shape as recorded beside a traffic figure."""
+    # the persistent schedule (which CTA takes which item) does not change the
+    # per-launch DRAM bytes and is left out
+    return f"{ls['tx']}x{ls['ty']}/{ls['threads']}/minctas{ls['min_ctas']}/producers{ls['producer_warps']}"
+
+
+def recorded_traffic(workload_name, form, tile):
+    """DRAM bytes per stage-kernel launch from the committed ncu summary, when
+    it was taken of these exact sources, this workload, form and tile; else None."""
+    try:
+        with open(TRAFFIC_FILE) as f:
+            kv = dict(line.split(":", 1) for line in f.read().splitlines() if ":" in line and not line.startswith("#"))
+    except OSError:
+        return None
+    kv = {k.strip(): v.strip() for k, v in kv.items()}
+    if kv.get("sources_sha256") != kernel_fingerprint() or kv.get("workload") != workload_name:
+        return None
+    if kv.get(f"{form}_tile") != tile:
+        return None
+    try:
+        return float(kv[f"{form}_dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
 def e2e_form(gb, torch, g, P, form, steps, stream):
-    """Through the public API with host buffers: every step copies the inputs
-    host->device from pinned memory, runs the step and reads the result back."""
+    """Through the public API with host buffers: every step copies its inputs
+    host->device from pinned memory, runs set_prims, the CFL step and the RK
+    step, and reads the primitives back device->host.  The copies run on
+    their own streams (one per direction, double-buffered device staging), so
+    step i+1's upload and step i-1's download overlap step i's kernels; all
+    of them are inside the timed region."""
     s = gb.Solver(g, form, stream=stream)
+    from paper_2108_12240_gb300 import autotune
+    autotune.cached_or_default(s)  # the shape time_form tuned for this grid and form
     host_in = torch.from_numpy(np.ascontiguousarray(P)).pin_memory()
-    host_out = torch.empty(host_in.shape, dtype=torch.float64).pin_memory()
-    dev = torch.empty(host_in.shape, dtype=torch.float64, device="cuda")
-    out_dev = torch.empty_like(dev)
+    host_out = [torch.empty(host_in.shape, dtype=torch.float64).pin_memory() for _ in range(2)]
+    dev_in = [torch.empty(host_in.shape, dtype=torch.float64, device="cuda") for _ in range(2)]
+    dev_out = [torch.empty(host_in.shape, dtype=torch.float64, device="cuda") for _ in range(2)]
+    h2d, d2h = torch.cuda.Stream(), torch.cuda.Stream()
     nbytes = host_in.numel() * 8
+    ev_in = [torch.cuda.Event() for _ in range(2)]      # upload into dev_in[b] done
+    ev_used = [torch.cuda.Event() for _ in range(2)]    # set_prims has consumed dev_in[b]
+    ev_out = [torch.cuda.Event() for _ in range(2)]     # dev_out[b] written
+    ev_read = [torch.cuda.Event() for _ in range(2)]    # dev_out[b] downloaded
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-    with torch.cuda.stream(stream):
-        ev[0].record(stream)
-        for _ in range(steps):
-            dev.copy_(host_in, non_blocking=True)
-            gb.bhac_set_prims(s.ctx, dev.data_ptr(), True)
+    t0.record(stream)
+    h2d.wait_event(t0)
+    d2h.wait_event(t0)
+    with torch.cuda.stream(h2d):
+        dev_in[0].copy_(host_in, non_blocking=True)
+        ev_in[0].record(h2d)
+    for i in range(steps):
+        b = i % 2
+        if i + 1 < steps:
+            with torch.cuda.stream(h2d):
+                if i >= 1:
+                    h2d.wait_event(ev_used[1 - b])
+                dev_in[1 - b].copy_(host_in, non_blocking=True)
+                ev_in[1 - b].record(h2d)
+        stream.wait_event(ev_in[b])
+        if i >= 2:
+            stream.wait_event(ev_read[b])
+        with torch.cuda.stream(stream):
+            gb.bhac_set_prims(s.ctx, dev_in[b].data_ptr(), True)
+            ev_used[b].record(stream)
             gb.bhac_cfl_dt(s.ctx, False)
             gb.bhac_step(s.ctx, 0.0)
-            gb.bhac_get_prims(s.ctx, out_dev.data_ptr(), True)
-            host_out.copy_(out_dev, non_blocking=True)
-        ev[1].record(stream)
+            gb.bhac_get_prims(s.ctx, dev_out[b].data_ptr(), True)
+            ev_out[b].record(stream)
+        with torch.cuda.stream(d2h):
+            d2h.wait_event(ev_out[b])
+            host_out[b].copy_(dev_out[b], non_blocking=True)
+            ev_read[b].record(d2h)
+    stream.wait_stream(d2h)
+    stream.wait_stream(h2d)
+    t1.record(stream)
     torch.cuda.synchronize()
-    ms = ev[0].elapsed_time(ev[1])
+    ms = t0.elapsed_time(t1)
     s.close()
     return {"value": g.ncells * 2 * steps / (ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": nbytes,
-            "d2h_bytes_per_step": nbytes, "ms_per_step": ms / steps, "kernels_per_step": 8}
+            "d2h_bytes_per_step": nbytes, "ms_per_step": ms / steps, "kernels_per_step": 8,
+            "copies": "H2D and D2H on their own streams, double-buffered, overlapping the step's kernels"}
 
 
 def sample_grid(name):
@@ -401,8 +475,11 @@ def main():
         cells = g.ncells
         ach64 = fl["fp64_flops"] * cells / stage_s / 1e12
         bytes_alg = (288 if form == "fp64" else 252) * cells
+        traffic = recorded_traffic(args.workload, form, shape_key(r["launch_shape"]))
         return {"bound": "alu", "achieved": ach64, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": ach64 / FP64_PEAK_TFLOPS, "traffic": None, "kernel": "stage_kernel",
+                "frac": ach64 / FP64_PEAK_TFLOPS, "traffic": traffic, "kernel": "stage_kernel",
+                "traffic_source": os.path.relpath(TRAFFIC_FILE, ROOT) if traffic else None,
+                "traffic_over_algorithmic": traffic / bytes_alg if traffic else None,
                 "stage_ms": r["stage_ms_mean"], "ghost_fill_ms": r["fill_ms"],
                 "peak_kind": "derived FP64: 152 SMs x 2070 MHz x 4 flops/clk/SM",
                 "fp64_flops_per_zone_stage": fl["fp64_flops"],
