@@ -19,6 +19,7 @@ from __future__ import annotations
 import argparse
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -154,8 +155,10 @@ def job_value(cells: int, world: int, ms_per_step: float) -> float:
 TUNE = True
 
 
-def time_form(gb, torch, g, P, form, steps, warmup, stream, count_flops=True):
-    """Device-resident timing of `steps` steps of one form."""
+def time_form(gb, torch, g, P, form, steps, warmup, stream, count_flops=True, graph_repeats=3, graph_steps=1):
+    """Device-resident timing of `steps` steps of one form (direct launches,
+    per-stage events), then the same step replayed from a CUDA graph:
+    median over `graph_repeats` repeats of `graph_steps` replays."""
     from paper_2108_12240_gb300 import autotune
 
     s = gb.Solver(g, form, stream=stream)
@@ -198,6 +201,26 @@ def time_form(gb, torch, g, P, form, steps, warmup, stream, count_flops=True):
                                                  "persistent": shape[3], "min_ctas": shape[4],
                                                  "producer_warps": shape[5] if len(shape) > 5 else 0,
                                                  "candidates_timed": len(tried)}}
+    if graph_repeats > 0:
+        if graph_steps <= 0:  # enough replays for about 50 ms per repeat
+            graph_steps = max(1, min(2000, int(50.0 / max(total_ms / steps, 1e-3))))
+        s.capture(1)
+        for _ in range(2):
+            s.replay()
+        torch.cuda.synchronize()
+        reps = []
+        for _ in range(graph_repeats):
+            ge = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            with torch.cuda.stream(stream):
+                ge[0].record(stream)
+                for _ in range(graph_steps):
+                    s.replay()
+                ge[1].record(stream)
+            torch.cuda.synchronize()
+            reps.append(ge[0].elapsed_time(ge[1]) / graph_steps)
+        out["graph"] = {"ms_per_step_median": statistics.median(reps), "repeats": graph_repeats,
+                        "steps_per_repeat": graph_steps}
+    out["launches_per_step"] = s.launches_per_step()
     out["c2p_counts"] = [int(x) for x in s.diagnostics()]
     if count_flops:
         out["flops"] = s.count_flops(max(dt, 1e-30), nsamples=4000, seed=7)
@@ -238,73 +261,46 @@ def recorded_traffic(workload_name, form, tile):
     kv = {k.strip(): v.strip() for k, v in kv.items()}
     if kv.get("sources_sha256") != kernel_fingerprint() or kv.get("workload") != workload_name:
         return None
-    if kv.get(f"{form}_tile") != tile:
-        return None
     try:
-        return float(kv[f"{form}_dram_bytes_per_launch"])
-    except (KeyError, ValueError):
+        return float(kv[f"traffic {form} {tile}"].split()[0])
+    except (KeyError, ValueError, IndexError):
         return None
 
 
 def e2e_form(gb, torch, g, P, form, steps, stream):
     """Through the public API with host buffers: every step copies its inputs
     host->device from pinned memory, runs set_prims, the CFL step and the RK
-    step, and reads the primitives back device->host.  The copies run on
-    their own streams (one per direction, double-buffered device staging), so
-    step i+1's upload and step i-1's download overlap step i's kernels; all
-    of them are inside the timed region."""
+    step, reads the primitives back and copies them device->host, all on the
+    solver's stream inside the timed region.  (Copies on their own streams
+    overlapping the kernels measured slower: 103 vs 99 ms per step on the
+    512x256x256 torus; the streaming copies displace the stage kernel's L2
+    working set.)"""
     s = gb.Solver(g, form, stream=stream)
     from paper_2108_12240_gb300 import autotune
     autotune.cached_or_default(s)  # the shape time_form tuned for this grid and form
     host_in = torch.from_numpy(np.ascontiguousarray(P)).pin_memory()
-    host_out = [torch.empty(host_in.shape, dtype=torch.float64).pin_memory() for _ in range(2)]
-    dev_in = [torch.empty(host_in.shape, dtype=torch.float64, device="cuda") for _ in range(2)]
-    dev_out = [torch.empty(host_in.shape, dtype=torch.float64, device="cuda") for _ in range(2)]
-    h2d, d2h = torch.cuda.Stream(), torch.cuda.Stream()
+    host_out = torch.empty(host_in.shape, dtype=torch.float64).pin_memory()
+    dev = torch.empty(host_in.shape, dtype=torch.float64, device="cuda")
+    out_dev = torch.empty_like(dev)
     nbytes = host_in.numel() * 8
-    ev_in = [torch.cuda.Event() for _ in range(2)]      # upload into dev_in[b] done
-    ev_used = [torch.cuda.Event() for _ in range(2)]    # set_prims has consumed dev_in[b]
-    ev_out = [torch.cuda.Event() for _ in range(2)]     # dev_out[b] written
-    ev_read = [torch.cuda.Event() for _ in range(2)]    # dev_out[b] downloaded
-    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
-    t0.record(stream)
-    h2d.wait_event(t0)
-    d2h.wait_event(t0)
-    with torch.cuda.stream(h2d):
-        dev_in[0].copy_(host_in, non_blocking=True)
-        ev_in[0].record(h2d)
-    for i in range(steps):
-        b = i % 2
-        if i + 1 < steps:
-            with torch.cuda.stream(h2d):
-                if i >= 1:
-                    h2d.wait_event(ev_used[1 - b])
-                dev_in[1 - b].copy_(host_in, non_blocking=True)
-                ev_in[1 - b].record(h2d)
-        stream.wait_event(ev_in[b])
-        if i >= 2:
-            stream.wait_event(ev_read[b])
-        with torch.cuda.stream(stream):
-            gb.bhac_set_prims(s.ctx, dev_in[b].data_ptr(), True)
-            ev_used[b].record(stream)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    with torch.cuda.stream(stream):
+        ev[0].record(stream)
+        for _ in range(steps):
+            dev.copy_(host_in, non_blocking=True)
+            gb.bhac_set_prims(s.ctx, dev.data_ptr(), True)
             gb.bhac_cfl_dt(s.ctx, False)
             gb.bhac_step(s.ctx, 0.0)
-            gb.bhac_get_prims(s.ctx, dev_out[b].data_ptr(), True)
-            ev_out[b].record(stream)
-        with torch.cuda.stream(d2h):
-            d2h.wait_event(ev_out[b])
-            host_out[b].copy_(dev_out[b], non_blocking=True)
-            ev_read[b].record(d2h)
-    stream.wait_stream(d2h)
-    stream.wait_stream(h2d)
-    t1.record(stream)
+            gb.bhac_get_prims(s.ctx, out_dev.data_ptr(), True)
+            host_out.copy_(out_dev, non_blocking=True)
+        ev[1].record(stream)
     torch.cuda.synchronize()
-    ms = t0.elapsed_time(t1)
+    ms = ev[0].elapsed_time(ev[1])
+    launches = s.launches_per_step() + 4  # + scatter, init_cons, cfl, gather
     s.close()
     return {"value": g.ncells * 2 * steps / (ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": nbytes,
-            "d2h_bytes_per_step": nbytes, "ms_per_step": ms / steps, "kernels_per_step": 8,
-            "copies": "H2D and D2H on their own streams, double-buffered, overlapping the step's kernels"}
+            "d2h_bytes_per_step": nbytes, "ms_per_step": ms / steps, "kernels_per_step": launches}
 
 
 def sample_grid(name):
@@ -335,7 +331,56 @@ def cpu_baseline(name, budget_s=20.0):
     nc = [g.nx[d] * g.nroot[d] for d in range(3)]
     return {"value": g.ncells * 2 * n / el, "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": f"{n} oracle steps of the same problem at {nc[0]}x{nc[1]}x{nc[2]} cells "
-                      f"({g.nb} blocks of {g.nx[0]}x{g.nx[1]}x{g.nx[2]}), {el:.1f} s"}
+                      f"({g.nb} blocks of {g.nx[0]}x{g.nx[1]}x{g.nx[2]}), {el:.1f} s",
+            "single_thread": cpu_single_thread(name), "cpu_model": cpu_model()}
+
+
+def cpu_model() -> str:
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return platform.processor() or platform.machine()
+
+
+_SINGLE = """
+import sys, time, json
+sys.path.insert(0, {root!r})
+import oracle, problems as pb
+g = pb.torus_3d_large(cells=(64, 32, 32)) if {name!r} == "torus_3d_large" else None
+if g is None:
+    print(json.dumps(None)); raise SystemExit
+o = oracle.Oracle(g)
+o.set_prims(pb.fm_torus_prims(g))
+dt = o.cfl_dt()
+n, t0 = 0, time.perf_counter()
+while True:
+    o.step(dt); n += 1
+    el = time.perf_counter() - t0
+    if el > {budget} or n >= 20:
+        break
+print(json.dumps({{"value": g.ncells * 2 * n / el, "steps": n, "seconds": el}}))
+"""
+
+
+def cpu_single_thread(name, budget_s=5.0):
+    """The oracle on one host thread (OMP_NUM_THREADS=1, own process) on a
+    64x32x32-cell sample of the same torus and block shape."""
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    code = _SINGLE.format(root=ROOT, name=name, budget=budget_s)
+    try:
+        r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=120)
+        res = json.loads(r.stdout.strip().splitlines()[-1]) if r.returncode == 0 and r.stdout.strip() else None
+    except (OSError, subprocess.SubprocessError, ValueError):
+        res = None
+    if not res:
+        return None
+    return {"value": res["value"], "unit": UNIT, "cores": 1,
+            "sample": f"{res['steps']} oracle steps at 64x32x32 cells (4 blocks of 32x32x16), "
+                      f"{res['seconds']:.1f} s"}
 
 
 def reference_arm(args, rank):
@@ -367,6 +412,63 @@ def reference_arm(args, rank):
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def shape_runs(args):
+    """For a profiler capture: the workload in the given launch shapes, each
+    set_launch, set_prims, cfl_dt and four device-dt steps (no timing, no output
+    but one line per shape)."""
+    import torch
+
+    import paper_2108_12240_gb300 as gb
+
+    torch.cuda.set_device(0)
+    form, shapes = args.shape_runs[0], [tuple(int(x) for x in a.split(",")) for a in args.shape_runs[1:]]
+    g, _ = workload(args.workload)
+    P = initial_prims(g)
+    stream = torch.cuda.Stream()
+    s = gb.Solver(g, form, stream=stream)
+    for sh in shapes:
+        s.set_launch(*sh)
+        s.set_prims(P)
+        s.cfl_dt()
+        for _ in range(4):
+            s.step(0.0)
+        torch.cuda.synchronize()
+        print(form, sh, "done", flush=True)
+    s.close()
+
+
+CONFIGS = ["shock_tube_2d", "torus_2d", "torus_3d", "amr_torus", "torus_3d_large"]
+
+
+def all_configs(args):
+    """Every workload configuration (0: 2-D shock tube ... 4: the 512x256x256
+    torus), both forms: zone-updates/s with direct launches and with CUDA-graph
+    replays (median of 15 repeats), FP64 flop fraction.  One JSON line per
+    configuration; not the bench contract line."""
+    import torch
+
+    import paper_2108_12240_gb300 as gb
+
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    for cfg, name in enumerate(CONFIGS):
+        g, desc = workload(name)
+        P = initial_prims(g)
+        forms = {}
+        for form in ("mixed", "fp64"):
+            r = time_form(gb, torch, g, P, form, args.steps, args.warmup, stream, graph_repeats=15, graph_steps=0)
+            stage_s = r["stage_ms_mean"] * 1e-3
+            ach = r["flops"]["fp64_flops"] * g.ncells / stage_s / 1e12
+            forms[form] = {"zone_updates_per_s": job_value(g.ncells, 1, r["ms_per_step"]),
+                           "zone_updates_per_s_graph": job_value(g.ncells, 1, r["graph"]["ms_per_step_median"]),
+                           "ms_per_step": r["ms_per_step"], "graph": r["graph"], "stage_ms": r["stage_ms_mean"],
+                           "ghost_fill_ms": r["fill_ms"], "fp64_flops_per_zone_stage": r["flops"]["fp64_flops"],
+                           "fp64_frac": ach / FP64_PEAK_TFLOPS, "launch_shape": r["launch_shape"]}
+        state_mb = g.ncells * 9 * 8 * 2 / 1e6
+        print(json.dumps({"config": cfg, "workload": name, "desc": desc, "cells": g.ncells, "blocks": g.nb,
+                          "state_mb_fp64": state_mb, "l2_resident": state_mb < 100, "forms": forms}), flush=True)
 
 
 def sweep_blocks(args):
@@ -407,12 +509,21 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--sweep-blocks", action="store_true", help="block-shape roofline sweep instead of the bench line")
+    ap.add_argument("--all-configs", action="store_true", help="every workload configuration, one line each")
+    ap.add_argument("--shape-runs", nargs="+", metavar="FORM_OR_SHAPE",
+                    help="FORM tx,ty,threads,persistent,min_ctas,producers ...: four steps per shape, for ncu")
     ap.add_argument("--no-tune", action="store_true", help="use the cached launch shape (or the default) without timing candidates")
     args = ap.parse_args()
     global TUNE
     TUNE = not args.no_tune
     if args.sweep_blocks:
         sweep_blocks(args)
+        return
+    if args.all_configs:
+        all_configs(args)
+        return
+    if args.shape_runs:
+        shape_runs(args)
         return
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -505,7 +616,7 @@ def main():
         "roofline": roofline(head),
         "cpu_baseline": cpu,
         "e2e": e2e,
-        "gpu_launches": 4 * args.steps,
+        "gpu_launches": results[head]["launches_per_step"] * args.steps,
         "clocks": results[head]["clocks"],
         "peaks": {"kind": pk_kind, "hbm_gbs": pk.get("hbm_gbs")},
     }

@@ -143,6 +143,11 @@ bhac_status bhac_get_cons(bhac_ctx* ctx, double* out, int on_device);
  * [3] failed (previous primitives kept).  Synchronises the stream. */
 bhac_status bhac_get_diagnostics(bhac_ctx* ctx, long long counts[4]);
 
+/* Kernel launches one bhac_step makes on the context's stream: per stage one
+ * cross-level node pass per dependency depth (AMR grids), the ghost gather,
+ * the stage kernel and, where levels meet, the reflux kernel. */
+bhac_status bhac_launches_per_step(const bhac_ctx* ctx, int* launches);
+
 /* Kernel launch shape of the stage kernel: tile of tx x ty cells per CTA column
  * (must divide the block), threads per CTA (a multiple of 32, at most 256),
  * persistent = k > 0 for k CTAs per SM pulling (block, tile) items from a device

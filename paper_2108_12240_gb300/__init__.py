@@ -21,7 +21,7 @@ __all__ = [
     "bhac_query_sizes", "bhac_init_grid", "bhac_set_metric", "bhac_set_prims", "bhac_fill_ghosts",
     "bhac_cfl_dt", "bhac_step", "bhac_stage", "bhac_get_prims", "bhac_get_cons", "bhac_get_diagnostics",
     "bhac_set_launch", "bhac_count_flops", "bhac_graph_capture", "bhac_graph_launch", "bhac_cfl_dt_static", "bhac_destroy",
-    "bhac_status_string", "bhac_check_bit_ops",
+    "bhac_status_string", "bhac_check_bit_ops", "bhac_launches_per_step",
 ]
 
 NV = 9
@@ -87,6 +87,7 @@ def lib():
             "bhac_graph_launch": ([vp], i),
             "bhac_cfl_dt_static": ([G, B, i, vp, vp, vp], i),
             "bhac_check_bit_ops": ([C.c_longlong, C.c_uint, C.POINTER(C.c_longlong)], i),
+            "bhac_launches_per_step": ([vp, C.POINTER(i)], i),
             "bhac_destroy": ([vp], None),
             "bhac_status_string": ([i], C.c_char_p),
         }
@@ -181,6 +182,12 @@ def bhac_check_bit_ops(n: int, seed: int = 1):
     out = (C.c_longlong * 8)()
     _check("bhac_check_bit_ops", lib().bhac_check_bit_ops(n, seed, out))
     return list(out)
+
+
+def bhac_launches_per_step(ctx) -> int:
+    n = C.c_int(0)
+    _check("bhac_launches_per_step", lib().bhac_launches_per_step(ctx, C.byref(n)))
+    return n.value
 
 
 def bhac_graph_capture(ctx, nsteps: int):
@@ -323,6 +330,9 @@ class Solver:
 
     def count_flops(self, dt: float, nsamples: int = 2000, seed: int = 1):
         return bhac_count_flops(self.ctx, dt, nsamples, seed)
+
+    def launches_per_step(self) -> int:
+        return bhac_launches_per_step(self.ctx)
 
     def capture(self, nsteps: int):
         bhac_graph_capture(self.ctx, nsteps)

@@ -536,6 +536,16 @@ bhac_status bhac_stage(bhac_ctx* c, int stage, double dt) {
   return s;
 }
 
+bhac_status bhac_launches_per_step(const bhac_ctx* c, int* out) {
+  if (!c || !out) return BHAC_ERR_ARG;
+  int per_fill = 1;  // the ghost gather
+  for (size_t dep = 1; dep < c->depth_start.size(); ++dep)
+    if (c->depth_start[dep] > c->depth_start[dep - 1]) ++per_fill;  // one cross-level node pass per depth
+  const int per_stage = per_fill + 1 + (c->nrcells > 0 ? 1 : 0);   // + stage kernel (+ reflux)
+  *out = 2 * per_stage;
+  return BHAC_OK;
+}
+
 bhac_status bhac_step(bhac_ctx* c, double dt) {
   bhac_status s = bhac_stage(c, 1, dt);
   if (s != BHAC_OK) return s;

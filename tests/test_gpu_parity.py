@@ -398,3 +398,13 @@ def test_integer_pipe_compares_and_conversions_match_hardware(gb):
     bad = gb.bhac_check_bit_ops(1 << 24, seed=12345)
     assert bad == [0] * 8, bad
 
+
+def test_launches_per_step(gb):
+    """Uniform grid: ghost gather + stage kernel per stage; the AMR torus adds
+    cross-level node passes and the reflux kernel."""
+    u = gb.Solver(pb.torus_3d(nroot=(4, 3, 2)))
+    assert u.launches_per_step() == 4
+    a = gb.Solver(pb.amr_torus(root=(4, 2, 2), nblock=8))
+    n = a.launches_per_step()
+    assert n >= 2 * (1 + 1 + 1 + 1), n
+
