@@ -33,7 +33,11 @@ def smem_bytes(tx: int, ty: int, ndim: int, precision: str, producers: int = 0) 
     return 9 * n * t
 
 
-def candidates(grid, precision: str):
+def candidates(grid, precision: str, include_ws: bool = False):
+    """Launch shapes to time.  160 threads (one-CTA register bound) lets two
+    CTAs of a ~190-register build share an SM with fewer idle threads in the
+    last round of a phase than 128 or 256.  The warp-specialised form measured
+    slower on every grid tried and is timed only on request."""
     nx, ny = grid.nx[0], grid.nx[1]
     tiles = [(tx, ty) for tx in (32, 16, 8) for ty in (16, 8, 4) if nx % tx == 0 and ny % ty == 0 and tx * ty >= 64]
     if not tiles:
@@ -42,13 +46,13 @@ def candidates(grid, precision: str):
     for tx, ty in tiles:
         if smem_bytes(tx, ty, grid.ndim, precision) > SMEM_LIMIT:
             continue
-        for threads in (256, 128):
+        for threads in (256, 160, 128):
             if threads > 2 * tx * ty:
                 continue
-            for minb in ((1, 2) if grid.ndim == 3 else (1,)):
+            for minb in ((1, 2) if grid.ndim == 3 and threads != 160 else (1,)):
                 out.append((tx, ty, threads, 0, minb, 0))
     # the warp-specialised form (3-D): producer warps feed consumer warps
-    if grid.ndim == 3:
+    if grid.ndim == 3 and include_ws:
         for tx, ty in tiles:
             for prod in (2, 4):
                 if smem_bytes(tx, ty, 3, precision, prod) > SMEM_LIMIT:

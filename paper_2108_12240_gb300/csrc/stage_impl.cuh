@@ -190,12 +190,17 @@ BHAC_HD int con2prim_t(const Met<T>& m, const T* U, const T* Pg, T rho_fl, T p_f
     }
   }
   if (solved) {
-    const T sq = sqrt_t(T(1.0) - v2);
-    const T W = T(1.0) / sq;
+    // W = 1/sqrt(1 - v^2) and sqrt(1 - v^2) from one reciprocal square root;
+    // 1/Z and 1/(Z + B^2) from one reciprocal of their product
+    const T omv = T(1.0) - v2;
+    const T W = rsqrt_t(omv);
+    const T sq = omv * W;
+    const T ZB = Z + q.Bsq;
+    const T r = rcp_t(Z * ZB);
     P[RHO] = q.D * sq;
-    P[PRS] = gf * (Z * (T(1.0) - v2) - q.D * sq);
-    const T c = W / (Z + q.Bsq);
-    const T bz = q.BS / Z;
+    P[PRS] = gf * (Z * omv - q.D * sq);
+    const T c = W * Z * r;
+    const T bz = q.BS * ZB * r;
     P[U1] = c * (Su1 + bz * U[B1]);
     P[U2] = c * (Su2 + bz * U[B2]);
     P[U3] = c * (Su3 + bz * U[B3]);
@@ -235,7 +240,7 @@ BHAC_HD int con2prim_t(const Met<T>& m, const T* U, const T* Pg, T rho_fl, T p_f
   return fl ? 2 : status;
 }
 
-static __device__ __noinline__ int con2prim(const Met<double>& m, const double* U, const double* Pg, double rho_fl,
+static __device__ __forceinline__ int con2prim(const Met<double>& m, const double* U, const double* Pg, double rho_fl,
                                             double p_fl, const StageArgs& a, double* P) {
   return con2prim_t<double>(m, U, Pg, rho_fl, p_fl, a.gam, a.gam_fac, a.wmax, a.c2p_tol, a.c2p_maxit, P);
 }

@@ -173,7 +173,8 @@ def test_launch_shapes_are_bitwise_identical(gb):
     P = pb.fm_torus_prims(g)
     outs = []
     for shape in [(16, 16, 256, 0), (16, 8, 128, 0), (8, 8, 64, 0), (16, 16, 256, 2), (16, 16, 256, 0, 2),
-                  (16, 16, 256, 0, 1, 2), (16, 8, 256, 2, 2, 4), (8, 8, 128, 0, 1, 1)]:
+                  (16, 16, 160, 0, 1), (8, 16, 160, 1, 1), (16, 16, 256, 0, 1, 2), (16, 8, 256, 2, 2, 4),
+                  (8, 8, 128, 0, 1, 1)]:
         s = gb.Solver(g)
         s.set_launch(*shape)
         s.set_prims(P)
