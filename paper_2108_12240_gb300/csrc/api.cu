@@ -169,6 +169,11 @@ StageArgs base_args(const bhac_ctx* c) {
   a.gam_fac = d.gamma_ad / (d.gamma_ad - 1.0);
   a.ch = d.ch;
   a.kappa = d.kappa;
+  a.gam_f = (float)a.gam;
+  a.gam_fac_f = (float)a.gam_fac;
+  a.ch_f = (float)a.ch;
+  a.kappa_f = (float)a.kappa;
+  a.ch2_f = (float)(a.ch * a.ch);
   a.cfl = d.cfl;
   a.c2p_tol = d.c2p_tol;
   a.c2p_maxit = d.c2p_maxit;

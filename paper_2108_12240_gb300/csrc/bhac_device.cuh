@@ -53,6 +53,7 @@ struct StageArgs {
   int flat;
   int recon, riemann;
   double gam, gam_fac, ch, kappa, cfl;
+  float gam_f, gam_fac_f, ch_f, kappa_f, ch2_f;  // FP32 copies for the mixed form's flux arithmetic
   double c2p_tol;
   int c2p_maxit;
   double wmax, rho_fl_c, p_fl_c;  // constant floors (flat coordinates)
@@ -102,6 +103,7 @@ struct LevelGeo {
   const float* tf2_32;
   int N1, N2;
   double idx[3];
+  float idx_f[3];
 };
 
 __host__ __device__ __forceinline__ LevelGeo level_geo(const StageArgs& a, int L) {
@@ -118,8 +120,18 @@ __host__ __device__ __forceinline__ LevelGeo level_geo(const StageArgs& a, int L
   g.idx[0] = a.idx[0] * s;
   g.idx[1] = a.idx[1] * s;
   g.idx[2] = a.ndim == 3 ? a.idx[2] * s : a.idx[2];
+  for (int d = 0; d < 3; ++d) g.idx_f[d] = (float)g.idx[d];
   return g;
 }
+
+// The kernel-argument scalar in the flux arithmetic T: the double for the
+// FP64 form, the float copy for the mixed form (no conversion per use).
+template <typename T>
+__host__ __device__ __forceinline__ T pick(double d, float f);
+template <>
+__host__ __device__ __forceinline__ double pick<double>(double d, float) { return d; }
+template <>
+__host__ __device__ __forceinline__ float pick<float>(double, float f) { return f; }
 
 template <typename T>
 struct Met {

@@ -396,7 +396,8 @@ __device__ __forceinline__ void face_solve(const StageArgs& a, const LevelGeo& g
     acg = T(d == 2 ? rec[C_ACG3] : rec[F_ACG]);
   }
   T F[NV];
-  riemann_flux(m, acg, PL, PR, d, a.riemann, T(a.gam), T(a.gam_fac), T(a.ch), F);
+  riemann_flux(m, acg, PL, PR, d, a.riemann, pick<T>(a.gam, a.gam_f), pick<T>(a.gam_fac, a.gam_fac_f),
+               pick<T>(a.ch, a.ch_f), F);
 #pragma unroll
   for (int v = 0; v < NV; ++v) out[v * ostride] = F[v];
 }
@@ -564,7 +565,8 @@ __device__ __forceinline__ void cell_update(const StageArgs& a, const LevelGeo& 
   // flux divergence in the flux arithmetic T (FP32 in the mixed form, whose
   // face fluxes carry FP32 rounding already), then widened once per variable
   T rdiv[NV];
-  const T ix = T(geo.idx[0]), iy = T(geo.idx[1]), iz = T(geo.idx[2]);
+  const T ix = pick<T>(geo.idx[0], geo.idx_f[0]), iy = pick<T>(geo.idx[1], geo.idx_f[1]),
+          iz = pick<T>(geo.idx[2], geo.idx_f[2]);
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
     T r = -(Fx[v * sFx + j * (tx + 1) + i + 1] - Fx[v * sFx + j * (tx + 1) + i]) * ix;
@@ -579,7 +581,7 @@ __device__ __forceinline__ void cell_update(const StageArgs& a, const LevelGeo& 
 #pragma unroll
     for (int v = 0; v < NV; ++v) Pc[v] = Pb[(size_t)v * a.ncell + cg];
     if (FLAT) {
-      rdiv[PSI] = rdiv[PSI] - T(a.kappa) * Pc[PSI];
+      rdiv[PSI] = rdiv[PSI] - pick<T>(a.kappa, a.kappa_f) * Pc[PSI];
 #pragma unroll
       for (int v = 0; v < NV; ++v) rhs[v] = to_double(rdiv[v]);
     } else {
@@ -591,12 +593,13 @@ __device__ __forceinline__ void cell_update(const StageArgs& a, const LevelGeo& 
         m = load_centre_metric<T>(geo.tc32 + (size_t)(I2 * geo.N1 + I1) * CREC);
       }
       Derived<T> s;
-      derive(m, Pc, T(a.gam_fac), s);
+      derive(m, Pc, pick<T>(a.gam_fac, a.gam_fac_f), s);
       cons_of(Pc, s, Uc);
       if (sizeof(T) == 8)
-        sources_of(m, crec, Pc, s, Uc, T(a.kappa), T(a.ch * a.ch), S);
+        sources_of(m, crec, Pc, s, Uc, pick<T>(a.kappa, a.kappa_f), pick<T>(a.ch * a.ch, a.ch2_f), S);
       else
-        sources_of(m, geo.tc32 + (size_t)(I2 * geo.N1 + I1) * CREC, Pc, s, Uc, T(a.kappa), T(a.ch * a.ch),
+        sources_of(m, geo.tc32 + (size_t)(I2 * geo.N1 + I1) * CREC, Pc, s, Uc, pick<T>(a.kappa, a.kappa_f),
+                   pick<T>(a.ch * a.ch, a.ch2_f),
                    S);
       if (sizeof(T) == 8) {
         const double sg = crec[C_SG];
