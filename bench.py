@@ -231,13 +231,19 @@ def time_form(gb, torch, g, P, form, steps, warmup, stream, count_flops=True, gr
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic_stage_kernel_torus_3d_large.txt")
 
 
+# the sources that decide the stage kernel's code, its arguments and the data
+# layout and block order it reads (test utilities, the flop counter and the
+# allocation-free CFL entry point are not among them)
+KERNEL_SOURCES = ["amr.cu", "amr.h", "api.cu", "aux.cu", "bhac_device.cuh", "ctx.h", "launch.h",
+                  "stage_fp64.cu", "stage_impl.cuh", "stage_mixed.cu"]
+
+
 def kernel_fingerprint() -> str:
-    """sha256 over the CUDA sources and the public header (sorted by name)."""
+    """sha256 over KERNEL_SOURCES (names and contents, in this order)."""
     import hashlib
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2108_12240_gb300", "csrc")
-    files = sorted(f for f in os.listdir(csrc) if f.endswith((".cu", ".cuh", ".h")))
-    for f in files + ["../../include/bhac_gb300.h"]:
+    for f in KERNEL_SOURCES:
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(f.encode() + b"\0" + fh.read())
     return h.hexdigest()

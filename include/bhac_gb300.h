@@ -138,6 +138,13 @@ bhac_status bhac_stage(bhac_ctx* ctx, int stage, double dt);
 bhac_status bhac_get_prims(bhac_ctx* ctx, double* out, int on_device);
 bhac_status bhac_get_cons(bhac_ctx* ctx, double* out, int on_device);
 
+/* The current FP64 primitive state including ghost cells, [block][var][k][j][i]
+ * over the ghosted extents (nx + 2 nghost per active dimension), e.g. after
+ * bhac_fill_ghosts to check the fill.  FP64 form only (BHAC_ERR_STATE for the
+ * mixed form, whose fills write the FP32 copy).  Host copies synchronise the
+ * stream. */
+bhac_status bhac_get_prims_ghosted(bhac_ctx* ctx, double* out, int on_device);
+
 /* Inversion outcome counts accumulated since init, per cell and stage:
  * [0] Newton converged, [1] backup solver used, [2] floors applied,
  * [3] failed (previous primitives kept).  Synchronises the stream. */
@@ -190,8 +197,8 @@ bhac_status bhac_count_flops(bhac_ctx* ctx, double dt, int nsamples, unsigned se
  * generated on the device from `seed` (random bit patterns; doubles in and
  * around the float range; round-to-nearest ties; neighbours one ulp apart;
  * zeros, subnormals, infinities, NaNs) and writes the number of disagreements
- * per operation to out[8]: [0] a < b on non-NaN pairs, [1] x > 0, [2] x <= 0,
- * [3] |a| < |b|, [4] IEEE a < b, a <= b, x < 0 with NaN operands included,
+ * per operation to out[8]: [0] a < b, [1] x > 0, [2] x <= 0, [3] |a| < |b|,
+ * [4] a <= b and x < 0 (all IEEE, NaN operands included),
  * [5] isfinite, [6] double -> float (bitwise; NaN as NaN), [7] float -> double.
  * n in [1, 1<<26].  Synchronous (default stream); the counters are a
  * file-scope device array, so concurrent calls race on them. */

@@ -21,7 +21,7 @@ __all__ = [
     "bhac_query_sizes", "bhac_init_grid", "bhac_set_metric", "bhac_set_prims", "bhac_fill_ghosts",
     "bhac_cfl_dt", "bhac_step", "bhac_stage", "bhac_get_prims", "bhac_get_cons", "bhac_get_diagnostics",
     "bhac_set_launch", "bhac_count_flops", "bhac_graph_capture", "bhac_graph_launch", "bhac_cfl_dt_static", "bhac_destroy",
-    "bhac_status_string", "bhac_check_bit_ops", "bhac_launches_per_step",
+    "bhac_status_string", "bhac_check_bit_ops", "bhac_launches_per_step", "bhac_get_prims_ghosted",
 ]
 
 NV = 9
@@ -88,6 +88,7 @@ def lib():
             "bhac_cfl_dt_static": ([G, B, i, vp, vp, vp], i),
             "bhac_check_bit_ops": ([C.c_longlong, C.c_uint, C.POINTER(C.c_longlong)], i),
             "bhac_launches_per_step": ([vp, C.POINTER(i)], i),
+            "bhac_get_prims_ghosted": ([vp, vp, i], i),
             "bhac_destroy": ([vp], None),
             "bhac_status_string": ([i], C.c_char_p),
         }
@@ -156,6 +157,10 @@ def bhac_get_prims(ctx, ptr: int, on_device: bool):
 
 def bhac_get_cons(ctx, ptr: int, on_device: bool):
     return _check("bhac_get_cons", lib().bhac_get_cons(ctx, C.c_void_p(ptr), int(on_device)))
+
+
+def bhac_get_prims_ghosted(ctx, ptr: int, on_device: bool):
+    _check("bhac_get_prims_ghosted", lib().bhac_get_prims_ghosted(ctx, C.c_void_p(ptr), int(on_device)))
 
 
 def bhac_get_diagnostics(ctx):
@@ -299,6 +304,14 @@ class Solver:
     def prims(self) -> np.ndarray:
         out = np.empty(self.shape)
         bhac_get_prims(self.ctx, out.ctypes.data, False)
+        return out
+
+    def prims_ghosted(self) -> np.ndarray:
+        """FP64 primitives with ghost cells, (blocks, 9, Nz, Ny, Nx) (FP64 form)."""
+        g = self.grid
+        gd = [g.ng if d < g.ndim else 0 for d in range(3)]
+        out = np.zeros((g.nb, NV, g.nx[2] + 2 * gd[2], g.nx[1] + 2 * gd[1], g.nx[0] + 2 * gd[0]))
+        bhac_get_prims_ghosted(self.ctx, out.ctypes.data, False)
         return out
 
     def cons(self) -> np.ndarray:

@@ -224,11 +224,11 @@ __device__ __forceinline__ double to_double(float x) { return widen_f32(x); }
 // lanes per clock.  The double overloads therefore compare an
 // order-preserving integer image of the operands: okey maps -0 and +0 to 0
 // and every other finite or infinite double so that okey(x) < okey(y)
-// exactly when x < y, so each decision is the IEEE compare's for non-NaN
-// operands.  gt0_t, le0_t and lt_abs_t are exact for NaN too (false, false,
-// false as IEEE); lt_t orders NaN arbitrarily and is used only where the
-// operands are values of a valid state.  The generic templates (float, and
-// the flop counter's counting type) are the plain compares.
+// exactly when x < y; every compare below also returns false when an
+// operand is NaN, so each decision is the IEEE compare's for all inputs.
+// The extra NaN tests are integer operations on the lightly used ALU pipe.
+// The generic templates (float, and the flop counter's counting type) are
+// the plain compares.
 __device__ __forceinline__ long long okey(double x) {
   const long long b = __double_as_longlong(x);
   return b < 0 ? (long long)(0x8000000000000000ULL - (unsigned long long)b) : b;
@@ -242,9 +242,10 @@ template <typename T>
 BHAC_HD bool le0_t(T x) { return x <= T(0); }
 template <typename T>
 BHAC_HD bool lt_abs_t(T a, T b) { return abs_t(a) < abs_t(b); }
+__device__ __forceinline__ bool isnan_bits(double x);
 BHAC_HD bool lt_t(double a, double b) {
 #ifdef __CUDA_ARCH__
-  return okey(a) < okey(b);
+  return okey(a) < okey(b) && !isnan_bits(a) && !isnan_bits(b);
 #else
   return a < b;
 #endif
@@ -266,24 +267,14 @@ BHAC_HD bool le0_t(double x) {
   return x <= 0.0;
 #endif
 }
-// IEEE compares of doubles (false when either operand is NaN), for the FP64
-// inversion, whose failure handling relies on NaN comparing false.
+// a <= b and x < 0 (the inversion's safeguards and convergence test)
 __device__ __forceinline__ bool isnan_bits(double x) {
   return ((unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFULL) > kExpAll;
 }
 template <typename T>
-BHAC_HD bool lt_x(T a, T b) { return a < b; }
-template <typename T>
 BHAC_HD bool le_x(T a, T b) { return a <= b; }
 template <typename T>
 BHAC_HD bool lt0_x(T x) { return x < T(0); }
-BHAC_HD bool lt_x(double a, double b) {
-#ifdef __CUDA_ARCH__
-  return okey(a) < okey(b) && !isnan_bits(a) && !isnan_bits(b);
-#else
-  return a < b;
-#endif
-}
 BHAC_HD bool le_x(double a, double b) {
 #ifdef __CUDA_ARCH__
   return okey(a) <= okey(b) && !isnan_bits(a) && !isnan_bits(b);

@@ -1,5 +1,7 @@
-// bhac_check_bit_ops: the integer-pipe compares and conversions of
-// bhac_device.cuh against the hardware instructions they replace.
+// Test utilities: bhac_check_bit_ops (the integer-pipe compares and
+// conversions of bhac_device.cuh against the hardware instructions they
+// replace) and bhac_get_prims_ghosted (the ghosted primitive state, to check
+// ghost fills cell by cell).
 #include <math.h>
 
 #include "ctx.h"
@@ -61,12 +63,11 @@ __global__ void check_kernel(long long n, unsigned long long seed, unsigned long
     if ((hb & 7ULL) == 0ULL) b = a;                                          // equal
     if ((hb & 7ULL) == 1ULL) b = __longlong_as_double(__double_as_longlong(a) + 1LL);  // one ulp away
     if ((hb & 7ULL) == 2ULL) b = -a;
-    const bool na = isnan(a), nb = isnan(b);
-    if (!na && !nb && lt_t(a, b) != (a < b)) ++loc[0];
+    if (lt_t(a, b) != (a < b)) ++loc[0];
     if (gt0_t(a) != (a > 0.0)) ++loc[1];
     if (le0_t(a) != (a <= 0.0)) ++loc[2];
     if (lt_abs_t(a, b) != (fabs(a) < fabs(b))) ++loc[3];
-    if (lt_x(a, b) != (a < b) || le_x(a, b) != (a <= b) || lt0_x(a) != (a < 0.0)) ++loc[4];
+    if (le_x(a, b) != (a <= b) || lt0_x(a) != (a < 0.0)) ++loc[4];
     if (finite_t(a) != (bool)isfinite(a)) ++loc[5];
     const float f1 = narrow_f64(a), f0 = __double2float_rn(a);
     if (!(isnan(f1) && isnan(f0)) && __float_as_uint(f1) != __float_as_uint(f0)) ++loc[6];
@@ -100,4 +101,14 @@ extern "C" bhac_status bhac_check_bit_ops(long long n, unsigned seed, long long 
   if (e != cudaSuccess) return BHAC_ERR_CUDA;
   for (int k = 0; k < 8; ++k) out[k] = (long long)h[k];
   return BHAC_OK;
+}
+
+extern "C" bhac_status bhac_get_prims_ghosted(bhac_ctx* c, double* out, int on_device) {
+  if (!c || !out) return BHAC_ERR_ARG;
+  if (!c->prims_ok || c->mixed) return BHAC_ERR_STATE;
+  const size_t bytes = sizeof(double) * NV * (size_t)c->nb * c->ncell;
+  cudaError_t e = cudaMemcpyAsync(out, c->P[c->cur], bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                  c->st);
+  if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(c->st);
+  return e == cudaSuccess ? BHAC_OK : BHAC_ERR_CUDA;
 }

@@ -156,7 +156,7 @@ BHAC_HD int con2prim_t(const Met<T>& m, const T* U, const T* Pg, T rho_fl, T p_f
       }
       if (conv) polish = true;
     }
-    if (solved && !(le_x(T(0.0), v2) && lt_x(v2, T(1.0)) && gt0_t(Z))) solved = false;
+    if (solved && !(le_x(T(0.0), v2) && lt_t(v2, T(1.0)) && gt0_t(Z))) solved = false;
     if (solved && !gt0_t(q.D * sqrt_t(T(1.0) - v2))) solved = false;
     if (!solved) {
       T lo = Z0, hi = Z0;
@@ -229,7 +229,7 @@ BHAC_HD int con2prim_t(const Met<T>& m, const T* U, const T* Pg, T rho_fl, T p_f
   const T gu2 = m.g22 * P[U2];
   const T gu3 = m.g13 * P[U1] + m.g33 * P[U3];
   const T usq = P[U1] * gu1 + P[U2] * gu2 + P[U3] * gu3;
-  if (lt_x(wmax * wmax, T(1.0) + usq)) {
+  if (lt_t(wmax * wmax, T(1.0) + usq)) {
     const T sc = sqrt_t((wmax * wmax - T(1.0)) / usq);
     P[U1] = P[U1] * sc;
     P[U2] = P[U2] * sc;

@@ -409,3 +409,67 @@ def test_launches_per_step(gb):
     n = a.launches_per_step()
     assert n >= 2 * (1 + 1 + 1 + 1), n
 
+
+@pytest.mark.parametrize("make", ["shock_tube", "torus_3d", "amr_torus"])
+def test_ghost_fill_matches_oracle(gb, make):
+    """After one fill, every ghost cell equals the oracle's: same-level copies
+    and the physical rules (periodic, outflow, polar axis with the phi + pi
+    cell and flipped u^theta, B^theta) bit for bit; cross-level values
+    (restriction, limited prolongation) to rounding."""
+    if make == "shock_tube":
+        g = pb.shock_tube_2d(nblock=16, nroot=2)
+        P = pb.shock_tube_prims(g)
+    elif make == "torus_3d":
+        g = pb.torus_3d(nroot=(4, 3, 2))
+        P = pb.fm_torus_prims(g)
+    else:
+        g = pb.amr_torus(root=(4, 2, 2), nblock=8)
+        P = pb.fm_torus_prims(g)
+    s = gb.Solver(g)
+    s.set_prims(P)
+    s.fill_ghosts()
+    got = s.prims_ghosted()
+    o = oracle.Oracle(g)
+    o.set_prims(P)
+    o.fill_ghosts()
+    ref = o.prims_ghosted()
+    assert got.shape == ref.shape
+    if make != "amr_torus":
+        assert np.array_equal(got, ref)
+    else:
+        same = got == ref
+        scale = np.abs(ref).max(axis=(0, 2, 3, 4), keepdims=True) + 1e-300
+        err = np.abs(got - ref) / scale
+        assert err.max() <= 1e-14, err.max()
+        assert same.mean() > 0.9  # all but the cross-level ghosts are copies
+
+
+def test_forged_bad_states_are_counted_not_fatal(gb):
+    """Host-forged states (NaN density, negative pressure, u^i beyond the
+    Lorentz-factor cap, zero density) in a few cells: the step completes, the
+    inversion outcome counts equal the oracle's, the diagnostics report the
+    failures through the status, and the context keeps working."""
+    g = pb.torus_3d(nroot=(4, 3, 2))
+    P = pb.fm_torus_prims(g).copy()
+    P[3, 0, 5, 5, 5] = np.nan
+    P[7, 1, 2, 3, 4] = -1e-3
+    P[11, 2, 6, 6, 6] = 1e3
+    P[13, 0, 1, 1, 1] = 0.0
+    s = gb.Solver(g)
+    s.set_prims(P)
+    dt = 1e-3
+    st = gb.lib().bhac_step(s.ctx, dt)
+    assert st in (0,), gb.status_string(st)
+    o = oracle.Oracle(g)
+    o.set_prims(P)
+    o.step(dt)
+    counts, status = gb.bhac_get_diagnostics(s.ctx)
+    assert np.array_equal(counts, o.c2p_counts()), (counts, o.c2p_counts())
+    assert counts[3] > 0 and status == 6  # BHAC_WARN_C2P
+    # the context keeps working: a clean state steps without new failures
+    s.set_prims(pb.fm_torus_prims(g))
+    before = np.array(s.diagnostics())
+    s.step(1e-3)
+    after = np.array(s.diagnostics())
+    assert after[3] == before[3]
+
