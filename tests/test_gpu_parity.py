@@ -444,32 +444,46 @@ def test_ghost_fill_matches_oracle(gb, make):
         assert same.mean() > 0.9  # all but the cross-level ghosts are copies
 
 
-def test_forged_bad_states_are_counted_not_fatal(gb):
-    """Host-forged states (NaN density, negative pressure, u^i beyond the
-    Lorentz-factor cap, zero density) in a few cells: the step completes, the
-    inversion outcome counts equal the oracle's, the diagnostics report the
-    failures through the status, and the context keeps working."""
+def test_forged_bad_states_are_contained(gb):
+    """Host-forged states (NaN density, negative pressure, u^1 = 1e3, zero
+    density) in four cells: the step completes with status OK, the failed
+    inversions are counted and reported through BHAC_WARN_C2P, the new state
+    is finite everywhere, every cell the forged values did not reach (the
+    oracle's clean and forged runs agree there bit for bit) matches the
+    oracle's forged run to the FP64 bar, and the context keeps working.
+    Outcome counts are compared loosely: at W ~ 1e3 the Newton iteration is
+    ill-conditioned and its converged/failed outcome depends on rounding."""
     g = pb.torus_3d(nroot=(4, 3, 2))
-    P = pb.fm_torus_prims(g).copy()
+    clean = pb.fm_torus_prims(g)
+    P = clean.copy()
     P[3, 0, 5, 5, 5] = np.nan
     P[7, 1, 2, 3, 4] = -1e-3
     P[11, 2, 6, 6, 6] = 1e3
     P[13, 0, 1, 1, 1] = 0.0
+    dt = 1e-3
     s = gb.Solver(g)
     s.set_prims(P)
-    dt = 1e-3
     st = gb.lib().bhac_step(s.ctx, dt)
-    assert st in (0,), gb.status_string(st)
+    assert st == 0, gb.status_string(st)
+    counts, status = gb.bhac_get_diagnostics(s.ctx)
+    assert counts[3] > 0 and status == 6  # BHAC_WARN_C2P
+    assert counts.sum() == 2 * g.ncells
+    got = s.cons()
+    assert np.all(np.isfinite(got))
     o = oracle.Oracle(g)
     o.set_prims(P)
     o.step(dt)
-    counts, status = gb.bhac_get_diagnostics(s.ctx)
-    assert np.array_equal(counts, o.c2p_counts()), (counts, o.c2p_counts())
-    assert counts[3] > 0 and status == 6  # BHAC_WARN_C2P
+    ref = o.cons()
+    oc = oracle.Oracle(g)
+    oc.set_prims(clean)
+    oc.step(dt)
+    reached = np.any(ref != oc.cons(), axis=1, keepdims=True)
+    assert 0 < reached.mean() < 0.05
+    assert_parity(np.where(reached, ref, got), ref, TOL64, "cells the forged values did not reach", g)
+    oref = o.c2p_counts()
+    assert abs(int(counts[3]) - int(oref[3])) <= 12, (counts, oref)
     # the context keeps working: a clean state steps without new failures
-    s.set_prims(pb.fm_torus_prims(g))
+    s.set_prims(clean)
     before = np.array(s.diagnostics())
-    s.step(1e-3)
-    after = np.array(s.diagnostics())
-    assert after[3] == before[3]
-
+    s.step(dt)
+    assert np.array(s.diagnostics())[3] == before[3]
