@@ -242,10 +242,16 @@ template <typename T>
 BHAC_HD bool le0_t(T x) { return x <= T(0); }
 template <typename T>
 BHAC_HD bool lt_abs_t(T a, T b) { return abs_t(a) < abs_t(b); }
-__device__ __forceinline__ bool isnan_bits(double x);
+// NaN keys lie outside [okey(-inf), okey(+inf)]: with ka < kb, a NaN operand
+// can only be a negative NaN a (ka below okey(-inf)) or a positive NaN b (kb
+// above okey(+inf)), so two range compares on the keys make a < b IEEE for
+// all inputs.  (A bit-mask NaN test here is recognised by the compiler and
+// lowered onto the FP64 unit.)
+constexpr long long kKeyPosInf = 0x7FF0000000000000LL, kKeyNegInf = -0x7FF0000000000000LL;
 BHAC_HD bool lt_t(double a, double b) {
 #ifdef __CUDA_ARCH__
-  return okey(a) < okey(b) && !isnan_bits(a) && !isnan_bits(b);
+  const long long ka = okey(a), kb = okey(b);
+  return ka < kb && ka >= kKeyNegInf && kb <= kKeyPosInf;
 #else
   return a < b;
 #endif
@@ -268,16 +274,14 @@ BHAC_HD bool le0_t(double x) {
 #endif
 }
 // a <= b and x < 0 (the inversion's safeguards and convergence test)
-__device__ __forceinline__ bool isnan_bits(double x) {
-  return ((unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFULL) > kExpAll;
-}
 template <typename T>
 BHAC_HD bool le_x(T a, T b) { return a <= b; }
 template <typename T>
 BHAC_HD bool lt0_x(T x) { return x < T(0); }
 BHAC_HD bool le_x(double a, double b) {
 #ifdef __CUDA_ARCH__
-  return okey(a) <= okey(b) && !isnan_bits(a) && !isnan_bits(b);
+  const long long ka = okey(a), kb = okey(b);
+  return ka <= kb && ka >= kKeyNegInf && kb <= kKeyPosInf;
 #else
   return a <= b;
 #endif
