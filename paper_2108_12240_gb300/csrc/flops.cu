@@ -117,11 +117,12 @@ void load_stencil(const StageArgs& a, const S* Pb, int d, int ig, int jg, int kg
 }
 
 // Flux through the face of direction d whose high-side cell is (ig, jg, kg).
+// tc, tf1, tf2 are the tables of the block's level, N1 x N2 cells.
 template <typename T, typename S, typename R>
-void face(const StageArgs& a, const S* Pb, const R* tc, const R* tf1, const R* tf2, int d, int ig, int jg, int kg,
-          int I1, int I2, double out[NV]) {
+void face(const StageArgs& a, const S* Pb, const R* tc, const R* tf1, const R* tf2, int N1, int N2, int d, int ig,
+          int jg, int kg, int I1, int I2, double out[NV]) {
   T PL[NV], PR[NV], F[NV];
-  if (!a.flat && d == 1 && ((I2 == 0 && a.axis_lo1) || (I2 == a.N2g && a.axis_hi1))) {
+  if (!a.flat && d == 1 && ((I2 == 0 && a.axis_lo1) || (I2 == N2 && a.axis_hi1))) {
     for (int v = 0; v < NV; ++v) out[v] = 0.0;
     return;
   }
@@ -129,8 +130,8 @@ void face(const StageArgs& a, const S* Pb, const R* tc, const R* tf1, const R* t
   Met<T> m = flat_metric<T>();
   T acg = T(1);
   if (!a.flat) {
-    const R* rec = d == 0 ? tf1 + (size_t)(I2 * (a.N1g + 1) + I1) * FREC
-                          : (d == 1 ? tf2 + (size_t)(I2 * a.N1g + I1) * FREC : tc + (size_t)(I2 * a.N1g + I1) * CREC);
+    const R* rec = d == 0 ? tf1 + (size_t)(I2 * (N1 + 1) + I1) * FREC
+                          : (d == 1 ? tf2 + (size_t)(I2 * N1 + I1) * FREC : tc + (size_t)(I2 * N1 + I1) * CREC);
     m = load_face_metric<T>(rec);
     acg = T(d == 2 ? rec[C_ACG3] : rec[F_ACG]);
   }
@@ -156,36 +157,44 @@ void cell(const StageArgs& a, const HostState& h, int sb, int i, int j, int k, d
     tf1 = (const R*)h.tf1.data();
     tf2 = (const R*)h.tf2.data();
   }
+  // the block's refinement level: its metric tables, extents and spacing
+  const int L = a.blk[4 * bidx];
+  const int N1 = a.N1l[L], N2 = a.N2l[L];
+  tc += (size_t)a.toff_c[L] * CREC;
+  tf1 += (size_t)a.toff_f1[L] * FREC;
+  tf2 += (size_t)a.toff_f2[L] * FREC;
+  const double lsc = (double)(1 << L);
+  const double idx[3] = {a.idx[0] * lsc, a.idx[1] * lsc, a.ndim == 3 ? a.idx[2] * lsc : a.idx[2]};
   const int ig = i + a.gx, jg = j + a.gy, kg = k + a.gz;
   const int I1 = a.blk[4 * bidx + 1] * a.nx + i, I2 = a.blk[4 * bidx + 2] * a.ny + j;
   double Flo[3][NV], Fhi[3][NV];
   for (int d = 0; d < a.ndim; ++d) {
     g_on = true;
-    face<T, S, R>(a, Pb, tc, tf1, tf2, d, ig, jg, kg, I1, I2, Flo[d]);
+    face<T, S, R>(a, Pb, tc, tf1, tf2, N1, N2, d, ig, jg, kg, I1, I2, Flo[d]);
     g_on = false;
-    face<T, S, R>(a, Pb, tc, tf1, tf2, d, ig + (d == 0), jg + (d == 1), kg + (d == 2), I1 + (d == 0), I2 + (d == 1),
-                  Fhi[d]);
+    face<T, S, R>(a, Pb, tc, tf1, tf2, N1, N2, d, ig + (d == 0), jg + (d == 1), kg + (d == 2), I1 + (d == 0),
+                  I2 + (d == 1), Fhi[d]);
   }
   g_on = true;
   // flux divergence in the flux arithmetic T, as the kernel forms it
   T rdiv[NV];
   N64 rhs[NV];
   for (int v = 0; v < NV; ++v) {
-    T r = -(T(Fhi[0][v]) - T(Flo[0][v])) * T(a.idx[0]);
-    r = r - (T(Fhi[1][v]) - T(Flo[1][v])) * T(a.idx[1]);
-    if (a.ndim == 3) r = r - (T(Fhi[2][v]) - T(Flo[2][v])) * T(a.idx[2]);
+    T r = -(T(Fhi[0][v]) - T(Flo[0][v])) * T(idx[0]);
+    r = r - (T(Fhi[1][v]) - T(Flo[1][v])) * T(idx[1]);
+    if (a.ndim == 3) r = r - (T(Fhi[2][v]) - T(Flo[2][v])) * T(idx[2]);
     rdiv[v] = r;
   }
   const int cg = (kg * a.Ny + jg) * a.Nx + ig;
   T Pc[NV];
   for (int v = 0; v < NV; ++v) Pc[v] = T(Pb[(size_t)v * a.ncell + cg]);
   double sg = 1.0, isg = 1.0, rho_fl = a.rho_fl_c, p_fl = a.p_fl_c;
-  const double* crec = a.flat ? nullptr : h.tc.data() + (size_t)(I2 * a.N1g + I1) * CREC;
+  const double* crec = a.flat ? nullptr : h.tc.data() + ((size_t)a.toff_c[L] + (size_t)I2 * N1 + I1) * CREC;
   if (a.flat) {
     rdiv[PSI] = rdiv[PSI] - T(a.kappa) * Pc[PSI];
     for (int v = 0; v < NV; ++v) rhs[v] = N64(to_double(rdiv[v]));
   } else {
-    const R* rec = tc + (size_t)(I2 * a.N1g + I1) * CREC;
+    const R* rec = tc + (size_t)(I2 * N1 + I1) * CREC;
     Met<T> m = load_centre_metric<T>(rec);
     Derived<T> s;
     T Uc[NV], S_[NV];
@@ -234,9 +243,9 @@ void cell(const StageArgs& a, const HostState& h, int sb, int i, int j, int k, d
       acg[2] = N64(crec[C_ACG3]);
     }
     if (a.ndim == 3)
-      (void)cfl_rate_t<N64, 3>(md, acg, Pn, a.gam, a.gam_fac, a.ch, a.idx);
+      (void)cfl_rate_t<N64, 3>(md, acg, Pn, a.gam, a.gam_fac, a.ch, idx);
     else
-      (void)cfl_rate_t<N64, 2>(md, acg, Pn, a.gam, a.gam_fac, a.ch, a.idx);
+      (void)cfl_rate_t<N64, 2>(md, acg, Pn, a.gam, a.gam_fac, a.ch, idx);
   }
 }
 
@@ -276,7 +285,12 @@ extern "C" bhac_status bhac_count_flops(bhac_ctx* c, double dt, int nsamples, un
                           sizeof(double) * NV * c->nint, cudaMemcpyDeviceToHost, c->st);
   }
   if (!c->flat && e == cudaSuccess) {
-    const size_t nc = (size_t)c->N1g * c->N2g, nf1 = (size_t)(c->N1g + 1) * c->N2g, nf2 = (size_t)c->N1g * (c->N2g + 1);
+    // every level's tables (levels follow one another in each table)
+    const StageArgs t = base_args(c);
+    const int Lt = t.nlev - 1;
+    const size_t nc = (size_t)t.toff_c[Lt] + (size_t)t.N1l[Lt] * t.N2l[Lt];
+    const size_t nf1 = (size_t)t.toff_f1[Lt] + (size_t)(t.N1l[Lt] + 1) * t.N2l[Lt];
+    const size_t nf2 = (size_t)t.toff_f2[Lt] + (size_t)t.N1l[Lt] * (t.N2l[Lt] + 1);
     e = fetch(h.tc, c->tab_c, nc * CREC, c->st);
     if (e == cudaSuccess) e = fetch(h.tf1, c->tab_f1, nf1 * FREC, c->st);
     if (e == cudaSuccess) e = fetch(h.tf2, c->tab_f2, nf2 * FREC, c->st);
