@@ -338,7 +338,8 @@ static int finite9(const double* x) {
 
 /* Primary solver: two-dimensional Newton-Raphson in (Z, v^2) on the momentum
  * and energy equations (the "2D" scheme of Noble et al. 2006), started from
- * the previous primitives; stop when |dZ| <= tol Z, then one polishing step.
+ * the previous primitives; stop when the step |dZ| <= tol Z (the iteration
+ * converges quadratically, so that iterate is accurate to round-off).
  * Backup: bracketed bisection on Z of the one-dimensional energy residual.
  * Last resort: keep the previous primitives (status 3).  Floors last. */
 int or_con2prim(const or_params* p, const or_metric* m, const double U[OR_NV], const double Pg[OR_NV],
@@ -376,7 +377,6 @@ int or_con2prim(const or_params* p, const or_metric* m, const double U[OR_NV], c
     Z = (Pg[OR_RHO] + gam / (gam - 1.0) * Pg[OR_P]) * (1.0 + u2);
     v2 = u2 / (1.0 + u2);
     if (!(Z > 0.0) || !isfinite(Z)) Z = q.E;
-    int polish = 0;
     for (int it = 0; it < p->c2p_maxit; ++it) {
       double sq = sqrt(1.0 - v2);
       double pr = gf * (Z * (1.0 - v2) - q.D * sq);
@@ -400,11 +400,10 @@ int or_con2prim(const or_params* p, const or_metric* m, const double U[OR_NV], c
       Z = Zn;
       v2 = v2n;
       if (!isfinite(Z) || !isfinite(v2)) break;
-      if (polish) {
+      if (conv) {
         solved = 1;
         break;
       }
-      if (conv) polish = 1;
     }
     if (solved && !(v2 >= 0.0 && v2 < 1.0 && Z > 0.0)) solved = 0;
     if (solved) {

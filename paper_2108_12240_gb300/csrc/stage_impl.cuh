@@ -63,8 +63,9 @@ BHAC_HD void sources_of(const Met<T>& m, const R* __restrict__ rec, const T* P,
 // ----------------------------------------------------------------------------
 // Conserved -> primitive inversion (FP64).  Two-dimensional Newton-Raphson in
 // (Z = rho h W^2, v^2) on the momentum and energy equations (Noble et al.
-// 2006), started from the previous primitives; converged when
-// |dZ| <= tol Z, then one polishing step.  Backup: bisection on Z of the
+// 2006), started from the previous primitives; converged when the step
+// |dZ| <= tol Z (quadratic convergence: that iterate is accurate to
+// round-off).  Backup: bisection on Z of the
 // one-dimensional energy residual over a bracket grown from the guess.  Last
 // resort: previous primitives (status 3).  Then floors (status 2).
 // ----------------------------------------------------------------------------
@@ -124,7 +125,6 @@ BHAC_HD int con2prim_t(const Met<T>& m, const T* U, const T* Pg, T rho_fl, T p_f
     Z = Z0;
     v2 = usq / (T(1.0) + usq);
     const T BS2 = q.BS * q.BS;
-    bool polish = false;
     for (int it = 0; it < maxit; ++it) {
       const T omv = T(1.0) - v2;
       const T isq = rsqrt_t(omv);
@@ -150,11 +150,10 @@ BHAC_HD int con2prim_t(const Met<T>& m, const T* U, const T* Pg, T rho_fl, T p_f
       Z = Zn;
       v2 = v2n;
       if (!finite_t(Z) || !finite_t(v2)) break;
-      if (polish) {
+      if (conv) {
         solved = true;
         break;
       }
-      if (conv) polish = true;
     }
     if (solved && !(le_x(T(0.0), v2) && lt_t(v2, T(1.0)) && gt0_t(Z))) solved = false;
     if (solved && !gt0_t(q.D * sqrt_t(T(1.0) - v2))) solved = false;
