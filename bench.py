@@ -238,14 +238,24 @@ KERNEL_SOURCES = ["amr.cu", "amr.h", "api.cu", "aux.cu", "bhac_device.cuh", "ctx
                   "stage_fp64.cu", "stage_impl.cuh", "stage_mixed.cu"]
 
 
+def _code_only(text: str) -> str:
+    """C/C++ source without comments and with whitespace collapsed (the
+    sources hold no string literal containing a comment marker)."""
+    import re
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return " ".join(text.split())
+
+
 def kernel_fingerprint() -> str:
-    """sha256 over KERNEL_SOURCES (names and contents, in this order)."""
+    """sha256 over the code (comments and layout removed) of KERNEL_SOURCES,
+    in this order."""
     import hashlib
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2108_12240_gb300", "csrc")
     for f in KERNEL_SOURCES:
-        with open(os.path.join(csrc, f), "rb") as fh:
-            h.update(f.encode() + b"\0" + fh.read())
+        with open(os.path.join(csrc, f), encoding="utf-8") as fh:
+            h.update(f.encode() + b"\0" + _code_only(fh.read()).encode())
     return h.hexdigest()
 
 

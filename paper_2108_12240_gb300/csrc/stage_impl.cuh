@@ -5,10 +5,11 @@
 // stage_mixed.cu, which instantiate it for FP64 and FP32 flux arithmetic.
 //
 // Work decomposition: one CTA owns a column of tx x ty cells of one block and
-// marches through its nz planes.  Per plane it computes every x-, y- and (top)
-// z-face flux of the column once into shared memory, then updates each cell;
-// the z-face flux at the top of a plane is carried over as the bottom of the
-// next, so no interior face flux is ever evaluated twice.
+// marches through its nz planes.  Per plane it reconstructs each cell's edges
+// once per direction into shared memory, computes every x-, y- and (top)
+// z-face flux of the column once from them, then updates each cell; the
+// z-face flux at the top of a plane is carried over as the bottom of the
+// next, so no interior face flux is evaluated twice.
 #pragma once
 
 #include "amr.h"
