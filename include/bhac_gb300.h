@@ -133,10 +133,24 @@ bhac_status bhac_step(bhac_ctx* ctx, double dt);
 /* One RK stage (1 or 2) with its preceding ghost fill. */
 bhac_status bhac_stage(bhac_ctx* ctx, int stage, double dt);
 
+/* Replaces the conserved state that bhac_set_prims derived from the
+ * primitives by `cons` (densitized, [block][var][k][j][i] interior, as
+ * bhac_get_cons returns it).  Call after bhac_set_prims.  Restoring both
+ * primitives and conserved variables of a saved state resumes a run bit for
+ * bit (the conserved state is not re-derived from the primitives).  Host
+ * copies synchronise the stream. */
+bhac_status bhac_set_cons(bhac_ctx* ctx, const double* cons, int on_device);
+
 /* Copies interior primitives (or densitized conserved variables) out, same
  * layout as bhac_set_prims; host copies synchronise the stream. */
 bhac_status bhac_get_prims(bhac_ctx* ctx, double* out, int on_device);
 bhac_status bhac_get_cons(bhac_ctx* ctx, double* out, int on_device);
+
+/* Per interior cell, the inversion outcome of the last stage run (0 Newton
+ * converged, 1 backup solver, 2 floors applied, 3 failed and kept the
+ * previous primitives), one byte per cell, [block][k][j][i].  Host copies
+ * synchronise the stream. */
+bhac_status bhac_get_c2p_status(bhac_ctx* ctx, unsigned char* out, int on_device);
 
 /* The current FP64 primitive state including ghost cells, [block][var][k][j][i]
  * over the ghosted extents (nx + 2 nghost per active dimension), e.g. after

@@ -91,6 +91,7 @@ def lib():
         L.or_stage_blocks.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_int, _IP]
         L.or_step.argtypes = [C.c_void_p, C.c_double]
         L.or_c2p_counts.argtypes = [C.c_void_p, _LP]
+        L.or_c2p_status.argtypes = [C.c_void_p, C.c_void_p]
         L.or_ghosted_cells.argtypes = [C.c_void_p]
         L.or_ghosted_cells.restype = C.c_int
         _lib = L
@@ -251,6 +252,13 @@ class Oracle:
 
     def step(self, dt: float):
         self.L.or_step(self.ctx, dt)
+
+    def c2p_status(self):
+        """Per interior cell (blocks, nz, ny, nx): the last stage's inversion outcome."""
+        g = self.grid
+        out = np.zeros((self.nb, g.nx[2], g.nx[1], g.nx[0]), dtype=np.uint8)
+        self.L.or_c2p_status(self.ctx, out.ctypes.data)
+        return out
 
     def c2p_counts(self):
         out = np.zeros(4, dtype=np.int64)

@@ -610,6 +610,7 @@ struct or_ctx {
   double* flux[3]; /* nb x NV x face-array per direction */
   int* lut[8];     /* per level: block id at block coordinates, -1 if not a leaf */
   long long counts[4];
+  unsigned char* status; /* nb x interior: inversion outcome of the last stage */
 };
 
 static long lut_size(const or_ctx* c, int L) {
@@ -669,6 +670,7 @@ or_ctx* or_create(const or_params* p, int nblocks, const int* blocks) {
   c->prim = (double*)calloc((size_t)nblocks * OR_NV * c->ncell, sizeof(double));
   c->ucur = (double*)calloc((size_t)nblocks * OR_NV * c->nint, sizeof(double));
   c->un = (double*)calloc((size_t)nblocks * OR_NV * c->nint, sizeof(double));
+  c->status = (unsigned char*)calloc((size_t)nblocks * c->nint, 1);
   for (int d = 0; d < p->ndim; ++d) {
     size_t nf = (size_t)c->nint / p->nx[d] * (p->nx[d] + 1);
     c->flux[d] = (double*)calloc((size_t)nblocks * OR_NV * nf, sizeof(double));
@@ -693,6 +695,7 @@ void or_destroy(or_ctx* c) {
   free(c->prim);
   free(c->ucur);
   free(c->un);
+  free(c->status);
   for (int d = 0; d < 3; ++d) free(c->flux[d]);
   for (int L = 0; L < 8; ++L) free(c->lut[L]);
   free(c);
@@ -741,6 +744,10 @@ void or_get_prims_ghosted(const or_ctx* c, double* prims) {
 
 void or_get_cons(const or_ctx* c, double* cons) {
   memcpy(cons, c->ucur, sizeof(double) * (size_t)c->nb * OR_NV * c->nint);
+}
+
+void or_c2p_status(const or_ctx* c, unsigned char* status) {
+  memcpy(status, c->status, (size_t)c->nb * c->nint);
 }
 
 void or_c2p_counts(const or_ctx* c, long long counts[4]) {
@@ -1060,6 +1067,7 @@ static void update_block(or_ctx* c, int b, int stage, double dt, long long cnt[4
         for (int v = 0; v < OR_NV; ++v) Uu[v] = U[v] / m.sqrtg;
         int st = or_con2prim(&c->p, &m, Uu, P, floor_radius(&c->p, x), Pn);
         cnt[st] += 1;
+        c->status[(size_t)b * c->nint + ((size_t)k * c->p.nx[1] + j) * c->p.nx[0] + i] = (unsigned char)st;
         if (st >= 2) {
           or_prim2con(&c->p, &m, Pn, Uu);
           for (int v = 0; v < OR_NV; ++v) U[v] = m.sqrtg * Uu[v];

@@ -99,6 +99,8 @@ void or_stage(or_ctx* c, int stage, double dt);
 void or_stage_blocks(or_ctx* c, int stage, double dt, int nsel, const int* sel);
 void or_step(or_ctx* c, double dt);
 void or_c2p_counts(const or_ctx* c, long long counts[4]);
+/* per interior cell ([block][k][j][i]): inversion outcome of the last stage */
+void or_c2p_status(const or_ctx* c, unsigned char* status);
 int or_ghosted_cells(const or_ctx* c);                    /* per block, with ghosts */
 
 #ifdef __cplusplus

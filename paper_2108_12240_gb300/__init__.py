@@ -22,6 +22,7 @@ __all__ = [
     "bhac_cfl_dt", "bhac_step", "bhac_stage", "bhac_get_prims", "bhac_get_cons", "bhac_get_diagnostics",
     "bhac_set_launch", "bhac_count_flops", "bhac_graph_capture", "bhac_graph_launch", "bhac_cfl_dt_static", "bhac_destroy",
     "bhac_status_string", "bhac_check_bit_ops", "bhac_launches_per_step", "bhac_get_prims_ghosted",
+    "bhac_get_c2p_status", "bhac_set_cons",
 ]
 
 NV = 9
@@ -89,6 +90,8 @@ def lib():
             "bhac_check_bit_ops": ([C.c_longlong, C.c_uint, C.POINTER(C.c_longlong)], i),
             "bhac_launches_per_step": ([vp, C.POINTER(i)], i),
             "bhac_get_prims_ghosted": ([vp, vp, i], i),
+            "bhac_get_c2p_status": ([vp, vp, i], i),
+            "bhac_set_cons": ([vp, vp, i], i),
             "bhac_destroy": ([vp], None),
             "bhac_status_string": ([i], C.c_char_p),
         }
@@ -157,6 +160,14 @@ def bhac_get_prims(ctx, ptr: int, on_device: bool):
 
 def bhac_get_cons(ctx, ptr: int, on_device: bool):
     return _check("bhac_get_cons", lib().bhac_get_cons(ctx, C.c_void_p(ptr), int(on_device)))
+
+
+def bhac_get_c2p_status(ctx, ptr: int, on_device: bool):
+    _check("bhac_get_c2p_status", lib().bhac_get_c2p_status(ctx, C.c_void_p(ptr), int(on_device)))
+
+
+def bhac_set_cons(ctx, ptr: int, on_device: bool):
+    _check("bhac_set_cons", lib().bhac_set_cons(ctx, C.c_void_p(ptr), int(on_device)))
 
 
 def bhac_get_prims_ghosted(ctx, ptr: int, on_device: bool):
@@ -305,6 +316,27 @@ class Solver:
         out = np.empty(self.shape)
         bhac_get_prims(self.ctx, out.ctypes.data, False)
         return out
+
+    def c2p_status(self) -> np.ndarray:
+        """Per interior cell (blocks, nz, ny, nx): the last stage's inversion outcome."""
+        g = self.grid
+        out = np.zeros((g.nb, g.nx[2], g.nx[1], g.nx[0]), dtype=np.uint8)
+        bhac_get_c2p_status(self.ctx, out.ctypes.data, False)
+        return out
+
+    def set_cons(self, cons):
+        """Replaces the conserved state derived by set_prims (densitized, as cons() returns it)."""
+        c = np.ascontiguousarray(cons, dtype=np.float64)
+        bhac_set_cons(self.ctx, c.ctypes.data, False)
+
+    def checkpoint(self) -> dict:
+        """The state a bit-identical resume needs: primitives and conserved variables."""
+        return {"prims": self.prims(), "cons": self.cons()}
+
+    def restore(self, state: dict):
+        """Resumes from checkpoint(): the next steps are bit-identical to an uninterrupted run."""
+        self.set_prims(state["prims"])
+        self.set_cons(state["cons"])
 
     def prims_ghosted(self) -> np.ndarray:
         """FP64 primitives with ghost cells, (blocks, 9, Nz, Ny, Nx) (FP64 form)."""

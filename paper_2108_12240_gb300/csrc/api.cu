@@ -1,6 +1,7 @@
 // The C ABI (include/bhac_gb300.h): context, arena carving, ghost maps, and the
 // launch sequence of a step.  No device memory is allocated here: every
 // device array is a slice of the caller's arena.
+#include <nvtx3/nvToolsExt.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -12,10 +13,20 @@
 using namespace bhac;
 
 namespace {
+// NVTX range around an ABI call, so profilers (ncu --nvtx, nsys) can group
+// its kernels; a no-op when no tool is attached.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
+}  // namespace
+
+
+namespace {
 
 struct Layout {
   size_t off_blk, off_order, off_src, off_flags, off_tmpl, off_tc, off_tf1, off_tf2, off_tc32, off_tf1_32, off_tf2_32;
-  size_t off_P[2], off_P32[2], off_U[2], off_scratch, off_small;
+  size_t off_P[2], off_P32[2], off_U[2], off_scratch, off_status, off_small;
   size_t off_nodes, off_ops, off_nodeval, off_cf, off_regoff, off_reg, off_rcells, off_rterms, total;
   long long toff_c[MAXLEV], toff_f1[MAXLEV], toff_f2[MAXLEV];
 };
@@ -110,6 +121,7 @@ Layout layout(const bhac_grid_desc* d, int nb, const HostMaps& M) {
   for (int s = 0; s < 2; ++s) L.off_P32[s] = take(mixed ? sizeof(float) * NV * (size_t)nb * ncell : 0);
   for (int s = 0; s < 2; ++s) L.off_U[s] = take(sizeof(double) * NV * (size_t)nb * nint);
   L.off_scratch = take(sizeof(double) * NV * (size_t)nb * nint);
+  L.off_status = take((size_t)nb * nint);
   L.off_small = take(256);
   L.off_nodes = take(sizeof(GhostNode) * M.nodes.size());
   L.off_ops = take(sizeof(long long) * M.ops.size());
@@ -190,6 +202,7 @@ StageArgs base_args(const bhac_ctx* c) {
   a.smax_in = c->smax;
   a.smax_out = c->smax;
   a.counts = c->counts;
+  a.status = c->d_status;
   a.work = c->work;
   a.nlev = c->d.nlevels;
   for (int l = 0; l < MAXLEV; ++l) {
@@ -359,6 +372,7 @@ bhac_status bhac_init_grid(bhac_ctx** out, const bhac_grid_desc* d, const bhac_b
     c->U[s] = (double*)(c->arena + L.off_U[s]);
   }
   c->scratch = (double*)(c->arena + L.off_scratch);
+  c->d_status = (unsigned char*)(c->arena + L.off_status);
   char* small = c->arena + L.off_small;
   c->dt_dev = (double*)small;
   c->smax = (unsigned long long*)(small + 8);
@@ -497,6 +511,7 @@ bhac_status bhac_set_prims(bhac_ctx* c, const double* prims, int on_device) {
   StageArgs a = base_args(c);
   cudaError_t e = launch_scatter_prims(a, src, c->P[0], c->P32[0], c->st);
   if (e == cudaSuccess) e = launch_init_cons(a, c->P[0], c->U[0], c->st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->d_status, 0, (size_t)c->nb * c->nint, c->st);
   if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(c->st);
   if (e != cudaSuccess) return BHAC_ERR_CUDA;
   c->prims_ok = true;
@@ -504,13 +519,25 @@ bhac_status bhac_set_prims(bhac_ctx* c, const double* prims, int on_device) {
   return BHAC_OK;
 }
 
+bhac_status bhac_set_cons(bhac_ctx* c, const double* cons, int on_device) {
+  if (!c || !cons) return BHAC_ERR_ARG;
+  if (!c->prims_ok) return BHAC_ERR_STATE;
+  const size_t bytes = sizeof(double) * NV * (size_t)c->nb * c->nint;
+  cudaError_t e = cudaMemcpyAsync(c->U[c->ucur], cons, bytes, on_device ? cudaMemcpyDeviceToDevice
+                                                                        : cudaMemcpyHostToDevice, c->st);
+  if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(c->st);
+  return cuda_status(e);
+}
+
 bhac_status bhac_fill_ghosts(bhac_ctx* c) {
+  NvtxRange range("bhac_fill_ghosts");
   if (!c) return BHAC_ERR_ARG;
   if (!c->prims_ok) return BHAC_ERR_STATE;
   return ghost_fill(c, c->cur, false);
 }
 
 bhac_status bhac_cfl_dt(bhac_ctx* c, double* dt_host) {
+  NvtxRange range("bhac_cfl_dt");
   if (!c) return BHAC_ERR_ARG;
   if (!c->prims_ok) return BHAC_ERR_STATE;
   if (cudaMemsetAsync(c->smax, 0, sizeof(unsigned long long), c->st) != cudaSuccess) return BHAC_ERR_CUDA;
@@ -531,6 +558,7 @@ bhac_status bhac_cfl_dt(bhac_ctx* c, double* dt_host) {
 }
 
 bhac_status bhac_stage(bhac_ctx* c, int stage, double dt) {
+  NvtxRange range(stage == 1 ? "bhac_stage 1" : "bhac_stage 2");
   if (!c || (stage != 1 && stage != 2)) return BHAC_ERR_ARG;
   if (!c->prims_ok) return BHAC_ERR_STATE;
   if (stage == 1 && !(dt > 0.0) && !c->cfl_ok) return BHAC_ERR_STATE;
@@ -588,6 +616,15 @@ bhac_status bhac_get_diagnostics(bhac_ctx* c, long long counts[4]) {
     return BHAC_ERR_CUDA;
   for (int i = 0; i < 4; ++i) counts[i] = (long long)h[i];
   return h[3] ? BHAC_WARN_C2P : BHAC_OK;
+}
+
+bhac_status bhac_get_c2p_status(bhac_ctx* c, unsigned char* out, int on_device) {
+  if (!c || !out) return BHAC_ERR_ARG;
+  if (!c->prims_ok) return BHAC_ERR_STATE;
+  cudaError_t e = cudaMemcpyAsync(out, c->d_status, (size_t)c->nb * c->nint,
+                                  on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->st);
+  if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(c->st);
+  return cuda_status(e);
 }
 
 bhac_status bhac_set_launch(bhac_ctx* c, int tx, int ty, int threads, int persistent, int min_ctas,

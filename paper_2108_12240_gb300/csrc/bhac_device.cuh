@@ -77,6 +77,7 @@ struct StageArgs {
   unsigned long long* smax_in;   // bits of the max CFL rate read by stage 1
   unsigned long long* smax_out;  // accumulated by stage 2 (and the CFL kernel)
   unsigned long long* counts;    // 4 inversion outcome counters
+  unsigned char* status;         // per interior cell: inversion outcome of this stage
   unsigned int* work;            // persistent work counter
   // refinement levels: table offsets (records) and extents per level
   int nlev;

@@ -35,6 +35,7 @@ struct bhac_ctx {
   double* dt_dev;
   unsigned long long* smax;
   unsigned long long* counts;
+  unsigned char* d_status;   // per interior cell: inversion outcome of the last stage
   unsigned int* work;
   // state
   int cur;       // primitive buffer holding the current state

@@ -496,6 +496,7 @@ __device__ __forceinline__ void finish_cell(const StageArgs& a, const LevelGeo& 
   }
   const int st = con2prim(md, Uu, Pg, rho_fl, p_fl, a, Pn);
   cnt[st] += 1u;
+  a.status[(size_t)b * a.nint + ci] = (unsigned char)st;
   if (st >= 2) {
     Derived<double> s;
     derive(md, Pn, a.gam_fac, s);

@@ -94,6 +94,7 @@ def test_shock_tube_one_step(gb):
     assert np.all(err <= TOL64), err
     assert np.abs(gp[:, 8] - rp[:, 8]).max() <= TOL64 * np.abs(rp[:, 5:8]).max()
     assert np.array_equal(s.diagnostics(), o.c2p_counts())
+    assert np.array_equal(s.c2p_status(), o.c2p_status())
 
 
 @pytest.mark.parametrize("k", [10, 50])
@@ -467,6 +468,9 @@ def test_forged_bad_states_are_contained(gb):
     assert st == 0, gb.status_string(st)
     counts, status = gb.bhac_get_diagnostics(s.ctx)
     assert counts[3] > 0 and status == 6  # BHAC_WARN_C2P
+    cell = s.c2p_status()
+    assert cell[3, 5, 5, 5] == 3  # the NaN cell failed (its stage-2 input still holds the NaN)
+    assert np.count_nonzero(cell == 3) <= counts[3]
     assert counts.sum() == 2 * g.ncells
     got = s.cons()
     assert np.all(np.isfinite(got))
@@ -487,3 +491,53 @@ def test_forged_bad_states_are_contained(gb):
     before = np.array(s.diagnostics())
     s.step(dt)
     assert np.array(s.diagnostics())[3] == before[3]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_resume_from_checkpoint_is_bit_identical(gb, precision):
+    """Two steps in one run equal one step, a checkpoint (primitives and
+    conserved state) restored into a new context, and one more step, bit for
+    bit (the conserved state is restored, not re-derived)."""
+    g = pb.torus_3d(nroot=(4, 3, 2))
+    P = pb.fm_torus_prims(g)
+    a = gb.Solver(g, precision)
+    a.set_prims(P)
+    a.cfl_dt()
+    a.step(0.0)
+    a.step(0.0)
+    b = gb.Solver(g, precision)
+    b.set_prims(P)
+    b.cfl_dt()
+    b.step(0.0)
+    state = b.checkpoint()
+    c = gb.Solver(g, precision)
+    c.restore(state)
+    c.cfl_dt()
+    c.step(0.0)
+    assert np.array_equal(c.cons(), a.cons())
+    assert np.array_equal(c.prims(), a.prims())
+    # restoring primitives alone re-derives the conserved state: not bit-identical
+    d = gb.Solver(g, precision)
+    d.set_prims(state["prims"])
+    assert not np.array_equal(d.cons(), state["cons"])
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_two_runs_are_bit_identical(gb, precision):
+    """Determinism: the same input stepped twice in fresh contexts (default
+    launch shape, persistent work queue) gives the same bits."""
+    g = pb.torus_3d(nroot=(4, 3, 2))
+    P = pb.fm_torus_prims(g)
+    outs = []
+    for _ in range(2):
+        s = gb.Solver(g, precision)
+        s.set_launch(persistent=2)
+        s.set_prims(P)
+        s.cfl_dt()
+        for _ in range(3):
+            s.step(0.0)
+        outs.append((s.cons(), s.c2p_status(), s.diagnostics()))
+    assert np.array_equal(outs[0][0], outs[1][0])
+    assert np.array_equal(outs[0][1], outs[1][1])
+    assert np.array_equal(outs[0][2], outs[1][2])
+
