@@ -102,3 +102,4 @@ def empty_prims(grid: Grid) -> np.ndarray:
 from .configs import *  # noqa: E402,F401,F403
 from .flat import *  # noqa: E402,F401,F403
 from .torus import *  # noqa: E402,F401,F403
+from .michel import *  # noqa: E402,F401,F403

@@ -149,6 +149,15 @@ def test_torus_3d_scheme_variants(gb, recon, riemann):
     assert_parity(s.cons(), o.cons(), TOL64, f"{recon}/{riemann}", g)
 
 
+@pytest.mark.parametrize("precision,tol", [("fp64", TOL64), ("mixed", TOLMIX)])
+def test_michel_accretion(gb, precision, tol):
+    """Michel inflow through the horizon (Kerr-Schild, a = 0), theta band with
+    outflow boundaries: two steps against the oracle."""
+    g = pb.michel_2d(nblock=16)
+    s, o, _ = one_step(gb, g, pb.michel_prims(g), precision=precision, steps=2)
+    assert_parity(s.cons(), o.cons(), tol, f"michel {precision}", g)
+
+
 def test_torus_3d_ragged_blocks(gb):
     """Blocks that are not multiples of the 16x16 tile (12 x 20 x 8 cells)."""
     g = pb.torus_3d(nblock=(12, 20, 8), nroot=(4, 3, 4))
