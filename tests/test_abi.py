@@ -52,3 +52,18 @@ def test_invalid_descriptions_are_rejected(bad):
 def test_status_strings():
     assert gb.status_string(0) == "ok"
     assert gb.status_string(3) == "arena too small"
+
+
+def test_empty_and_inconsistent_block_lists_are_rejected():
+    """No blocks, a block outside the root grid, a duplicate block, and a
+    level beyond the grid's levels: BHAC_ERR_ARG before any device work."""
+    g = pb.shock_tube_2d(nblock=16, nroot=2)
+    d = gb.desc_of(g)
+    for blocks in ([], [(0, 0, 0, 0), (0, 2, 0, 0)], [(0, 0, 0, 0), (0, 0, 0, 0)], [(3, 0, 0, 0)]):
+        arr = (gb.BlockDesc * len(blocks))()
+        for n, (lev, ix, iy, iz) in enumerate(blocks):
+            arr[n].level, arr[n].ix, arr[n].iy, arr[n].iz = lev, ix, iy, iz
+        with pytest.raises(gb.BhacError) as e:
+            gb.bhac_query_sizes(d, arr)
+        assert e.value.status == 1, blocks
+

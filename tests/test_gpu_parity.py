@@ -158,6 +158,25 @@ def test_michel_accretion(gb, precision, tol):
     assert_parity(s.cons(), o.cons(), tol, f"michel {precision}", g)
 
 
+@pytest.mark.parametrize("ndim", [2, 3])
+def test_single_periodic_block(gb, ndim):
+    """One block, periodic in every direction: every ghost cell comes from the
+    block itself.  Random smooth plus discontinuous flat-space state, two
+    steps against the oracle."""
+    g = pb.periodic_box(ndim=ndim, nblock=8, nroot=1)
+    P = pb.random_periodic_prims(g)
+    s, o, _ = one_step(gb, g, P, steps=2)
+    assert_parity(s.cons(), o.cons(), TOL64, f"single periodic block {ndim}-D", g)
+
+
+def test_smallest_blocks(gb):
+    """Blocks of 4 x 4 x 4 interior cells (fewer than the 6-cell stencil, so
+    every face stencil reaches into ghost cells of both sides)."""
+    g = pb.torus_3d(nblock=(4, 4, 4), nroot=(8, 4, 4))
+    s, o, _ = one_step(gb, g, pb.fm_torus_prims(g))
+    assert_parity(s.cons(), o.cons(), TOL64, "4^3 blocks", g)
+
+
 def test_torus_3d_ragged_blocks(gb):
     """Blocks that are not multiples of the 16x16 tile (12 x 20 x 8 cells)."""
     g = pb.torus_3d(nblock=(12, 20, 8), nroot=(4, 3, 4))
