@@ -629,7 +629,9 @@ def main():
         "dtype": "f32+f64" if head == "mixed" else "f64",
         "data": "synthetic (seeded Fishbone-Moncrief torus)",
         "config": {"workload": desc, "form": head, "replicas": world,
-                   "l2": "inputs larger than L2 (state ~17 GB), no flush",
+                   "l2": (f"inputs larger than L2 (arena {gb.bhac_query_sizes(gb.desc_of(g, head), gb.blocks_of(g)) / 1e9:.1f} GB"
+                          f" against {getattr(torch.cuda.get_device_properties(local), 'L2_cache_size', 0) / 1e6:.0f} MB"
+                          " of L2), no flush"),
                    "launch": "per step: ghost fill + stage kernel, twice; device dt; shape by autotuner"},
         "forms": {f: {"value": results[f]["value"], "ms_per_step": results[f]["ms_per_step"],
                       "roofline": roofline(f), "c2p_counts": results[f]["c2p_counts"],
