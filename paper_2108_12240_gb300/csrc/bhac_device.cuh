@@ -227,9 +227,9 @@ __device__ __forceinline__ double to_double(float x) { return widen_f32(x); }
 // and every other finite or infinite double so that okey(x) < okey(y)
 // exactly when x < y; every compare below also returns false when an
 // operand is NaN, so each decision is the IEEE compare's for all inputs.
-// The extra NaN tests are integer operations on the lightly used ALU pipe.
-// The generic templates (float, and the flop counter's counting type) are
-// the plain compares.
+// The NaN exclusions are integer compares too (on the keys or the bits), on
+// the lightly used ALU pipe.  The generic templates (float, and the flop
+// counter's counting type) are the plain compares.
 __device__ __forceinline__ long long okey(double x) {
   const long long b = __double_as_longlong(x);
   return b < 0 ? (long long)(0x8000000000000000ULL - (unsigned long long)b) : b;

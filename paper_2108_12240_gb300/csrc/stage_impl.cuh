@@ -792,7 +792,10 @@ __global__ void __launch_bounds__(256, MINB) stage_kernel(StageArgs a) {
 // buffered (x and y faces per plane parity, z faces in three slots: plane k
 // reads faces k and k+1 while plane k+1's producer writes face k+2); named
 // barriers FULL[parity] (producers -> consumers) and EMPTY[parity]
-// (consumers -> producers) hand the buffers over.
+// (consumers -> producers) hand the buffers over.  It reconstructs per face
+// (recon_var), gives each role only part of the CTA's warps, and measured
+// slower than the phased kernel on the tori; it is selected only by an
+// explicit producer-warp count in bhac_set_launch.
 // ----------------------------------------------------------------------------
 // Named barriers (ids 1..4; 0 is __syncthreads).  Producer and consumer roles
 // are whole warps; each warp reconverges before the barrier instruction.
