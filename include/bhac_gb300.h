@@ -73,7 +73,7 @@ typedef struct {
   double gamma_ad;       /* ideal-gas index */
   double cfl;            /* Courant number */
   double ch, kappa;      /* GLM cleaning speed and damping rate */
-  double c2p_tol;        /* Newton tolerance on |dZ|/Z (then one polishing step) */
+  double c2p_tol;        /* Newton stops at the first step with |dZ| <= c2p_tol Z */
   int c2p_maxit;         /* Newton iteration cap */
   double rho_floor, rho_floor_pow, p_floor, p_floor_pow, w_max;
                          /* floors rho >= rho_floor r^rho_floor_pow, p >= p_floor r^p_floor_pow,
@@ -146,6 +146,37 @@ bhac_status bhac_set_cons(bhac_ctx* ctx, const double* cons, int on_device);
 bhac_status bhac_get_prims(bhac_ctx* ctx, double* out, int on_device);
 bhac_status bhac_get_cons(bhac_ctx* ctx, double* out, int on_device);
 
+/* Pipelined host transfers, for a host-side loop that feeds every step its
+ * primitives from host memory and reads every result back while the kernels of
+ * the neighbouring steps run.  The context owns two copy streams, one per
+ * direction, and the arena two staging buffers of the interior primitives
+ * (bhac_query_sizes counts them); the host link carries both directions at
+ * once.
+ *
+ * bhac_set_prims_host_async: copies interior primitives ([block][var][k][j][i],
+ * FP64) from page-locked host memory into the input staging buffer on the
+ * host-to-device copy stream, as soon as the previous load's scatter has
+ * consumed that buffer; the context's stream then waits for the copy and
+ * scatters and sets the conserved state as bhac_set_prims does.  Returns once
+ * enqueued; `host_prims` must stay unchanged until a later bhac_host_fence()
+ * has been followed by a synchronisation of the context's stream.
+ *
+ * bhac_get_prims_host_async: gathers the current interior primitives into the
+ * output staging buffer on the context's stream, after the previous read-back
+ * has drained it, then copies them to page-locked `host_prims` on the
+ * device-to-host copy stream.  Returns once enqueued.
+ *
+ * bhac_host_fence: orders the copy streams and the context's stream both ways:
+ * transfers enqueued after the fence start after the work enqueued on the
+ * stream before it, and work enqueued on the stream after the fence starts
+ * after every transfer enqueued before it.  Synchronising the stream after a
+ * fence therefore waits for all transfers.
+ *
+ * Pageable host memory is rejected (BHAC_ERR_ARG). */
+bhac_status bhac_set_prims_host_async(bhac_ctx* ctx, const double* host_prims);
+bhac_status bhac_get_prims_host_async(bhac_ctx* ctx, double* host_prims);
+bhac_status bhac_host_fence(bhac_ctx* ctx);
+
 /* Per interior cell, the inversion outcome of the last stage run (0 Newton
  * converged, 1 backup solver, 2 floors applied, 3 failed and kept the
  * previous primitives), one byte per cell, [block][k][j][i].  Host copies
@@ -178,7 +209,11 @@ bhac_status bhac_launches_per_step(const bhac_ctx* ctx, int* launches);
  * for the warp-specialised form: p warps compute the next plane's face fluxes
  * while the others update the current plane's cells (0: the phased form).
  * tx, ty, threads, min_ctas = 0 keep the current setting.  Results do not
- * depend on the launch shape. */
+ * depend on the launch shape.  The default after bhac_init_grid: 256 threads,
+ * one CTA per item, and the largest of the tiles 32x16, 16x16, 16x8, 8x8
+ * that divides the block and fits the shared-memory limit; in the 3-D mixed
+ * form the largest of them up to 16x16 that leaves room for two CTAs per SM,
+ * with min_ctas = 2. */
 bhac_status bhac_set_launch(bhac_ctx* ctx, int tx, int ty, int threads, int persistent, int min_ctas,
                             int producer_warps);
 

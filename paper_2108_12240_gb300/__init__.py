@@ -22,7 +22,8 @@ __all__ = [
     "bhac_cfl_dt", "bhac_step", "bhac_stage", "bhac_get_prims", "bhac_get_cons", "bhac_get_diagnostics",
     "bhac_set_launch", "bhac_count_flops", "bhac_graph_capture", "bhac_graph_launch", "bhac_cfl_dt_static", "bhac_destroy",
     "bhac_status_string", "bhac_check_bit_ops", "bhac_launches_per_step", "bhac_get_prims_ghosted",
-    "bhac_get_c2p_status", "bhac_set_cons",
+    "bhac_get_c2p_status", "bhac_set_cons", "bhac_set_prims_host_async", "bhac_get_prims_host_async",
+    "bhac_host_fence",
 ]
 
 NV = 9
@@ -92,6 +93,9 @@ def lib():
             "bhac_get_prims_ghosted": ([vp, vp, i], i),
             "bhac_get_c2p_status": ([vp, vp, i], i),
             "bhac_set_cons": ([vp, vp, i], i),
+            "bhac_set_prims_host_async": ([vp, vp], i),
+            "bhac_get_prims_host_async": ([vp, vp], i),
+            "bhac_host_fence": ([vp], i),
             "bhac_destroy": ([vp], None),
             "bhac_status_string": ([i], C.c_char_p),
         }
@@ -168,6 +172,18 @@ def bhac_get_c2p_status(ctx, ptr: int, on_device: bool):
 
 def bhac_set_cons(ctx, ptr: int, on_device: bool):
     _check("bhac_set_cons", lib().bhac_set_cons(ctx, C.c_void_p(ptr), int(on_device)))
+
+
+def bhac_set_prims_host_async(ctx, ptr: int):
+    _check("bhac_set_prims_host_async", lib().bhac_set_prims_host_async(ctx, C.c_void_p(ptr)))
+
+
+def bhac_get_prims_host_async(ctx, ptr: int):
+    _check("bhac_get_prims_host_async", lib().bhac_get_prims_host_async(ctx, C.c_void_p(ptr)))
+
+
+def bhac_host_fence(ctx):
+    _check("bhac_host_fence", lib().bhac_host_fence(ctx))
 
 
 def bhac_get_prims_ghosted(ctx, ptr: int, on_device: bool):
@@ -316,6 +332,27 @@ class Solver:
         out = np.empty(self.shape)
         bhac_get_prims(self.ctx, out.ctypes.data, False)
         return out
+
+    def _pinned(self, t):
+        torch = self.torch
+        if not (isinstance(t, torch.Tensor) and t.device.type == "cpu" and t.is_pinned()
+                and t.dtype == torch.float64 and t.is_contiguous() and tuple(t.shape) == self.shape):
+            raise ValueError(f"expected a contiguous pinned CPU float64 tensor of shape {self.shape}")
+        return t.data_ptr()
+
+    def set_prims_host_async(self, host):
+        """Enqueues a load of the primitives from a pinned CPU tensor; the copy
+        overlaps kernels already enqueued (see bhac_set_prims_host_async)."""
+        bhac_set_prims_host_async(self.ctx, self._pinned(host))
+
+    def get_prims_host_async(self, host):
+        """Enqueues a read-back of the primitives into a pinned CPU tensor; the
+        copy overlaps kernels enqueued afterwards."""
+        bhac_get_prims_host_async(self.ctx, self._pinned(host))
+
+    def host_fence(self):
+        """Orders the copy streams and the solver's stream both ways."""
+        bhac_host_fence(self.ctx)
 
     def c2p_status(self) -> np.ndarray:
         """Per interior cell (blocks, nz, ny, nx): the last stage's inversion outcome."""

@@ -16,6 +16,7 @@ import os
 
 DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune.json")
 SMEM_LIMIT = 226 * 1024
+TWO_CTA_SMEM = 113 * 1024  # per CTA, two CTAs on one SM
 # names the stage kernel's shared-memory design; cached shapes of another
 # design are not reused
 KERNEL_TAG = "edge-staged"
@@ -140,8 +141,13 @@ def cached_or_default(solver, cache_path: str = DEFAULT_CACHE):
         shape = tuple(cache[key]["shape"])
         solver.set_launch(*shape)
         return shape
+    # the library's own default (the rule of bhac_init_grid)
     nx, ny = solver.grid.nx[0], solver.grid.nx[1]
+    two = solver.grid.ndim == 3 and solver.precision == "mixed"
     for tx, ty in ((32, 16), (16, 16), (16, 8), (8, 8)):
-        if nx % tx == 0 and ny % ty == 0 and smem_bytes(tx, ty, solver.grid.ndim, solver.precision) <= SMEM_LIMIT:
-            return (tx, ty, 256, 0, 1, 0)
+        if two and tx * ty > 256:
+            continue
+        limit = TWO_CTA_SMEM if two else SMEM_LIMIT
+        if nx % tx == 0 and ny % ty == 0 and smem_bytes(tx, ty, solver.grid.ndim, solver.precision) <= limit:
+            return (tx, ty, 256, 0, 2 if two else 1, 0)
     return (nx, ny, 256, 0, 1, 0)

@@ -26,7 +26,7 @@ namespace {
 
 struct Layout {
   size_t off_blk, off_order, off_src, off_flags, off_tmpl, off_tc, off_tf1, off_tf2, off_tc32, off_tf1_32, off_tf2_32;
-  size_t off_P[2], off_P32[2], off_U[2], off_scratch, off_status, off_small;
+  size_t off_P[2], off_P32[2], off_U[2], off_scratch, off_scratch_out, off_status, off_small;
   size_t off_nodes, off_ops, off_nodeval, off_cf, off_regoff, off_reg, off_rcells, off_rterms, total;
   long long toff_c[MAXLEV], toff_f1[MAXLEV], toff_f2[MAXLEV];
 };
@@ -121,6 +121,7 @@ Layout layout(const bhac_grid_desc* d, int nb, const HostMaps& M) {
   for (int s = 0; s < 2; ++s) L.off_P32[s] = take(mixed ? sizeof(float) * NV * (size_t)nb * ncell : 0);
   for (int s = 0; s < 2; ++s) L.off_U[s] = take(sizeof(double) * NV * (size_t)nb * nint);
   L.off_scratch = take(sizeof(double) * NV * (size_t)nb * nint);
+  L.off_scratch_out = take(sizeof(double) * NV * (size_t)nb * nint);
   L.off_status = take((size_t)nb * nint);
   L.off_small = take(256);
   L.off_nodes = take(sizeof(GhostNode) * M.nodes.size());
@@ -372,6 +373,7 @@ bhac_status bhac_init_grid(bhac_ctx** out, const bhac_grid_desc* d, const bhac_b
     c->U[s] = (double*)(c->arena + L.off_U[s]);
   }
   c->scratch = (double*)(c->arena + L.off_scratch);
+  c->scratch_out = (double*)(c->arena + L.off_scratch_out);
   c->d_status = (unsigned char*)(c->arena + L.off_status);
   char* small = c->arena + L.off_small;
   c->dt_dev = (double*)small;
@@ -394,24 +396,33 @@ bhac_status bhac_init_grid(bhac_ctx** out, const bhac_grid_desc* d, const bhac_b
   c->ucur = 0;
   c->threads = 256;
   // default launch shape: the largest of these tiles that divides the block
-  // and fits the shared-memory limit, else the whole block face
+  // and fits the shared-memory limit, else the whole block face.  The 3-D
+  // mixed form takes the largest tile of at most 16 x 16 whose workspace lets
+  // two CTAs share an SM, with the two-CTA register bound: the fastest shape
+  // family on every 3-D grid the autotuner has timed.
+  c->minb = 1;
   {
     static const int tiles[][2] = {{32, 16}, {16, 16}, {16, 8}, {8, 8}};
     c->tx = d->nx[0];
     c->ty = d->nx[1];
+    const bool two_ctas = d->ndim == 3 && c->mixed;
     for (const auto& t : tiles) {
-      if (d->nx[0] % t[0] == 0 && d->nx[1] % t[1] == 0 && stage_smem(c, t[0], t[1], 0) <= (size_t)kMaxDynSmem) {
+      if (two_ctas && t[0] * t[1] > 256) continue;
+      const size_t limit = two_ctas ? (size_t)kTwoCtaSmem : (size_t)kMaxDynSmem;
+      if (d->nx[0] % t[0] == 0 && d->nx[1] % t[1] == 0 && stage_smem(c, t[0], t[1], 0) <= limit) {
         c->tx = t[0];
         c->ty = t[1];
+        if (two_ctas) c->minb = 2;
         break;
       }
     }
   }
   c->persistent = 0;
-  c->minb = 1;
   c->pwarps = 0;
   c->graph = nullptr;
   c->graph_steps = 0;
+  c->cp_in = c->cp_out = nullptr;
+  c->ev_h2d = c->ev_scat = c->ev_gath = c->ev_d2h = c->ev_fence = c->ev_join_in = c->ev_join_out = nullptr;
   c->blk.resize(4 * nb);
   for (int i = 0; i < nb; ++i) {
     c->blk[4 * i] = b[i].level;
@@ -447,8 +458,13 @@ bhac_status bhac_init_grid(bhac_ctx** out, const bhac_grid_desc* d, const bhac_b
   if (e == cudaSuccess) e = up(c->d_rterms, M.rterms.data(), sizeof(RefluxTerm) * M.rterms.size());
   if (e == cudaSuccess) e = cudaMemsetAsync(small, 0, 256, c->st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);  // the host maps die here
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->cp_in, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->cp_out, cudaStreamNonBlocking);
+  for (cudaEvent_t* ev : {&c->ev_h2d, &c->ev_scat, &c->ev_gath, &c->ev_d2h, &c->ev_fence, &c->ev_join_in,
+                          &c->ev_join_out})
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
   if (e != cudaSuccess) {
-    delete c;
+    bhac_destroy(c);
     return BHAC_ERR_CUDA;
   }
   c->metric_ok = c->flat;
@@ -529,6 +545,68 @@ bhac_status bhac_set_cons(bhac_ctx* c, const double* cons, int on_device) {
   return cuda_status(e);
 }
 
+// Host memory the copy engines can read and write without staging.
+static bool page_locked(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeHost;
+}
+
+bhac_status bhac_set_prims_host_async(bhac_ctx* c, const double* host_prims) {
+  if (!c || !host_prims) return BHAC_ERR_ARG;
+  if (!c->metric_ok) return BHAC_ERR_STATE;
+  if (!page_locked(host_prims)) return BHAC_ERR_ARG;
+  const size_t bytes = sizeof(double) * NV * (size_t)c->nb * c->nint;
+  // the copy starts once the previous load's scatter has consumed the staging buffer
+  cudaError_t e = cudaStreamWaitEvent(c->cp_in, c->ev_scat, 0);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->scratch, host_prims, bytes, cudaMemcpyHostToDevice, c->cp_in);
+  if (e == cudaSuccess) e = cudaEventRecord(c->ev_h2d, c->cp_in);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(c->st, c->ev_h2d, 0);
+  if (e != cudaSuccess) return BHAC_ERR_CUDA;
+  c->cur = 0;
+  c->ucur = 0;
+  StageArgs a = base_args(c);
+  e = launch_scatter_prims(a, c->scratch, c->P[0], c->P32[0], c->st);
+  if (e == cudaSuccess) e = cudaEventRecord(c->ev_scat, c->st);
+  if (e == cudaSuccess) e = launch_init_cons(a, c->P[0], c->U[0], c->st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->d_status, 0, (size_t)c->nb * c->nint, c->st);
+  if (e != cudaSuccess) return BHAC_ERR_CUDA;
+  c->prims_ok = true;
+  c->cfl_ok = false;
+  return BHAC_OK;
+}
+
+bhac_status bhac_get_prims_host_async(bhac_ctx* c, double* host_prims) {
+  if (!c || !host_prims) return BHAC_ERR_ARG;
+  if (!c->prims_ok) return BHAC_ERR_STATE;
+  if (!page_locked(host_prims)) return BHAC_ERR_ARG;
+  const size_t bytes = sizeof(double) * NV * (size_t)c->nb * c->nint;
+  StageArgs a = base_args(c);
+  // the gather waits until the previous read-back has drained the staging buffer
+  cudaError_t e = cudaStreamWaitEvent(c->st, c->ev_d2h, 0);
+  if (e == cudaSuccess) e = launch_gather_interior(a, c->P[c->cur], c->scratch_out, c->st);
+  if (e == cudaSuccess) e = cudaEventRecord(c->ev_gath, c->st);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(c->cp_out, c->ev_gath, 0);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(host_prims, c->scratch_out, bytes, cudaMemcpyDeviceToHost, c->cp_out);
+  if (e == cudaSuccess) e = cudaEventRecord(c->ev_d2h, c->cp_out);
+  return cuda_status(e);
+}
+
+bhac_status bhac_host_fence(bhac_ctx* c) {
+  if (!c) return BHAC_ERR_ARG;
+  cudaError_t e = cudaEventRecord(c->ev_fence, c->st);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(c->cp_in, c->ev_fence, 0);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(c->cp_out, c->ev_fence, 0);
+  if (e == cudaSuccess) e = cudaEventRecord(c->ev_join_in, c->cp_in);
+  if (e == cudaSuccess) e = cudaEventRecord(c->ev_join_out, c->cp_out);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(c->st, c->ev_join_in, 0);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(c->st, c->ev_join_out, 0);
+  return cuda_status(e);
+}
+
 bhac_status bhac_fill_ghosts(bhac_ctx* c) {
   NvtxRange range("bhac_fill_ghosts");
   if (!c) return BHAC_ERR_ARG;
@@ -598,8 +676,10 @@ bhac_status bhac_get_prims(bhac_ctx* c, double* out, int on_device) {
   if (!c->prims_ok) return BHAC_ERR_STATE;
   StageArgs a = base_args(c);
   if (on_device) return cuda_status(launch_gather_interior(a, c->P[c->cur], out, c->st));
-  if (launch_gather_interior(a, c->P[c->cur], c->scratch, c->st) != cudaSuccess) return BHAC_ERR_CUDA;
-  return copy_out(c, c->scratch, out, 0);
+  // the output staging buffer, once an asynchronous read-back still copying from it is done
+  if (c->ev_d2h && cudaStreamWaitEvent(c->st, c->ev_d2h, 0) != cudaSuccess) return BHAC_ERR_CUDA;
+  if (launch_gather_interior(a, c->P[c->cur], c->scratch_out, c->st) != cudaSuccess) return BHAC_ERR_CUDA;
+  return copy_out(c, c->scratch_out, out, 0);
 }
 
 bhac_status bhac_get_cons(bhac_ctx* c, double* out, int on_device) {
@@ -685,6 +765,13 @@ bhac_status bhac_graph_launch(bhac_ctx* c) {
 void bhac_destroy(bhac_ctx* c) {
   if (!c) return;
   if (c->graph) cudaGraphExecDestroy(c->graph);
+  for (cudaStream_t s : {c->cp_in, c->cp_out})
+    if (s) {
+      cudaStreamSynchronize(s);
+      cudaStreamDestroy(s);
+    }
+  for (cudaEvent_t e : {c->ev_h2d, c->ev_scat, c->ev_gath, c->ev_d2h, c->ev_fence, c->ev_join_in, c->ev_join_out})
+    if (e) cudaEventDestroy(e);
   delete c;
 }
 

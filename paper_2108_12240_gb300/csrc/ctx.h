@@ -31,7 +31,8 @@ struct bhac_ctx {
   double* P[2];
   float* P32[2];
   double* U[2];
-  double* scratch;
+  double* scratch;      // interior primitives: host loads (input staging)
+  double* scratch_out;  // interior primitives: host read-backs (output staging)
   double* dt_dev;
   unsigned long long* smax;
   unsigned long long* counts;
@@ -61,6 +62,10 @@ struct bhac_ctx {
   // captured steps
   cudaGraphExec_t graph;
   int graph_steps;
+  // pipelined host transfers: one copy stream per direction and the events
+  // that order them with the context's stream
+  cudaStream_t cp_in, cp_out;
+  cudaEvent_t ev_h2d, ev_scat, ev_gath, ev_d2h, ev_fence, ev_join_in, ev_join_out;
 };
 
 // Shared helpers of the ABI units (api.cu).

@@ -11,6 +11,9 @@ namespace bhac {
 // opt-in per-CTA limit of sm_103a (227 KB) less room for the kernels' static
 // shared memory (the attribute plus the static size must fit the limit).
 constexpr int kMaxDynSmem = 226 * 1024;
+// dynamic shared memory per CTA that still lets two CTAs share an SM (228 KB
+// per SM, 1 KB of it reserved per resident CTA)
+constexpr int kTwoCtaSmem = 113 * 1024;
 
 // stage kernels (stage_fp64.cu / stage_mixed.cu)
 cudaError_t launch_stage_fp64(const StageArgs& a, int grid, int threads, size_t smem, cudaStream_t st);

@@ -551,6 +551,58 @@ def test_resume_from_checkpoint_is_bit_identical(gb, precision):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_pipelined_host_transfers_match_synchronous_ones(gb, precision):
+    """Steps fed from and read back to pinned host memory through the
+    asynchronous transfers (the next step's load overlapping this step's
+    kernels, this step's read-back overlapping the next step's kernels) give,
+    step by step, the bits of the synchronous host path.  Every step has its
+    own input and output buffer, so a copy that ran out of order would show."""
+    import torch
+    g = pb.torus_3d(nroot=(4, 3, 2))
+    P0 = pb.fm_torus_prims(g)
+    K = 4
+    ins = []
+    for n in range(K):
+        P = P0.copy()
+        P[:, 1] *= 1.0 + 0.01 * n  # a different pressure level per step
+        ins.append(torch.from_numpy(P).pin_memory())
+    outs = [torch.zeros(ins[0].shape, dtype=torch.float64).pin_memory() for _ in range(K)]
+    s = gb.Solver(g, precision)
+    s.host_fence()
+    s.set_prims_host_async(ins[0])
+    for n in range(K):
+        gb.bhac_cfl_dt(s.ctx, False)
+        s.step(0.0)
+        s.get_prims_host_async(outs[n])
+        if n + 1 < K:
+            s.set_prims_host_async(ins[n + 1])
+    s.host_fence()
+    s.stream.synchronize()
+    ref = gb.Solver(g, precision)
+    for n in range(K):
+        ref.set_prims(ins[n].numpy())
+        gb.bhac_cfl_dt(ref.ctx, False)
+        ref.step(0.0)
+        assert np.array_equal(outs[n].numpy(), ref.prims()), n
+    # the synchronous read-back shares the output staging buffer: still the same bits
+    assert np.array_equal(s.prims(), outs[K - 1].numpy())
+
+
+def test_pipelined_host_transfers_reject_pageable_memory(gb):
+    g = pb.torus_2d(nblock=8)
+    s = gb.Solver(g)
+    a = np.ascontiguousarray(pb.fm_torus_prims(g))
+    with pytest.raises(gb.BhacError) as e:
+        gb.bhac_set_prims_host_async(s.ctx, a.ctypes.data)
+    assert e.value.status == 1
+    s.set_prims(a)
+    out = np.empty_like(a)
+    with pytest.raises(gb.BhacError) as e:
+        gb.bhac_get_prims_host_async(s.ctx, out.ctypes.data)
+    assert e.value.status == 1
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_two_runs_are_bit_identical(gb, precision):
     """Determinism: the same input stepped twice in fresh contexts (default
     launch shape, persistent work queue) gives the same bits."""
