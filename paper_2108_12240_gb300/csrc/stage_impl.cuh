@@ -116,6 +116,7 @@ BHAC_HD int con2prim_t(const Met<T>& m, const T* U, const T* Pg, T rho_fl, T p_f
   int status = 0;
   bool solved = false;
   T Z = T(0.0), v2 = T(0.0);
+  T W = T(0.0), sq = T(0.0);  // 1/sqrt(1 - v^2) and sqrt(1 - v^2) of the accepted solution
   if (fin && gt0_t(q.D) && gt0_t(q.E)) {
     const T gu1 = m.g11 * Pg[U1] + m.g13 * Pg[U3];
     const T gu2 = m.g22 * Pg[U2];
@@ -157,7 +158,13 @@ BHAC_HD int con2prim_t(const Met<T>& m, const T* U, const T* Pg, T rho_fl, T p_f
       }
     }
     if (solved && !(le_x(T(0.0), v2) && lt_t(v2, T(1.0)) && gt0_t(Z))) solved = false;
-    if (solved && !gt0_t(q.D * sqrt_t(T(1.0) - v2))) solved = false;
+    // the recovered density D sqrt(1 - v^2) must be positive; sqrt(1 - v^2)
+    // is formed as (1 - v^2) / sqrt(1 - v^2), the factor the recovery uses
+    if (solved) {
+      W = rsqrt_t(T(1.0) - v2);
+      sq = (T(1.0) - v2) * W;
+      if (!gt0_t(q.D * sq)) solved = false;
+    }
     if (!solved) {
       T lo = Z0, hi = Z0;
       int k = 0;
@@ -185,16 +192,16 @@ BHAC_HD int con2prim_t(const Met<T>& m, const T* U, const T* Pg, T rho_fl, T p_f
         if (finite_t(Z) && Z > T(0.0)) {
           solved = true;
           status = 1;
+          W = rsqrt_t(T(1.0) - v2);
+          sq = (T(1.0) - v2) * W;
         }
       }
     }
   }
   if (solved) {
-    // W = 1/sqrt(1 - v^2) and sqrt(1 - v^2) from one reciprocal square root;
-    // 1/Z and 1/(Z + B^2) from one reciprocal of their product
+    // W = 1/sqrt(1 - v^2) and sqrt(1 - v^2) came from one reciprocal square
+    // root; 1/Z and 1/(Z + B^2) from one reciprocal of their product
     const T omv = T(1.0) - v2;
-    const T W = rsqrt_t(omv);
-    const T sq = omv * W;
     const T ZB = Z + q.Bsq;
     const T r = rcp_t(Z * ZB);
     P[RHO] = q.D * sq;
