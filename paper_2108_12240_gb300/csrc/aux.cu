@@ -10,17 +10,18 @@ namespace bhac {
 // every block is a gather from one interior cell (same-level neighbour or the
 // boundary rule's source), with the sign flips of the polar axis and the
 // no-inflow clamps applied.  One thread per (block, ghost slot); the nine
-// variables are moved by the same thread.
+// variables are moved by the same thread.  CTA rows (blockIdx.y) walk the
+// blocks and the threads of a row walk one block's slots, so no thread
+// divides a flat (block, slot) index.
 // ----------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) ghost_fill_kernel(GhostArgs g) {
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+  if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
     if (g.work_reset) *g.work_reset = 0u;
     if (g.smax_reset) *g.smax_reset = 0ull;
   }
-  const long long n = (long long)g.nblocks * g.nslots;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
-    const int b = (int)(t / g.nslots);
-    const int s = (int)(t - (long long)b * g.nslots);
+  for (int b = blockIdx.y; b < g.nblocks; b += gridDim.y)
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < g.nslots; s += gridDim.x * blockDim.x) {
+    const size_t t = (size_t)b * g.nslots + s;
     const int src = g.src[t];
     const size_t dout = (size_t)b * NV * g.ncell + g.tmpl[s];
     if (src < 0) {
@@ -82,7 +83,11 @@ static int grid_for(long long n, int threads) {
 }
 
 cudaError_t launch_ghost_fill(const GhostArgs& g, cudaStream_t st) {
-  ghost_fill_kernel<<<grid_for((long long)g.nblocks * g.nslots, 256), 256, 0, st>>>(g);
+  // x: the CTAs covering one block's slots; y: blocks (a CTA row loops over
+  // blocks beyond the grid's y limit)
+  const int gx = g.nslots > 0 ? (g.nslots + 255) / 256 : 1;
+  const int gy = g.nblocks < 1 ? 1 : (g.nblocks < 65535 ? g.nblocks : 65535);
+  ghost_fill_kernel<<<dim3(gx, gy), 256, 0, st>>>(g);
   return cudaGetLastError();
 }
 
