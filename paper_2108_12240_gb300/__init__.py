@@ -308,6 +308,10 @@ class Solver:
 
     def close(self):
         if getattr(self, "ctx", None):
+            # the arena returns to PyTorch's allocator with the tensor, so the
+            # kernels and transfers still reading or writing it finish first
+            bhac_host_fence(self.ctx)
+            self.stream.synchronize()
             bhac_destroy(self.ctx)
             self.ctx = None
 
