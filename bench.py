@@ -34,6 +34,7 @@ import numpy as np  # noqa: E402
 
 import problems as pb  # noqa: E402
 
+NVAR = 9  # primitive (and conserved) variables per cell
 METRIC = "zone-updates/s per RK stage"
 UNIT = "zone-updates/s"
 # FP64 peak derived from the part's unit counts and clock: 152 SMs x 2070 MHz x
@@ -257,6 +258,20 @@ def kernel_fingerprint() -> str:
         with open(os.path.join(csrc, f), encoding="utf-8") as fh:
             h.update(f.encode() + b"\0" + _code_only(fh.read()).encode())
     return h.hexdigest()
+
+
+def fill_roofline(g, form: str, fill_ms: float, hbm_gbs):
+    """HBM roofline of one ghost fill (the paper's fill_gc_srl), a gather:
+    per ghost cell the nine values read and written (FP64 in the FP64 form,
+    the FP32 copy in the mixed form) plus the map's int32 source index and
+    flag byte."""
+    ghosts = g.nb * (int(np.prod([g.nx[d] + (2 * g.ng if d < g.ndim else 0) for d in range(3)]))
+                     - int(np.prod(g.nx)))
+    fill_bytes = ghosts * (NVAR * (8 if form == "fp64" else 4) * 2 + 5)
+    gbs = fill_bytes / (fill_ms * 1e-3) / 1e9 if fill_ms > 0 else None
+    return {"bound": "hbm", "achieved": gbs, "peak": hbm_gbs, "unit": "GB/s",
+            "frac": gbs / hbm_gbs if (gbs and hbm_gbs) else None,
+            "bytes_per_fill": fill_bytes, "ghost_cells": ghosts, "ms": fill_ms}
 
 
 def shape_key(ls) -> str:
@@ -609,6 +624,7 @@ def main():
         ach64 = fl["fp64_flops"] * cells / stage_s / 1e12
         bytes_alg = (288 if form == "fp64" else 252) * cells
         traffic = recorded_traffic(args.workload, form, shape_key(r["launch_shape"]))
+        fill = fill_roofline(g, form, r["fill_ms"], pk.get("hbm_gbs"))
         return {"bound": "alu", "achieved": ach64, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": ach64 / FP64_PEAK_TFLOPS, "traffic": traffic, "kernel": "stage_kernel",
                 "traffic_source": os.path.relpath(TRAFFIC_FILE, ROOT) if traffic else None,
@@ -619,7 +635,8 @@ def main():
                 "fp32_flops_per_zone_stage": fl["fp32_flops"],
                 "fp32_frac_of_peak": fl["fp32_flops"] * cells / stage_s / 1e12 / FP32_PEAK_TFLOPS,
                 "hbm_bytes_per_zone_stage": bytes_alg / cells,
-                "hbm_frac_of_measured": bytes_alg / stage_s / 1e9 / pk["hbm_gbs"]}
+                "hbm_frac_of_measured": bytes_alg / stage_s / 1e9 / pk["hbm_gbs"],
+                "ghost_fill": fill}
 
     r = results[head]
     line = {

@@ -55,3 +55,16 @@ def test_recorded_traffic_is_dropped_for_other_sources(record):
 def test_recorded_traffic_without_a_record(monkeypatch, tmp_path):
     monkeypatch.setattr(bench, "TRAFFIC_FILE", str(tmp_path / "missing.txt"))
     assert bench.recorded_traffic("torus_3d_large", "mixed", "16x16/256/minctas2/producers0") is None
+
+
+def test_fill_roofline_counts_ghost_cells_and_bytes():
+    import problems as pb
+    g = pb.torus_3d_large()
+    r = bench.fill_roofline(g, "fp64", 1.0, 6792.1)
+    assert r["ghost_cells"] == 2048 * (38 * 38 * 22 - 32 * 32 * 16)
+    assert r["bytes_per_fill"] == r["ghost_cells"] * 149
+    assert abs(r["achieved"] - r["bytes_per_fill"] / 1e-3 / 1e9) < 1e-6
+    assert abs(r["frac"] - r["achieved"] / 6792.1) < 1e-12
+    m = bench.fill_roofline(pb.torus_2d(), "mixed", 0.5, None)
+    assert m["ghost_cells"] == 256 * (22 * 22 - 16 * 16)
+    assert m["bytes_per_fill"] == m["ghost_cells"] * 77 and m["frac"] is None
