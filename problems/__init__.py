@@ -103,3 +103,4 @@ from .configs import *  # noqa: E402,F401,F403
 from .flat import *  # noqa: E402,F401,F403
 from .torus import *  # noqa: E402,F401,F403
 from .michel import *  # noqa: E402,F401,F403
+from .monopole import *  # noqa: E402,F401,F403

@@ -691,16 +691,9 @@ def _monopole_residuals(nr_blocks, nblock=16):
     3 <= r <= 5, at every resolution, away from the radial boundaries (whose
     zero-gradient ghosts are wrong for B^r ~ 1/r^2; one stage reaches three
     cells in)."""
-    g = pb.Grid(ndim=2, nx=(nblock, nblock, 1), nroot=(nr_blocks, nr_blocks // 2, 1),
-                xmin=(2.0, math.pi / 4, 0.0), xmax=(6.0, 3 * math.pi / 4, 2 * math.pi), coords="ks",
-                spin=0.0, mass=0.0, bc=(("outflow", "outflow"), ("outflow", "outflow"), ("periodic", "periodic")),
-                recon="ppm", riemann="hll", gamma_ad=4.0 / 3.0, ch=1.0, kappa=0.1)
+    g = pb.monopole_flat_spherical(nr_blocks, nblock)
     r = pb.cell_centres(g)[0]
-    P = pb.empty_prims(g)
-    B0 = 4.0 * math.sqrt(0.1)  # B^2 = p at r = 2
-    P[:, 0] = 1.0
-    P[:, 1] = 0.1
-    P[:, 5] = B0 / r ** 2
+    P = pb.monopole_prims(g)
     o = oracle.Oracle(g)
     o.set_prims(P)
     U0 = o.cons()
