@@ -13,6 +13,14 @@
  * in the order the method applies them; every reading of a point the paper
  * leaves open is listed in the design notes of the repository.
  *
+ * Parity unpinned (no fact outside the oracle fixes them; the tests check
+ * the special cases that have one):
+ *   - the metric terms of the GLM source, -psi d_i beta^i + c_h^2 B^i d_i alpha,
+ *     beyond their flat-space reduction to -kappa psi (the paper gives no
+ *     cleaning equations; the terms are a reading);
+ *   - the SRMHD shock tube as a whole, beyond a stored regression profile
+ *     written by the oracle itself (the paper prints no reference solution).
+ *
  * Conventions
  *   primitive order : rho, p, u^1, u^2, u^3, B^1, B^2, B^3, psi
  *                     (u^i = W v^i, contravariant code-coordinate components)
