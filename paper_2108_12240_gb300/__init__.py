@@ -286,15 +286,26 @@ def blocks_of(grid):
 
 
 class Solver:
-    """A grid on the current CUDA device: arena from torch, stream from torch."""
+    """A grid on the current CUDA device: arena from torch, stream from torch.
+    The library launches on the device current at each call, so the arena,
+    the stream and the calls all belong to that device (select it with
+    torch.cuda.set_device first; one process per GPU)."""
 
-    def __init__(self, grid, precision: str = "fp64", device: str = "cuda:0", stream=None):
+    def __init__(self, grid, precision: str = "fp64", device=None, stream=None):
         import torch
 
         self.torch = torch
         self.grid = grid
         self.precision = precision
-        self.device = torch.device(device)
+        cur = torch.device("cuda", torch.cuda.current_device())
+        self.device = cur if device is None else torch.device(device)
+        if self.device.index is None:
+            self.device = torch.device("cuda", torch.cuda.current_device())
+        if self.device != cur:
+            raise ValueError(f"Solver device {self.device} is not the current CUDA device {cur}; "
+                             "call torch.cuda.set_device first")
+        if stream is not None and stream.device != self.device:
+            raise ValueError(f"stream on {stream.device}, solver on {self.device}")
         self.desc = desc_of(grid, precision)
         self.blocks = blocks_of(grid)
         self.nbytes = bhac_query_sizes(self.desc, self.blocks)
