@@ -26,6 +26,13 @@ def test_library_exports_every_declared_entry_point():
         assert hasattr(L, n), n
 
 
+def test_python_binding_has_every_declared_entry_point():
+    """The binding mirrors the header name for name (marshalling only)."""
+    missing = [n for n in declared_functions() if not callable(getattr(gb, n, None))]
+    assert not missing, missing
+    assert set(declared_functions()) <= set(gb.__all__)
+
+
 def test_query_sizes_counts_state_and_tables():
     g = pb.torus_3d(nroot=(2, 2, 2))
     n64 = gb.bhac_query_sizes(gb.desc_of(g, "fp64"), gb.blocks_of(g))
