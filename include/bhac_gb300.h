@@ -172,7 +172,9 @@ bhac_status bhac_get_cons(bhac_ctx* ctx, double* out, int on_device);
  * after every transfer enqueued before it.  Synchronising the stream after a
  * fence therefore waits for all transfers.
  *
- * Pageable host memory is rejected (BHAC_ERR_ARG). */
+ * Pageable host memory is rejected (BHAC_ERR_ARG).  These calls order work
+ * across the context's copy streams with events; they are not meant for a
+ * stream that is being captured (bhac_graph_capture records steps only). */
 bhac_status bhac_set_prims_host_async(bhac_ctx* ctx, const double* host_prims);
 bhac_status bhac_get_prims_host_async(bhac_ctx* ctx, double* host_prims);
 bhac_status bhac_host_fence(bhac_ctx* ctx);
