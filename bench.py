@@ -37,10 +37,11 @@ import problems as pb  # noqa: E402
 NVAR = 9  # primitive (and conserved) variables per cell
 METRIC = "zone-updates/s per RK stage"
 UNIT = "zone-updates/s"
-# FP64 peak derived from the part's unit counts and clock: 152 SMs x 2070 MHz x
-# 2 DFMA (4 flops) per clock per SM = 1.26 TFLOP/s (nominal 1.25 TFLOP/s)
-FP64_PEAK_TFLOPS = 152 * 2.07e9 * 4 / 1e12
-FP32_PEAK_TFLOPS = 152 * 2.07e9 * 256 / 1e12  # 128 FFMA per clock per SM
+# ALU peaks derived from the part's unit counts and clock: per SM and clock,
+# 2 FP64 fused multiply-adds (4 flops) and 128 FP32 ones (256 flops); the SM
+# count is read from the device and the clock is the maximum SM clock
+FP64_FLOPS_PER_SM_CLK = 4
+FP32_FLOPS_PER_SM_CLK = 256
 SAMPLE_CELLS = (128, 64, 64)  # bounded CPU sample of the torus workload
 
 
@@ -81,6 +82,28 @@ def peaks():
             return json.load(f), "measured"
     except OSError:
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def alu_peaks(torch, pk, device=0):
+    """Derived FP64 and FP32 peaks in TFLOP/s: SMs x max SM clock x flops per
+    SM and clock.  SM count from the device; clock from MEASURED_PEAKS.json
+    (2070 MHz, the part's maximum, if that file lacks it)."""
+    sms = torch.cuda.get_device_properties(device).multi_processor_count
+    mhz = float(pk.get("sm_max_mhz") or 2070.0)
+    return {"sms": sms, "sm_max_mhz": mhz,
+            "fp64_tflops": sms * mhz * 1e6 * FP64_FLOPS_PER_SM_CLK / 1e12,
+            "fp32_tflops": sms * mhz * 1e6 * FP32_FLOPS_PER_SM_CLK / 1e12,
+            "kind": f"derived: {sms} SMs x {mhz:.0f} MHz x {FP64_FLOPS_PER_SM_CLK} FP64 / "
+                    f"{FP32_FLOPS_PER_SM_CLK} FP32 flops per SM and clock"}
+
+
+def probe_peaks(gb, torch, stream):
+    """The arithmetic units' measured throughput (bhac_measure_peaks), outside
+    any timed region."""
+    r = gb.bhac_measure_peaks(1 << 14, stream.cuda_stream)
+    return {"fp64_tflops": r["fp64_flops"] / 1e12, "fp32_tflops": r["fp32_flops"] / 1e12,
+            "fp64_div_per_s": r["fp64_div"], "fp64_sqrt_per_s": r["fp64_sqrt"],
+            "fp64_rsqrt_per_s": r["fp64_rsqrt"], "sms": r["sms"]}
 
 
 class Clocks:
@@ -490,19 +513,22 @@ def all_configs(args):
 
     torch.cuda.set_device(0)
     stream = torch.cuda.Stream()
+    alu = alu_peaks(torch, peaks()[0])
     for cfg, name in enumerate(CONFIGS):
         g, desc = workload(name)
         P = initial_prims(g)
         forms = {}
         for form in ("mixed", "fp64"):
-            r = time_form(gb, torch, g, P, form, args.steps, args.warmup, stream, graph_repeats=15, graph_steps=0)
+            with Clocks(0) as ck:
+                r = time_form(gb, torch, g, P, form, args.steps, args.warmup, stream, graph_repeats=15, graph_steps=0)
             stage_s = r["stage_ms_mean"] * 1e-3
             ach = r["flops"]["fp64_flops"] * g.ncells / stage_s / 1e12
             forms[form] = {"zone_updates_per_s": job_value(g.ncells, 1, r["ms_per_step"]),
                            "zone_updates_per_s_graph": job_value(g.ncells, 1, r["graph"]["ms_per_step_median"]),
                            "ms_per_step": r["ms_per_step"], "graph": r["graph"], "stage_ms": r["stage_ms_mean"],
                            "ghost_fill_ms": r["fill_ms"], "fp64_flops_per_zone_stage": r["flops"]["fp64_flops"],
-                           "fp64_frac": ach / FP64_PEAK_TFLOPS, "launch_shape": r["launch_shape"]}
+                           "fp64_frac": ach / alu["fp64_tflops"], "launch_shape": r["launch_shape"],
+                           "clocks": ck.summary()}
         state_mb = g.ncells * 9 * 8 * 2 / 1e6
         print(json.dumps({"config": cfg, "workload": name, "desc": desc, "cells": g.ncells, "blocks": g.nb,
                           "state_mb_fp64": state_mb, "l2_resident": state_mb < 100, "forms": forms}), flush=True)
@@ -517,19 +543,24 @@ def sweep_blocks(args):
 
     torch.cuda.set_device(0)
     stream = torch.cuda.Stream()
+    pk = peaks()[0]
+    alu = alu_peaks(torch, pk)
     rows = []
     for nb in [(8, 8, 8), (16, 16, 16), (32, 32, 16), (32, 32, 32)]:
         g = pb.torus_3d_large(nblock=nb)
         P = initial_prims(g)
         for form in ("mixed", "fp64"):
-            r = time_form(gb, torch, g, P, form, args.steps, args.warmup, stream)
+            with Clocks(0) as ck:
+                r = time_form(gb, torch, g, P, form, args.steps, args.warmup, stream)
             stage_s = r["stage_ms_mean"] * 1e-3
             ach = r["flops"]["fp64_flops"] * g.ncells / stage_s / 1e12
             rows.append({"block": "x".join(map(str, nb)), "blocks": g.nb, "form": form,
                          "zone_updates_per_s": job_value(g.ncells, 1, r["ms_per_step"]),
                          "stage_ms": r["stage_ms_mean"], "ghost_fill_ms": r["fill_ms"],
                          "fp64_flops_per_zone_stage": r["flops"]["fp64_flops"],
-                         "fp64_frac": ach / FP64_PEAK_TFLOPS, "launch_shape": r["launch_shape"]})
+                         "fp64_frac": ach / alu["fp64_tflops"], "launch_shape": r["launch_shape"],
+                         "ghost_fill": fill_roofline(g, form, r["fill_ms"], pk.get("hbm_gbs")),
+                         "clocks": ck.summary()})
             print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
         del P
     print(json.dumps({"sweep": "block shape", "workload": "512x256x256 torus", "rows": rows}), flush=True)
@@ -619,6 +650,10 @@ def main():
         return
 
     pk, pk_kind = peaks()
+    alu = alu_peaks(torch, pk, local)
+    with Clocks(local) as ck_probe:
+        probe = probe_peaks(gb, torch, stream)
+    probe["clocks"] = ck_probe.summary()
 
     def roofline(form):
         r = results[form]
@@ -629,15 +664,16 @@ def main():
         bytes_alg = (288 if form == "fp64" else 252) * cells
         traffic = recorded_traffic(args.workload, form, shape_key(r["launch_shape"]))
         fill = fill_roofline(g, form, r["fill_ms"], pk.get("hbm_gbs"))
-        return {"bound": "alu", "achieved": ach64, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": ach64 / FP64_PEAK_TFLOPS, "traffic": traffic, "kernel": "stage_kernel",
+        return {"bound": "alu", "achieved": ach64, "peak": alu["fp64_tflops"], "unit": "TFLOP/s",
+                "frac": ach64 / alu["fp64_tflops"], "traffic": traffic, "kernel": "stage_kernel",
                 "traffic_source": os.path.relpath(TRAFFIC_FILE, ROOT) if traffic else None,
                 "traffic_over_algorithmic": traffic / bytes_alg if traffic else None,
                 "stage_ms": r["stage_ms_mean"], "ghost_fill_ms": r["fill_ms"],
-                "peak_kind": "derived FP64: 152 SMs x 2070 MHz x 4 flops/clk/SM",
+                "peak_kind": alu["kind"],
+                "peak_probe": probe["fp64_tflops"], "frac_of_probe": ach64 / probe["fp64_tflops"],
                 "fp64_flops_per_zone_stage": fl["fp64_flops"],
                 "fp32_flops_per_zone_stage": fl["fp32_flops"],
-                "fp32_frac_of_peak": fl["fp32_flops"] * cells / stage_s / 1e12 / FP32_PEAK_TFLOPS,
+                "fp32_frac_of_peak": fl["fp32_flops"] * cells / stage_s / 1e12 / alu["fp32_tflops"],
                 "hbm_bytes_per_zone_stage": bytes_alg / cells,
                 "hbm_frac_of_measured": bytes_alg / stage_s / 1e9 / pk["hbm_gbs"],
                 "ghost_fill": fill}
@@ -663,7 +699,7 @@ def main():
         "e2e": e2e,
         "gpu_launches": results[head]["launches_per_step"] * args.steps,
         "clocks": results[head]["clocks"],
-        "peaks": {"kind": pk_kind, "hbm_gbs": pk.get("hbm_gbs")},
+        "peaks": {"kind": pk_kind, "hbm_gbs": pk.get("hbm_gbs"), "alu": alu, "probe": probe},
     }
     print(json.dumps(line), flush=True)
     if dist:

@@ -86,11 +86,18 @@ typedef struct {
 } bhac_block_desc;
 
 /* Device bytes the arena must hold for this grid (tables, state, ghost maps).
- * Returns BHAC_ERR_ARG for an invalid description. */
+ * Returns BHAC_ERR_ARG for an invalid description.
+ * Source: Sec. 2 (the block-based grid whose blocks carry ghost cells); sizing
+ * the caller-owned arena has no counterpart in the paper, whose Fortran code
+ * allocates its own blocks. */
 bhac_status bhac_query_sizes(const bhac_grid_desc* desc, const bhac_block_desc* blocks, int nblocks,
                              size_t* device_bytes_out);
 
-/* Creates a context on the current CUDA device.  `device_arena` must be a device
+/* Source: Sec. 2 (leaf blocks of a block-based tree grid, each with its ghost
+ * cells); the ghost maps built here are the device form of the ghost-cell
+ * exchange of Sec. 4.3 (fill_gc_srl) and Sec. 5.1.
+ *
+ * Creates a context on the current CUDA device.  `device_arena` must be a device
  * pointer to >= bhac_query_sizes() bytes, 256-byte aligned; it stays owned by
  * the caller and must outlive the context.  `cuda_stream` is a cudaStream_t (or
  * NULL for the legacy default stream).  Builds the ghost-cell maps on the host
@@ -98,7 +105,11 @@ bhac_status bhac_query_sizes(const bhac_grid_desc* desc, const bhac_block_desc* 
 bhac_status bhac_init_grid(bhac_ctx** out, const bhac_grid_desc* desc, const bhac_block_desc* blocks,
                            int nblocks, void* device_arena, size_t arena_bytes, void* cuda_stream);
 
-/* Evaluates the metric tables on the device in FP64: lapse, shift, spatial
+/* Source: Sec. 2 (the scheme works in general covariant coordinates); the paper names no
+ * metric, so the Kerr-Schild / modified Kerr-Schild forms (x1 = ln r,
+ * theta = pi x2, no polar squeeze) are the hot-path reading of the torus set-ups.
+ *
+ * Evaluates the metric tables on the device in FP64: lapse, shift, spatial
  * metric, its inverse, sqrt(gamma), their first derivatives along x1 and x2
  * (forward-mode dual numbers) and the floor profiles, at cell centres and at
  * x1- and x2-faces.  The metric must be phi-independent.  `kind` and `spin_a`,
@@ -106,23 +117,43 @@ bhac_status bhac_init_grid(bhac_ctx** out, const bhac_grid_desc* desc, const bha
  * and may be NULL. */
 bhac_status bhac_set_metric(bhac_ctx* ctx, int kind, double spin_a, double mass, const double* mks_params);
 
-/* Loads interior primitives ([block][var][k][j][i], FP64; host pointer if
+/* Source: Sec. 2 (the scheme evolves integrated conserved variables and
+ * recovers primitives from them); this is the inverse map, primitives to
+ * conserved, used to load a state.  The paper has no entry point of its own.
+ *
+ * Loads interior primitives ([block][var][k][j][i], FP64; host pointer if
  * on_device == 0, device pointer otherwise) and sets the conserved state from
  * them.  Floors are not applied. */
 bhac_status bhac_set_prims(bhac_ctx* ctx, const double* prims, int on_device);
 
-/* Fills every ghost cell from the owning block (same level) or the boundary
+/* Source: Sec. 4.3 (fill_gc_srl, the same-level ghost-cell fill the roofline
+ * analysis singles out) and Sec. 5.1 (the ghost-cell exchange whose serial
+ * region was the main bottleneck); cross-level values by restriction and
+ * prolongation follow the block-based AMR of Sec. 2.  The physical boundary
+ * rules (axis, no-inflow) are the hot-path reading: the paper is silent.
+ *
+ * Fills every ghost cell from the owning block (same level) or the boundary
  * rule: periodic wrap; outflow copy; no-inflow (outflow, then u^d clamped so
  * that nothing enters); polar axis (mirror in theta, flip u^theta and B^theta,
  * and take the cell at phi + pi in 3-D). */
 bhac_status bhac_fill_ghosts(bhac_ctx* ctx);
 
-/* Computes dt = cfl / max over interior cells of sum_d c_d/dx_d (c_d: largest of
+/* Source: Sec. 2 (explicit high-resolution shock-capturing scheme, hence a
+ * Courant limit); the paper gives no CFL formula, so the "maxsum" form below is
+ * the hot-path reading (one rate per cell summed over directions).
+ *
+ * Computes dt = cfl / max over interior cells of sum_d c_d/dx_d (c_d: largest of
  * the fast-magnetosonic speeds and the GLM speeds along d) into device memory;
  * also returns it through dt_host when non-NULL (synchronises the stream). */
 bhac_status bhac_cfl_dt(bhac_ctx* ctx, double* dt_host_or_null);
 
-/* One SSP-RK2 step (two stages) of size dt: ghost fill, stage 1, ghost fill,
+/* Source: Sec. 2 (second-order time stepping of a finite-volume scheme with PPM
+ * reconstruction and Newton-Raphson inversion with backup strategies) and
+ * Sec. 4.2 (one cell-update = one cell through one sub-step of the two-step
+ * integrator).  The stepper (SSP-RK2), the Riemann solvers, the GLM cleaning and
+ * the inversion's formulation are the hot-path readings of that paragraph.
+ *
+ * One SSP-RK2 step (two stages) of size dt: ghost fill, stage 1, ghost fill,
  * stage 2; each stage reconstructs, computes HLL/TVDLF face fluxes, adds the
  * geometric and GLM sources, updates the conserved state and inverts it to
  * primitives.  dt <= 0 uses the device dt of the last CFL evaluation (the step
@@ -130,7 +161,7 @@ bhac_status bhac_cfl_dt(bhac_ctx* ctx, double* dt_host_or_null);
  * a CUDA graph with no host round trip. */
 bhac_status bhac_step(bhac_ctx* ctx, double dt);
 
-/* One RK stage (1 or 2) with its preceding ghost fill. */
+/* One RK stage (1 or 2) with its preceding ghost fill (Sec. 4.2: a sub-step). */
 bhac_status bhac_stage(bhac_ctx* ctx, int stage, double dt);
 
 /* Replaces the conserved state that bhac_set_prims derived from the
@@ -142,7 +173,9 @@ bhac_status bhac_stage(bhac_ctx* ctx, int stage, double dt);
 bhac_status bhac_set_cons(bhac_ctx* ctx, const double* cons, int on_device);
 
 /* Copies interior primitives (or densitized conserved variables) out, same
- * layout as bhac_set_prims; host copies synchronise the stream. */
+ * layout as bhac_set_prims; host copies synchronise the stream.
+ * Source: Sec. 2 (primitive and integrated conserved variables of the scheme);
+ * reading state back has no counterpart in the paper. */
 bhac_status bhac_get_prims(bhac_ctx* ctx, double* out, int on_device);
 bhac_status bhac_get_cons(bhac_ctx* ctx, double* out, int on_device);
 
@@ -192,7 +225,10 @@ bhac_status bhac_get_c2p_status(bhac_ctx* ctx, unsigned char* out, int on_device
  * stream. */
 bhac_status bhac_get_prims_ghosted(bhac_ctx* ctx, double* out, int on_device);
 
-/* Inversion outcome counts accumulated since init, per cell and stage:
+/* Source: Sec. 2 (Newton-Raphson inversion backed by fall-back solvers); the
+ * outcome classes are the hot-path reading of those fall-backs.
+ *
+ * Inversion outcome counts accumulated since init, per cell and stage:
  * [0] Newton converged, [1] backup solver used, [2] floors applied,
  * [3] failed (previous primitives kept).  Synchronises the stream. */
 bhac_status bhac_get_diagnostics(bhac_ctx* ctx, long long counts[4]);
@@ -243,25 +279,41 @@ bhac_status bhac_count_flops(bhac_ctx* ctx, double dt, int nsamples, unsigned se
 
 /* Self-check utility (the paper has no counterpart).  The stage kernels
  * replace FP64 compares and FP32<->FP64 conversions by integer bit operations
- * (GB300 runs those FP64-unit instructions at the cost of an FP64 FMA).  This
- * runs each replacement beside the hardware instruction on `n` operand pairs
- * generated on the device from `seed` (random bit patterns; doubles in and
- * around the float range; round-to-nearest ties; neighbours one ulp apart;
- * zeros, subnormals, infinities, NaNs) and writes the number of disagreements
- * per operation to out[8]: [0] a < b, [1] x > 0, [2] x <= 0, [3] |a| < |b|,
- * [4] a <= b and x < 0 (all IEEE, NaN operands included),
- * [5] isfinite, [6] double -> float (bitwise; NaN as NaN), [7] float -> double.
+ * (GB300 runs those FP64-unit instructions at the cost of an FP64 FMA), and
+ * FP64 reciprocals and square roots by an FP32 hardware seed refined with
+ * fused multiply-adds.  This runs each replacement beside the hardware or IEEE
+ * operation on `n` operand pairs generated on the device from `seed` (random
+ * bit patterns; doubles in and around the float range; round-to-nearest ties;
+ * neighbours one ulp apart; zeros, subnormals, infinities, NaNs) and writes the
+ * number of disagreements per operation to out[11]: [0] a < b, [1] x > 0,
+ * [2] x <= 0, [3] |a| < |b|, [4] a <= b and x < 0 (all IEEE, NaN operands
+ * included), [5] isfinite, [6] double -> float (bitwise; NaN as NaN),
+ * [7] float -> double; and the operands whose result lies farther than the
+ * bound from the reference: [8] 1/x more than 1 ulp from the IEEE reciprocal,
+ * [9] x^(-1/2) more than 2 ulp from CUDA's rsqrt, [10] sqrt x more than 2 ulp
+ * from the IEEE square root (special values must match exactly).
  * n in [1, 1<<26].  Synchronous (default stream); the counters are a
  * file-scope device array, so concurrent calls race on them. */
-bhac_status bhac_check_bit_ops(long long n, unsigned seed, long long out[8]);
+bhac_status bhac_check_bit_ops(long long n, unsigned seed, long long out[11]);
+
+/* Measurement utility for the roofline (the paper has no counterpart): the
+ * arithmetic throughput of the current device, each figure from one kernel that
+ * keeps 8 CTAs of 256 threads per SM busy with 8 independent chains per
+ * thread, timed with CUDA events on `cuda_stream` after one warm-up launch.
+ * out[0] FP64 flops/s of fused multiply-adds (2 flops each), out[1] the same for
+ * FP32, out[2] FP64 IEEE divisions/s, out[3] FP64 IEEE square roots/s,
+ * out[4] FP64 reciprocal square roots/s, out[5] SM count, out[6] CTAs,
+ * out[7] threads per CTA.  `iters` (1 .. 2^20) sets the FP64 chain length
+ * (FP32: 16x; the special functions: 1/8).  Synchronises the stream; writes
+ * only a file-scope device word, never in practice. */
+bhac_status bhac_measure_peaks(int iters, void* cuda_stream, double out[8]);
 
 /* Allocation-free CFL time step, for callers that cannot allocate device memory
  * (no counterpart in the paper: it exists only because of how some callers run).
- * Such callers include code that runs while another component captures the
- * stream into a CUDA graph (allocation is not allowed there), hosts whose
- * device memory is entirely owned by another allocator and that therefore hand
- * this library no arena, and per-step diagnostics that must never enter an
- * allocator because cudaMalloc can synchronise the device.
+ * Such callers include hosts whose device memory is entirely owned by another
+ * allocator and that therefore hand this library no arena, and per-step
+ * diagnostics that must never enter an allocator because cudaMalloc can
+ * synchronise the device and stall the streams that the step keeps busy.
  *
  * Computes dt = cfl / max over interior cells of sum_d c_d / dx_d (the same
  * rate as bhac_cfl_dt) for the FP64 interior primitives `prims` (device pointer,
@@ -277,8 +329,11 @@ bhac_status bhac_check_bit_ops(long long n, unsigned seed, long long out[8]);
  * before any stream capture.  Every call reuses the same arrays and leaves its
  * contents there; each call writes every partial it reads, so nothing has to be
  * cleared between calls.  Calls whose kernels overlap on the GPU (other streams,
- * other threads) race on the arrays: serialise them.  Asynchronous on `stream`;
- * the host block table is copied before the call returns. */
+ * other threads) race on the arrays: serialise them.  Asynchronous on `stream`.
+ * The block table `blocks` is copied to the device on `stream`: from pageable
+ * host memory that copy is complete when the call returns, but from page-locked
+ * memory it is asynchronous, so such a table must stay unchanged until the
+ * stream has reached the call (e.g. until the stream is synchronised). */
 #define BHAC_STATIC_MAX_BLOCKS 16384
 bhac_status bhac_cfl_dt_static(const bhac_grid_desc* desc, const bhac_block_desc* blocks, int nblocks,
                                const double* prims, double* dt, void* cuda_stream);

@@ -23,7 +23,7 @@ __all__ = [
     "bhac_set_launch", "bhac_count_flops", "bhac_graph_capture", "bhac_graph_launch", "bhac_cfl_dt_static", "bhac_destroy",
     "bhac_status_string", "bhac_check_bit_ops", "bhac_launches_per_step", "bhac_get_prims_ghosted",
     "bhac_get_c2p_status", "bhac_set_cons", "bhac_set_prims_host_async", "bhac_get_prims_host_async",
-    "bhac_host_fence",
+    "bhac_host_fence", "bhac_measure_peaks",
 ]
 
 NV = 9
@@ -96,6 +96,7 @@ def lib():
             "bhac_set_prims_host_async": ([vp, vp], i),
             "bhac_get_prims_host_async": ([vp, vp], i),
             "bhac_host_fence": ([vp], i),
+            "bhac_measure_peaks": ([i, vp, C.POINTER(d)], i),
             "bhac_destroy": ([vp], None),
             "bhac_status_string": ([i], C.c_char_p),
         }
@@ -210,10 +211,19 @@ def bhac_count_flops(ctx, dt: float, nsamples: int = 2000, seed: int = 1):
 
 def bhac_check_bit_ops(n: int, seed: int = 1):
     """Disagreement counts of the integer-pipe compares and conversions with
-    the hardware instructions (see the header for the eight operations)."""
-    out = (C.c_longlong * 8)()
+    the hardware instructions, and of the FP64 reciprocal and square roots
+    beyond their ulp bounds (see the header for the eleven checks)."""
+    out = (C.c_longlong * 11)()
     _check("bhac_check_bit_ops", lib().bhac_check_bit_ops(n, seed, out))
     return list(out)
+
+
+def bhac_measure_peaks(iters: int = 1 << 14, stream_ptr: int = 0):
+    """Arithmetic throughput of the current device (see the header)."""
+    out = (C.c_double * 8)()
+    _check("bhac_measure_peaks", lib().bhac_measure_peaks(iters, C.c_void_p(stream_ptr), out))
+    return {"fp64_flops": out[0], "fp32_flops": out[1], "fp64_div": out[2], "fp64_sqrt": out[3],
+            "fp64_rsqrt": out[4], "sms": int(out[5]), "ctas": int(out[6]), "threads": int(out[7])}
 
 
 def bhac_launches_per_step(ctx) -> int:

@@ -191,6 +191,8 @@ StageArgs base_args(const bhac_ctx* c) {
   a.c2p_tol = d.c2p_tol;
   a.c2p_maxit = d.c2p_maxit;
   a.wmax = d.w_max;
+  a.c2p_gf = (d.gamma_ad - 1.0) / d.gamma_ad;
+  a.c2p_v2max = 1.0 - 1.0 / (d.w_max * d.w_max);
   a.rho_fl_c = d.rho_floor;
   a.p_fl_c = d.p_floor;
   a.tab_c = c->tab_c;

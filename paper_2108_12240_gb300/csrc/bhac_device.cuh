@@ -56,6 +56,7 @@ struct StageArgs {
   float gam_f, gam_fac_f, ch_f, kappa_f, ch2_f;  // FP32 copies for the mixed form's flux arithmetic
   double c2p_tol;
   int c2p_maxit;
+  double c2p_gf, c2p_v2max;  // (Gamma - 1)/Gamma and 1 - 1/W_max^2
   double wmax, rho_fl_c, p_fl_c;  // constant floors (flat coordinates)
   // state
   const double* P_in;    // FP64 primitives, ghosted
@@ -171,11 +172,8 @@ BHAC_HD Met<T> load_centre_metric(const R* __restrict__ rec) {
 
 // Scalar helpers.  The double/float overloads are the device arithmetic; the
 // flop counter provides overloads for its counting type.
-__device__ __forceinline__ double rsqrt_t(double x) { return rsqrt(x); }
 __device__ __forceinline__ float rsqrt_t(float x) { return rsqrtf(x); }
-__device__ __forceinline__ double sqrt_t(double x) { return sqrt(x); }
 __device__ __forceinline__ float sqrt_t(float x) { return sqrtf(x); }
-__device__ __forceinline__ double rcp_t(double x) { return 1.0 / x; }
 __device__ __forceinline__ float rcp_t(float x) { return __frcp_rn(x); }
 __device__ __forceinline__ double abs_t(double x) { return fabs(x); }
 __device__ __forceinline__ float abs_t(float x) { return fabsf(x); }
@@ -215,6 +213,72 @@ __device__ __forceinline__ float narrow_f64(double x) {
   }
   if (((hi & 0x7FFFFFFFu) | lo) == 0u) return __uint_as_float(hi & 0x80000000u);
   return __double2float_rn(x);
+}
+// FP64 reciprocal, reciprocal square root and square root on the FP64 unit's
+// budget.  GB300 runs an IEEE FP64 division or square root at about a tenth of
+// its fused-multiply-add rate, and the inversion and the wave speeds take
+// several per cell.  Here the FP32 hardware approximation (PTX rcp.approx /
+// rsqrt.approx, on the special-function unit) of the operand rounded down to
+// 20 significand bits seeds one step of a third-order (Householder) iteration
+// in FP64 fused multiply-adds:
+//   1/x:       e = 1 - x y,    y <- y (1 + e + e^2)          (error e0^3)
+//   x^(-1/2):  e = 1 - x y^2,  y <- y (1 + e/2 + 3 e^2/8)    (error 5/2 e0^3)
+// With |e0| < 2^-19 the iteration error is below 2^-57, so the result is the
+// exact value up to the rounding of the last operations: within one unit in the
+// last place for 1/x and x^(-1/2), 1.5 for sqrt x = x x^(-1/2)
+// (bhac_check_bit_ops measures each against the IEEE operations on 2^24
+// operands).  Operands whose binary exponent lies outside [-120, 120) (where
+// the FP32 seed would leave the normal range), zeros, negatives (for the
+// square roots), infinities and NaNs take the IEEE operation.
+__device__ __forceinline__ float rcp_approx_f32(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float rsqrt_approx_f32(float x) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+// the FP32 value of a double whose biased exponent E is in [903, 1143),
+// significand truncated to its top 20 bits (hi: the double's high word)
+__device__ __forceinline__ float seed_of(unsigned hi, unsigned E) {
+  return __uint_as_float((hi & 0x80000000u) | ((E - 896u) << 23) | ((hi & 0xFFFFFu) << 3));
+}
+// exact widening of a normal float (integer pipes)
+__device__ __forceinline__ double widen_normal(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned hi = (u & 0x80000000u) | ((((u >> 23) & 0xFFu) + 896u) << 20) | ((u >> 3) & 0xFFFFFu);
+  return __hiloint2double((int)hi, (int)(u << 29));
+}
+__device__ __forceinline__ bool seed_range(unsigned hi, unsigned& E) {
+  E = (hi >> 20) & 0x7FFu;
+  return E - 903u < 240u;
+}
+__device__ __forceinline__ double rcp_t(double x) {
+  const unsigned hi = (unsigned)__double2hiint(x);
+  unsigned E;
+  if (!seed_range(hi, E)) return 1.0 / x;
+  const double y = widen_normal(rcp_approx_f32(seed_of(hi, E)));
+  const double e = fma(-x, y, 1.0);
+  return fma(y, fma(e, e, e), y);
+}
+__device__ __forceinline__ double rsqrt_pos(double x, unsigned hi, unsigned E) {
+  const double y = widen_normal(rsqrt_approx_f32(seed_of(hi, E)));
+  const double e = fma(-(x * y), y, 1.0);
+  return fma(y * e, fma(e, 0.375, 0.5), y);
+}
+__device__ __forceinline__ double rsqrt_t(double x) {
+  const unsigned hi = (unsigned)__double2hiint(x);
+  unsigned E;
+  if ((hi >> 31) || !seed_range(hi, E)) return rsqrt(x);
+  return rsqrt_pos(x, hi, E);
+}
+__device__ __forceinline__ double sqrt_t(double x) {
+  const unsigned hi = (unsigned)__double2hiint(x);
+  unsigned E;
+  if ((hi >> 31) || !seed_range(hi, E)) return sqrt(x);
+  return x * rsqrt_pos(x, hi, E);
 }
 __device__ __forceinline__ double to_double(double x) { return x; }
 __device__ __forceinline__ double to_double(float x) { return widen_f32(x); }

@@ -227,8 +227,8 @@ void cell(const StageArgs& a, const HostState& h, int sb, int i, int j, int k, d
     Uu[v] = U[v] * N64(isg);
     Pg[v] = N64(Pd[(size_t)v * a.ncell]);
   }
-  const int st = con2prim_t<N64>(md, Uu, Pg, N64(rho_fl), N64(p_fl), a.gam, a.gam_fac, a.wmax, a.c2p_tol,
-                                 a.c2p_maxit, Pn);
+  const int st = con2prim_t<N64>(md, Uu, Pg, N64(rho_fl), N64(p_fl), a.c2p_gf, a.gam_fac, a.wmax, a.c2p_v2max,
+                                 a.c2p_tol, a.c2p_maxit, Pn);
   if (st >= 2) {
     Derived<N64> s;
     derive(md, Pn, N64(a.gam_fac), s);

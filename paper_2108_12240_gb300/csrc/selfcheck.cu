@@ -1,6 +1,6 @@
 // Test utilities: bhac_check_bit_ops (the integer-pipe compares and
 // conversions of bhac_device.cuh against the hardware instructions they
-// replace) and bhac_get_prims_ghosted (the ghosted primitive state, to check
+// replace, and its FP64 reciprocal and square roots against the IEEE ones) and bhac_get_prims_ghosted (the ghosted primitive state, to check
 // ghost fills cell by cell).
 #include <math.h>
 
@@ -9,6 +9,8 @@
 
 namespace bhac {
 namespace {
+
+constexpr int kChecks = 11;
 
 // splitmix64 (Steele, Lea and Flood 2014): counter-based 64-bit generator
 __device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
@@ -54,8 +56,18 @@ __device__ double operand(unsigned long long seed, long long i, int which) {
   return __longlong_as_double((long long)bits);
 }
 
+// Distance in units of the last place between two doubles of the same sign;
+// any sign disagreement or NaN counts as far apart (unless both are NaN).
+__device__ long long ulp_dist(double x, double y) {
+  if (isnan(x) && isnan(y)) return 0;
+  if (isnan(x) || isnan(y)) return 1LL << 62;
+  const long long a = __double_as_longlong(x), b = __double_as_longlong(y);
+  if ((a ^ b) < 0) return (x == y) ? 0 : (1LL << 62);  // +0 and -0 are equal
+  return a > b ? a - b : b - a;
+}
+
 __global__ void check_kernel(long long n, unsigned long long seed, unsigned long long* bad) {
-  unsigned long long loc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  unsigned long long loc[kChecks] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     const double a = operand(seed, i, 0);
     double b = operand(seed, i, 1);
@@ -74,22 +86,26 @@ __global__ void check_kernel(long long n, unsigned long long seed, unsigned long
     const float g = __uint_as_float((unsigned)(hb >> 32));
     const double w1 = widen_f32(g), w0 = (double)g;
     if (!(isnan(w1) && isnan(w0)) && __double_as_longlong(w1) != __double_as_longlong(w0)) ++loc[7];
+    // the FP64 unit's reciprocal and square roots against the IEEE operations
+    if (ulp_dist(rcp_t(a), __drcp_rn(a)) > 1) ++loc[8];
+    if (ulp_dist(rsqrt_t(a), rsqrt(a)) > 2) ++loc[9];
+    if (ulp_dist(sqrt_t(a), __dsqrt_rn(a)) > 2) ++loc[10];
   }
-  for (int k = 0; k < 8; ++k)
+  for (int k = 0; k < kChecks; ++k)
     if (loc[k]) atomicAdd(bad + k, loc[k]);
 }
 
 // disagreement counters (file scope: the library allocates no device memory)
-static __device__ unsigned long long g_bad[8];
+static __device__ unsigned long long g_bad[kChecks];
 
 }  // namespace
 }  // namespace bhac
 
 using namespace bhac;
 
-extern "C" bhac_status bhac_check_bit_ops(long long n, unsigned seed, long long out[8]) {
+extern "C" bhac_status bhac_check_bit_ops(long long n, unsigned seed, long long out[11]) {
   if (!out || n < 1 || n > (1LL << 26)) return BHAC_ERR_ARG;
-  unsigned long long h[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  unsigned long long h[kChecks] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
   unsigned long long* d = nullptr;
   cudaError_t e = cudaGetSymbolAddress((void**)&d, g_bad);
   if (e == cudaSuccess) e = cudaMemcpy(d, h, sizeof(h), cudaMemcpyHostToDevice);
@@ -99,7 +115,7 @@ extern "C" bhac_status bhac_check_bit_ops(long long n, unsigned seed, long long 
   }
   if (e == cudaSuccess) e = cudaMemcpy(h, d, sizeof(h), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return BHAC_ERR_CUDA;
-  for (int k = 0; k < 8; ++k) out[k] = (long long)h[k];
+  for (int k = 0; k < kChecks; ++k) out[k] = (long long)h[k];
   return BHAC_OK;
 }
 

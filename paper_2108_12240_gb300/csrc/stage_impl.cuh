@@ -93,12 +93,13 @@ BHAC_HD T c2p_f1d(const C2PQ<T>& q, T gf, T v2max, T Z) {
 }
 
 // U undensitized; Pg the previous primitives; writes P; returns the status.
+// gf_d = (Gamma - 1)/Gamma and v2max_d = 1 - 1/W_max^2 come precomputed.
 template <typename T>
-BHAC_HD int con2prim_t(const Met<T>& m, const T* U, const T* Pg, T rho_fl, T p_fl, double gam_d,
-                       double gam_fac, double wmax_d, double tol, int maxit, T* P) {
-  const T gam = T(gam_d), gf = (gam - T(1.0)) / gam;
+BHAC_HD int con2prim_t(const Met<T>& m, const T* U, const T* Pg, T rho_fl, T p_fl, double gf_d,
+                       double gam_fac, double wmax_d, double v2max_d, double tol, int maxit, T* P) {
+  const T gf = T(gf_d);
   const T wmax = T(wmax_d);
-  const T v2max = T(1.0) - T(1.0) / (wmax * wmax);
+  const T v2max = T(v2max_d);
   C2PQ<T> q;
   q.D = U[CD];
   q.E = U[CTAU] + U[CD];
@@ -125,14 +126,14 @@ BHAC_HD int con2prim_t(const Met<T>& m, const T* U, const T* Pg, T rho_fl, T p_f
     const T Z0g = (Pg[RHO] + T(gam_fac) * Pg[PRS]) * (T(1.0) + usq);
     const T Z0 = (gt0_t(Z0g) && finite_t(Z0g)) ? Z0g : q.E;
     Z = Z0;
-    v2 = usq / (T(1.0) + usq);
+    v2 = usq * rcp_t(T(1.0) + usq);
     const T BS2 = q.BS * q.BS;
     for (int it = 0; it < maxit; ++it) {
       const T omv = T(1.0) - v2;
       const T isq = rsqrt_t(omv);
       const T sq = omv * isq;
       const T pr = gf * (Z * omv - q.D * sq);
-      const T iZ = T(1.0) / Z;
+      const T iZ = rcp_t(Z);
       const T iZ2 = iZ * iZ;
       const T ZB = Z + q.Bsq;
       const T f1 = ZB * ZB * v2 - BS2 * (T(2.0) * Z + q.Bsq) * iZ2 - q.S2;
@@ -141,7 +142,7 @@ BHAC_HD int con2prim_t(const Met<T>& m, const T* U, const T* Pg, T rho_fl, T p_f
       const T j12 = ZB * ZB;
       const T j21 = T(1.0) - gf * omv + BS2 * iZ2 * iZ;
       const T j22 = -gf * (-Z + T(0.5) * q.D * isq) + T(0.5) * q.Bsq;
-      const T idet = T(1.0) / (j11 * j22 - j12 * j21);
+      const T idet = rcp_t(j11 * j22 - j12 * j21);
       const T dZ = (-f1 * j22 + f2 * j12) * idet;
       const T dv2 = (-f2 * j11 + f1 * j21) * idet;
       T Zn = Z + dZ, v2n = v2 + dv2;
@@ -249,7 +250,8 @@ BHAC_HD int con2prim_t(const Met<T>& m, const T* U, const T* Pg, T rho_fl, T p_f
 
 static __device__ __forceinline__ int con2prim(const Met<double>& m, const double* U, const double* Pg, double rho_fl,
                                             double p_fl, const StageArgs& a, double* P) {
-  return con2prim_t<double>(m, U, Pg, rho_fl, p_fl, a.gam, a.gam_fac, a.wmax, a.c2p_tol, a.c2p_maxit, P);
+  return con2prim_t<double>(m, U, Pg, rho_fl, p_fl, a.c2p_gf, a.gam_fac, a.wmax, a.c2p_v2max, a.c2p_tol, a.c2p_maxit,
+                            P);
 }
 
 // CFL rate of one cell: sum over active d of c_d / dx_d, where c_d is the

@@ -1,13 +1,13 @@
 // Allocation-free CFL time step (see bhac_cfl_dt_static in the public header).
 //
-// Some callers cannot call cudaMalloc at all: code that runs while another
-// component captures the stream into a CUDA graph, a host whose device memory
-// is entirely owned by another allocator and hands this library no arena, or a
+// Some callers cannot call cudaMalloc at all: a host whose device memory is
+// entirely owned by another allocator and hands this library no arena, or a
 // per-step diagnostic that must never enter an allocator (cudaMalloc can
-// synchronise the device).  For them this file keeps the reduction's scratch in
-// file-scope device arrays of fixed size instead of an arena: the leaf-block
-// table and one partial maximum per block.  Every GPU that loads the library
-// holds these arrays (BHAC_STATIC_MAX_BLOCKS x 24 bytes) until the process exits.
+// synchronise the device and stall the streams the time step keeps busy).  For
+// them this file keeps the reduction's scratch in file-scope device arrays of
+// fixed size instead of an arena: the leaf-block table and one partial maximum
+// per block.  Every GPU that loads the library holds these arrays
+// (BHAC_STATIC_MAX_BLOCKS x 24 bytes) until the process exits.
 #include <math.h>
 #include <mutex>
 

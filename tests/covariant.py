@@ -96,3 +96,46 @@ def sources(P, metric_fn, x, gamma_ad, h=1e-5):
             Gam0[m, n] = 0.5 * sum(Gi[0, s] * (dG[m][s, n] + dG[n][s, m] - dG[s][m, n]) for s in range(4))
     Stau = alpha * (T[:, 0] @ dal - alpha * np.sum(T * Gam0))
     return SS, Stau
+
+
+def glm_source(P, metric_fn, x, ch, kappa, h=1e-5):
+    """Source of the cleaning scalar psi for the conservative form
+        d_t(sqrt(gamma) psi) + d_i[sqrt(gamma) (alpha ch^2 B^i - beta^i psi)] = sqrt(gamma) S
+    implied by the covariant damped cleaning equation
+        (d_t - beta^i d_i) psi = -alpha ch^2 D_i B^i - alpha kappa psi
+    (the time derivative along the normal observer; D_i B^i the covariant
+    divergence) in a stationary metric:
+        S_cov = -alpha kappa psi + ch^2 B^i d_i alpha - psi D_i beta^i,
+        D_i beta^i = d_i(sqrt(gamma) beta^i) / sqrt(gamma).
+    Returns (S_cov, psi beta^i d_i ln sqrt(gamma)).  alpha, beta^i and
+    sqrt(gamma) are read off the inverse 4-metric of metric_fn(y) ->
+    (alpha, beta, g): alpha = (-g^00)^(-1/2), beta^i = alpha^2 g^0i,
+    sqrt(gamma) = sqrt(-det g_4) / alpha; derivatives by fourth-order central
+    differences."""
+    def lapse_shift_vol(y):
+        a_, b_, g_ = metric_fn(y)
+        G = four_metric(a_, b_, g_)
+        Gi = np.linalg.inv(G)
+        al = 1.0 / np.sqrt(-Gi[0, 0])
+        be = al * al * Gi[0, 1:]
+        sg = np.sqrt(-np.linalg.det(G)) / al
+        return al, be, sg
+
+    alpha, beta, sg = lapse_shift_vol(np.asarray(x, float))
+    dal = np.zeros(3)
+    dln = np.zeros(3)
+    div = 0.0
+    for k in range(3):
+        vals = []
+        for s in (h, -h, 2 * h, -2 * h):
+            y = np.array(x, float)
+            y[k] += s
+            vals.append(lapse_shift_vol(y))
+        (a1, b1, s1), (am1, bm1, sm1), (a2, b2, s2), (am2, bm2, sm2) = vals
+        dal[k] = (8 * (a1 - am1) - (a2 - am2)) / (12 * h)
+        dln[k] = (8 * (np.log(s1) - np.log(sm1)) - (np.log(s2) - np.log(sm2))) / (12 * h)
+        div += (8 * (s1 * b1[k] - sm1 * bm1[k]) - (s2 * b2[k] - sm2 * bm2[k])) / (12 * h) / sg
+    B = np.asarray(P[5:8], float)
+    psi = P[8]
+    s_cov = -alpha * kappa * psi + ch * ch * (B @ dal) - psi * div
+    return s_cov, psi * (beta @ dln)

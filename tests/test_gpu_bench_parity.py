@@ -1,0 +1,167 @@
+"""Parity at exactly what the benchmark measures, and on the inversion's
+backup path.
+
+The benchmark workload is the 512x256x256 torus as 2048 blocks of 32x32x16,
+run at the launch shape the autotuner picks for it (16x16 tiles, 256 threads,
+a persistent queue of two CTAs per SM slot; the two-CTA register bound in the
+mixed form, the one-CTA bound in the FP64 form).  One GPU step is compared
+with the oracle on 64 blocks in eight 2x2x2 clusters spread over the torus
+body, both polar-axis rows, the inner and outer radial boundaries and the
+phi seam; the oracle recomputes stage 1 on every block within one block of
+a sampled one (through the axis by phi + pi, periodic in phi) and stage 2
+on the sampled blocks.  Error metric and bars as in test_gpu_parity: energy-
+scaled per cell and conserved variable, 1e-12 (FP64 form) and 1e-5 (mixed
+form); the per-variable figures are printed (pytest -rP)."""
+import numpy as np
+import pytest
+
+import oracle
+import problems as pb
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+TOLMIX = 1e-5
+BENCH_SHAPE = {"fp64": (16, 16, 256, 2, 1, 0), "mixed": (16, 16, 256, 2, 2, 0)}
+# first corner (ix, iy, iz) of each 2x2x2 cluster on the 16x8x16 block grid:
+# torus body (r ~ 12 M, theta ~ pi/2) at two phi, both axis rows, the inner and
+# outer radial boundaries, the phi seam, and mid-radius blocks
+CLUSTERS = [(4, 3, 0), (3, 3, 8), (4, 0, 2), (5, 6, 12), (0, 3, 5), (14, 4, 10), (6, 2, 15), (9, 5, 6)]
+
+
+@pytest.fixture(scope="module")
+def gb():
+    import torch
+    assert torch.cuda.is_available()
+    import paper_2108_12240_gb300 as m
+    return m
+
+
+@pytest.fixture(scope="module")
+def large():
+    g = pb.torus_3d_large()
+    return g, pb.fm_torus_prims(g)
+
+
+def energy_scaled(got, ref, grid, blocks):
+    from tests.test_gpu_parity import energy_scaled as es
+    return es(got, ref, grid, blocks)
+
+
+def sampled_blocks(g):
+    blocks = np.asarray(g.blocks)
+    nr = g.nroot
+    index = {tuple(b[1:]): n for n, b in enumerate(blocks)}
+    sel = set()
+    for cx, cy, cz in CLUSTERS:
+        for dx in (0, 1):
+            for dy in (0, 1):
+                for dz in (0, 1):
+                    sel.add(index[(cx + dx, cy + dy, (cz + dz) % nr[2])])
+    hood = set()
+    for n in sel:
+        _, ix, iy, iz = blocks[n]
+        for dx in (-1, 0, 1):
+            for dy in (-1, 0, 1):
+                for dz in (-1, 0, 1):
+                    jx, jy, jz = ix + dx, iy + dy, (iz + dz) % nr[2]
+                    if not 0 <= jx < nr[0]:
+                        continue
+                    if not 0 <= jy < nr[1]:
+                        jy = iy
+                        jz = (jz + nr[2] // 2) % nr[2]
+                    hood.add(index[(jx, jy, jz)])
+                    hood.add(index[(jx, jy, (jz + nr[2] // 2) % nr[2])])
+    return sorted(sel), sorted(hood)
+
+
+@pytest.mark.parametrize("form", ["fp64", "mixed"])
+def test_bench_workload_at_bench_shape(gb, large, form):
+    import torch
+
+    g, P = large
+    s = gb.Solver(g, form)
+    s.set_launch(*BENCH_SHAPE[form])
+    s.set_prims(P)
+    dt = s.cfl_dt()
+    s.step(dt)
+    got = s.cons()
+    s.close()
+    del s
+    torch.cuda.empty_cache()
+    sel, hood = sampled_blocks(g)
+    assert len(sel) == 64
+    o = oracle.Oracle(g)
+    o.set_prims(P)
+    o.stage(1, dt, blocks=hood)
+    o.stage(2, dt, blocks=sel)
+    ref = o.cons()
+    assert np.all(np.isfinite(got[sel]))
+    err = energy_scaled(got[sel], ref[sel], g, sel)
+    print(f"512x256x256 torus, {form} form at the benchmark launch shape, 64 sampled blocks: "
+          f"energy-scaled error per conserved variable (D S1 S2 S3 tau B1 B2 B3 psi) {err.tolist()}")
+    assert np.all(err <= (TOL64 if form == "fp64" else TOLMIX)), err
+    assert np.abs(ref[sel][:, 0]).max() > 0.1  # the torus body is among the samples
+    blocks = np.asarray(g.blocks)[sel]
+    assert blocks[:, 2].min() == 0 and blocks[:, 2].max() == g.nroot[1] - 1  # both axis rows
+    assert blocks[:, 1].min() == 0 and blocks[:, 1].max() == g.nroot[0] - 1  # both radial boundaries
+
+
+def test_launch_shapes_are_bitwise_identical_mixed(gb):
+    """The mixed form: tiles, threads, register bounds, persistent queues and
+    the warp-specialised form all give the same bits (the launch shape only
+    changes which CTA takes which (block, tile) item)."""
+    g = pb.torus_3d(nroot=(4, 3, 2))
+    P = pb.fm_torus_prims(g)
+    outs = []
+    for shape in [(16, 16, 256, 0, 2), (16, 16, 256, 2, 2), (16, 16, 256, 1, 1), (16, 8, 128, 0, 1),
+                  (8, 8, 64, 0, 2), (16, 16, 160, 0, 1), (8, 16, 256, 2, 2), (16, 16, 256, 0, 1, 2),
+                  (16, 8, 256, 2, 2, 4)]:
+        s = gb.Solver(g, "mixed")
+        s.set_launch(*shape)
+        s.set_prims(P)
+        dt = s.cfl_dt()
+        s.step(dt)
+        s.step(0.0)
+        outs.append((shape, s.cons(), s.prims()))
+    for shape, c, p in outs[1:]:
+        assert np.array_equal(c, outs[0][1]), shape
+        assert np.array_equal(p, outs[0][2]), shape
+
+
+@pytest.mark.parametrize("form", ["fp64", "mixed"])
+def test_backup_inversion_matches_oracle(gb, form):
+    """Newton capped at one iteration (c2p_maxit = 1) on the torus: the cells
+    whose first Newton step is not yet below tol Z go to the backup bisection.
+    FP64 form: per-cell inversion outcome equal to the oracle's (a cell whose
+    first step lands within rounding of the stopping threshold may take either
+    of Newton's or the backup's answer, which agree to round-off: at most 1e-4
+    of the cells may differ, and only between outcomes 0 and 1), conserved
+    state within 1e-12.  Mixed form: the backup is taken in the same share of
+    cells and the conserved state is within 1e-5."""
+    g = pb.torus_3d(nroot=(4, 3, 2)).with_(c2p_maxit=1)
+    P = pb.fm_torus_prims(g)
+    s = gb.Solver(g, form)
+    s.set_prims(P)
+    o = oracle.Oracle(g)
+    o.set_prims(P)
+    dt = o.cfl_dt()
+    for stage in (1, 2):
+        o.stage(stage, dt)
+        s.stage(stage, dt)
+        got_st, ref_st = s.c2p_status(), o.c2p_status()
+        n1 = int((ref_st == 1).sum())
+        assert n1 > 0.05 * ref_st.size, (stage, np.bincount(ref_st.ravel()))  # the backup is exercised
+        assert not np.any(ref_st == 3)
+        diff = got_st != ref_st
+        if form == "fp64":
+            pairs = {(int(a), int(b)) for a, b in zip(got_st[diff], ref_st[diff])}
+            assert pairs <= {(0, 1), (1, 0)}, pairs
+            assert diff.sum() <= max(1, 1e-4 * ref_st.size), diff.sum()
+        else:
+            assert abs(int((got_st == 1).sum()) - n1) <= 0.01 * ref_st.size
+    got, ref = s.cons(), o.cons()
+    from tests.test_gpu_parity import assert_parity
+    err = assert_parity(got, ref, TOL64 if form == "fp64" else TOLMIX, f"backup path ({form})", g)
+    print(f"backup inversion ({form}), statuses {np.bincount(ref_st.ravel(), minlength=4).tolist()}: "
+          f"energy-scaled error per conserved variable {err.tolist()}")

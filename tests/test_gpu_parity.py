@@ -139,7 +139,8 @@ def test_torus_3d_full_size(gb):
     """192x96x96 torus as 432 blocks of 16^3 (polar axis across phi + pi)."""
     g = pb.torus_3d()
     s, o, _ = one_step(gb, g, pb.fm_torus_prims(g))
-    assert_parity(s.cons(), o.cons(), TOL64, "cons", g)
+    err = assert_parity(s.cons(), o.cons(), TOL64, "cons", g)
+    print("fp64 config 2 vs oracle per conserved variable (D S1 S2 S3 tau B1 B2 B3 psi):", err.tolist())
 
 
 @pytest.mark.parametrize("recon,riemann", [("minmod", "hll"), ("minmod", "tvdlf")])
@@ -251,50 +252,6 @@ def test_device_dt_path(gb):
     for _ in range(2):
         o.step(o.cfl_dt())
     assert_parity(s.cons(), o.cons(), TOL64, "device dt", g)
-
-
-def test_bench_workload_sampled(gb):
-    """512x256x256 torus as 2048 blocks of 32x32x16 (the benchmark's launch
-    configuration): one GPU step; the oracle recomputes stage 1 on a set of
-    sampled blocks and their neighbours and stage 2 on the sampled blocks."""
-    g = pb.torus_3d_large()
-    P = pb.fm_torus_prims(g)
-    s = gb.Solver(g)
-    s.set_prims(P)
-    dt = s.cfl_dt()
-    s.step(dt)
-    got = s.cons()
-    rng = np.random.default_rng(5)
-    nb = g.nb
-    blocks = np.asarray(g.blocks)
-    nr = g.nroot
-    index = {tuple(b[1:]): n for n, b in enumerate(blocks)}
-    # torus body (r ~ 12, theta ~ pi/2), polar-axis rows, inner and outer radial
-    # boundaries, and random blocks
-    picks = [(4, 3, 0), (4, 4, 5), (5, 4, 9), (3, 0, 2), (4, nr[1] - 1, 13), (0, 3, 7), (nr[0] - 1, 5, 1)]
-    sel = sorted({index[p] for p in picks} | set(rng.choice(nb, size=3, replace=False).tolist()))
-    # neighbourhood: blocks within one block in every direction (periodic in phi, axis wraps by pi)
-    hood = set()
-    for n in sel:
-        _, ix, iy, iz = blocks[n]
-        for dx in (-1, 0, 1):
-            for dy in (-1, 0, 1):
-                for dz in (-1, 0, 1):
-                    jx, jy, jz = ix + dx, iy + dy, (iz + dz) % nr[2]
-                    if not 0 <= jx < nr[0]:
-                        continue
-                    if not 0 <= jy < nr[1]:
-                        jy = iy
-                        jz = (jz + nr[2] // 2) % nr[2]
-                    hood.add(index[(jx, jy, jz)])
-                    hood.add(index[(jx, jy, (jz + nr[2] // 2) % nr[2])])
-    o = oracle.Oracle(g)
-    o.set_prims(P)
-    o.stage(1, dt, blocks=sorted(hood))
-    o.stage(2, dt, blocks=sel)
-    ref = o.cons()
-    err = assert_parity(got[sel], ref[sel], TOL64, "sampled blocks", g, sel)
-    assert np.abs(ref[sel][:, 0]).max() > 0.1  # the torus body is among the samples
 
 
 def test_cuda_graph_replay_is_bitwise_identical(gb):
@@ -424,9 +381,11 @@ def test_mixed_full_config_2_per_variable(gb):
 def test_integer_pipe_compares_and_conversions_match_hardware(gb):
     """The stage kernels' integer-bit replacements of FP64 compares and of
     FP32 <-> FP64 conversions agree with the hardware instructions on 2^24
-    generated operand pairs (ties, zeros, subnormals, overflow edge, NaN)."""
+    generated operand pairs (ties, zeros, subnormals, overflow edge, NaN), and
+    their FP64 reciprocal, reciprocal square root and square root stay within
+    1, 2 and 2 ulp of the IEEE (CUDA) operations, special values exact."""
     bad = gb.bhac_check_bit_ops(1 << 24, seed=12345)
-    assert bad == [0] * 8, bad
+    assert bad == [0] * 11, bad
 
 
 def test_launches_per_step(gb):

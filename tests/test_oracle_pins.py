@@ -350,6 +350,152 @@ def test_con2prim_floors_and_failure():
     assert st == 3 and np.all(Q[:5] == Pg[:5]) and np.all(Q[5:] == U[5:])
 
 
+def _root_Z_mp(U, g, gam, Ztrue, mp):
+    """Z = rho h W^2 solving the momentum and energy relations of the
+    conserved state U (metric g) at 50 digits: bisection of the energy
+    residual with v^2(Z) from the momentum relation, bracketed around Ztrue."""
+    gi = [[mp.mpf(x) for x in row] for row in np.linalg.inv(g)]
+    gm = [[mp.mpf(x) for x in row] for row in g]
+    D, tau = mp.mpf(U[0]), mp.mpf(U[4])
+    S = [mp.mpf(x) for x in U[1:4]]
+    B = [mp.mpf(x) for x in U[5:8]]
+    S2 = sum(gi[i][j] * S[i] * S[j] for i in range(3) for j in range(3))
+    B2 = sum(gm[i][j] * B[i] * B[j] for i in range(3) for j in range(3))
+    BS = sum(B[i] * S[i] for i in range(3))
+    G = mp.mpf(gam)
+
+    def v2(Z):
+        return (S2 + BS * BS * (2 * Z + B2) / (Z * Z)) / (Z + B2) ** 2
+
+    def f(Z):
+        w2 = v2(Z)
+        pr = (G - 1) / G * (Z * (1 - w2) - D * mp.sqrt(1 - w2))
+        return Z - pr + B2 * (1 + w2) / 2 - BS * BS / (2 * Z * Z) - (tau + D)
+
+    lo, hi = mp.mpf(Ztrue) * (1 - mp.mpf("1e-6")), mp.mpf(Ztrue) * (1 + mp.mpf("1e-6"))
+    assert f(lo) < 0 < f(hi)
+    for _ in range(300):
+        mid = (lo + hi) / 2
+        if f(mid) > 0:
+            hi = mid
+        else:
+            lo = mid
+    return (lo + hi) / 2
+
+
+@pytest.mark.parametrize("coords", ["cart", "mks"])
+def test_con2prim_backup_bisection_round_trip(coords):
+    """The backup solver on its own (the Newton stage given no iterations,
+    c2p_maxit = 0): prim -> con -> prim over rho in [1e-8, 1e2], p/rho in
+    [1e-6, 1e2], W in [1, 20], sigma in [0, 100], guess 0.1% away.  Every
+    state is recovered by the bisection (status 1) with forward error
+    <= max(1e-12, 8 cond eps) against the state that made U, and on a subset
+    its Z = rho h W^2 equals the 50-digit root of the momentum/energy system
+    to 1e-12.  A bracket grown the wrong way, a swapped bisection update or a
+    wrong recovery formula fails here."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 50
+    grid = ks_grid("mks") if coords == "mks" else pb.periodic_box(gamma_ad=4.0 / 3.0)
+    grid = grid.with_(rho_floor=1e-30, p_floor=1e-30, rho_floor_pow=0.0, p_floor_pow=0.0, c2p_maxit=0)
+    pt = oracle.Point(grid)
+    rng = np.random.default_rng(17)
+    n_well = 0
+    for trial in range(300):
+        x = [math.log(rng.uniform(1.3, 100)), rng.uniform(0.05, 0.95), 1.0] if coords == "mks" else [0.5] * 3
+        m = pt.metric(x, derivs=False)
+        rho = 10 ** rng.uniform(-8, 2)
+        p = rho * 10 ** rng.uniform(-6, 2)
+        W = 1 + 19 * rng.random() ** 2
+        d = rng.normal(size=3)
+        u = d * math.sqrt((W * W - 1) / (d @ m.g @ d))
+        e = rng.normal(size=3)
+        sigma = 100 * rng.random() ** 2
+        B = e * math.sqrt(sigma * rho * W * W / (e @ m.g @ e))
+        P = np.array([rho, p, *u, *B, 0.01])
+        U = pt.prim2con(m, P)
+        guess = P * (1 + 1e-3 * rng.normal(size=9))
+        Q, st = pt.con2prim(m, U, guess)
+        assert st == 1, (P, st)
+        cond = (U[4] + U[0] + np.abs(U[1:4]).sum() + B @ m.g @ B) / p
+        unorm = max(math.sqrt(u @ m.g @ u), 1e-300)
+        err = np.abs(Q[:5] - P[:5]) / np.array([rho, p, unorm, unorm, unorm])
+        tol = max(1e-12, 8 * cond * 2.2e-16)
+        assert err.max() < tol, (P, Q, err, cond)
+        assert np.array_equal(Q[5:], U[5:])
+        n_well += cond < 1e3
+        if trial % 30 == 0:
+            Ztrue = (rho + 4 * p) * W * W
+            Z = _root_Z_mp(U, m.g, grid.gamma_ad, Ztrue, mp)
+            Wq2 = 1 + Q[2:5] @ m.g @ Q[2:5]
+            Zq = (Q[0] + 4 * Q[1]) * Wq2
+            assert Zq == pytest.approx(float(Z), rel=max(1e-12, 8 * cond * 2.2e-16))
+    assert n_well >= 5
+
+
+def test_con2prim_backup_clamps_at_w_max():
+    """A conserved state whose momentum implies W = 30 > W_max = 10 (B = 0,
+    Newton given no iterations): the backup's residual takes
+    v^2 = 1 - 1/W_max^2, so the energy relation is linear in Z with the root
+    Z = (E - gf D / W_max) / (1 - gf / W_max^2), gf = (Gamma - 1)/Gamma.
+    The result has rho = D / W_max, p = gf (Z / W_max^2 - D / W_max), and u
+    along S_i raised, rescaled by the floors to W = W_max (status 2)."""
+    gam = 4.0 / 3.0
+    gf = (gam - 1) / gam
+    wmax = 10.0
+    grid = pb.periodic_box(gamma_ad=gam, w_max=wmax, rho_floor=1e-30, p_floor=1e-30, c2p_maxit=0)
+    pt = oracle.Point(grid)
+    m = pt.metric([0.5] * 3)
+    for ux, uy, rho, p in [(30.0, 0.0, 1.0, 0.01), (20.0, -21.0, 0.1, 1e-4), (0.0, 29.9, 2.0, 0.2)]:
+        P = np.array([rho, p, ux, uy, 0.0, 0.0, 0.0, 0.0, 0.0])
+        U = pt.prim2con(m, P)
+        D, E = U[0], U[4] + U[0]
+        Z = (E - gf * D / wmax) / (1 - gf / wmax ** 2)
+        S = U[1:4]
+        assert S @ S / Z ** 2 > 1 - 1 / wmax ** 2  # the clamp is active at the root
+        Q, st = pt.con2prim(m, U, P)
+        assert st == 2
+        assert Q[0] == pytest.approx(D / wmax, rel=1e-13)
+        assert Q[1] == pytest.approx(gf * (Z / wmax ** 2 - D / wmax), rel=1e-9)
+        uq = Q[2:5]
+        assert math.sqrt(1 + uq @ uq) == pytest.approx(wmax, rel=1e-14)
+        np.testing.assert_allclose(uq / np.linalg.norm(uq), S / np.linalg.norm(S), rtol=0, atol=1e-14)
+
+
+@pytest.mark.parametrize("coords", ["ks", "mks"])
+def test_glm_source_matches_covariant_form(coords):
+    """The cleaning scalar's source S(psi) = -alpha kappa psi - psi d_i beta^i
+    + ch^2 B^i d_i alpha (the reading of the method's GLM terms) against the
+    source implied by the covariant damped cleaning equation, -alpha kappa psi
+    + ch^2 B^i d_i alpha - psi D_i beta^i with D_i beta^i the covariant
+    divergence, computed from the 4-metric by finite differences: the two
+    differ by exactly psi beta^i d_i ln sqrt(gamma), the flat divergence of the
+    shift standing in for the covariant one.  Each term is checked to matter
+    (ch = 0.8, so a missing ch^2 fails too)."""
+    grid = ks_grid(coords).with_(ch=0.8, kappa=0.3)
+    pt = oracle.Point(grid)
+
+    def mfn(y):
+        mm = pt.metric(y, derivs=False)
+        return mm.alpha, mm.beta.copy(), mm.g.copy()
+
+    rng = np.random.default_rng(21)
+    big = np.zeros(3)
+    for _ in range(25):
+        r = rng.uniform(1.5, 30)
+        x = np.array([math.log(r) if coords == "mks" else r, rng.uniform(0.05, 0.95) * (1 if coords == "mks" else math.pi), 2.0])
+        m = pt.metric(x)
+        P = random_state(rng, m.g)
+        P[8] = rng.normal()
+        S = pt.sources(m, P)
+        s_cov, extra = cov.glm_source(P, mfn, x, grid.ch, grid.kappa)
+        div_term = -P[8] * sum(m.db[i][i] for i in range(3))
+        alpha_term = grid.ch ** 2 * (P[5:8] @ m.da)
+        scale = abs(grid.kappa * m.alpha * P[8]) + abs(div_term) + abs(alpha_term)
+        assert S[8] == pytest.approx(s_cov + extra, rel=1e-7, abs=1e-8 * scale)
+        big = np.maximum(big, np.abs([alpha_term, div_term, extra]) / scale)
+    assert np.all(big > 0.05), big
+
+
 # --------------------------------------------------------------------------
 # reconstruction and the numerical flux
 # --------------------------------------------------------------------------
