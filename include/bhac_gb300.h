@@ -53,6 +53,7 @@ enum { BHAC_BC_PERIODIC = 0, BHAC_BC_OUTFLOW = 1, BHAC_BC_AXIS = 2, BHAC_BC_NOIN
 enum { BHAC_RECON_PPM = 0, BHAC_RECON_MINMOD = 1 };
 enum { BHAC_RIEMANN_HLL = 0, BHAC_RIEMANN_TVDLF = 1 };
 enum { BHAC_PREC_FP64 = 0, BHAC_PREC_MIXED = 1 };
+enum { BHAC_DIVB_GLM = 0, BHAC_DIVB_CT = 1 };
 
 /* Grid and scheme description, copied at init. */
 typedef struct {
@@ -78,6 +79,10 @@ typedef struct {
   double rho_floor, rho_floor_pow, p_floor, p_floor_pow, w_max;
                          /* floors rho >= rho_floor r^rho_floor_pow, p >= p_floor r^p_floor_pow,
                             W <= w_max; r = 1 in Cartesian coordinates */
+  int divb;              /* BHAC_DIVB_GLM: GLM cleaning (psi evolved with ch, kappa);
+                            BHAC_DIVB_CT: staggered-mesh constrained transport of face
+                            fields (uniform grids, nlevels = 1, FP64 form; psi stays 0,
+                            ch and kappa are ignored) */
 } bhac_grid_desc;
 
 /* One leaf block: refinement level and integer block coordinates at that level. */
@@ -179,6 +184,26 @@ bhac_status bhac_set_cons(bhac_ctx* ctx, const double* cons, int on_device);
 bhac_status bhac_get_prims(bhac_ctx* ctx, double* out, int on_device);
 bhac_status bhac_get_cons(bhac_ctx* ctx, double* out, int on_device);
 
+/* Constrained transport (divb = BHAC_DIVB_CT).  Source: Sec. 2 (staggered-mesh
+ * constrained transport in covariant coordinates); the edge electric field is
+ * the hot-path reading: the mean of the four upwinded (HLL/TVDLF) face fluxes
+ * of B around each edge, the face update the discrete curl, so each cell's
+ * sum_d (Phi^d_high - Phi^d_low) / dx_d keeps its initial value to round-off.
+ *
+ * The evolved field is Phi^d = sqrt(gamma) B^d at the centre of every face
+ * normal to an active direction d.  Layout: for each block, for each active d
+ * in order, the block's faces 0..nx_d along d and its cells across, [k][j][i],
+ * i fastest (a face on a block boundary appears in both blocks, with equal
+ * values).  bhac_set_faces loads them (host pointer if on_device == 0, device
+ * pointer otherwise; host copies synchronise the stream) after bhac_set_prims,
+ * replaces the cell field of the primitives by the face means
+ * (sqrt(gamma) B^d = (Phi^d_low + Phi^d_high) / 2), sets psi = 0 and recomputes
+ * the conserved state; a step before it returns BHAC_ERR_STATE.
+ * bhac_get_faces reads them back in the same layout.  BHAC_ERR_STATE for a
+ * grid in the cleaning form. */
+bhac_status bhac_set_faces(bhac_ctx* ctx, const double* faces, int on_device);
+bhac_status bhac_get_faces(bhac_ctx* ctx, double* faces, int on_device);
+
 /* Pipelined host transfers, for a host-side loop that feeds every step its
  * primitives from host memory and reads every result back while the kernels of
  * the neighbouring steps run.  The context owns two copy streams, one per
@@ -235,7 +260,9 @@ bhac_status bhac_get_diagnostics(bhac_ctx* ctx, long long counts[4]);
 
 /* Kernel launches one bhac_step makes on the context's stream: per stage one
  * cross-level node pass per dependency depth (AMR grids), the ghost gather,
- * the stage kernel and, where levels meet, the reflux kernel. */
+ * the stage kernel and, where levels meet, the reflux kernel; with constrained
+ * transport the ghost gather, the ring-face copy, the face-flux, face-update
+ * and cell kernels. */
 bhac_status bhac_launches_per_step(const bhac_ctx* ctx, int* launches);
 
 /* Kernel launch shape of the stage kernel: tile of tx x ty cells per CTA column

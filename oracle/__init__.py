@@ -55,7 +55,7 @@ class OrParams(C.Structure):
         ("gamma_ad", C.c_double), ("cfl", C.c_double), ("ch", C.c_double), ("kappa", C.c_double),
         ("c2p_tol", C.c_double), ("c2p_maxit", C.c_int),
         ("rho_floor", C.c_double), ("rho_floor_pow", C.c_double), ("p_floor", C.c_double),
-        ("p_floor_pow", C.c_double), ("w_max", C.c_double),
+        ("p_floor_pow", C.c_double), ("w_max", C.c_double), ("ct", C.c_int),
     ]
 
 
@@ -94,6 +94,10 @@ def lib():
         L.or_c2p_status.argtypes = [C.c_void_p, C.c_void_p]
         L.or_ghosted_cells.argtypes = [C.c_void_p]
         L.or_ghosted_cells.restype = C.c_int
+        L.or_face_count.argtypes = [C.c_void_p]
+        L.or_face_count.restype = C.c_long
+        L.or_set_faces.argtypes = [C.c_void_p, _DP]
+        L.or_get_faces.argtypes = [C.c_void_p, _DP]
         _lib = L
     return _lib
 
@@ -127,6 +131,7 @@ def params_of(grid) -> OrParams:
     p.p_floor = grid.p_floor
     p.p_floor_pow = grid.p_floor_pow
     p.w_max = grid.w_max
+    p.ct = 1 if getattr(grid, "divb", "glm") == "ct" else 0
     return p
 
 
@@ -258,6 +263,18 @@ class Oracle:
         g = self.grid
         out = np.zeros((self.nb, g.nx[2], g.nx[1], g.nx[0]), dtype=np.uint8)
         self.L.or_c2p_status(self.ctx, out.ctypes.data)
+        return out
+
+    def set_faces(self, faces):
+        """Face fields Phi^d = sqrt(gamma) B^d (constrained transport), owned
+        faces in [block][d][k][j][i] order (problems.face_layout)."""
+        a = np.ascontiguousarray(faces, dtype=np.float64)
+        assert a.size == self.L.or_face_count(self.ctx)
+        self.L.or_set_faces(self.ctx, a)
+
+    def faces(self):
+        out = np.zeros(self.L.or_face_count(self.ctx))
+        self.L.or_get_faces(self.ctx, out)
         return out
 
     def c2p_counts(self):

@@ -611,6 +611,14 @@ struct or_ctx {
   int* lut[8];     /* per level: block id at block coordinates, -1 if not a leaf */
   long long counts[4];
   unsigned char* status; /* nb x interior: inversion outcome of the last stage */
+  /* constrained transport: per active direction d, the face field Phi^d and the
+   * fluxes through the faces normal to d, over the block's faces plus a ring
+   * of one face across in every active transverse direction */
+  int fe[3][3];          /* extents of the direction-d face arrays */
+  int fo[3][3];          /* position of local index 0 inside them */
+  double* fc[3];         /* Phi^d = sqrt(gamma) B^d at face centres */
+  double* fcn[3];        /* Phi^d at the start of the step */
+  double* xf[3];         /* fluxes through those faces, NV per face, densitized */
 };
 
 static long lut_size(const or_ctx* c, int L) {
@@ -675,6 +683,23 @@ or_ctx* or_create(const or_params* p, int nblocks, const int* blocks) {
     size_t nf = (size_t)c->nint / p->nx[d] * (p->nx[d] + 1);
     c->flux[d] = (double*)calloc((size_t)nblocks * OR_NV * nf, sizeof(double));
   }
+  if (p->ct) {
+    /* psi is not evolved: no cleaning speed, no damping */
+    c->p.ch = 0.0;
+    c->p.kappa = 0.0;
+    for (int d = 0; d < p->ndim; ++d) {
+      size_t n = (size_t)nblocks;
+      for (int e = 0; e < 3; ++e) {
+        int across = e != d && e < p->ndim;
+        c->fe[d][e] = e == d ? p->nx[e] + 1 : p->nx[e] + (across ? 2 : 0);
+        c->fo[d][e] = across ? 1 : 0;
+        n *= c->fe[d][e];
+      }
+      c->fc[d] = (double*)calloc(n, sizeof(double));
+      c->fcn[d] = (double*)calloc(n, sizeof(double));
+      c->xf[d] = (double*)calloc(n * OR_NV, sizeof(double));
+    }
+  }
   for (int L = 0; L < p->nlevels && L < 8; ++L) {
     long n = lut_size(c, L);
     c->lut[L] = (int*)malloc(sizeof(int) * n);
@@ -696,7 +721,12 @@ void or_destroy(or_ctx* c) {
   free(c->ucur);
   free(c->un);
   free(c->status);
-  for (int d = 0; d < 3; ++d) free(c->flux[d]);
+  for (int d = 0; d < 3; ++d) {
+    free(c->flux[d]);
+    free(c->fc[d]);
+    free(c->fcn[d]);
+    free(c->xf[d]);
+  }
   for (int L = 0; L < 8; ++L) free(c->lut[L]);
   free(c);
 }
@@ -924,6 +954,257 @@ double or_cfl_dt(or_ctx* c) {
   return c->p.cfl / smax;
 }
 
+/* ---- constrained transport (uniform grids) ---- */
+
+/* Staggered-mesh constrained transport: the field normal to each face is
+ * evolved as Phi^d = sqrt(gamma) B^d at the face centre, by the induction
+ * equation in integral form, d_t Phi = -curl E, with the electric field at
+ * cell edges.  The face fluxes of B already are E up to sign:
+ *   F^2(B^1) = -F^1(B^2) = E_3,  F^3(B^2) = -F^2(B^3) = E_1,
+ *   F^1(B^3) = -F^3(B^1) = E_2    (E = -(alpha v - beta) x B, densitized),
+ * so the EMF at an edge is the mean of the four upwinded (HLL/TVDLF) face
+ * fluxes around it (the flux-interpolated constrained transport of Balsara &
+ * Spicer 1999).  Because the face update is a discrete curl, the discrete
+ * divergence sum_d (Phi^d_high - Phi^d_low) / dx_d of every cell keeps its
+ * initial value to round-off.  At a face the normal field in both reconstructed
+ * states is Phi^d / sqrt(gamma) of the face itself.  Cell-centred
+ * sqrt(gamma) B^d = (Phi^d_low + Phi^d_high) / 2.  A block owns its faces
+ * 0..nx_d along d; the ring of faces one cell outside it across (needed by the
+ * EMFs at the block's edges) is filled from the neighbours like ghost cells, so
+ * both blocks sharing a face compute the same EMFs and keep the same value. */
+
+static size_t fcx(const or_ctx* c, int d, int b, int i, int j, int k) {
+  const int* e = c->fe[d];
+  const int* o = c->fo[d];
+  return (((size_t)b * e[2] + (k + o[2])) * e[1] + (j + o[1])) * e[0] + (i + o[0]);
+}
+
+static size_t xfx(const or_ctx* c, int d, int b, int v, int i, int j, int k) {
+  const int* e = c->fe[d];
+  const int* o = c->fo[d];
+  return ((((size_t)b * OR_NV + v) * e[2] + (k + o[2])) * e[1] + (j + o[1])) * e[0] + (i + o[0]);
+}
+
+/* Owner and local index of face (d; f local) of block b after the boundary
+ * rules across it: periodic wrap, outflow / no-inflow copy of the nearest
+ * face, polar axis mirror in theta (and phi + pi in 3-D).  Returns -1 if no
+ * block owns it. */
+static int ct_face_source(const or_ctx* c, int d, int b, const int f[3], int lf[3]) {
+  const int* nx = c->p.nx;
+  long G[3], N[3];
+  for (int e = 0; e < 3; ++e) {
+    G[e] = (long)c->blk[4 * b + 1 + e] * nx[e] + f[e];
+    N[e] = (long)c->p.nroot[e] * nx[e];
+  }
+  for (int e = 0; e < c->p.ndim; ++e) {
+    if (e == d) continue;
+    for (int side = 0; side < 2; ++side) {
+      int out = side == 0 ? G[e] < 0 : G[e] >= N[e];
+      if (!out) continue;
+      int kind = c->p.bc[e][side];
+      if (kind == OR_BC_PERIODIC) {
+        G[e] = ((G[e] % N[e]) + N[e]) % N[e];
+      } else if (kind == OR_BC_OUTFLOW || kind == OR_BC_NOINFLOW) {
+        G[e] = side == 0 ? 0 : N[e] - 1;
+      } else if (kind == OR_BC_AXIS) {
+        G[e] = side == 0 ? -1 - G[e] : 2 * N[e] - 1 - G[e];
+        if (c->p.ndim == 3) G[2] = ((G[2] + N[2] / 2) % N[2] + N[2]) % N[2];
+      }
+    }
+  }
+  if (c->p.ndim == 3 && d != 2 && c->p.bc[2][0] == OR_BC_PERIODIC) G[2] = ((G[2] % N[2]) + N[2]) % N[2];
+  long bc[3];
+  for (int e = 0; e < 3; ++e) {
+    if (e == d) {
+      bc[e] = G[e] / nx[e];
+      if (bc[e] >= c->p.nroot[e]) bc[e] = c->p.nroot[e] - 1;
+      lf[e] = (int)(G[e] - bc[e] * nx[e]);
+    } else {
+      bc[e] = G[e] / nx[e];
+      lf[e] = (int)(G[e] % nx[e]);
+    }
+  }
+  return lut_get(c, 0, bc);
+}
+
+static void ct_fill_face_ring(or_ctx* c) {
+#pragma omp parallel for schedule(dynamic)
+  for (int b = 0; b < c->nb; ++b)
+    for (int d = 0; d < c->p.ndim; ++d) {
+      const int* e = c->fe[d];
+      const int* o = c->fo[d];
+      for (int k = -o[2]; k < e[2] - o[2]; ++k)
+        for (int j = -o[1]; j < e[1] - o[1]; ++j)
+          for (int i = -o[0]; i < e[0] - o[0]; ++i) {
+            int f[3] = {i, j, k}, ring = 0;
+            for (int t = 0; t < 3; ++t)
+              if (t != d && (f[t] < 0 || f[t] >= c->p.nx[t])) ring = 1;
+            if (!ring) continue;
+            int lf[3];
+            int ob = ct_face_source(c, d, b, f, lf);
+            c->fc[d][fcx(c, d, b, i, j, k)] = ob >= 0 ? c->fc[d][fcx(c, d, ob, lf[0], lf[1], lf[2])] : 0.0;
+          }
+    }
+}
+
+/* Fluxes through every face of direction d of block b and its ring. */
+static void ct_block_xfluxes(or_ctx* c, int b, int d) {
+  int L = c->blk[4 * b];
+  const int* e = c->fe[d];
+  const int* o = c->fo[d];
+  long Nd = (long)c->p.nroot[d] * c->p.nx[d];
+  for (int k = -o[2]; k < e[2] - o[2]; ++k)
+    for (int j = -o[1]; j < e[1] - o[1]; ++j)
+      for (int i = -o[0]; i < e[0] - o[0]; ++i) {
+        int f[3] = {i, j, k};
+        double x[3], F[OR_NV];
+        long G[3];
+        for (int t = 0; t < 3; ++t) {
+          G[t] = (long)c->blk[4 * b + 1 + t] * c->p.nx[t] + f[t];
+          x[t] = coord(c, t, L, G[t], t == d ? 0.0 : 0.5);
+        }
+        int axis = (G[d] == 0 && c->p.bc[d][0] == OR_BC_AXIS) || (G[d] == Nd && c->p.bc[d][1] == OR_BC_AXIS);
+        if (axis) {
+          for (int v = 0; v < OR_NV; ++v) F[v] = 0.0;
+        } else {
+          double st[6][OR_NV], PL[OR_NV], PR[OR_NV];
+          for (int s = 0; s < 6; ++s) {
+            int g[3] = {i + c->gd[0], j + c->gd[1], k + c->gd[2]};
+            g[d] += s - 3;
+            for (int v = 0; v < OR_NV; ++v) st[s][v] = c->prim[pidx(c, b, v, g[0], g[1], g[2])];
+          }
+          or_reconstruct(&c->p, (const double(*)[OR_NV])st, PL, PR);
+          or_metric m;
+          or_metric_at(&c->p, x, 0, &m);
+          double Bn = c->fc[d][fcx(c, d, b, i, j, k)] / m.sqrtg;
+          PL[OR_B1 + d] = Bn;
+          PR[OR_B1 + d] = Bn;
+          or_face_flux(&c->p, &m, PL, PR, d, F);
+        }
+        for (int v = 0; v < OR_NV; ++v) c->xf[d][xfx(c, d, b, v, i, j, k)] = F[v];
+      }
+}
+
+/* Edge EMFs of block b: E_3 at the edge (i-1/2, j-1/2) of cell layer k, E_1
+ * at (j-1/2, k-1/2) of column i, E_2 at (k-1/2, i-1/2) of row j, each the
+ * mean of the four face fluxes around the edge. */
+static double ct_emf3(const or_ctx* c, int b, int i, int j, int k) {
+  return 0.25 * (c->xf[1][xfx(c, 1, b, OR_B1, i, j, k)] + c->xf[1][xfx(c, 1, b, OR_B1, i - 1, j, k)] -
+                 c->xf[0][xfx(c, 0, b, OR_B2, i, j, k)] - c->xf[0][xfx(c, 0, b, OR_B2, i, j - 1, k)]);
+}
+static double ct_emf1(const or_ctx* c, int b, int i, int j, int k) {
+  return 0.25 * (c->xf[2][xfx(c, 2, b, OR_B2, i, j, k)] + c->xf[2][xfx(c, 2, b, OR_B2, i, j - 1, k)] -
+                 c->xf[1][xfx(c, 1, b, OR_B3, i, j, k)] - c->xf[1][xfx(c, 1, b, OR_B3, i, j, k - 1)]);
+}
+static double ct_emf2(const or_ctx* c, int b, int i, int j, int k) {
+  return 0.25 * (c->xf[0][xfx(c, 0, b, OR_B3, i, j, k)] + c->xf[0][xfx(c, 0, b, OR_B3, i, j, k - 1)] -
+                 c->xf[2][xfx(c, 2, b, OR_B1, i, j, k)] - c->xf[2][xfx(c, 2, b, OR_B1, i - 1, j, k)]);
+}
+
+/* d_t Phi = -curl E on the owned faces of block b, then the stage combination
+ * (stage 1: Phi1 = Phin + dt R; stage 2: Phi = Phin/2 + (Phi1 + dt R)/2).
+ * Faces on the polar axis (sqrt(gamma) = 0) stay zero. */
+static void ct_update_faces(or_ctx* c, int b, int stage, double dt) {
+  int L = c->blk[4 * b];
+  const int* nx = c->p.nx;
+  int three = c->p.ndim == 3;
+  double dx[3];
+  for (int t = 0; t < 3; ++t) dx[t] = dxl(c, t, L);
+  for (int d = 0; d < c->p.ndim; ++d) {
+    long Nd = (long)c->p.nroot[d] * nx[d];
+    int n[3] = {nx[0], nx[1], nx[2]};
+    n[d] += 1;
+    for (int k = 0; k < n[2]; ++k)
+      for (int j = 0; j < n[1]; ++j)
+        for (int i = 0; i < n[0]; ++i) {
+          size_t q = fcx(c, d, b, i, j, k);
+          int f[3] = {i, j, k};
+          long Gd = (long)c->blk[4 * b + 1 + d] * nx[d] + f[d];
+          if (d == 1 && ((Gd == 0 && c->p.bc[1][0] == OR_BC_AXIS) || (Gd == Nd && c->p.bc[1][1] == OR_BC_AXIS))) {
+            c->fc[d][q] = 0.0;
+            if (stage == 1) c->fcn[d][q] = 0.0;
+            continue;
+          }
+          double R;
+          if (d == 0) {
+            R = -(ct_emf3(c, b, i, j + 1, k) - ct_emf3(c, b, i, j, k)) / dx[1];
+            if (three) R += (ct_emf2(c, b, i, j, k + 1) - ct_emf2(c, b, i, j, k)) / dx[2];
+          } else if (d == 1) {
+            R = (ct_emf3(c, b, i + 1, j, k) - ct_emf3(c, b, i, j, k)) / dx[0];
+            if (three) R -= (ct_emf1(c, b, i, j, k + 1) - ct_emf1(c, b, i, j, k)) / dx[2];
+          } else {
+            R = -(ct_emf2(c, b, i + 1, j, k) - ct_emf2(c, b, i, j, k)) / dx[0] +
+                (ct_emf1(c, b, i, j + 1, k) - ct_emf1(c, b, i, j, k)) / dx[1];
+          }
+          if (stage == 1) {
+            c->fcn[d][q] = c->fc[d][q];
+            c->fc[d][q] = c->fcn[d][q] + dt * R;
+          } else {
+            c->fc[d][q] = 0.5 * c->fcn[d][q] + 0.5 * (c->fc[d][q] + dt * R);
+          }
+        }
+  }
+}
+
+long or_face_count(const or_ctx* c) {
+  long n = 0;
+  for (int d = 0; d < c->p.ndim; ++d) {
+    long m = c->nb;
+    for (int t = 0; t < 3; ++t) m *= c->p.nx[t] + (t == d ? 1 : 0);
+    n += m;
+  }
+  return n;
+}
+
+/* owned faces in [block][d][k][j][i] order */
+static void ct_copy_faces(or_ctx* c, double* io, int to_ctx) {
+  const int* nx = c->p.nx;
+  size_t q = 0;
+  for (int b = 0; b < c->nb; ++b)
+    for (int d = 0; d < c->p.ndim; ++d) {
+      int n[3] = {nx[0], nx[1], nx[2]};
+      n[d] += 1;
+      for (int k = 0; k < n[2]; ++k)
+        for (int j = 0; j < n[1]; ++j)
+          for (int i = 0; i < n[0]; ++i, ++q) {
+            if (to_ctx)
+              c->fc[d][fcx(c, d, b, i, j, k)] = io[q];
+            else
+              io[q] = c->fc[d][fcx(c, d, b, i, j, k)];
+          }
+    }
+}
+
+void or_set_faces(or_ctx* c, const double* faces) {
+  ct_copy_faces(c, (double*)faces, 1);
+  const int* nx = c->p.nx;
+  for (int b = 0; b < c->nb; ++b)
+    for (int k = 0; k < nx[2]; ++k)
+      for (int j = 0; j < nx[1]; ++j)
+        for (int i = 0; i < nx[0]; ++i) {
+          double x[3], P[OR_NV], U[OR_NV];
+          or_metric m;
+          cell_centre(c, b, i, j, k, x);
+          or_metric_at(&c->p, x, 0, &m);
+          int g[3] = {i + c->gd[0], j + c->gd[1], k + c->gd[2]};
+          for (int v = 0; v < OR_NV; ++v) P[v] = c->prim[pidx(c, b, v, g[0], g[1], g[2])];
+          for (int d = 0; d < c->p.ndim; ++d) {
+            int hi[3] = {i, j, k};
+            hi[d] += 1;
+            double Bd = 0.5 * (c->fc[d][fcx(c, d, b, i, j, k)] + c->fc[d][fcx(c, d, b, hi[0], hi[1], hi[2])]);
+            P[OR_B1 + d] = Bd / m.sqrtg;
+          }
+          P[OR_PSI] = 0.0;
+          or_prim2con(&c->p, &m, P, U);
+          for (int v = 0; v < OR_NV; ++v) {
+            c->prim[pidx(c, b, v, g[0], g[1], g[2])] = P[v];
+            c->ucur[uidx(c, b, v, i, j, k)] = m.sqrtg * U[v];
+          }
+        }
+}
+
+void or_get_faces(const or_ctx* c, double* faces) { ct_copy_faces((or_ctx*)c, faces, 0); }
+
 /* ---- one Runge-Kutta stage ---- */
 
 static size_t fidx(const or_ctx* c, int d, int b, int v, int i, int j, int k) {
@@ -1033,6 +1314,12 @@ static void reflux_block(or_ctx* c, int b) {
 /* L = -sum_d (F_d(+) - F_d(-)) / dx_d + sqrt(gamma) S, then the SSP-RK2 stage
  * (Shu & Osher 1988): stage 1  U1 = Un + dt L(Pn);
  * stage 2  U = 1/2 Un + 1/2 (U1 + dt L(P1)); then the inversion per cell. */
+/* flux through face (i, j, k) of direction d of block b (the ring-extended
+ * arrays in constrained transport) */
+static double face_flux_at(const or_ctx* c, int d, int b, int v, int i, int j, int k) {
+  return c->p.ct ? c->xf[d][xfx(c, d, b, v, i, j, k)] : c->flux[d][fidx(c, d, b, v, i, j, k)];
+}
+
 static void update_block(or_ctx* c, int b, int stage, double dt, long long cnt[4]) {
   int L = c->blk[4 * b];
   const int* nx = c->p.nx;
@@ -1051,7 +1338,7 @@ static void update_block(or_ctx* c, int b, int stage, double dt, long long cnt[4
           ip[d] += 1;
           double dx = dxl(c, d, L);
           for (int v = 0; v < OR_NV; ++v)
-            rhs[v] += -(c->flux[d][fidx(c, d, b, v, ip[0], ip[1], ip[2])] - c->flux[d][fidx(c, d, b, v, i, j, k)]) / dx;
+            rhs[v] += -(face_flux_at(c, d, b, v, ip[0], ip[1], ip[2]) - face_flux_at(c, d, b, v, i, j, k)) / dx;
         }
         for (int v = 0; v < OR_NV; ++v) rhs[v] += m.sqrtg * S[v];
         for (int v = 0; v < OR_NV; ++v) {
@@ -1062,6 +1349,15 @@ static void update_block(or_ctx* c, int b, int stage, double dt, long long cnt[4
           } else {
             U[v] = 0.5 * c->un[u] + 0.5 * (c->ucur[u] + dt * rhs[v]);
           }
+        }
+        if (c->p.ct) {
+          /* the field along active directions is the mean of the updated faces */
+          for (int d = 0; d < c->p.ndim; ++d) {
+            int hi[3] = {i, j, k};
+            hi[d] += 1;
+            U[OR_B1 + d] = 0.5 * (c->fc[d][fcx(c, d, b, i, j, k)] + c->fc[d][fcx(c, d, b, hi[0], hi[1], hi[2])]);
+          }
+          U[OR_PSI] = 0.0;
         }
         double Uu[OR_NV];
         for (int v = 0; v < OR_NV; ++v) Uu[v] = U[v] / m.sqrtg;
@@ -1081,6 +1377,28 @@ static void update_block(or_ctx* c, int b, int stage, double dt, long long cnt[4
 
 void or_stage_blocks(or_ctx* c, int stage, double dt, int nsel, const int* sel) {
   or_fill_ghosts(c);
+  if (c->p.ct) {
+    /* constrained transport (uniform grids): ring faces, ring-extended fluxes,
+     * the face update, then the cells */
+    ct_fill_face_ring(c);
+#pragma omp parallel for schedule(dynamic)
+    for (int q = 0; q < nsel; ++q)
+      for (int d = 0; d < c->p.ndim; ++d) ct_block_xfluxes(c, sel[q], d);
+    long long tot[4] = {0, 0, 0, 0};
+#pragma omp parallel
+    {
+      long long cnt[4] = {0, 0, 0, 0};
+#pragma omp for schedule(dynamic)
+      for (int q = 0; q < nsel; ++q) {
+        ct_update_faces(c, sel[q], stage, dt);
+        update_block(c, sel[q], stage, dt, cnt);
+      }
+#pragma omp critical
+      for (int s = 0; s < 4; ++s) tot[s] += cnt[s];
+    }
+    for (int s = 0; s < 4; ++s) c->counts[s] += tot[s];
+    return;
+  }
   int all = c->p.nlevels > 1; /* refluxing needs the fine neighbours' fluxes */
 #pragma omp parallel for schedule(dynamic)
   for (int q = 0; q < (all ? c->nb : nsel); ++q) {

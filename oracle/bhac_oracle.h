@@ -13,13 +13,12 @@
  * in the order the method applies them; every reading of a point the paper
  * leaves open is listed in the design notes of the repository.
  *
- * Parity unpinned (no fact outside the oracle fixes them; the tests check
- * the special cases that have one):
- *   - the metric terms of the GLM source, -psi d_i beta^i + c_h^2 B^i d_i alpha,
- *     beyond their flat-space reduction to -kappa psi (the paper gives no
- *     cleaning equations; the terms are a reading);
- *   - the SRMHD shock tube as a whole, beyond a stored regression profile
- *     written by the oracle itself (the paper prints no reference solution).
+ * Parity unpinned (no fact outside the oracle fixes it): the SRMHD shock
+ * tube as a whole, beyond a stored regression profile written by the oracle
+ * itself (the paper prints no reference solution); its ingredients are each
+ * pinned.  The GLM source's metric terms are a reading (the paper gives no
+ * cleaning equations), pinned against the covariant damped cleaning equation
+ * plus the one term the reading adds.
  *
  * Conventions
  *   primitive order : rho, p, u^1, u^2, u^3, B^1, B^2, B^3, psi
@@ -64,6 +63,8 @@ typedef struct {
   double c2p_tol;        /* Newton stopping tolerance on |dZ|/Z */
   int c2p_maxit;         /* Newton iteration cap */
   double rho_floor, rho_floor_pow, p_floor, p_floor_pow, w_max;
+  int ct;                /* 0: GLM cleaning; 1: staggered-mesh constrained transport
+                            (uniform grids; psi is not evolved, ch and kappa are ignored) */
 } or_params;
 
 /* Spatial metric at a point plus its first derivatives along the code
@@ -110,6 +111,17 @@ void or_c2p_counts(const or_ctx* c, long long counts[4]);
 /* per interior cell ([block][k][j][i]): inversion outcome of the last stage */
 void or_c2p_status(const or_ctx* c, unsigned char* status);
 int or_ghosted_cells(const or_ctx* c);                    /* per block, with ghosts */
+
+/* ---- constrained transport (params.ct = 1, uniform grids) ----
+ * The evolved field is Phi^d = sqrt(gamma) B^d at the centre of each face
+ * normal to an active direction d.  Owned faces of a block: index 0..nx_d
+ * along d, the block's cells across; layout [block][d][k][j][i] over the
+ * active d in order, each over (nx_d + 1) x (cells across), i fastest.
+ * or_set_faces replaces B^d of the loaded state by the face averages
+ * (sqrt(gamma) B^d = (Phi^d_low + Phi^d_high) / 2) and recomputes U. */
+long or_face_count(const or_ctx* c);                      /* owned faces, all blocks */
+void or_set_faces(or_ctx* c, const double* faces);
+void or_get_faces(const or_ctx* c, double* faces);
 
 #ifdef __cplusplus
 }

@@ -23,7 +23,7 @@ __all__ = [
     "bhac_set_launch", "bhac_count_flops", "bhac_graph_capture", "bhac_graph_launch", "bhac_cfl_dt_static", "bhac_destroy",
     "bhac_status_string", "bhac_check_bit_ops", "bhac_launches_per_step", "bhac_get_prims_ghosted",
     "bhac_get_c2p_status", "bhac_set_cons", "bhac_set_prims_host_async", "bhac_get_prims_host_async",
-    "bhac_host_fence", "bhac_measure_peaks",
+    "bhac_host_fence", "bhac_measure_peaks", "bhac_set_faces", "bhac_get_faces",
 ]
 
 NV = 9
@@ -44,7 +44,7 @@ class GridDesc(C.Structure):
         ("riemann", C.c_int), ("precision", C.c_int), ("gamma_ad", C.c_double), ("cfl", C.c_double),
         ("ch", C.c_double), ("kappa", C.c_double), ("c2p_tol", C.c_double), ("c2p_maxit", C.c_int),
         ("rho_floor", C.c_double), ("rho_floor_pow", C.c_double), ("p_floor", C.c_double),
-        ("p_floor_pow", C.c_double), ("w_max", C.c_double),
+        ("p_floor_pow", C.c_double), ("w_max", C.c_double), ("divb", C.c_int),
     ]
 
 
@@ -97,6 +97,8 @@ def lib():
             "bhac_get_prims_host_async": ([vp, vp], i),
             "bhac_host_fence": ([vp], i),
             "bhac_measure_peaks": ([i, vp, C.POINTER(d)], i),
+            "bhac_set_faces": ([vp, vp, i], i),
+            "bhac_get_faces": ([vp, vp, i], i),
             "bhac_destroy": ([vp], None),
             "bhac_status_string": ([i], C.c_char_p),
         }
@@ -185,6 +187,14 @@ def bhac_get_prims_host_async(ctx, ptr: int):
 
 def bhac_host_fence(ctx):
     _check("bhac_host_fence", lib().bhac_host_fence(ctx))
+
+
+def bhac_set_faces(ctx, ptr: int, on_device: bool):
+    _check("bhac_set_faces", lib().bhac_set_faces(ctx, C.c_void_p(ptr), int(on_device)))
+
+
+def bhac_get_faces(ctx, ptr: int, on_device: bool):
+    _check("bhac_get_faces", lib().bhac_get_faces(ctx, C.c_void_p(ptr), int(on_device)))
 
 
 def bhac_get_prims_ghosted(ctx, ptr: int, on_device: bool):
@@ -285,6 +295,7 @@ def desc_of(grid, precision: str = "fp64") -> GridDesc:
     d.p_floor = grid.p_floor
     d.p_floor_pow = grid.p_floor_pow
     d.w_max = grid.w_max
+    d.divb = 1 if getattr(grid, "divb", "glm") == "ct" else 0
     return d
 
 
@@ -399,6 +410,19 @@ class Solver:
         """Resumes from checkpoint(): the next steps are bit-identical to an uninterrupted run."""
         self.set_prims(state["prims"])
         self.set_cons(state["cons"])
+
+    def set_faces(self, faces):
+        """Face fields Phi^d = sqrt(gamma) B^d (constrained transport), owned
+        faces per block and direction (problems.ct layout); call after set_prims."""
+        a = np.ascontiguousarray(faces, dtype=np.float64)
+        bhac_set_faces(self.ctx, a.ctypes.data, False)
+
+    def faces(self) -> np.ndarray:
+        n = self.grid.nb * sum(int(np.prod([self.grid.nx[e] + (e == d) for e in range(3)]))
+                               for d in range(self.grid.ndim))
+        out = np.empty(n)
+        bhac_get_faces(self.ctx, out.ctypes.data, False)
+        return out
 
     def prims_ghosted(self) -> np.ndarray:
         """FP64 primitives with ghost cells, (blocks, 9, Nz, Ny, Nx) (FP64 form)."""

@@ -27,7 +27,9 @@ namespace {
 struct Layout {
   size_t off_blk, off_order, off_src, off_flags, off_tmpl, off_tc, off_tf1, off_tf2, off_tc32, off_tf1_32, off_tf2_32;
   size_t off_P[2], off_P32[2], off_U[2], off_scratch, off_scratch_out, off_status, off_small;
-  size_t off_nodes, off_ops, off_nodeval, off_cf, off_regoff, off_reg, off_rcells, off_rterms, total;
+  size_t off_nodes, off_ops, off_nodeval, off_cf, off_regoff, off_reg, off_rcells, off_rterms;
+  size_t off_phi[2], off_xf, off_te_c, off_te_f1, off_te_f2, off_te_c32, off_te_f1_32, off_te_f2_32, off_ring[2];
+  size_t total;
   long long toff_c[MAXLEV], toff_f1[MAXLEV], toff_f2[MAXLEV];
 };
 
@@ -50,6 +52,9 @@ bool valid_desc(const bhac_grid_desc* d, const bhac_block_desc* b, int nb) {
   if (d->recon < 0 || d->recon > 1 || d->riemann < 0 || d->riemann > 1) return false;
   if (!(d->gamma_ad > 1.0) || !(d->cfl > 0.0) || !(d->ch > 0.0) || d->c2p_maxit < 1) return false;
   if (!(d->w_max > 1.0)) return false;
+  // constrained transport: uniform grids in the FP64 form
+  if (d->divb < 0 || d->divb > 1) return false;
+  if (d->divb == BHAC_DIVB_CT && (d->nlevels != 1 || d->precision != BHAC_PREC_FP64)) return false;
   // the axis rule is for x2 (theta) only; phi must be periodic with an even cell count in 3-D
   for (int k = 0; k < 3; ++k)
     for (int s = 0; s < 2; ++s)
@@ -82,7 +87,7 @@ void geometry(const bhac_grid_desc* d, int g[3], int N[3], int& ncell, int& nint
   nslots = ncell - nint;
 }
 
-Layout layout(const bhac_grid_desc* d, int nb, const HostMaps& M) {
+Layout layout(const bhac_grid_desc* d, int nb, const HostMaps& M, long long nring) {
   int g[3], N[3], ncell, nint, nslots;
   geometry(d, g, N, ncell, nint, nslots);
   const bool flat = d->coords == BHAC_COORDS_CART;
@@ -132,6 +137,22 @@ Layout layout(const bhac_grid_desc* d, int nb, const HostMaps& M) {
   L.off_reg = take(sizeof(double) * (size_t)M.reg_elems);
   L.off_rcells = take(sizeof(RefluxCell) * M.rcells.size());
   L.off_rterms = take(sizeof(RefluxTerm) * M.rterms.size());
+  // constrained transport: face fields, fluxes, extended metric tables, ring map
+  const bool ct = d->divb == BHAC_DIVB_CT;
+  const CtGeom cg = ct_geom(d);
+  const size_t nfaces = ct ? (size_t)nb * cg.nfb : 0;
+  for (int s = 0; s < 2; ++s) L.off_phi[s] = take(sizeof(double) * nfaces);
+  L.off_xf = take(sizeof(double) * NV * nfaces);
+  const size_t n1 = (size_t)d->nroot[0] * d->nx[0], n2 = (size_t)d->nroot[1] * d->nx[1];
+  const size_t ec = ct && !flat ? (n1 + 2) * (n2 + 2) : 0, ef1 = ct && !flat ? (n1 + 3) * (n2 + 2) : 0,
+               ef2 = ct && !flat ? (n1 + 2) * (n2 + 3) : 0;
+  L.off_te_c = take(sizeof(double) * CREC * ec);
+  L.off_te_f1 = take(sizeof(double) * FREC * ef1);
+  L.off_te_f2 = take(sizeof(double) * FREC * ef2);
+  L.off_te_c32 = take(sizeof(float) * CREC * ec);
+  L.off_te_f1_32 = take(sizeof(float) * FREC * ef1);
+  L.off_te_f2_32 = take(sizeof(float) * FREC * ef2);
+  for (int s = 0; s < 2; ++s) L.off_ring[s] = take(sizeof(long long) * (ct ? (size_t)nring : 0));
   L.total = o;
   return L;
 }
@@ -180,8 +201,9 @@ StageArgs base_args(const bhac_ctx* c) {
   a.riemann = d.riemann;
   a.gam = d.gamma_ad;
   a.gam_fac = d.gamma_ad / (d.gamma_ad - 1.0);
-  a.ch = d.ch;
-  a.kappa = d.kappa;
+  // constrained transport does not evolve psi: no cleaning speed, no damping
+  a.ch = c->ct ? 0.0 : d.ch;
+  a.kappa = c->ct ? 0.0 : d.kappa;
   a.gam_f = (float)a.gam;
   a.gam_fac_f = (float)a.gam_fac;
   a.ch_f = (float)a.ch;
@@ -306,6 +328,52 @@ bhac_status run_stage(bhac_ctx* c, int stage, double dt) {
   return BHAC_OK;
 }
 
+// Arguments of the constrained-transport kernels for the current buffers.
+CtArgs ct_args(const bhac_ctx* c) {
+  CtArgs t;
+  t.g = c->ctg;
+  t.phi_in = c->phi[c->pcur];
+  t.phi_out = c->phi[1 - c->pcur];
+  t.phi_n = c->phi[1 - c->pcur];
+  t.xf = c->xf;
+  t.te_c = c->te_c;
+  t.te_f1 = c->te_f1;
+  t.te_f2 = c->te_f2;
+  t.axis_lo = c->d.bc[1][0] == BHAC_BC_AXIS;
+  t.axis_hi = c->d.bc[1][1] == BHAC_BC_AXIS;
+  return t;
+}
+
+// One constrained-transport stage after the ghost fill: ring faces, face
+// fluxes, face update, cells.  Face buffers: stage 1 reads the step's start
+// (pcur) and writes the other; stage 2 reads that one and writes the start
+// buffer (Phi = Phi_n / 2 + (Phi_1 + dt R) / 2 in place), so the roles are
+// back where they were after every step.
+bhac_status run_stage_ct(bhac_ctx* c, int stage, double dt) {
+  StageArgs a = base_args(c);
+  const int in = c->cur, out = 1 - c->cur;
+  a.stage = stage;
+  a.dt_host = dt;
+  a.P_in = c->P[in];
+  a.P_out = c->P[out];
+  if (stage == 1) {
+    a.Un = c->U[c->ucur];
+    a.U1 = nullptr;
+    a.Uout = c->U[1 - c->ucur];
+  } else {
+    a.Un = c->U[1 - c->ucur];
+    a.U1 = c->U[c->ucur];
+    a.Uout = c->U[1 - c->ucur];
+  }
+  CtArgs t = ct_args(c);
+  if (launch_ct_ring(c->ring_dst, c->ring_src, c->nring, c->phi[c->pcur], c->st) != cudaSuccess) return BHAC_ERR_CUDA;
+  if (launch_ct_stage(a, t, c->st) != cudaSuccess) return BHAC_ERR_CUDA;
+  c->cur = out;
+  c->ucur = 1 - c->ucur;
+  c->pcur = 1 - c->pcur;
+  return BHAC_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -329,7 +397,9 @@ bhac_status bhac_query_sizes(const bhac_grid_desc* d, const bhac_block_desc* b, 
   geometry(d, g, N, ncell, nint, nslots);
   const HostMaps M = build_maps(d, b, nb, g, N, ncell);
   if (!M.ok) return BHAC_ERR_ARG;
-  *out = layout(d, nb, M).total;
+  std::vector<long long> rd, rs;
+  if (d->divb == BHAC_DIVB_CT && !ct_ring_map(d, b, nb, ct_geom(d), rd, rs)) return BHAC_ERR_ARG;
+  *out = layout(d, nb, M, (long long)rd.size()).total;
   return BHAC_OK;
 }
 
@@ -340,7 +410,9 @@ bhac_status bhac_init_grid(bhac_ctx** out, const bhac_grid_desc* d, const bhac_b
   geometry(d, g, N, ncell, nint, nslots);
   const HostMaps M = build_maps(d, b, nb, g, N, ncell);
   if (!M.ok) return BHAC_ERR_ARG;  // a boundary rule or a level points at a missing block
-  const Layout L = layout(d, nb, M);
+  std::vector<long long> ring_dst, ring_src;
+  if (d->divb == BHAC_DIVB_CT && !ct_ring_map(d, b, nb, ct_geom(d), ring_dst, ring_src)) return BHAC_ERR_ARG;
+  const Layout L = layout(d, nb, M, (long long)ring_dst.size());
   if (arena_bytes < L.total) return BHAC_ERR_NOMEM;
   bhac_ctx* c = new bhac_ctx();
   c->d = *d;
@@ -394,6 +466,21 @@ bhac_status bhac_init_grid(bhac_ctx** out, const bhac_grid_desc* d, const bhac_b
   c->d_rcells = (RefluxCell*)(c->arena + L.off_rcells);
   c->d_rterms = (RefluxTerm*)(c->arena + L.off_rterms);
   c->nrcells = (int)M.rcells.size();
+  c->ct = d->divb == BHAC_DIVB_CT;
+  c->faces_ok = false;
+  c->ctg = ct_geom(d);
+  for (int s = 0; s < 2; ++s) c->phi[s] = (double*)(c->arena + L.off_phi[s]);
+  c->pcur = 0;
+  c->xf = (double*)(c->arena + L.off_xf);
+  c->te_c = (double*)(c->arena + L.off_te_c);
+  c->te_f1 = (double*)(c->arena + L.off_te_f1);
+  c->te_f2 = (double*)(c->arena + L.off_te_f2);
+  c->te_c32 = (float*)(c->arena + L.off_te_c32);
+  c->te_f1_32 = (float*)(c->arena + L.off_te_f1_32);
+  c->te_f2_32 = (float*)(c->arena + L.off_te_f2_32);
+  c->ring_dst = (long long*)(c->arena + L.off_ring[0]);
+  c->ring_src = (long long*)(c->arena + L.off_ring[1]);
+  c->nring = (long long)ring_dst.size();
   c->cur = 0;
   c->ucur = 0;
   c->threads = 256;
@@ -458,6 +545,8 @@ bhac_status bhac_init_grid(bhac_ctx** out, const bhac_grid_desc* d, const bhac_b
   if (e == cudaSuccess) e = up(c->d_regoff, M.regoff.data(), sizeof(long long) * M.regoff.size());
   if (e == cudaSuccess) e = up(c->d_rcells, M.rcells.data(), sizeof(RefluxCell) * M.rcells.size());
   if (e == cudaSuccess) e = up(c->d_rterms, M.rterms.data(), sizeof(RefluxTerm) * M.rterms.size());
+  if (e == cudaSuccess) e = up(c->ring_dst, ring_dst.data(), sizeof(long long) * ring_dst.size());
+  if (e == cudaSuccess) e = up(c->ring_src, ring_src.data(), sizeof(long long) * ring_src.size());
   if (e == cudaSuccess) e = cudaMemsetAsync(small, 0, 256, c->st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);  // the host maps die here
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->cp_in, cudaStreamNonBlocking);
@@ -510,6 +599,33 @@ bhac_status bhac_set_metric(bhac_ctx* c, int kind, double spin, double mass, con
     M.tab_f2_32 = c->tab_f2_32 + c->toff_f2[l] * FREC;
     if (launch_metric_tables(M, c->st) != cudaSuccess) return BHAC_ERR_CUDA;
   }
+  if (c->ct) {
+    // the same tables on the grid extended by one cell on each side in x1 and
+    // x2, for the faces around each block (a face beyond the polar axis sees
+    // the mirrored metric, which depends on sin^2 and cos^2 of theta only)
+    MetricArgs M;
+    M.coords = kind;
+    M.spin = spin;
+    M.mass = mass;
+    M.dx1 = (c->d.xmax[0] - c->d.xmin[0]) / c->N1g;
+    M.dx2 = (c->d.xmax[1] - c->d.xmin[1]) / c->N2g;
+    M.x1min = c->d.xmin[0] - M.dx1;
+    M.x2min = c->d.xmin[1] - M.dx2;
+    M.N1 = c->N1g + 2;
+    M.N2 = c->N2g + 2;
+    M.axis_lo = M.axis_hi = 0;
+    M.rho_floor = c->d.rho_floor;
+    M.rho_pow = c->d.rho_floor_pow;
+    M.p_floor = c->d.p_floor;
+    M.p_pow = c->d.p_floor_pow;
+    M.tab_c = c->te_c;
+    M.tab_f1 = c->te_f1;
+    M.tab_f2 = c->te_f2;
+    M.tab_c32 = c->te_c32;
+    M.tab_f1_32 = c->te_f1_32;
+    M.tab_f2_32 = c->te_f2_32;
+    if (launch_metric_tables(M, c->st) != cudaSuccess) return BHAC_ERR_CUDA;
+  }
   c->metric_ok = true;
   return BHAC_OK;
 }
@@ -534,6 +650,8 @@ bhac_status bhac_set_prims(bhac_ctx* c, const double* prims, int on_device) {
   if (e != cudaSuccess) return BHAC_ERR_CUDA;
   c->prims_ok = true;
   c->cfl_ok = false;
+  c->faces_ok = false;
+  c->pcur = 0;
   return BHAC_OK;
 }
 
@@ -578,6 +696,8 @@ bhac_status bhac_set_prims_host_async(bhac_ctx* c, const double* host_prims) {
   if (e != cudaSuccess) return BHAC_ERR_CUDA;
   c->prims_ok = true;
   c->cfl_ok = false;
+  c->faces_ok = false;
+  c->pcur = 0;
   return BHAC_OK;
 }
 
@@ -642,9 +762,10 @@ bhac_status bhac_stage(bhac_ctx* c, int stage, double dt) {
   if (!c || (stage != 1 && stage != 2)) return BHAC_ERR_ARG;
   if (!c->prims_ok) return BHAC_ERR_STATE;
   if (stage == 1 && !(dt > 0.0) && !c->cfl_ok) return BHAC_ERR_STATE;
+  if (c->ct && !c->faces_ok) return BHAC_ERR_STATE;
   bhac_status s = ghost_fill(c, c->cur, stage == 2);
   if (s != BHAC_OK) return s;
-  s = run_stage(c, stage, dt);
+  s = c->ct ? run_stage_ct(c, stage, dt) : run_stage(c, stage, dt);
   if (s == BHAC_OK && stage == 2) c->cfl_ok = true;
   return s;
 }
@@ -654,7 +775,8 @@ bhac_status bhac_launches_per_step(const bhac_ctx* c, int* out) {
   int per_fill = 1;  // the ghost gather
   for (size_t dep = 1; dep < c->depth_start.size(); ++dep)
     if (c->depth_start[dep] > c->depth_start[dep - 1]) ++per_fill;  // one cross-level node pass per depth
-  const int per_stage = per_fill + 1 + (c->nrcells > 0 ? 1 : 0);   // + stage kernel (+ reflux)
+  const int per_stage = c->ct ? per_fill + 4  // + ring copy, face fluxes, face update, cells
+                             : per_fill + 1 + (c->nrcells > 0 ? 1 : 0);   // + stage kernel (+ reflux)
   *out = 2 * per_stage;
   return BHAC_OK;
 }
@@ -737,13 +859,14 @@ bhac_status bhac_graph_capture(bhac_ctx* c, int nsteps) {
   }
   if ((c->mixed ? prepare_stage_mixed() : prepare_stage_fp64()) != cudaSuccess) return BHAC_ERR_CUDA;
   if (cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return BHAC_ERR_CUDA;
-  const int cur = c->cur, ucur = c->ucur;
+  const int cur = c->cur, ucur = c->ucur, pcur = c->pcur;
   bhac_status s = BHAC_OK;
   for (int k = 0; k < nsteps && s == BHAC_OK; ++k) s = bhac_step(c, 0.0);
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamEndCapture(c->st, &g);
   c->cur = cur;  // buffer roles return to the same state after every step
   c->ucur = ucur;
+  c->pcur = pcur;
   if (s != BHAC_OK || e != cudaSuccess) {
     if (g) cudaGraphDestroy(g);
     return s != BHAC_OK ? s : BHAC_ERR_CUDA;
@@ -762,6 +885,43 @@ bhac_status bhac_graph_launch(bhac_ctx* c) {
   if (!c) return BHAC_ERR_ARG;
   if (!c->graph) return BHAC_ERR_STATE;
   return cuda_status(cudaGraphLaunch(c->graph, c->st));
+}
+
+bhac_status bhac_set_faces(bhac_ctx* c, const double* faces, int on_device) {
+  if (!c || !faces) return BHAC_ERR_ARG;
+  if (!c->ct || !c->prims_ok) return BHAC_ERR_STATE;
+  const size_t n = (size_t)c->nb * c->ctg.nown_b;
+  const double* src = faces;
+  double* stage_buf = c->xf;  // the flux array is free between stages: it stages a host load
+  if (!on_device) {
+    if (cudaMemcpyAsync(stage_buf, faces, sizeof(double) * n, cudaMemcpyHostToDevice, c->st) != cudaSuccess)
+      return BHAC_ERR_CUDA;
+    src = stage_buf;
+  }
+  c->pcur = 0;
+  StageArgs a = base_args(c);
+  CtArgs t = ct_args(c);
+  cudaError_t e = launch_ct_copy_faces(a, c->ctg, src, c->phi[0], 1, c->st);
+  // the cell field of the loaded primitives from the faces, then U
+  if (e == cudaSuccess) e = launch_ct_cell_field(a, t, c->P[c->cur], c->st);
+  if (e == cudaSuccess) e = launch_init_cons(a, c->P[c->cur], c->U[c->ucur], c->st);
+  if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(c->st);
+  if (e != cudaSuccess) return BHAC_ERR_CUDA;
+  c->faces_ok = true;
+  c->cfl_ok = false;
+  return BHAC_OK;
+}
+
+bhac_status bhac_get_faces(bhac_ctx* c, double* out, int on_device) {
+  if (!c || !out) return BHAC_ERR_ARG;
+  if (!c->ct || !c->faces_ok) return BHAC_ERR_STATE;
+  const size_t n = (size_t)c->nb * c->ctg.nown_b;
+  StageArgs a = base_args(c);
+  double* dst = on_device ? out : c->xf;
+  cudaError_t e = launch_ct_copy_faces(a, c->ctg, c->phi[c->pcur], dst, 0, c->st);
+  if (e == cudaSuccess && !on_device) e = cudaMemcpyAsync(out, dst, sizeof(double) * n, cudaMemcpyDeviceToHost, c->st);
+  if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(c->st);
+  return cuda_status(e);
 }
 
 void bhac_destroy(bhac_ctx* c) {

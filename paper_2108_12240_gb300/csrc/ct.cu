@@ -1,0 +1,413 @@
+// Staggered-mesh constrained transport (the div B control of the method's
+// Sec. 2) on uniform grids, FP64.
+//
+// Evolved field: Phi^d = sqrt(gamma) B^d at the centre of every face normal to
+// an active direction d.  A stage runs, after the usual ghost-cell fill:
+//   ring   the faces one cell outside each block (across, in every active
+//          transverse direction) copied from the neighbour that owns them;
+//   flux   every face of the block and its ring: PPM/minmod states from the
+//          ghosted primitives, the normal field of both states set to the
+//          face's own Phi^d / sqrt(gamma), HLL/TVDLF flux (densitized);
+//   faces  d_t Phi = -curl E on the block's faces, the edge EMF the mean of
+//          the four face fluxes of B around the edge (E_3 = F^2(B^1) =
+//          -F^1(B^2), and cyclically), then the RK stage combination;
+//   cells  flux divergence, sources and RK combination of D, S_i, tau (and of
+//          B^3 in 2-D), cell field sqrt(gamma) B^d = (Phi^d_low + Phi^d_high)/2,
+//          then the inversion, floors and CFL rate of the stage kernel.
+// Both blocks sharing a face compute its update from identical inputs (their
+// ghost cells and ring faces hold the same values), so their copies agree and
+// the discrete divergence sum_d dPhi^d/dx_d of every cell stays at round-off.
+// psi is not evolved (zero), and no cleaning speed enters the fluxes.
+#include <algorithm>
+
+#include "ct.h"
+#include "stage_impl.cuh"
+
+namespace bhac {
+
+CtGeom ct_geom(const bhac_grid_desc* d) {
+  CtGeom g;
+  g.ndim = d->ndim;
+  for (int e = 0; e < 3; ++e) g.nx[e] = d->nx[e];
+  long long off = 0, own = 0;
+  for (int dd = 0; dd < 3; ++dd) {
+    long long nf = 1, no = 1;
+    for (int e = 0; e < 3; ++e) {
+      const bool across = e != dd && e < d->ndim;
+      g.fe[dd][e] = e == dd ? d->nx[e] + 1 : d->nx[e] + (across ? 2 : 0);
+      g.fo[dd][e] = across ? 1 : 0;
+      nf *= g.fe[dd][e];
+      no *= d->nx[e] + (e == dd ? 1 : 0);
+    }
+    if (dd >= d->ndim) nf = no = 0;
+    g.foff[dd] = off;
+    g.nfd[dd] = nf;
+    off += nf;
+    g.own_off[dd] = own;
+    g.nown_d[dd] = no;
+    own += no;
+  }
+  g.nfb = off;
+  g.nown_b = own;
+  return g;
+}
+
+static long long ring_index_h(const CtGeom& g, int d, int i, int j, int k) {
+  return g.foff[d] + ((long long)(k + g.fo[d][2]) * g.fe[d][1] + (j + g.fo[d][1])) * g.fe[d][0] + (i + g.fo[d][0]);
+}
+
+bool ct_ring_map(const bhac_grid_desc* desc, const bhac_block_desc* blocks, int nb, const CtGeom& g,
+                 std::vector<long long>& dst, std::vector<long long>& src) {
+  const int* nr = desc->nroot;
+  std::vector<int> lut((size_t)nr[0] * nr[1] * nr[2], -1);
+  for (int b = 0; b < nb; ++b) lut[((size_t)blocks[b].iz * nr[1] + blocks[b].iy) * nr[0] + blocks[b].ix] = b;
+  long long N[3];
+  for (int e = 0; e < 3; ++e) N[e] = (long long)nr[e] * desc->nx[e];
+  dst.clear();
+  src.clear();
+  for (int b = 0; b < nb; ++b) {
+    const int bc[3] = {blocks[b].ix, blocks[b].iy, blocks[b].iz};
+    for (int d = 0; d < desc->ndim; ++d)
+      for (int k = -g.fo[d][2]; k < g.fe[d][2] - g.fo[d][2]; ++k)
+        for (int j = -g.fo[d][1]; j < g.fe[d][1] - g.fo[d][1]; ++j)
+          for (int i = -g.fo[d][0]; i < g.fe[d][0] - g.fo[d][0]; ++i) {
+            const int f[3] = {i, j, k};
+            bool ring = false;
+            for (int e = 0; e < 3; ++e)
+              if (e != d && (f[e] < 0 || f[e] >= desc->nx[e])) ring = true;
+            if (!ring) continue;
+            long long G[3];
+            for (int e = 0; e < 3; ++e) G[e] = (long long)bc[e] * desc->nx[e] + f[e];
+            // boundary rules across the face (the along-d index is a face index and stays)
+            for (int e = 0; e < desc->ndim; ++e) {
+              if (e == d) continue;
+              const int side = G[e] < 0 ? 0 : (G[e] >= N[e] ? 1 : -1);
+              if (side < 0) continue;
+              const int kind = desc->bc[e][side];
+              if (kind == BHAC_BC_PERIODIC) {
+                G[e] = ((G[e] % N[e]) + N[e]) % N[e];
+              } else if (kind == BHAC_BC_OUTFLOW || kind == BHAC_BC_NOINFLOW) {
+                G[e] = side == 0 ? 0 : N[e] - 1;
+              } else {  // polar axis (x2): mirror, and phi + pi in 3-D
+                G[e] = side == 0 ? -1 - G[e] : 2 * N[e] - 1 - G[e];
+                if (desc->ndim == 3) G[2] = ((G[2] + N[2] / 2) % N[2] + N[2]) % N[2];
+              }
+            }
+            if (desc->ndim == 3 && d != 2 && desc->bc[2][0] == BHAC_BC_PERIODIC) G[2] = ((G[2] % N[2]) + N[2]) % N[2];
+            int ob[3], lf[3];
+            for (int e = 0; e < 3; ++e) {
+              if (G[e] < 0 || G[e] > N[e] || (e != d && G[e] == N[e])) return false;
+              ob[e] = (int)(G[e] / desc->nx[e]);
+              if (e == d && ob[e] >= nr[e]) ob[e] = nr[e] - 1;
+              lf[e] = (int)(G[e] - (long long)ob[e] * desc->nx[e]);
+            }
+            const int o = lut[((size_t)ob[2] * nr[1] + ob[1]) * nr[0] + ob[0]];
+            if (o < 0) return false;
+            dst.push_back((long long)b * g.nfb + ring_index_h(g, d, i, j, k));
+            src.push_back((long long)o * g.nfb + ring_index_h(g, d, lf[0], lf[1], lf[2]));
+          }
+  }
+  return true;
+}
+
+namespace {
+
+__device__ __forceinline__ long long ring_index(const CtGeom& g, int d, int i, int j, int k) {
+  return g.foff[d] + ((long long)(k + g.fo[d][2]) * g.fe[d][1] + (j + g.fo[d][1])) * g.fe[d][0] + (i + g.fo[d][0]);
+}
+
+// flux of variable v through face (d; i, j, k) of block b
+__device__ __forceinline__ double xf_at(const CtArgs& c, int b, int d, int v, int i, int j, int k) {
+  return c.xf[(long long)b * NV * c.g.nfb + NV * c.g.foff[d] + v * c.g.nfd[d] + (ring_index(c.g, d, i, j, k) - c.g.foff[d])];
+}
+
+__global__ void __launch_bounds__(256) ct_ring_kernel(const long long* __restrict__ dst, const long long* __restrict__ src,
+                                                      long long n, double* phi) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
+    phi[dst[t]] = phi[src[t]];
+}
+
+// Flux through face (D; i, j, k) of block b (D a compile-time direction, so
+// the states stay in registers), q its index among the direction's faces.
+template <int D, bool FLAT>
+__device__ __forceinline__ void ct_one_face(const StageArgs& a, const CtArgs& c, int b, int i, int j, int k,
+                                            long long q) {
+  const int G1 = a.blk[4 * b + 1] * a.nx + i, G2 = a.blk[4 * b + 2] * a.ny + j;
+  double F[NV];
+  const bool axis = !FLAT && D == 1 && ((G2 == 0 && c.axis_lo) || (G2 == a.N2g && c.axis_hi));
+  if (axis) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) F[v] = 0.0;
+  } else {
+    const int sd = D == 0 ? 1 : (D == 1 ? a.Nx : a.Nx * a.Ny);
+    const int c0 = ((k + a.gz) * a.Ny + (j + a.gy)) * a.Nx + (i + a.gx);  // the cell above the face
+    const double* Pb = a.P_in + (size_t)b * NV * a.ncell;
+    double PL[NV], PR[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const double* p = Pb + (size_t)v * a.ncell + c0;
+      recon_var(a.recon, p[-3 * sd], p[-2 * sd], p[-sd], p[0], p[sd], p[2 * sd], PL[v], PR[v]);
+    }
+    positivity_fallback(a, Pb, sd, c0, PL, PR);
+    Met<double> m;
+    double acg = 1.0;
+    if (FLAT) {
+      m = flat_metric<double>();
+    } else if (D == 0) {
+      const double* rec = c.te_f1 + ((size_t)(G2 + 1) * (a.N1g + 3) + (G1 + 1)) * FREC;
+      m = load_face_metric<double>(rec);
+      acg = rec[F_ACG];
+    } else if (D == 1) {
+      const double* rec = c.te_f2 + ((size_t)(G2 + 1) * (a.N1g + 2) + (G1 + 1)) * FREC;
+      m = load_face_metric<double>(rec);
+      acg = rec[F_ACG];
+    } else {
+      const double* rec = c.te_c + ((size_t)(G2 + 1) * (a.N1g + 2) + (G1 + 1)) * CREC;
+      m = load_centre_metric<double>(rec);
+      acg = rec[C_ACG3];
+    }
+    const double Bn = c.phi_in[(long long)b * c.g.nfb + ring_index(c.g, D, i, j, k)] / m.sg;
+    PL[B1 + D] = Bn;
+    PR[B1 + D] = Bn;
+    riemann_flux(m, acg, PL, PR, D, a.riemann, a.gam, a.gam_fac, 0.0, F);
+  }
+  const long long o = (long long)b * NV * c.g.nfb + NV * c.g.foff[D] + q;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) c.xf[o + v * c.g.nfd[D]] = F[v];
+}
+
+// Fluxes through every face of every block and its ring, one thread per face.
+template <bool FLAT>
+__global__ void __launch_bounds__(256) ct_flux_kernel(StageArgs a, CtArgs c) {
+  const long long n = (long long)a.nblocks * c.g.nfb;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    const int b = (int)(t / c.g.nfb);
+    const long long r = t - (long long)b * c.g.nfb;
+    const int d = (c.g.ndim == 3 && r >= c.g.foff[2]) ? 2 : (r >= c.g.foff[1] ? 1 : 0);
+    const long long q = r - c.g.foff[d];
+    const int e0 = c.g.fe[d][0], e1 = c.g.fe[d][1];
+    const int i = (int)(q % e0) - c.g.fo[d][0];
+    const int j = (int)((q / e0) % e1) - c.g.fo[d][1];
+    const int k = (int)(q / ((long long)e0 * e1)) - c.g.fo[d][2];
+    if (d == 0)
+      ct_one_face<0, FLAT>(a, c, b, i, j, k, q);
+    else if (d == 1)
+      ct_one_face<1, FLAT>(a, c, b, i, j, k, q);
+    else
+      ct_one_face<2, FLAT>(a, c, b, i, j, k, q);
+  }
+}
+
+// Edge EMFs: E_3 at (i-1/2, j-1/2) of cell layer k, E_1 at (j-1/2, k-1/2) of
+// column i, E_2 at (k-1/2, i-1/2) of row j.
+__device__ __forceinline__ double emf3(const CtArgs& c, int b, int i, int j, int k) {
+  return 0.25 * (xf_at(c, b, 1, B1, i, j, k) + xf_at(c, b, 1, B1, i - 1, j, k) - xf_at(c, b, 0, B2, i, j, k) -
+                 xf_at(c, b, 0, B2, i, j - 1, k));
+}
+__device__ __forceinline__ double emf1(const CtArgs& c, int b, int i, int j, int k) {
+  return 0.25 * (xf_at(c, b, 2, B2, i, j, k) + xf_at(c, b, 2, B2, i, j - 1, k) - xf_at(c, b, 1, B3, i, j, k) -
+                 xf_at(c, b, 1, B3, i, j, k - 1));
+}
+__device__ __forceinline__ double emf2(const CtArgs& c, int b, int i, int j, int k) {
+  return 0.25 * (xf_at(c, b, 0, B3, i, j, k) + xf_at(c, b, 0, B3, i, j, k - 1) - xf_at(c, b, 2, B1, i, j, k) -
+                 xf_at(c, b, 2, B1, i - 1, j, k));
+}
+
+__device__ __forceinline__ void owned_face(const CtGeom& g, long long r, int& d, int& i, int& j, int& k) {
+  d = (g.ndim == 3 && r >= g.own_off[2]) ? 2 : (r >= g.own_off[1] ? 1 : 0);
+  const long long q = r - g.own_off[d];
+  const int n0 = g.nx[0] + (d == 0), n1 = g.nx[1] + (d == 1);
+  i = (int)(q % n0);
+  j = (int)((q / n0) % n1);
+  k = (int)(q / ((long long)n0 * n1));
+}
+
+// d_t Phi = -curl E and the stage combination, one thread per owned face.
+template <int DIM>
+__global__ void __launch_bounds__(256) ct_face_kernel(StageArgs a, CtArgs c) {
+  const double dt = stage_dt(a);
+  const long long n = (long long)a.nblocks * c.g.nown_b;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    const int b = (int)(t / c.g.nown_b);
+    int d, i, j, k;
+    owned_face(c.g, t - (long long)b * c.g.nown_b, d, i, j, k);
+    const long long o = (long long)b * c.g.nfb + ring_index(c.g, d, i, j, k);
+    const int G2 = a.blk[4 * b + 2] * a.ny + j;
+    if (!a.flat && d == 1 && ((G2 == 0 && c.axis_lo) || (G2 == a.N2g && c.axis_hi))) {
+      c.phi_out[o] = 0.0;  // sqrt(gamma) = 0 on the axis
+      continue;
+    }
+    double R;
+    if (d == 0) {
+      R = -(emf3(c, b, i, j + 1, k) - emf3(c, b, i, j, k)) / a.dxl0[1];
+      if (DIM == 3) R += (emf2(c, b, i, j, k + 1) - emf2(c, b, i, j, k)) / a.dxl0[2];
+    } else if (d == 1) {
+      R = (emf3(c, b, i + 1, j, k) - emf3(c, b, i, j, k)) / a.dxl0[0];
+      if (DIM == 3) R -= (emf1(c, b, i, j, k + 1) - emf1(c, b, i, j, k)) / a.dxl0[2];
+    } else {
+      R = -(emf2(c, b, i + 1, j, k) - emf2(c, b, i, j, k)) / a.dxl0[0] +
+          (emf1(c, b, i, j + 1, k) - emf1(c, b, i, j, k)) / a.dxl0[1];
+    }
+    if (a.stage == 1)
+      c.phi_out[o] = c.phi_in[o] + dt * R;
+    else
+      c.phi_out[o] = 0.5 * c.phi_n[o] + 0.5 * (c.phi_in[o] + dt * R);
+  }
+}
+
+// Flux divergence, sources, RK combination, the cell field from the updated
+// faces, then the stage kernel's inversion, floors, outputs and CFL rate.
+template <int DIM, bool FLAT>
+__global__ void __launch_bounds__(256) ct_cell_kernel(StageArgs a, CtArgs c) {
+  const double dt = stage_dt(a);
+  if (a.stage == 1 && blockIdx.x == 0 && threadIdx.x == 0) *a.dt_dev = dt;
+  unsigned cnt[4] = {0u, 0u, 0u, 0u};
+  double rate_max = 0.0;
+  const LevelGeo geo = level_geo(a, 0);
+  const long long n = (long long)a.nblocks * a.nint;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    const int b = (int)(t / a.nint);
+    const int ci = (int)(t - (long long)b * a.nint);
+    const int i = ci % a.nx, j = (ci / a.nx) % a.ny, k = ci / (a.nx * a.ny);
+    const int cg = ((k + a.gz) * a.Ny + (j + a.gy)) * a.Nx + (i + a.gx);
+    const int I1 = a.blk[4 * b + 1] * a.nx + i, I2 = a.blk[4 * b + 2] * a.ny + j;
+    double rhs[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) rhs[v] = 0.0;
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+      const int ih = i + (d == 0), jh = j + (d == 1), kh = k + (d == 2);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) rhs[v] += -(xf_at(c, b, d, v, ih, jh, kh) - xf_at(c, b, d, v, i, j, k)) / a.dxl0[d];
+    }
+    if (!FLAT) {
+      const double* crec = geo.tc + (size_t)(I2 * geo.N1 + I1) * CREC;
+      double Pc[NV], Uc[NV], S[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) Pc[v] = a.P_in[(size_t)b * NV * a.ncell + (size_t)v * a.ncell + cg];
+      const Met<double> m = load_centre_metric<double>(crec);
+      Derived<double> s;
+      derive(m, Pc, a.gam_fac, s);
+      cons_of(Pc, s, Uc);
+      sources_of(m, crec, Pc, s, Uc, 0.0, 0.0, S);
+      const double sg = crec[C_SG];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) rhs[v] += sg * S[v];
+    }
+    const size_t ub = (size_t)b * NV * a.nint + ci;
+    double U[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const double un = a.Un[ub + (size_t)v * a.nint];
+      U[v] = a.stage == 1 ? un + dt * rhs[v] : 0.5 * un + 0.5 * (a.U1[ub + (size_t)v * a.nint] + dt * rhs[v]);
+    }
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+      const long long lo = (long long)b * c.g.nfb + ring_index(c.g, d, i, j, k);
+      const long long hi = (long long)b * c.g.nfb + ring_index(c.g, d, i + (d == 0), j + (d == 1), k + (d == 2));
+      U[B1 + d] = 0.5 * (c.phi_out[lo] + c.phi_out[hi]);
+    }
+    U[PSI] = 0.0;
+    finish_cell<double, DIM, FLAT>(a, geo, b, ci, cg, I1, I2, U, cnt, rate_max);
+  }
+  reduce_outputs(a, cnt, rate_max);
+}
+
+// The cell field of the loaded state from its faces.
+template <int DIM>
+__global__ void __launch_bounds__(256) ct_cell_field_kernel(StageArgs a, CtArgs c, double* P) {
+  const long long n = (long long)a.nblocks * a.nint;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    const int b = (int)(t / a.nint);
+    const int ci = (int)(t - (long long)b * a.nint);
+    const int i = ci % a.nx, j = (ci / a.nx) % a.ny, k = ci / (a.nx * a.ny);
+    const int cg = ((k + a.gz) * a.Ny + (j + a.gy)) * a.Nx + (i + a.gx);
+    double sg = 1.0;
+    if (!a.flat) {
+      const int I1 = a.blk[4 * b + 1] * a.nx + i, I2 = a.blk[4 * b + 2] * a.ny + j;
+      sg = a.tab_c[(size_t)(I2 * a.N1g + I1) * CREC + C_SG];
+    }
+    double* Pc = P + (size_t)b * NV * a.ncell + cg;
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+      const long long lo = (long long)b * c.g.nfb + ring_index(c.g, d, i, j, k);
+      const long long hi = (long long)b * c.g.nfb + ring_index(c.g, d, i + (d == 0), j + (d == 1), k + (d == 2));
+      Pc[(size_t)(B1 + d) * a.ncell] = 0.5 * (c.phi_in[lo] + c.phi_in[hi]) / sg;
+    }
+    Pc[(size_t)PSI * a.ncell] = 0.0;
+  }
+}
+
+__global__ void __launch_bounds__(256) ct_copy_kernel(int nblocks, CtGeom g, const double* __restrict__ src, double* dst,
+                                                      int to_ring) {
+  const long long n = (long long)nblocks * g.nown_b;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    const int b = (int)(t / g.nown_b);
+    int d, i, j, k;
+    owned_face(g, t - (long long)b * g.nown_b, d, i, j, k);
+    const long long o = (long long)b * g.nfb + ring_index(g, d, i, j, k);
+    if (to_ring)
+      dst[o] = src[t];
+    else
+      dst[t] = src[o];
+  }
+}
+
+int grid_of(long long n) {
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  long long g = (n + 255) / 256;
+  const long long cap = 32LL * nsm;
+  if (g > cap) g = cap;
+  return g < 1 ? 1 : (int)g;
+}
+
+}  // namespace
+
+cudaError_t launch_ct_ring(const long long* dst, const long long* src, long long n, double* phi, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  ct_ring_kernel<<<grid_of(n), 256, 0, st>>>(dst, src, n, phi);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ct_stage(const StageArgs& a, const CtArgs& c, cudaStream_t st) {
+  const long long nf = (long long)a.nblocks * c.g.nfb, no = (long long)a.nblocks * c.g.nown_b,
+                  nc = (long long)a.nblocks * a.nint;
+  if (a.flat)
+    ct_flux_kernel<true><<<grid_of(nf), 256, 0, st>>>(a, c);
+  else
+    ct_flux_kernel<false><<<grid_of(nf), 256, 0, st>>>(a, c);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if (a.ndim == 3)
+    ct_face_kernel<3><<<grid_of(no), 256, 0, st>>>(a, c);
+  else
+    ct_face_kernel<2><<<grid_of(no), 256, 0, st>>>(a, c);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if (a.ndim == 3)
+    a.flat ? ct_cell_kernel<3, true><<<grid_of(nc), 256, 0, st>>>(a, c)
+           : ct_cell_kernel<3, false><<<grid_of(nc), 256, 0, st>>>(a, c);
+  else
+    a.flat ? ct_cell_kernel<2, true><<<grid_of(nc), 256, 0, st>>>(a, c)
+           : ct_cell_kernel<2, false><<<grid_of(nc), 256, 0, st>>>(a, c);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ct_cell_field(const StageArgs& a, const CtArgs& c, double* P, cudaStream_t st) {
+  const long long nc = (long long)a.nblocks * a.nint;
+  if (a.ndim == 3)
+    ct_cell_field_kernel<3><<<grid_of(nc), 256, 0, st>>>(a, c, P);
+  else
+    ct_cell_field_kernel<2><<<grid_of(nc), 256, 0, st>>>(a, c, P);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ct_copy_faces(const StageArgs& a, const CtGeom& g, const double* src, double* dst, int to_ring,
+                                 cudaStream_t st) {
+  ct_copy_kernel<<<grid_of((long long)a.nblocks * g.nown_b), 256, 0, st>>>(a.nblocks, g, src, dst, to_ring);
+  return cudaGetLastError();
+}
+
+}  // namespace bhac

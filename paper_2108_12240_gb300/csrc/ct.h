@@ -1,0 +1,53 @@
+// Staggered-mesh constrained transport on uniform grids: face-field layout,
+// the host-built map of the ring faces, and the kernel launchers (ct.cu).
+#pragma once
+
+#include <vector>
+
+#include "../../include/bhac_gb300.h"
+#include "bhac_device.cuh"
+
+namespace bhac {
+
+// Per block, for each active direction d: the face field Phi^d = sqrt(gamma) B^d
+// (and the NV fluxes) on the faces normal to d, over the block's own faces
+// (index 0..nx_d along d, the block's cells across) plus a ring of one face
+// across in every active transverse direction.  fe[d][e]: extent along e;
+// fo[d][e]: where local index 0 sits inside it; foff[d]: first face of
+// direction d inside one block's record; nfb: faces per block.
+struct CtGeom {
+  int ndim, nx[3];
+  int fe[3][3], fo[3][3];
+  long long foff[3], nfd[3], nfb;
+  long long own_off[3], nown_d[3], nown_b;  // owned faces only (the public layout)
+};
+
+CtGeom ct_geom(const bhac_grid_desc* d);
+
+// Ring faces: for every block and ring slot, the Phi index it copies (a face
+// owned by the neighbour across, after the boundary rules).  Returns false if a
+// rule points at a missing block.
+bool ct_ring_map(const bhac_grid_desc* d, const bhac_block_desc* b, int nb, const CtGeom& g,
+                 std::vector<long long>& dst, std::vector<long long>& src);
+
+struct CtArgs {
+  CtGeom g;
+  const double* phi_in;   // Phi of the stage's input state, ring filled
+  double* phi_out;        // Phi written by the face update
+  const double* phi_n;    // Phi at the start of the step (stage 2)
+  double* xf;             // fluxes [block][d][var][face], ring-extended
+  const double* te_c;     // metric records on the grid extended by one cell each side in x1, x2
+  const double* te_f1;
+  const double* te_f2;
+  int axis_lo, axis_hi;   // polar axis at the low / high x2 boundary
+};
+
+cudaError_t launch_ct_ring(const long long* dst, const long long* src, long long n, double* phi, cudaStream_t st);
+cudaError_t launch_ct_stage(const StageArgs& a, const CtArgs& c, cudaStream_t st);
+// B^d of the interior cells of P from the faces, psi = 0 (after a face load)
+cudaError_t launch_ct_cell_field(const StageArgs& a, const CtArgs& c, double* P, cudaStream_t st);
+// owned faces <-> the ring layout
+cudaError_t launch_ct_copy_faces(const StageArgs& a, const CtGeom& g, const double* src, double* dst, int to_ring,
+                                 cudaStream_t st);
+
+}  // namespace bhac

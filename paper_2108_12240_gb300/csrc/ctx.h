@@ -6,6 +6,7 @@
 
 #include "../../include/bhac_gb300.h"
 #include "amr.h"
+#include "ct.h"
 #include "launch.h"
 
 struct bhac_ctx {
@@ -59,6 +60,19 @@ struct bhac_ctx {
   bhac::RefluxCell* d_rcells;
   bhac::RefluxTerm* d_rterms;
   int nrcells;
+  // constrained transport (uniform grids, FP64): face fields in ring layout
+  // (two buffers, pcur the current state's), ring-extended face fluxes, the
+  // metric records on the grid extended by one cell in x1 and x2, and the
+  // ring-face copy map
+  bool ct, faces_ok;
+  bhac::CtGeom ctg;
+  double* phi[2];
+  int pcur;
+  double* xf;
+  double *te_c, *te_f1, *te_f2;
+  float *te_c32, *te_f1_32, *te_f2_32;
+  long long *ring_dst, *ring_src;
+  long long nring;
   // captured steps
   cudaGraphExec_t graph;
   int graph_steps;
