@@ -179,18 +179,25 @@ def job_value(cells: int, world: int, ms_per_step: float) -> float:
 TUNE = True
 
 
-def time_form(gb, torch, g, P, form, steps, warmup, stream, count_flops=True, graph_repeats=3, graph_steps=1):
+def time_form(gb, torch, g, P, form, steps, warmup, stream, count_flops=True, graph_repeats=3, graph_steps=1,
+              faces=None):
     """Device-resident timing of `steps` steps of one form (direct launches,
     per-stage events), then the same step replayed from a CUDA graph:
-    median over `graph_repeats` repeats of `graph_steps` replays."""
+    median over `graph_repeats` repeats of `graph_steps` replays.  With
+    `faces` the grid runs constrained transport (its own kernels: no launch
+    shape to tune)."""
     from paper_2108_12240_gb300 import autotune
 
     s = gb.Solver(g, form, stream=stream)
-    if TUNE:
+    if faces is not None:
+        shape, tried = (0, 0, 0, 0, 0, 0), {}
+    elif TUNE:
         shape, tried = autotune.tune(s, P)  # launch shape for this grid and form (outside the timed region)
     else:
         shape, tried = autotune.cached_or_default(s), {}
     s.set_prims(P)
+    if faces is not None:
+        s.set_faces(faces)
     dt = s.cfl_dt()
     for _ in range(warmup):
         s.step(0.0)  # device dt: the same path as the timed loop
@@ -290,7 +297,7 @@ def fill_roofline(g, form: str, fill_ms: float, hbm_gbs):
     flag byte."""
     ghosts = g.nb * (int(np.prod([g.nx[d] + (2 * g.ng if d < g.ndim else 0) for d in range(3)]))
                      - int(np.prod(g.nx)))
-    fill_bytes = ghosts * (NVAR * (8 if form == "fp64" else 4) * 2 + 5)
+    fill_bytes = ghosts * (NVAR * (4 if form == "mixed" else 8) * 2 + 5)
     gbs = fill_bytes / (fill_ms * 1e-3) / 1e9 if fill_ms > 0 else None
     return {"bound": "hbm", "achieved": gbs, "peak": hbm_gbs, "unit": "GB/s",
             "frac": gbs / hbm_gbs if (gbs and hbm_gbs) else None,
@@ -576,6 +583,7 @@ def main():
     ap.add_argument("--form", default="both", choices=["both", "mixed", "fp64"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-ct", action="store_true", help="skip the constrained-transport form")
     ap.add_argument("--sweep-blocks", action="store_true", help="block-shape roofline sweep instead of the bench line")
     ap.add_argument("--all-configs", action="store_true", help="every workload configuration, one line each")
     ap.add_argument("--shape-runs", nargs="+", metavar="FORM_OR_SHAPE",
@@ -624,13 +632,24 @@ def main():
     P = initial_prims(g)
     stream = torch.cuda.Stream()
     forms = ["mixed", "fp64"] if args.form == "both" else [args.form]
+    ct_faces = None
+    if args.form == "both" and not args.no_ct and g.nlevels == 1 and g.coords == "mks":
+        # constrained transport beside the cleaning forms: the same torus with
+        # its loop field as face fields, FP64
+        from problems import ct as pct
+        ct_faces = pct.fm_torus_faces(g, P)
+        forms.append("fp64_ct")
     results = {}
     for form in forms:
         if dist:
             dist.barrier()
         torch.cuda.synchronize()
         with Clocks(local) as ck:
-            results[form] = time_form(gb, torch, g, P, form, args.steps, args.warmup, stream)
+            if form == "fp64_ct":
+                results[form] = time_form(gb, torch, g.with_(divb="ct"), P, "fp64", args.steps, args.warmup, stream,
+                                          faces=ct_faces)
+            else:
+                results[form] = time_form(gb, torch, g, P, form, args.steps, args.warmup, stream)
         results[form]["clocks"] = ck.summary()
         results[form]["ms_per_step"] = aggregate_ms(results[form]["ms_per_step"], dist, "cuda")
         # each rank advances its own full replica (weak scaling)
@@ -661,11 +680,14 @@ def main():
         stage_s = r["stage_ms_mean"] * 1e-3
         cells = g.ncells
         ach64 = fl["fp64_flops"] * cells / stage_s / 1e12
-        bytes_alg = (288 if form == "fp64" else 252) * cells
+        # FP64: 288 B per zone-stage; mixed: 252; constrained
+        # transport adds the face fields read and written (3 x 8 B each way)
+        bytes_alg = {"fp64": 288, "mixed": 252, "fp64_ct": 336}[form] * cells
         traffic = recorded_traffic(args.workload, form, shape_key(r["launch_shape"]))
         fill = fill_roofline(g, form, r["fill_ms"], pk.get("hbm_gbs"))
         return {"bound": "alu", "achieved": ach64, "peak": alu["fp64_tflops"], "unit": "TFLOP/s",
-                "frac": ach64 / alu["fp64_tflops"], "traffic": traffic, "kernel": "stage_kernel",
+                "frac": ach64 / alu["fp64_tflops"], "traffic": traffic,
+                "kernel": "ct_flux/ct_face/ct_cell kernels" if form == "fp64_ct" else "stage_kernel",
                 "traffic_source": os.path.relpath(TRAFFIC_FILE, ROOT) if traffic else None,
                 "traffic_over_algorithmic": traffic / bytes_alg if traffic else None,
                 "stage_ms": r["stage_ms_mean"], "ghost_fill_ms": r["fill_ms"],

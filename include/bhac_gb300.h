@@ -83,6 +83,11 @@ typedef struct {
                             BHAC_DIVB_CT: staggered-mesh constrained transport of face
                             fields (uniform grids, nlevels = 1, FP64 form; psi stays 0,
                             ch and kappa are ignored) */
+  int imex;              /* 0: the cleaning damping -alpha kappa psi is an explicit source
+                            of both stages; 1: it is the implicit part of the IMEX-SSP2(2,2,2)
+                            scheme (Pareschi & Russo 2005) whose explicit part is the SSP-RK2
+                            step, so any kappa dt is stable (Sec. 2: implicit/explicit time
+                            stepping for stiff sources).  Ignored with constrained transport. */
 } bhac_grid_desc;
 
 /* One leaf block: refinement level and integer block coordinates at that level. */
@@ -262,7 +267,7 @@ bhac_status bhac_get_diagnostics(bhac_ctx* ctx, long long counts[4]);
  * cross-level node pass per dependency depth (AMR grids), the ghost gather,
  * the stage kernel and, where levels meet, the reflux kernel; with constrained
  * transport the ghost gather, the ring-face copy, the face-flux, face-update
- * and cell kernels. */
+ * and cell kernels; with IMEX one more pass before stage 1. */
 bhac_status bhac_launches_per_step(const bhac_ctx* ctx, int* launches);
 
 /* Kernel launch shape of the stage kernel: tile of tx x ty cells per CTA column

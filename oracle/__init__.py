@@ -55,7 +55,7 @@ class OrParams(C.Structure):
         ("gamma_ad", C.c_double), ("cfl", C.c_double), ("ch", C.c_double), ("kappa", C.c_double),
         ("c2p_tol", C.c_double), ("c2p_maxit", C.c_int),
         ("rho_floor", C.c_double), ("rho_floor_pow", C.c_double), ("p_floor", C.c_double),
-        ("p_floor_pow", C.c_double), ("w_max", C.c_double), ("ct", C.c_int),
+        ("p_floor_pow", C.c_double), ("w_max", C.c_double), ("ct", C.c_int), ("imex", C.c_int),
     ]
 
 
@@ -132,6 +132,7 @@ def params_of(grid) -> OrParams:
     p.p_floor_pow = grid.p_floor_pow
     p.w_max = grid.w_max
     p.ct = 1 if getattr(grid, "divb", "glm") == "ct" else 0
+    p.imex = 1 if getattr(grid, "imex", False) else 0
     return p
 
 

@@ -294,7 +294,8 @@ void or_sources(const or_params* p, const or_metric* m, const double P[OR_NV], d
   for (int j = 0; j < 3; ++j) t -= Sup[j] * m->da[j];
   S[OR_TAU] = t;
   double divb = m->db[0][0] + m->db[1][1] + m->db[2][2];
-  double ps = -m->alpha * p->kappa * s.psi - s.psi * divb;
+  double damp = p->imex ? 0.0 : p->kappa; /* with IMEX the damping is the implicit part */
+  double ps = -m->alpha * damp * s.psi - s.psi * divb;
   for (int i = 0; i < 3; ++i) ps += p->ch * p->ch * s.B[i] * m->da[i];
   S[OR_PSI] = ps;
 }
@@ -1350,6 +1351,24 @@ static void update_block(or_ctx* c, int b, int stage, double dt, long long cnt[4
             U[v] = 0.5 * c->un[u] + 0.5 * (c->ucur[u] + dt * rhs[v]);
           }
         }
+        if (c->p.imex && !c->p.ct) {
+          /* IMEX-SSP2(2,2,2) (Pareschi & Russo 2005; gamma = 1 - 1/sqrt 2) for
+           * the stiff damping S(psi) = -lam psi, lam = alpha kappa, with the
+           * explicit SSP-RK2 part above:
+           *   Y1 = psi_n / (1 + gamma z),  z = lam dt     (stage 1's fluxes see Y1)
+           *   Y2 = (psi_n + dt F(Y1) - (1 - 2 gamma) z Y1) / (1 + gamma z)
+           *   psi = psi_n + dt/2 (F(Y1) + F(Y2)) - z/2 (Y1 + Y2),
+           * written with U1 = Y2 and the stage-2 explicit combination. */
+          const double g = 1.0 - 1.0 / sqrt(2.0);
+          const double z = m.alpha * c->p.kappa * dt;
+          size_t u = uidx(c, b, OR_PSI, i, j, k);
+          double y1 = c->un[u] / (1.0 + g * z);
+          if (stage == 1)
+            U[OR_PSI] = (c->un[u] + dt * rhs[OR_PSI] - (1.0 - 2.0 * g) * z * y1) / (1.0 + g * z);
+          else
+            U[OR_PSI] = 0.5 * c->un[u] + 0.5 * (c->ucur[u] + dt * rhs[OR_PSI]) - 0.5 * z * (1.0 - g) * c->ucur[u] -
+                        g * z * y1;
+        }
         if (c->p.ct) {
           /* the field along active directions is the mean of the updated faces */
           for (int d = 0; d < c->p.ndim; ++d) {
@@ -1375,7 +1394,27 @@ static void update_block(or_ctx* c, int b, int stage, double dt, long long cnt[4
       }
 }
 
+/* IMEX stage 1: the fluxes are evaluated at Y1, whose psi is
+ * psi_n / (1 + gamma alpha kappa dt) (the implicit first stage); the other
+ * primitives are those of U_n. */
+static void imex_first_stage_psi(or_ctx* c, double dt) {
+  const double g = 1.0 - 1.0 / sqrt(2.0);
+  const int* nx = c->p.nx;
+  for (int b = 0; b < c->nb; ++b)
+    for (int k = 0; k < nx[2]; ++k)
+      for (int j = 0; j < nx[1]; ++j)
+        for (int i = 0; i < nx[0]; ++i) {
+          double x[3];
+          or_metric m;
+          cell_centre(c, b, i, j, k, x);
+          or_metric_at(&c->p, x, 0, &m);
+          size_t q = pidx(c, b, OR_PSI, i + c->gd[0], j + c->gd[1], k + c->gd[2]);
+          c->prim[q] = c->prim[q] / (1.0 + g * m.alpha * c->p.kappa * dt);
+        }
+}
+
 void or_stage_blocks(or_ctx* c, int stage, double dt, int nsel, const int* sel) {
+  if (c->p.imex && !c->p.ct && stage == 1) imex_first_stage_psi(c, dt);
   or_fill_ghosts(c);
   if (c->p.ct) {
     /* constrained transport (uniform grids): ring faces, ring-extended fluxes,

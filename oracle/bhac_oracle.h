@@ -65,6 +65,8 @@ typedef struct {
   double rho_floor, rho_floor_pow, p_floor, p_floor_pow, w_max;
   int ct;                /* 0: GLM cleaning; 1: staggered-mesh constrained transport
                             (uniform grids; psi is not evolved, ch and kappa are ignored) */
+  int imex;              /* 0: the cleaning damping -alpha kappa psi is an explicit source;
+                            1: it is the implicit part of IMEX-SSP2(2,2,2) */
 } or_params;
 
 /* Spatial metric at a point plus its first derivatives along the code

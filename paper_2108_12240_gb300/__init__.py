@@ -44,7 +44,7 @@ class GridDesc(C.Structure):
         ("riemann", C.c_int), ("precision", C.c_int), ("gamma_ad", C.c_double), ("cfl", C.c_double),
         ("ch", C.c_double), ("kappa", C.c_double), ("c2p_tol", C.c_double), ("c2p_maxit", C.c_int),
         ("rho_floor", C.c_double), ("rho_floor_pow", C.c_double), ("p_floor", C.c_double),
-        ("p_floor_pow", C.c_double), ("w_max", C.c_double), ("divb", C.c_int),
+        ("p_floor_pow", C.c_double), ("w_max", C.c_double), ("divb", C.c_int), ("imex", C.c_int),
     ]
 
 
@@ -296,6 +296,7 @@ def desc_of(grid, precision: str = "fp64") -> GridDesc:
     d.p_floor_pow = grid.p_floor_pow
     d.w_max = grid.w_max
     d.divb = 1 if getattr(grid, "divb", "glm") == "ct" else 0
+    d.imex = 1 if getattr(grid, "imex", False) else 0
     return d
 
 

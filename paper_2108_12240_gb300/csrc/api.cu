@@ -2,6 +2,7 @@
 // launch sequence of a step.  No device memory is allocated here: every
 // device array is a slice of the caller's arena.
 #include <nvtx3/nvToolsExt.h>
+#include <math.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -55,6 +56,7 @@ bool valid_desc(const bhac_grid_desc* d, const bhac_block_desc* b, int nb) {
   // constrained transport: uniform grids in the FP64 form
   if (d->divb < 0 || d->divb > 1) return false;
   if (d->divb == BHAC_DIVB_CT && (d->nlevels != 1 || d->precision != BHAC_PREC_FP64)) return false;
+  if (d->imex < 0 || d->imex > 1) return false;
   // the axis rule is for x2 (theta) only; phi must be periodic with an even cell count in 3-D
   for (int k = 0; k < 3; ++k)
     for (int s = 0; s < 2; ++s)
@@ -213,6 +215,8 @@ StageArgs base_args(const bhac_ctx* c) {
   a.c2p_tol = d.c2p_tol;
   a.c2p_maxit = d.c2p_maxit;
   a.wmax = d.w_max;
+  a.imex = d.imex && !c->ct;
+  a.imex_g = 1.0 - 1.0 / sqrt(2.0);
   a.c2p_gf = (d.gamma_ad - 1.0) / d.gamma_ad;
   a.c2p_v2max = 1.0 - 1.0 / (d.w_max * d.w_max);
   a.rho_fl_c = d.rho_floor;
@@ -763,6 +767,15 @@ bhac_status bhac_stage(bhac_ctx* c, int stage, double dt) {
   if (!c->prims_ok) return BHAC_ERR_STATE;
   if (stage == 1 && !(dt > 0.0) && !c->cfl_ok) return BHAC_ERR_STATE;
   if (c->ct && !c->faces_ok) return BHAC_ERR_STATE;
+  if (stage == 1 && c->d.imex && !c->ct) {
+    // the IMEX first stage: the fluxes of stage 1 see psi of Y1
+    StageArgs a = base_args(c);
+    a.stage = 1;
+    a.dt_host = dt;
+    a.P_in = c->P[c->cur];
+    a.P32_in = c->P32[c->cur];
+    if (launch_imex_first_stage(a, c->P[c->cur], c->P32[c->cur], c->st) != cudaSuccess) return BHAC_ERR_CUDA;
+  }
   bhac_status s = ghost_fill(c, c->cur, stage == 2);
   if (s != BHAC_OK) return s;
   s = c->ct ? run_stage_ct(c, stage, dt) : run_stage(c, stage, dt);
@@ -777,7 +790,7 @@ bhac_status bhac_launches_per_step(const bhac_ctx* c, int* out) {
     if (c->depth_start[dep] > c->depth_start[dep - 1]) ++per_fill;  // one cross-level node pass per depth
   const int per_stage = c->ct ? per_fill + 4  // + ring copy, face fluxes, face update, cells
                              : per_fill + 1 + (c->nrcells > 0 ? 1 : 0);   // + stage kernel (+ reflux)
-  *out = 2 * per_stage;
+  *out = 2 * per_stage + (c->d.imex && !c->ct ? 1 : 0);  // + the IMEX first-stage pass
   return BHAC_OK;
 }
 

@@ -23,6 +23,10 @@ cudaError_t launch_cfl(const StageArgs& a, cudaStream_t st);
 cudaError_t prepare_stage_fp64();
 cudaError_t prepare_stage_mixed();
 
+// IMEX first stage (imex.cu): psi of the interior primitives (FP64 and, in the
+// mixed form, FP32) scaled by 1 / (1 + gamma alpha kappa dt)
+cudaError_t launch_imex_first_stage(const StageArgs& a, double* P, float* P32, cudaStream_t st);
+
 // auxiliary kernels (aux.cu)
 struct GhostArgs {
   const int* src;               // per (block, slot): source ghosted-cell index over all blocks,

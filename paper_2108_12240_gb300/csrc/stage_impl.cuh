@@ -585,13 +585,16 @@ __device__ __forceinline__ void cell_update(const StageArgs& a, const LevelGeo& 
     rdiv[v] = r;
   }
   double rhs[NV];
+  // explicit damping rate of the cleaning source (with IMEX it is implicit)
+  const double kap_x = a.imex ? 0.0 : a.kappa;
+  const float kap_xf = a.imex ? 0.f : a.kappa_f;
   // sources from the cell's primitives
   {
     T Pc[NV], Uc[NV], S[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) Pc[v] = Pb[(size_t)v * a.ncell + cg];
     if (FLAT) {
-      rdiv[PSI] = rdiv[PSI] - pick<T>(a.kappa, a.kappa_f) * Pc[PSI];
+      rdiv[PSI] = rdiv[PSI] - pick<T>(kap_x, kap_xf) * Pc[PSI];
 #pragma unroll
       for (int v = 0; v < NV; ++v) rhs[v] = to_double(rdiv[v]);
     } else {
@@ -606,9 +609,9 @@ __device__ __forceinline__ void cell_update(const StageArgs& a, const LevelGeo& 
       derive(m, Pc, pick<T>(a.gam_fac, a.gam_fac_f), s);
       cons_of(Pc, s, Uc);
       if (sizeof(T) == 8)
-        sources_of(m, crec, Pc, s, Uc, pick<T>(a.kappa, a.kappa_f), pick<T>(a.ch * a.ch, a.ch2_f), S);
+        sources_of(m, crec, Pc, s, Uc, pick<T>(kap_x, kap_xf), pick<T>(a.ch * a.ch, a.ch2_f), S);
       else
-        sources_of(m, geo.tc32 + (size_t)(I2 * geo.N1 + I1) * CREC, Pc, s, Uc, pick<T>(a.kappa, a.kappa_f),
+        sources_of(m, geo.tc32 + (size_t)(I2 * geo.N1 + I1) * CREC, Pc, s, Uc, pick<T>(kap_x, kap_xf),
                    pick<T>(a.ch * a.ch, a.ch2_f),
                    S);
       if (sizeof(T) == 8) {
@@ -632,6 +635,21 @@ __device__ __forceinline__ void cell_update(const StageArgs& a, const LevelGeo& 
       U[v] = un + dt * rhs[v];
     else
       U[v] = 0.5 * un + 0.5 * (a.U1[ub + (size_t)v * a.nint] + dt * rhs[v]);
+  }
+  if (a.imex) {
+    // IMEX-SSP2(2,2,2) for the damping -lam psi (lam = alpha kappa, z = lam dt):
+    // Y1 = psi_n/(1 + g z); stage 1: Y2 = (psi_n + dt F(Y1) - (1 - 2g) z Y1)/(1 + g z);
+    // stage 2: psi = psi_n/2 + (Y2 + dt F(Y2))/2 - z (1 - g) Y2 / 2 - g z Y1
+    const double al = FLAT ? 1.0 : geo.tc[(size_t)(I2 * geo.N1 + I1) * CREC + C_AL];
+    const double z = al * a.kappa * dt, g = a.imex_g;
+    const double un = a.Un[ub + (size_t)PSI * a.nint];
+    const double y1 = un / (1.0 + g * z);
+    if (a.stage == 1) {
+      U[PSI] = (un + dt * rhs[PSI] - (1.0 - 2.0 * g) * z * y1) / (1.0 + g * z);
+    } else {
+      const double u1 = a.U1[ub + (size_t)PSI * a.nint];
+      U[PSI] = 0.5 * un + 0.5 * (u1 + dt * rhs[PSI]) - 0.5 * z * (1.0 - g) * u1 - g * z * y1;
+    }
   }
   // cells next to a face bordering finer blocks are finished by the reflux pass
   const bool later = cfb && (((cfb & 1u) && x0 + i == 0) || ((cfb & 2u) && x0 + i == a.nx - 1) ||
@@ -949,7 +967,11 @@ __global__ void __launch_bounds__(128) reflux_kernel(StageArgs a) {
         for (int m = 0; m < T_.nfine; ++m) acc += a.reg[T_.fine[m] + (long long)v * T_.fstride];
         const double Ff = acc / T_.nfine;
         const double Fc = a.reg[T_.coarse + (long long)v * T_.cstride];
-        U[v] += w * (Ff - Fc);
+        // the IMEX first stage divides the explicit increment of psi by 1 + g z
+        const double wv = (v == PSI && a.imex && a.stage == 1)
+                              ? w / (1.0 + a.imex_g * geo.tc[(size_t)(rc.I2 * geo.N1 + rc.I1) * CREC + C_AL] * a.kappa * dt)
+                              : w;
+        U[v] += wv * (Ff - Fc);
       }
     }
     finish_cell<T, DIM, FLAT>(a, geo, rc.b, rc.ci, rc.cg, rc.I1, rc.I2, U, cnt, rate_max);

@@ -44,6 +44,7 @@ class Grid:
     p_floor_pow: float = 0.0
     w_max: float = 50.0
     divb: str = "glm"         # "glm" (cleaning) or "ct" (constrained transport, uniform grids)
+    imex: bool = False        # cleaning damping as the implicit part of IMEX-SSP2(2,2,2)
     ng: int = 3
     nlevels: int = 1
     blocks: np.ndarray = field(default=None, repr=False)  # (nb, 4) int32: level, ix, iy, iz

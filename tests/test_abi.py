@@ -94,3 +94,12 @@ def test_constrained_transport_descriptors():
     with pytest.raises(gb.BhacError) as e:
         gb.bhac_query_sizes(gb.desc_of(amr), gb.blocks_of(amr))
     assert e.value.status == 1
+
+
+def test_imex_flag_is_validated():
+    g = pb.shock_tube_2d(nblock=16, nroot=2)
+    d = gb.desc_of(g)
+    d.imex = 2
+    with pytest.raises(gb.BhacError) as e:
+        gb.bhac_query_sizes(d, gb.blocks_of(g))
+    assert e.value.status == 1
