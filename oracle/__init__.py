@@ -94,6 +94,11 @@ def lib():
         L.or_c2p_status.argtypes = [C.c_void_p, C.c_void_p]
         L.or_ghosted_cells.argtypes = [C.c_void_p]
         L.or_ghosted_cells.restype = C.c_int
+        L.or_estimate.argtypes = [C.c_void_p, C.c_double, _DP]
+        L.or_regrid_plan.argtypes = [C.POINTER(OrParams), C.c_int, _IP, _DP, C.c_double, C.c_double, C.c_int,
+                                     C.c_int, _IP]
+        L.or_regrid_plan.restype = C.c_int
+        L.or_regrid_transfer.argtypes = [C.c_void_p, C.c_void_p]
         L.or_face_count.argtypes = [C.c_void_p]
         L.or_face_count.restype = C.c_long
         L.or_set_faces.argtypes = [C.c_void_p, _DP]
@@ -277,6 +282,29 @@ class Oracle:
         out = np.zeros(self.L.or_face_count(self.ctx))
         self.L.or_get_faces(self.ctx, out)
         return out
+
+    def estimate(self, eps=0.01):
+        """Loehner's estimator on the density, maximum per block."""
+        out = np.zeros(self.nb)
+        self.L.or_estimate(self.ctx, eps, out)
+        return out
+
+    def regrid_plan(self, block_err, tol_refine, tol_coarsen, max_level):
+        """The new leaf list, (n, 4) int32 rows (level, ix, iy, iz)."""
+        blocks = np.ascontiguousarray(self.grid.blocks, dtype=np.int32).reshape(-1, 4)
+        err = np.ascontiguousarray(block_err, dtype=np.float64)
+        cap = 64 * self.nb + 64
+        out = np.zeros(4 * cap, dtype=np.int32)
+        n = self.L.or_regrid_plan(C.byref(self.p), self.nb, blocks, err, tol_refine, tol_coarsen, max_level, cap, out)
+        assert n >= 0
+        return out[:4 * n].reshape(n, 4)
+
+    def regridded(self, new_blocks):
+        """A new oracle grid with the leaf list new_blocks, its state the
+        conservative transfer of this one's."""
+        fresh = Oracle(self.grid.with_(blocks=np.asarray(new_blocks, dtype=np.int32)))
+        self.L.or_regrid_transfer(self.ctx, fresh.ctx)
+        return fresh
 
     def c2p_counts(self):
         out = np.zeros(4, dtype=np.int64)

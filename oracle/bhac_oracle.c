@@ -1471,3 +1471,378 @@ void or_step(or_ctx* c, double dt) {
   or_stage(c, 1, dt);
   or_stage(c, 2, dt);
 }
+
+/* ------------------------------------------------------------------------ */
+/* AMR regridding                                                             */
+/* ------------------------------------------------------------------------ */
+
+/* Loehner (1987) estimator: the second difference of the density normalised
+ * by its first differences plus a noise filter eps times the local values,
+ * combined over the active directions. */
+void or_estimate(or_ctx* c, double eps, double* block_err) {
+  or_fill_ghosts(c);
+  const int* nx = c->p.nx;
+  for (int b = 0; b < c->nb; ++b) {
+    double emax = 0.0;
+    for (int k = 0; k < nx[2]; ++k)
+      for (int j = 0; j < nx[1]; ++j)
+        for (int i = 0; i < nx[0]; ++i) {
+          int g[3] = {i + c->gd[0], j + c->gd[1], k + c->gd[2]};
+          double num2 = 0.0, den2 = 0.0;
+          double u0 = c->prim[pidx(c, b, OR_RHO, g[0], g[1], g[2])];
+          for (int d = 0; d < c->p.ndim; ++d) {
+            int lo[3] = {g[0], g[1], g[2]}, hi[3] = {g[0], g[1], g[2]};
+            lo[d] -= 1;
+            hi[d] += 1;
+            double um = c->prim[pidx(c, b, OR_RHO, lo[0], lo[1], lo[2])];
+            double up = c->prim[pidx(c, b, OR_RHO, hi[0], hi[1], hi[2])];
+            double n = up - 2.0 * u0 + um;
+            double dd = fabs(up - u0) + fabs(u0 - um) + eps * (fabs(up) + 2.0 * fabs(u0) + fabs(um));
+            num2 += n * n;
+            den2 += dd * dd;
+          }
+          double e = den2 > 0.0 ? sqrt(num2 / den2) : 0.0;
+          if (e > emax) emax = e;
+        }
+    block_err[b] = emax;
+  }
+}
+
+/* The leaf set as one flag array per level over the block lattice. */
+typedef struct {
+  int ndim, nlev, nx[3], bc[3][2];
+  long nbl[8][3];
+  unsigned char* leaf[8];
+} rg_tree;
+
+static long rg_idx(const rg_tree* t, int L, const long c[3]) {
+  return (c[2] * t->nbl[L][1] + c[1]) * t->nbl[L][0] + c[0];
+}
+
+static int rg_in(const rg_tree* t, int L, const long c[3]) {
+  if (L < 0 || L >= t->nlev) return 0;
+  for (int k = 0; k < 3; ++k)
+    if (c[k] < 0 || c[k] >= t->nbl[L][k]) return 0;
+  return 1;
+}
+
+static int rg_leaf(const rg_tree* t, int L, const long c[3]) { return rg_in(t, L, c) && t->leaf[L][rg_idx(t, L, c)]; }
+
+/* level of the leaf covering the block region (L, c), or L + 1 if finer
+ * leaves subdivide it */
+static int rg_cover(const rg_tree* t, int L, const long c[3]) {
+  for (int Lc = L; Lc >= 0; --Lc) {
+    long a[3];
+    for (int k = 0; k < 3; ++k) a[k] = k < t->ndim ? c[k] >> (L - Lc) : c[k];
+    if (rg_leaf(t, Lc, a)) return Lc;
+  }
+  return L + 1;
+}
+
+/* block regions at level L across offset dl from c, after the boundary rules
+ * (none beyond an outflow boundary; through the polar axis the mirrored row at
+ * phi + pi, whose cells can span two blocks) */
+static int rg_neighbours(const rg_tree* t, int L, const long c[3], const int dl[3], long out[2][3]) {
+  long n[3];
+  int axis = 0;
+  for (int k = 0; k < 3; ++k) n[k] = c[k] + dl[k];
+  for (int k = 0; k < t->ndim; ++k) {
+    long N = t->nbl[L][k];
+    if (n[k] >= 0 && n[k] < N) continue;
+    int side = n[k] < 0 ? 0 : 1, kind = t->bc[k][side];
+    if (kind == OR_BC_PERIODIC) {
+      n[k] = ((n[k] % N) + N) % N;
+    } else if (kind == OR_BC_AXIS) {
+      n[k] = side == 0 ? -1 - n[k] : 2 * N - 1 - n[k];
+      axis = 1;
+    } else {
+      return 0;
+    }
+  }
+  for (int k = 0; k < 3; ++k) out[0][k] = n[k];
+  if (!axis || t->ndim != 3) return 1;
+  long nz = t->nx[2], Nc = t->nbl[L][2] * nz, half = Nc / 2;
+  long first = ((n[2] * nz + half) % Nc) / nz, last = (((n[2] + 1) * nz - 1 + half) % Nc) / nz;
+  out[0][2] = first;
+  if (last == first) return 1;
+  for (int k = 0; k < 3; ++k) out[1][k] = n[k];
+  out[1][2] = last;
+  return 2;
+}
+
+static void rg_split(rg_tree* t, int L, const long c[3]) {
+  t->leaf[L][rg_idx(t, L, c)] = 0;
+  for (int s = 0; s < (1 << t->ndim); ++s) {
+    long ch[3] = {c[0], c[1], c[2]};
+    for (int k = 0; k < t->ndim; ++k) ch[k] = 2 * c[k] + ((s >> k) & 1);
+    t->leaf[L + 1][rg_idx(t, L + 1, ch)] = 1;
+  }
+}
+
+/* offsets dl in {-1, 0, 1}^ndim \ {0}, enumerated in a fixed order */
+static int rg_offsets(int ndim, int dl[26][3]) {
+  int n = 0;
+  for (int a = -1; a <= 1; ++a)
+    for (int b = -1; b <= 1; ++b)
+      for (int e = -1; e <= 1; ++e) {
+        if (ndim < 3 && e != 0) continue;
+        if (a == 0 && b == 0 && e == 0) continue;
+        dl[n][0] = a;
+        dl[n][1] = b;
+        dl[n][2] = e;
+        ++n;
+      }
+  return n;
+}
+
+/* whether the region (L, r), subdivided, holds leaves finer than L + 1 */
+static int rg_deeper(const rg_tree* t, int L, const long r[3]) {
+  for (int s = 0; s < (1 << t->ndim); ++s) {
+    long ch[3] = {r[0], r[1], r[2]};
+    for (int k = 0; k < t->ndim; ++k) ch[k] = 2 * r[k] + ((s >> k) & 1);
+    if (rg_cover(t, L + 1, ch) == L + 2) return 1;
+  }
+  return 0;
+}
+
+int or_regrid_plan(const or_params* p, int nb, const int* blocks, const double* block_err, double tol_refine,
+                   double tol_coarsen, int max_level, int cap, int* new_blocks) {
+  rg_tree t;
+  memset(&t, 0, sizeof(t));
+  t.ndim = p->ndim;
+  t.nlev = max_level + 1;
+  for (int L = 0; L < nb; ++L)
+    if (blocks[4 * L] + 1 > t.nlev) t.nlev = blocks[4 * L] + 1;
+  if (t.nlev > 8) return -1;
+  for (int k = 0; k < 3; ++k) {
+    t.nx[k] = p->nx[k];
+    t.bc[k][0] = p->bc[k][0];
+    t.bc[k][1] = p->bc[k][1];
+  }
+  int* orig[8];
+  for (int L = 0; L < t.nlev; ++L) {
+    long n = 1;
+    for (int k = 0; k < 3; ++k) {
+      t.nbl[L][k] = (long)p->nroot[k] << (k < p->ndim ? L : 0);
+      n *= t.nbl[L][k];
+    }
+    t.leaf[L] = (unsigned char*)calloc(n, 1);
+    orig[L] = (int*)malloc(sizeof(int) * n);
+    for (long q = 0; q < n; ++q) orig[L][q] = -1;
+  }
+  for (int b = 0; b < nb; ++b) {
+    long c[3] = {blocks[4 * b + 1], blocks[4 * b + 2], blocks[4 * b + 3]};
+    t.leaf[blocks[4 * b]][rg_idx(&t, blocks[4 * b], c)] = 1;
+    orig[blocks[4 * b]][rg_idx(&t, blocks[4 * b], c)] = b;
+  }
+  /* refinement requests */
+  for (int b = 0; b < nb; ++b) {
+    int L = blocks[4 * b];
+    long c[3] = {blocks[4 * b + 1], blocks[4 * b + 2], blocks[4 * b + 3]};
+    if (L < max_level && block_err[b] > tol_refine) rg_split(&t, L, c);
+  }
+  /* 2:1 balance by refinement, to a fixed point */
+  int dl[26][3];
+  int nd = rg_offsets(p->ndim, dl);
+  for (;;) {
+    int changed = 0;
+    for (int L = 0; L < t.nlev; ++L) {
+      long n = t.nbl[L][0] * t.nbl[L][1] * t.nbl[L][2];
+      unsigned char* mark = (unsigned char*)calloc(n, 1);
+      unsigned char* markc[8] = {0};
+      for (int Lc = 0; Lc < L; ++Lc) markc[Lc] = (unsigned char*)calloc(t.nbl[Lc][0] * t.nbl[Lc][1] * t.nbl[Lc][2], 1);
+      for (long q = 0; q < n; ++q) {
+        if (!t.leaf[L][q]) continue;
+        long c[3] = {q % t.nbl[L][0], (q / t.nbl[L][0]) % t.nbl[L][1], q / (t.nbl[L][0] * t.nbl[L][1])};
+        for (int o = 0; o < nd; ++o) {
+          long r[2][3];
+          int nr = rg_neighbours(&t, L, c, dl[o], r);
+          for (int m = 0; m < nr; ++m) {
+            int st = rg_cover(&t, L, r[m]);
+            if (st < L - 1) {
+              long a[3];
+              for (int k = 0; k < 3; ++k) a[k] = k < t.ndim ? r[m][k] >> (L - st) : r[m][k];
+              markc[st][rg_idx(&t, st, a)] = 1;
+            } else if (st == L + 1 && L + 1 < t.nlev && rg_deeper(&t, L, r[m])) {
+              mark[q] = 1;
+            }
+          }
+        }
+      }
+      for (long q = 0; q < n; ++q)
+        if (mark[q] && L + 1 < t.nlev) {
+          long c[3] = {q % t.nbl[L][0], (q / t.nbl[L][0]) % t.nbl[L][1], q / (t.nbl[L][0] * t.nbl[L][1])};
+          rg_split(&t, L, c);
+          changed = 1;
+        }
+      for (int Lc = 0; Lc < L; ++Lc) {
+        long m = t.nbl[Lc][0] * t.nbl[Lc][1] * t.nbl[Lc][2];
+        for (long q = 0; q < m; ++q)
+          if (markc[Lc][q] && t.leaf[Lc][q]) {
+            long c[3] = {q % t.nbl[Lc][0], (q / t.nbl[Lc][0]) % t.nbl[Lc][1], q / (t.nbl[Lc][0] * t.nbl[Lc][1])};
+            rg_split(&t, Lc, c);
+            changed = 1;
+          }
+        free(markc[Lc]);
+      }
+      free(mark);
+    }
+    if (!changed) break;
+  }
+  /* coarsening: complete sibling groups of original leaves below tol_coarsen,
+   * where the parent keeps the balance (checked against the refined set) */
+  int ngroups = 0;
+  long(*groups)[4] = (long(*)[4])malloc(sizeof(long[4]) * (size_t)(nb + 1));
+  for (int L = 1; L < t.nlev; ++L) {
+    long n = t.nbl[L - 1][0] * t.nbl[L - 1][1] * t.nbl[L - 1][2];
+    for (long q = 0; q < n; ++q) {
+      long pc[3] = {q % t.nbl[L - 1][0], (q / t.nbl[L - 1][0]) % t.nbl[L - 1][1],
+                    q / (t.nbl[L - 1][0] * t.nbl[L - 1][1])};
+      int ok = 1;
+      for (int s = 0; s < (1 << t.ndim) && ok; ++s) {
+        long ch[3] = {pc[0], pc[1], pc[2]};
+        for (int k = 0; k < t.ndim; ++k) ch[k] = 2 * pc[k] + ((s >> k) & 1);
+        int ob = rg_in(&t, L, ch) ? orig[L][rg_idx(&t, L, ch)] : -1;
+        if (ob < 0 || !rg_leaf(&t, L, ch) || !(block_err[ob] < tol_coarsen)) ok = 0;
+      }
+      for (int o = 0; o < nd && ok; ++o) {
+        long r[2][3];
+        int nr = rg_neighbours(&t, L - 1, pc, dl[o], r);
+        for (int m = 0; m < nr && ok; ++m) {
+          int st = rg_cover(&t, L - 1, r[m]);
+          if (st < L - 2 || (st == L && rg_deeper(&t, L - 1, r[m]))) ok = 0;
+        }
+      }
+      if (ok) {
+        groups[ngroups][0] = L - 1;
+        for (int k = 0; k < 3; ++k) groups[ngroups][1 + k] = pc[k];
+        ++ngroups;
+      }
+    }
+  }
+  for (int g = 0; g < ngroups; ++g) {
+    int Lp = (int)groups[g][0];
+    long pc[3] = {groups[g][1], groups[g][2], groups[g][3]};
+    for (int s = 0; s < (1 << t.ndim); ++s) {
+      long ch[3] = {pc[0], pc[1], pc[2]};
+      for (int k = 0; k < t.ndim; ++k) ch[k] = 2 * pc[k] + ((s >> k) & 1);
+      t.leaf[Lp + 1][rg_idx(&t, Lp + 1, ch)] = 0;
+    }
+    t.leaf[Lp][rg_idx(&t, Lp, pc)] = 1;
+  }
+  free(groups);
+  /* output in (level, iz, iy, ix) order */
+  int count = 0;
+  for (int L = 0; L < t.nlev; ++L) {
+    long n = t.nbl[L][0] * t.nbl[L][1] * t.nbl[L][2];
+    for (long q = 0; q < n; ++q)
+      if (t.leaf[L][q]) {
+        if (count < cap) {
+          new_blocks[4 * count] = L;
+          new_blocks[4 * count + 1] = (int)(q % t.nbl[L][0]);
+          new_blocks[4 * count + 2] = (int)((q / t.nbl[L][0]) % t.nbl[L][1]);
+          new_blocks[4 * count + 3] = (int)(q / (t.nbl[L][0] * t.nbl[L][1]));
+        }
+        ++count;
+      }
+    free(t.leaf[L]);
+    free(orig[L]);
+  }
+  return count <= cap ? count : -1;
+}
+
+/* Conservative transfer of the densitized state to a new leaf list, then the
+ * inversion of every new cell. */
+void or_regrid_transfer(const or_ctx* old, or_ctx* c) {
+  const int* nx = c->p.nx;
+  const int nd = c->p.ndim, nch = 1 << nd;
+  long long cnt[4] = {0, 0, 0, 0};
+  for (int b = 0; b < c->nb; ++b) {
+    int L = c->blk[4 * b];
+    long bc[3] = {c->blk[4 * b + 1], c->blk[4 * b + 2], c->blk[4 * b + 3]};
+    int kind, ob = lut_get(old, L, bc);
+    long pb[3];
+    for (int k = 0; k < 3; ++k) pb[k] = k < nd ? bc[k] >> 1 : bc[k];
+    if (ob >= 0) {
+      kind = 0;
+    } else if (L > 0 && (ob = lut_get(old, L - 1, pb)) >= 0) {
+      kind = 1;
+    } else {
+      kind = 2;
+    }
+    for (int k = 0; k < nx[2]; ++k)
+      for (int j = 0; j < nx[1]; ++j)
+        for (int i = 0; i < nx[0]; ++i) {
+          int loc[3] = {i, j, k};
+          long G[3];
+          for (int e = 0; e < 3; ++e) G[e] = bc[e] * nx[e] + loc[e];
+          double U[OR_NV], Pg[OR_NV];
+          if (kind == 0) {
+            for (int v = 0; v < OR_NV; ++v) {
+              U[v] = old->ucur[uidx(old, ob, v, i, j, k)];
+              Pg[v] = old->prim[pidx(old, ob, v, i + old->gd[0], j + old->gd[1], k + old->gd[2])];
+            }
+          } else if (kind == 1) {
+            /* the parent cell, and minmod slopes within the parent block */
+            int pl[3];
+            for (int e = 0; e < 3; ++e) pl[e] = (int)((e < nd ? G[e] >> 1 : G[e]) - pb[e] * nx[e]);
+            for (int v = 0; v < OR_NV; ++v) {
+              double Uc = old->ucur[uidx(old, ob, v, pl[0], pl[1], pl[2])];
+              double u = Uc;
+              for (int d = 0; d < nd; ++d) {
+                double s = 0.0;
+                if (pl[d] > 0 && pl[d] < nx[d] - 1) {
+                  int lo[3] = {pl[0], pl[1], pl[2]}, hi[3] = {pl[0], pl[1], pl[2]};
+                  lo[d] -= 1;
+                  hi[d] += 1;
+                  double Um = old->ucur[uidx(old, ob, v, lo[0], lo[1], lo[2])];
+                  double Up = old->ucur[uidx(old, ob, v, hi[0], hi[1], hi[2])];
+                  s = minmod(Uc - Um, Up - Uc);
+                }
+                u += ((G[d] & 1) ? 0.25 : -0.25) * s;
+              }
+              U[v] = u;
+              Pg[v] = old->prim[pidx(old, ob, v, pl[0] + old->gd[0], pl[1] + old->gd[1], pl[2] + old->gd[2])];
+            }
+          } else {
+            /* the mean of the 2^d finer cells */
+            for (int v = 0; v < OR_NV; ++v) U[v] = Pg[v] = 0.0;
+            for (int s = 0; s < nch; ++s) {
+              long F[3], fb[3];
+              int fl[3];
+              for (int e = 0; e < 3; ++e) {
+                F[e] = e < nd ? 2 * G[e] + ((s >> e) & 1) : G[e];
+                fb[e] = F[e] / nx[e];
+                fl[e] = (int)(F[e] - fb[e] * nx[e]);
+              }
+              int fbi = lut_get(old, L + 1, fb);
+              for (int v = 0; v < OR_NV; ++v) {
+                U[v] += old->ucur[uidx(old, fbi, v, fl[0], fl[1], fl[2])];
+                Pg[v] += old->prim[pidx(old, fbi, v, fl[0] + old->gd[0], fl[1] + old->gd[1], fl[2] + old->gd[2])];
+              }
+            }
+            for (int v = 0; v < OR_NV; ++v) {
+              U[v] /= nch;
+              Pg[v] /= nch;
+            }
+          }
+          double x[3], Uu[OR_NV], Pn[OR_NV];
+          or_metric m;
+          cell_centre(c, b, i, j, k, x);
+          or_metric_at(&c->p, x, 0, &m);
+          for (int v = 0; v < OR_NV; ++v) Uu[v] = U[v] / m.sqrtg;
+          int st = or_con2prim(&c->p, &m, Uu, Pg, floor_radius(&c->p, x), Pn);
+          cnt[st] += 1;
+          c->status[(size_t)b * c->nint + ((size_t)k * nx[1] + j) * nx[0] + i] = (unsigned char)st;
+          if (st >= 2) {
+            or_prim2con(&c->p, &m, Pn, Uu);
+            for (int v = 0; v < OR_NV; ++v) U[v] = m.sqrtg * Uu[v];
+          }
+          for (int v = 0; v < OR_NV; ++v) {
+            c->ucur[uidx(c, b, v, i, j, k)] = U[v];
+            c->prim[pidx(c, b, v, i + c->gd[0], j + c->gd[1], k + c->gd[2])] = Pn[v];
+          }
+        }
+  }
+  for (int s = 0; s < 4; ++s) c->counts[s] += cnt[s];
+}

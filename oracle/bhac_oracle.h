@@ -125,6 +125,29 @@ long or_face_count(const or_ctx* c);                      /* owned faces, all bl
 void or_set_faces(or_ctx* c, const double* faces);
 void or_get_faces(const or_ctx* c, double* faces);
 
+/* ---- AMR regridding ----
+ * or_estimate: Loehner's error estimator on the density of every interior cell
+ * (ghosts filled first), E = sqrt(sum_d N_d^2 / sum_d D_d^2) with
+ * N_d = u_+ - 2 u_0 + u_-, D_d = |u_+ - u_0| + |u_0 - u_-| + eps (|u_+| + 2|u_0| + |u_-|),
+ * maximum per block into block_err[nb].
+ * or_regrid_plan: the new leaf list from the old one and the block errors:
+ * refine a leaf with err > tol_refine below max_level, balance 2:1 across
+ * faces, edges and corners (boundary rules included) by refining coarser
+ * neighbours, then coarsen every complete sibling group whose members all
+ * have err < tol_coarsen where the parent keeps the 2:1 balance.  Output
+ * sorted by (level, iz, iy, ix); returns the count, or -1 if cap is too small.
+ * or_regrid_transfer: conservative transfer of the densitized conserved state
+ * from `old` to `fresh` (same parameters, new leaf list): a kept block is
+ * copied, a refined one prolonged (each child cell the parent value plus
+ * minmod-limited slopes times +-1/4, slopes within the parent block only),
+ * a coarsened one restricted (the mean of its 2^d children); then every cell
+ * is inverted (guess: the parent's or the children's mean primitives) with
+ * floors, as after a stage. */
+void or_estimate(or_ctx* c, double eps, double* block_err);
+int or_regrid_plan(const or_params* p, int nb, const int* blocks, const double* block_err, double tol_refine,
+                   double tol_coarsen, int max_level, int cap, int* new_blocks);
+void or_regrid_transfer(const or_ctx* old, or_ctx* fresh);
+
 #ifdef __cplusplus
 }
 #endif
