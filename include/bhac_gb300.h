@@ -209,6 +209,45 @@ bhac_status bhac_get_cons(bhac_ctx* ctx, double* out, int on_device);
 bhac_status bhac_set_faces(bhac_ctx* ctx, const double* faces, int on_device);
 bhac_status bhac_get_faces(bhac_ctx* ctx, double* faces, int on_device);
 
+/* AMR regridding.  Source: Sec. 2 (block-based tree AMR) and Sec. 7 (extending
+ * the work to AMR runs); the paper names no refinement criterion, so the
+ * estimator is the reading: Loehner's normalised second difference of the
+ * density, E = sqrt(sum_d N_d^2 / sum_d D_d^2) over the active directions with
+ * N_d = u_+ - 2 u_0 + u_- and D_d = |u_+ - u_0| + |u_0 - u_-| + eps (|u_+| + 2|u_0| + |u_-|),
+ * the default of the MPI-AMRVAC toolkit BHAC is built on.
+ *
+ * bhac_estimate: fills the ghost cells and writes the largest E of each block's
+ * interior cells to the host array block_err[nblocks] (block order of the
+ * context); synchronises the stream.  (Mixed form: on the FP32 primitives.)
+ *
+ * bhac_regrid_plan (host only): the new leaf list.  Leaves with
+ * block_err > tol_refine below max_level (< desc->nlevels) are split; then
+ * coarser leaves are split until every pair of leaves touching across a face,
+ * an edge or a corner (through periodic and polar-axis boundaries too) differs
+ * by at most one level, a leaf next to a block region holding leaves two or
+ * more levels finer counting as touching them; then every complete group of
+ * 2^ndim sibling leaves of the input, each with block_err < tol_coarsen, whose
+ * parent would keep that balance, is merged into the parent.  Output in
+ * (level, iz, iy, ix) order into out[cap]; *nout is the count
+ * (BHAC_ERR_NOMEM if it exceeds cap; BHAC_ERR_ARG for an invalid list).
+ *
+ * bhac_regrid_transfer: moves the state of `old` to `fresh`, a context made by
+ * bhac_init_grid + bhac_set_metric with the same descriptor and the planned
+ * leaves (each new leaf kept, one level finer or one level coarser than
+ * leaves of `old`).  The densitized conserved state is copied, prolonged
+ * (parent value plus minmod-limited slopes within the parent block, zero at
+ * its faces, times +-1/4 per direction) or restricted (mean of the 2^ndim
+ * children), so its volume integrals are unchanged; every new cell is then
+ * inverted with floors (guess: the parent's or the children's mean
+ * primitives) as after a stage.  Asynchronous on fresh's stream, which first
+ * waits for the work enqueued on old's; `old` may be destroyed once fresh's
+ * stream has passed the call.  Cleaning form only (BHAC_ERR_ARG otherwise). */
+bhac_status bhac_estimate(bhac_ctx* ctx, double eps, double* block_err);
+bhac_status bhac_regrid_plan(const bhac_grid_desc* desc, const bhac_block_desc* blocks, int nblocks,
+                             const double* block_err, double tol_refine, double tol_coarsen, int max_level,
+                             bhac_block_desc* out, int cap, int* nout);
+bhac_status bhac_regrid_transfer(const bhac_ctx* old_ctx, bhac_ctx* fresh_ctx);
+
 /* Pipelined host transfers, for a host-side loop that feeds every step its
  * primitives from host memory and reads every result back while the kernels of
  * the neighbouring steps run.  The context owns two copy streams, one per

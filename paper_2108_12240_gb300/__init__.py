@@ -24,6 +24,7 @@ __all__ = [
     "bhac_status_string", "bhac_check_bit_ops", "bhac_launches_per_step", "bhac_get_prims_ghosted",
     "bhac_get_c2p_status", "bhac_set_cons", "bhac_set_prims_host_async", "bhac_get_prims_host_async",
     "bhac_host_fence", "bhac_measure_peaks", "bhac_set_faces", "bhac_get_faces",
+    "bhac_estimate", "bhac_regrid_plan", "bhac_regrid_transfer",
 ]
 
 NV = 9
@@ -98,6 +99,9 @@ def lib():
             "bhac_host_fence": ([vp], i),
             "bhac_measure_peaks": ([i, vp, C.POINTER(d)], i),
             "bhac_set_faces": ([vp, vp, i], i),
+            "bhac_estimate": ([vp, d, C.POINTER(d)], i),
+            "bhac_regrid_plan": ([G, B, i, C.POINTER(d), d, d, i, B, i, C.POINTER(i)], i),
+            "bhac_regrid_transfer": ([vp, vp], i),
             "bhac_get_faces": ([vp, vp, i], i),
             "bhac_destroy": ([vp], None),
             "bhac_status_string": ([i], C.c_char_p),
@@ -187,6 +191,29 @@ def bhac_get_prims_host_async(ctx, ptr: int):
 
 def bhac_host_fence(ctx):
     _check("bhac_host_fence", lib().bhac_host_fence(ctx))
+
+
+def bhac_estimate(ctx, eps: float, nblocks: int) -> np.ndarray:
+    out = np.zeros(nblocks)
+    _check("bhac_estimate", lib().bhac_estimate(ctx, eps, out.ctypes.data_as(C.POINTER(C.c_double))))
+    return out
+
+
+def bhac_regrid_plan(desc: GridDesc, blocks, block_err, tol_refine: float, tol_coarsen: float, max_level: int):
+    """The new leaf list as an (n, 4) int32 array of (level, ix, iy, iz)."""
+    err = np.ascontiguousarray(block_err, dtype=np.float64)
+    cap = 64 * len(blocks) + 64
+    out = (BlockDesc * cap)()
+    n = C.c_int(0)
+    _check("bhac_regrid_plan", lib().bhac_regrid_plan(C.byref(desc), blocks, len(blocks),
+                                                      err.ctypes.data_as(C.POINTER(C.c_double)), tol_refine,
+                                                      tol_coarsen, max_level, out, cap, C.byref(n)))
+    return np.array([(out[k].level, out[k].ix, out[k].iy, out[k].iz) for k in range(n.value)],
+                    dtype=np.int32).reshape(-1, 4)
+
+
+def bhac_regrid_transfer(old_ctx, fresh_ctx):
+    _check("bhac_regrid_transfer", lib().bhac_regrid_transfer(old_ctx, fresh_ctx))
 
 
 def bhac_set_faces(ctx, ptr: int, on_device: bool):
@@ -424,6 +451,18 @@ class Solver:
         out = np.empty(n)
         bhac_get_faces(self.ctx, out.ctypes.data, False)
         return out
+
+    def estimate(self, eps: float = 0.01) -> np.ndarray:
+        """Loehner's estimator on the density, maximum per block (bhac_estimate)."""
+        return bhac_estimate(self.ctx, eps, self.grid.nb)
+
+    def regridded(self, new_blocks):
+        """A new Solver on the leaf list new_blocks (same descriptor, device and
+        stream) holding the conservative transfer of this one's state."""
+        g = self.grid.with_(blocks=np.asarray(new_blocks, dtype=np.int32).reshape(-1, 4))
+        fresh = Solver(g, self.precision, device=self.device, stream=self.stream)
+        bhac_regrid_transfer(self.ctx, fresh.ctx)
+        return fresh
 
     def prims_ghosted(self) -> np.ndarray:
         """FP64 primitives with ghost cells, (blocks, 9, Nz, Ny, Nx) (FP64 form)."""

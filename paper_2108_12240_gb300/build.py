@@ -14,7 +14,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libbhac_gb300.so")
-UNITS = ["api.cu", "aux.cu", "amr.cu", "stage_fp64.cu", "stage_mixed.cu", "flops.cu", "static_cfl.cu", "selfcheck.cu", "peaks.cu", "ct.cu", "imex.cu"]
+UNITS = ["api.cu", "aux.cu", "amr.cu", "stage_fp64.cu", "stage_mixed.cu", "flops.cu", "static_cfl.cu", "selfcheck.cu", "peaks.cu", "ct.cu", "imex.cu", "regrid.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE]
 _lock = threading.Lock()
