@@ -13,12 +13,14 @@
  * in the order the method applies them; every reading of a point the paper
  * leaves open is listed in the design notes of the repository.
  *
- * Parity unpinned (no fact outside the oracle fixes it): the SRMHD shock
- * tube as a whole, beyond a stored regression profile written by the oracle
- * itself (the paper prints no reference solution); its ingredients are each
- * pinned.  The GLM source's metric terms are a reading (the paper gives no
- * cleaning equations), pinned against the covariant damped cleaning equation
- * plus the one term the reading adds.
+ * Every function here is pinned by the tests against facts outside the
+ * oracle (closed forms, the covariant formulation, invariants, brute force,
+ * convergence to exact solutions).  The GLM source's metric terms are a
+ * reading (the paper gives no cleaning equations), pinned against the
+ * covariant damped cleaning equation plus the one term the reading adds.  The
+ * SRMHD shock tube is a configuration with no printed reference solution in
+ * the paper: its stored profile is a regression record written by the oracle,
+ * not a pin; the functions it exercises are each pinned.
  *
  * Conventions
  *   primitive order : rho, p, u^1, u^2, u^3, B^1, B^2, B^3, psi
