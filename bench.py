@@ -483,8 +483,9 @@ def reference_arm(args, rank):
 
 def shape_runs(args):
     """For a profiler capture: the workload in the given launch shapes, each
-    set_launch, set_prims, cfl_dt and four device-dt steps (no timing, no output
-    but one line per shape)."""
+    set_launch (and, with a seventh value, bhac_set_split's chunk count),
+    set_prims, cfl_dt and four device-dt steps (no timing, no output but one
+    line per shape)."""
     import torch
 
     import paper_2108_12240_gb300 as gb
@@ -496,7 +497,8 @@ def shape_runs(args):
     stream = torch.cuda.Stream()
     s = gb.Solver(g, form, stream=stream)
     for sh in shapes:
-        s.set_launch(*sh)
+        s.set_launch(*sh[:6])
+        s.set_split(sh[6] if len(sh) > 6 else 0)
         s.set_prims(P)
         s.cfl_dt()
         for _ in range(4):
@@ -504,6 +506,55 @@ def shape_runs(args):
         torch.cuda.synchronize()
         print(form, sh, "done", flush=True)
     s.close()
+
+
+def split_sweep(args):
+    """Fused stage kernel against the split form (face kernel, then cell kernel
+    on a second stream, in chunks): ms per step of the workload for each chunk
+    count, persistent setting and register bound, both forms, with the clocks.
+    One JSON line; not the bench contract line."""
+    import torch
+
+    import paper_2108_12240_gb300 as gb
+
+    torch.cuda.set_device(0)
+    g, desc = workload(args.workload)
+    P = initial_prims(g)
+    stream = torch.cuda.Stream()
+    out = {"sweep": "split form", "workload": desc, "forms": {}}
+    for form in ("mixed", "fp64"):
+        s = gb.Solver(g, form, stream=stream)
+        # the fused shapes the autotuner picks on this torus, then the split ones
+        cases = [(0, 2, 2), (0, 1, 1)] if form == "mixed" else [(0, 1, 1), (0, 2, 2)]
+        for chunks in ((1, 4, 8) if form == "mixed" else (1, 8)):
+            for minb in ((1, 2, 3) if form == "mixed" else (1, 2)):
+                for pers in (0, minb):
+                    cases.append((chunks, pers, minb))
+        rows = []
+        with Clocks(0) as ck:
+            for chunks, pers, minb in cases:
+                s.set_launch(16, 16, 256, pers, minb, 0)
+                s.set_split(chunks)
+                s.set_prims(P)
+                s.cfl_dt()
+                for _ in range(args.warmup):
+                    s.step(0.0)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for _ in range(args.steps):
+                    s.step(0.0)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1) / args.steps
+                rows.append({"chunks": chunks, "persistent": pers, "min_ctas": minb, "ms_per_step": ms,
+                             "zone_updates_per_s": job_value(g.ncells, 1, ms)})
+                print(json.dumps({"form": form, **rows[-1]}), file=sys.stderr, flush=True)
+        s.close()
+        del s
+        torch.cuda.empty_cache()
+        out["forms"][form] = {"rows": rows, "clocks": ck.summary()}
+    print(json.dumps(out), flush=True)
 
 
 CONFIGS = ["shock_tube_2d", "torus_2d", "torus_3d", "amr_torus", "torus_3d_large"]
@@ -588,6 +639,8 @@ def main():
     ap.add_argument("--all-configs", action="store_true", help="every workload configuration, one line each")
     ap.add_argument("--shape-runs", nargs="+", metavar="FORM_OR_SHAPE",
                     help="FORM tx,ty,threads,persistent,min_ctas,producers ...: four steps per shape, for ncu")
+    ap.add_argument("--split-sweep", action="store_true",
+                    help="fused stage kernel against the split form (face + cell kernels), one line")
     ap.add_argument("--no-tune", action="store_true", help="use the cached launch shape (or the default) without timing candidates")
     args = ap.parse_args()
     global TUNE
@@ -600,6 +653,9 @@ def main():
         return
     if args.shape_runs:
         shape_runs(args)
+        return
+    if args.split_sweep:
+        split_sweep(args)
         return
 
     world = int(os.environ.get("WORLD_SIZE", "1"))

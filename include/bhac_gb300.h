@@ -42,7 +42,7 @@ typedef enum {
   BHAC_OK = 0,
   BHAC_ERR_ARG = 1,      /* invalid argument or descriptor */
   BHAC_ERR_CUDA = 2,     /* a CUDA runtime call failed */
-  BHAC_ERR_NOMEM = 3,    /* the arena is smaller than bhac_query_sizes() */
+  BHAC_ERR_NOMEM = 3,    /* the arena is smaller than bhac_query_sizes(), or a device allocation failed */
   BHAC_ERR_STATE = 4,    /* call out of order (e.g. step before set_prims) */
   BHAC_ERR_TIMEOUT = 5,  /* a bounded device wait gave up */
   BHAC_WARN_C2P = 6      /* some cells failed the inversion and kept their previous state */
@@ -312,9 +312,10 @@ bhac_status bhac_launches_per_step(const bhac_ctx* ctx, int* launches);
 /* Kernel launch shape of the stage kernel: tile of tx x ty cells per CTA column
  * (must divide the block), threads per CTA (a multiple of 32, at most 256),
  * persistent = k > 0 for k CTAs per SM pulling (block, tile) items from a device
- * work counter (0: one CTA per item), and min_ctas = 1 or 2: the register bound
- * the 3-D kernel is compiled for (2 trades a few spilled registers for two
- * resident CTAs per SM), and producer_warps = p > 0 (3-D only, p * 32 < threads)
+ * work counter (0: one CTA per item), and min_ctas = 1, 2 or 3: the register
+ * bound the 3-D kernel is compiled for (2 trades a few spilled registers for two
+ * resident CTAs per SM; 3 applies to the face kernel of the split form, see
+ * bhac_set_split, and means 2 for the fused kernel), and producer_warps = p > 0 (3-D only, p * 32 < threads)
  * for the warp-specialised form: p warps compute the next plane's face fluxes
  * while the others update the current plane's cells (0: the phased form).
  * tx, ty, threads, min_ctas = 0 keep the current setting.  Results do not
@@ -325,6 +326,24 @@ bhac_status bhac_launches_per_step(const bhac_ctx* ctx, int* launches);
  * with min_ctas = 2. */
 bhac_status bhac_set_launch(bhac_ctx* ctx, int tx, int ty, int threads, int persistent, int min_ctas,
                             int producer_warps);
+
+/* Split form of the stage (a measured alternative to the fused kernel, off by
+ * default; chunks = 0 restores the fused form).  chunks = n > 0 runs each stage
+ * as n chunks of (block, tile) items: a face kernel (reconstruction, Riemann
+ * fluxes, flux divergence and sources, compiled without the inversion code)
+ * stores the stage right-hand side in a buffer of one value per (block,
+ * variable, interior cell) in the form's flux type (FP32 for the mixed form,
+ * FP64 otherwise); a cell kernel on a second stream then applies the RK
+ * combination, inversion, floors and CFL rate of that chunk, overlapping the
+ * next chunk's face kernel.  Same arithmetic as the fused kernel, so results
+ * are identical bit for bit.  Source: the per-cell update of Sec. 2 (flux
+ * divergence, sources, two-stage RK and inversion), reorganised into two
+ * kernels.  First use allocates the second stream, its events and the
+ * buffer (BHAC_ERR_NOMEM if the device has no room).  BHAC_ERR_ARG: chunks
+ * outside [0, 32], or chunks > 0 with constrained transport or a
+ * warp-specialised launch shape.  Not for graph capture (bhac_graph_capture
+ * returns BHAC_ERR_STATE while chunks > 0). */
+bhac_status bhac_set_split(bhac_ctx* ctx, int chunks);
 
 /* Records `nsteps` steps with the device time step (bhac_step(ctx, 0.0)) into a
  * CUDA graph on the context's stream and instantiates it; bhac_graph_launch()

@@ -24,7 +24,7 @@ __all__ = [
     "bhac_status_string", "bhac_check_bit_ops", "bhac_launches_per_step", "bhac_get_prims_ghosted",
     "bhac_get_c2p_status", "bhac_set_cons", "bhac_set_prims_host_async", "bhac_get_prims_host_async",
     "bhac_host_fence", "bhac_measure_peaks", "bhac_set_faces", "bhac_get_faces",
-    "bhac_estimate", "bhac_regrid_plan", "bhac_regrid_transfer",
+    "bhac_estimate", "bhac_regrid_plan", "bhac_regrid_transfer", "bhac_set_split",
 ]
 
 NV = 9
@@ -33,7 +33,7 @@ BCS = {"periodic": 0, "outflow": 1, "axis": 2, "noinflow": 3}
 RECON = {"ppm": 0, "minmod": 1}
 RIEMANN = {"hll": 0, "tvdlf": 1}
 PREC = {"fp64": 0, "mixed": 1}
-STATUS = {0: "ok", 1: "invalid argument", 2: "CUDA error", 3: "arena too small", 4: "call out of order",
+STATUS = {0: "ok", 1: "invalid argument", 2: "CUDA error", 3: "arena too small or device allocation failed", 4: "call out of order",
           5: "device wait timed out", 6: "inversion failures"}
 
 
@@ -85,6 +85,7 @@ def lib():
             "bhac_get_cons": ([vp, vp, i], i),
             "bhac_get_diagnostics": ([vp, C.POINTER(C.c_longlong)], i),
             "bhac_set_launch": ([vp, i, i, i, i, i, i], i),
+            "bhac_set_split": ([vp, i], i),
             "bhac_count_flops": ([vp, d, i, C.c_uint, C.POINTER(d)], i),
             "bhac_graph_capture": ([vp, i], i),
             "bhac_graph_launch": ([vp], i),
@@ -237,6 +238,10 @@ def bhac_get_diagnostics(ctx):
 def bhac_set_launch(ctx, tx=0, ty=0, threads=0, persistent=0, min_ctas=0, producer_warps=0):
     return _check("bhac_set_launch", lib().bhac_set_launch(ctx, tx, ty, threads, persistent, min_ctas,
                                                            producer_warps))
+
+
+def bhac_set_split(ctx, chunks: int):
+    return _check("bhac_set_split", lib().bhac_set_split(ctx, chunks))
 
 
 def bhac_count_flops(ctx, dt: float, nsamples: int = 2000, seed: int = 1):
@@ -513,6 +518,10 @@ class Solver:
 
     def set_launch(self, tx=0, ty=0, threads=0, persistent=0, min_ctas=0, producer_warps=0):
         bhac_set_launch(self.ctx, tx, ty, threads, persistent, min_ctas, producer_warps)
+
+    def set_split(self, chunks: int):
+        """Split form of the stage in `chunks` chunks (0: the fused kernel)."""
+        bhac_set_split(self.ctx, chunks)
 
 
 # Fail loudly at import if the library cannot be loaded.

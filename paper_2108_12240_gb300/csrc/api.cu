@@ -185,6 +185,10 @@ StageArgs base_args(const bhac_ctx* c) {
   a.nty = d.nx[1] / c->ty;
   a.nblocks = c->nb;
   a.nitems = c->nb * a.ntx * a.nty;
+  a.item0 = 0;
+  a.item1 = a.nitems;
+  a.split = 0;
+  a.R = c->Rbuf;
   a.persistent = c->persistent;
   a.minb = c->minb;
   a.pwarps = c->pwarps;
@@ -324,8 +328,40 @@ bhac_status run_stage(bhac_ctx* c, int stage, double dt) {
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     grid = nsm * c->persistent;
   }
-  cudaError_t e = c->mixed ? launch_stage_mixed(a, grid, c->threads, smem, c->st)
-                           : launch_stage_fp64(a, grid, c->threads, smem, c->st);
+  cudaError_t e = cudaSuccess;
+  if (c->split <= 0) {
+    e = c->mixed ? launch_stage_mixed(a, grid, c->threads, smem, c->st)
+                 : launch_stage_fp64(a, grid, c->threads, smem, c->st);
+  } else {
+    // split form: chunk q's face kernel on st, its cell kernel on st2 after it;
+    // the face kernel of chunk q + 1 overlaps the cell kernel of chunk q
+    const int nch = c->split;
+    a.split = 1;
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    e = cudaMemsetAsync(c->work, 0, sizeof(unsigned int) * 32, c->st);  // one counter per chunk
+    if (e == cudaSuccess) e = cudaEventRecord(c->ev_fork, c->st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(c->st2, c->ev_fork, 0);
+    for (int q = 0; q < nch && e == cudaSuccess; ++q) {
+      StageArgs f = a;
+      f.item0 = (int)((long long)a.nitems * q / nch);
+      f.item1 = (int)((long long)a.nitems * (q + 1) / nch);
+      f.work = c->work + q;
+      const int g = c->persistent ? grid : f.item1 - f.item0;
+      e = c->mixed ? launch_stage_mixed(f, g, c->threads, smem, c->st) : launch_stage_fp64(f, g, c->threads, smem, c->st);
+      if (e == cudaSuccess) e = cudaEventRecord(c->ev_chunk[q], c->st);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(c->st2, c->ev_chunk[q], 0);
+      const long long cells = (long long)(f.item1 - f.item0) * c->tx * c->ty * c->d.nx[2];
+      long long cg = (cells + 255) / 256;
+      if (cg > 8LL * nsm) cg = 8LL * nsm;
+      if (e == cudaSuccess)
+        e = c->mixed ? launch_cells_mixed(f, (int)(cg < 1 ? 1 : cg), c->st2) : launch_cells_fp64(f, (int)(cg < 1 ? 1 : cg), c->st2);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(c->ev_join2, c->st2);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(c->st, c->ev_join2, 0);
+    if (e == cudaSuccess) e = c->mixed ? launch_reflux_mixed(a, c->st) : launch_reflux_fp64(a, c->st);
+  }
   if (e != cudaSuccess) return BHAC_ERR_CUDA;
   c->cur = out;
   c->ucur = 1 - c->ucur;
@@ -387,7 +423,7 @@ const char* bhac_status_string(bhac_status s) {
     case BHAC_OK: return "ok";
     case BHAC_ERR_ARG: return "invalid argument";
     case BHAC_ERR_CUDA: return "CUDA error";
-    case BHAC_ERR_NOMEM: return "arena too small";
+    case BHAC_ERR_NOMEM: return "arena too small or device allocation failed";
     case BHAC_ERR_STATE: return "call out of order";
     case BHAC_ERR_TIMEOUT: return "device wait timed out";
     case BHAC_WARN_C2P: return "inversion failures";
@@ -453,6 +489,11 @@ bhac_status bhac_init_grid(bhac_ctx** out, const bhac_grid_desc* d, const bhac_b
   c->scratch = (double*)(c->arena + L.off_scratch);
   c->scratch_out = (double*)(c->arena + L.off_scratch_out);
   c->d_status = (unsigned char*)(c->arena + L.off_status);
+  c->Rbuf = nullptr;
+  c->split = 0;
+  c->st2 = nullptr;
+  c->ev_fork = c->ev_join2 = nullptr;
+  for (int q = 0; q < 32; ++q) c->ev_chunk[q] = nullptr;
   char* small = c->arena + L.off_small;
   c->dt_dev = (double*)small;
   c->smax = (unsigned long long*)(small + 8);
@@ -846,7 +887,7 @@ bhac_status bhac_get_c2p_status(bhac_ctx* c, unsigned char* out, int on_device) 
 
 bhac_status bhac_set_launch(bhac_ctx* c, int tx, int ty, int threads, int persistent, int min_ctas,
                             int producer_warps) {
-  if (!c || min_ctas < 0 || min_ctas > 2 || producer_warps < 0) return BHAC_ERR_ARG;
+  if (!c || min_ctas < 0 || min_ctas > 3 || producer_warps < 0) return BHAC_ERR_ARG;
   if (producer_warps > 0 && (c->d.ndim != 3 || producer_warps * 32 >= (threads > 0 ? threads : c->threads)))
     return BHAC_ERR_ARG;
   const int ntx = tx > 0 ? tx : c->tx, nty = ty > 0 ? ty : c->ty, nth = threads > 0 ? threads : c->threads;
@@ -863,8 +904,34 @@ bhac_status bhac_set_launch(bhac_ctx* c, int tx, int ty, int threads, int persis
   return BHAC_OK;
 }
 
+bhac_status bhac_set_split(bhac_ctx* c, int chunks) {
+  if (!c || chunks < 0 || chunks > 32) return BHAC_ERR_ARG;
+  if (chunks > 0 && (c->pwarps > 0 || c->ct)) return BHAC_ERR_ARG;
+  if (chunks > 0 && !c->Rbuf) {
+    // the second stream, its events and the right-hand-side buffer are made
+    // on first use: the fused form needs none of them
+    cudaError_t e = cudaSuccess;
+    if (!c->st2) e = cudaStreamCreateWithFlags(&c->st2, cudaStreamNonBlocking);
+    for (cudaEvent_t* ev : {&c->ev_fork, &c->ev_join2})
+      if (e == cudaSuccess && !*ev) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+    for (int q = 0; q < 32 && e == cudaSuccess; ++q)
+      if (!c->ev_chunk[q]) e = cudaEventCreateWithFlags(&c->ev_chunk[q], cudaEventDisableTiming);
+    const size_t bytes = (c->mixed ? sizeof(float) : sizeof(double)) * NV * (size_t)c->nb * c->nint;
+    if (e == cudaSuccess) e = cudaMalloc(&c->Rbuf, bytes);
+    if (e == cudaErrorMemoryAllocation) {
+      c->Rbuf = nullptr;
+      cudaGetLastError();
+      return BHAC_ERR_NOMEM;
+    }
+    if (e != cudaSuccess) return BHAC_ERR_CUDA;
+  }
+  c->split = chunks;
+  return BHAC_OK;
+}
+
 bhac_status bhac_graph_capture(bhac_ctx* c, int nsteps) {
   if (!c || nsteps < 1) return BHAC_ERR_ARG;
+  if (c->split > 0) return BHAC_ERR_STATE;  // the split form runs on two streams
   if (!c->prims_ok || !c->cfl_ok) return BHAC_ERR_STATE;
   if (c->graph) {
     cudaGraphExecDestroy(c->graph);
@@ -945,8 +1012,16 @@ void bhac_destroy(bhac_ctx* c) {
       cudaStreamSynchronize(s);
       cudaStreamDestroy(s);
     }
-  for (cudaEvent_t e : {c->ev_h2d, c->ev_scat, c->ev_gath, c->ev_d2h, c->ev_fence, c->ev_join_in, c->ev_join_out})
+  for (cudaEvent_t e : {c->ev_h2d, c->ev_scat, c->ev_gath, c->ev_d2h, c->ev_fence, c->ev_join_in, c->ev_join_out,
+                        c->ev_fork, c->ev_join2})
     if (e) cudaEventDestroy(e);
+  for (int q = 0; q < 32; ++q)
+    if (c->ev_chunk[q]) cudaEventDestroy(c->ev_chunk[q]);
+  if (c->st2) {
+    cudaStreamSynchronize(c->st2);
+    cudaStreamDestroy(c->st2);
+  }
+  if (c->Rbuf) cudaFree(c->Rbuf);
   delete c;
 }
 

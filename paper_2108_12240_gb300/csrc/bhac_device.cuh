@@ -57,6 +57,9 @@ struct StageArgs {
   double c2p_tol;
   int c2p_maxit;
   double c2p_gf, c2p_v2max;  // (Gamma - 1)/Gamma and 1 - 1/W_max^2
+  int split;                 // face kernel stores the stage right-hand side; a cell kernel finishes
+  void* R;                   // that right-hand side, T per (block, var, interior cell)
+  int item0, item1;          // (block, tile) items of this launch, in the visiting order
   int imex;                  // the cleaning damping is the implicit part of IMEX-SSP2(2,2,2)
   double imex_g;             // its gamma = 1 - 1/sqrt(2)
   double wmax, rho_fl_c, p_fl_c;  // constant floors (flat coordinates)

@@ -73,6 +73,12 @@ struct bhac_ctx {
   float *te_c32, *te_f1_32, *te_f2_32;
   long long *ring_dst, *ring_src;
   long long nring;
+  // split form: chunks of items, the face kernel on st and the cell kernel on
+  // st2, chunk by chunk; R holds the stage right-hand side
+  int split;
+  cudaStream_t st2;
+  cudaEvent_t ev_chunk[32], ev_fork, ev_join2;
+  double* Rbuf;
   // captured steps
   cudaGraphExec_t graph;
   int graph_steps;

@@ -19,6 +19,11 @@ constexpr int kTwoCtaSmem = 113 * 1024;
 cudaError_t launch_stage_fp64(const StageArgs& a, int grid, int threads, size_t smem, cudaStream_t st);
 cudaError_t launch_stage_mixed(const StageArgs& a, int grid, int threads, size_t smem, cudaStream_t st);
 cudaError_t launch_cfl(const StageArgs& a, cudaStream_t st);
+// split form: the cell kernel over a range of items, and the reflux pass
+cudaError_t launch_cells_fp64(const StageArgs& a, int grid, cudaStream_t st);
+cudaError_t launch_cells_mixed(const StageArgs& a, int grid, cudaStream_t st);
+cudaError_t launch_reflux_fp64(const StageArgs& a, cudaStream_t st);
+cudaError_t launch_reflux_mixed(const StageArgs& a, cudaStream_t st);
 // set kernel attributes ahead of a stream capture
 cudaError_t prepare_stage_fp64();
 cudaError_t prepare_stage_mixed();

@@ -9,6 +9,9 @@ cudaError_t launch_stage_fp64(const StageArgs& a, int grid, int threads, size_t 
 
 cudaError_t prepare_stage_fp64() { return configure_all_t<double>(); }
 
+cudaError_t launch_cells_fp64(const StageArgs& a, int grid, cudaStream_t st) { return launch_cells_any<double>(a, grid, st); }
+cudaError_t launch_reflux_fp64(const StageArgs& a, cudaStream_t st) { return launch_reflux_any<double>(a, st); }
+
 cudaError_t launch_cfl(const StageArgs& a, cudaStream_t st) {
   int nsm = 0, dev = 0;
   cudaGetDevice(&dev);

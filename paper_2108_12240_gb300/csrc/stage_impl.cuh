@@ -555,10 +555,15 @@ __device__ __forceinline__ void reduce_outputs(const StageArgs& a, const unsigne
   }
 }
 
+template <typename T, int DIM, bool FLAT>
+__device__ __forceinline__ void rk_finish(const StageArgs& a, const LevelGeo& geo, int b, int ci, int cg, int I1, int I2,
+                                          int bi, int bj, int k, const double rhs[NV], double dt, unsigned cfb,
+                                          unsigned cnt[4], double& rate_max);
+
 // Divergence of the face fluxes staged in shared memory, sources, RK stage
 // combination and (unless the reflux pass owns the cell) the inversion of cell
 // c of plane k in the tile at (x0, y0) of block b.
-template <typename T, int DIM, bool FLAT>
+template <typename T, int DIM, bool FLAT, bool SPLIT>
 __device__ __forceinline__ void cell_update(const StageArgs& a, const LevelGeo& geo, const T* __restrict__ Pb, int b,
                                             int x0, int y0, int k, int c, const T* Fx, const T* Fy, const T* Fz0,
                                             const T* Fz1, double dt, unsigned cfb, unsigned cnt[4],
@@ -625,7 +630,21 @@ __device__ __forceinline__ void cell_update(const StageArgs& a, const LevelGeo& 
       }
     }
   }
-  // RK combination
+  if (SPLIT) {  // the cell kernel completes the stage from the stored right-hand side
+    T* R = reinterpret_cast<T*>(a.R) + (size_t)b * NV * a.nint + ci;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) R[(size_t)v * a.nint] = sizeof(T) == 4 ? (T)narrow_f64(rhs[v]) : (T)rhs[v];
+    return;
+  }
+  rk_finish<T, DIM, FLAT>(a, geo, b, ci, cg, I1, I2, x0 + i, y0 + j, k, rhs, dt, cfb, cnt, rate_max);
+}
+
+// RK combination (and the IMEX damping), then the inversion, floors, outputs
+// and CFL rate of cell (bi, bj, k) of block b, given the stage right-hand side.
+template <typename T, int DIM, bool FLAT>
+__device__ __forceinline__ void rk_finish(const StageArgs& a, const LevelGeo& geo, int b, int ci, int cg, int I1, int I2,
+                                          int bi, int bj, int k, const double rhs[NV], double dt, unsigned cfb,
+                                          unsigned cnt[4], double& rate_max) {
   const size_t ub = (size_t)b * NV * a.nint + ci;
   double U[NV];
 #pragma unroll
@@ -652,8 +671,8 @@ __device__ __forceinline__ void cell_update(const StageArgs& a, const LevelGeo& 
     }
   }
   // cells next to a face bordering finer blocks are finished by the reflux pass
-  const bool later = cfb && (((cfb & 1u) && x0 + i == 0) || ((cfb & 2u) && x0 + i == a.nx - 1) ||
-                             ((cfb & 4u) && y0 + j == 0) || ((cfb & 8u) && y0 + j == a.ny - 1) ||
+  const bool later = cfb && (((cfb & 1u) && bi == 0) || ((cfb & 2u) && bi == a.nx - 1) ||
+                             ((cfb & 4u) && bj == 0) || ((cfb & 8u) && bj == a.ny - 1) ||
                              ((cfb & 16u) && k == 0) || ((cfb & 32u) && k == a.nz - 1));
   if (later) {
 #pragma unroll
@@ -683,7 +702,7 @@ __device__ __forceinline__ void cell_update(const StageArgs& a, const LevelGeo& 
 // Shared memory (T): Fx, Fy, [Fz0, Fz1, EzR in 3-D], ExL, ExR, EyL, EyR.
 // ----------------------------------------------------------------------------
 template <typename T, int DIM, bool FLAT, int MINB>
-__global__ void __launch_bounds__(256, MINB) stage_kernel(StageArgs a) {
+__global__ void __launch_bounds__(256, MINB % 10) stage_kernel(StageArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int tx = a.tx, ty = a.ty;
   const int sFx = ty * (tx + 1), sFy = (ty + 1) * tx, sFz = tx * ty;
@@ -709,15 +728,15 @@ __global__ void __launch_bounds__(256, MINB) stage_kernel(StageArgs a) {
   const int sy = a.Nx, sz = a.Nx * a.Ny;
   const int nzc = DIM == 3 ? sFz : 0;
 
-  int item = a.persistent ? -1 : (int)blockIdx.x;
+  int item = a.persistent ? -1 : (int)blockIdx.x + a.item0;
   for (;;) {
     if (a.persistent) {
       __syncthreads();
-      if (threadIdx.x == 0) s_item = (int)atomicAdd(a.work, 1u);
+      if (threadIdx.x == 0) s_item = a.item0 + (int)atomicAdd(a.work, 1u);
       __syncthreads();
       item = s_item;
     }
-    if (item >= a.nitems) break;
+    if (item >= a.item1) break;
     const int ord = item / ntile;
     const int b = a.order[ord];
     const int tile = item - ord * ntile;
@@ -800,7 +819,7 @@ __global__ void __launch_bounds__(256, MINB) stage_kernel(StageArgs a) {
       __syncthreads();
       // C: cell updates
       for (int c = threadIdx.x; c < sFz; c += blockDim.x)
-        cell_update<T, DIM, FLAT>(a, geo, Pb, b, x0, y0, k, c, Fx, Fy, Fz0, Fz1, dt, cfb, cnt, rate_max);
+        cell_update<T, DIM, FLAT, (MINB >= 10)>(a, geo, Pb, b, x0, y0, k, c, Fx, Fy, Fz0, Fz1, dt, cfb, cnt, rate_max);
       __syncthreads();
       T* tmp = Fz0;
       Fz0 = Fz1;
@@ -925,7 +944,7 @@ __global__ void __launch_bounds__(256, MINB) stage_kernel_ws(StageArgs a) {
         const int par = k & 1;
         named_sync(BAR_FULL + par, nthr);
         for (int c = threadIdx.x - nprod; c < sFz; c += ncons)
-          cell_update<T, 3, FLAT>(a, geo, Pb, b, x0, y0, k, c, FxB[par], FyB[par], FzB[k % 3], FzB[(k + 1) % 3], dt,
+          cell_update<T, 3, FLAT, false>(a, geo, Pb, b, x0, y0, k, c, FxB[par], FyB[par], FzB[k % 3], FzB[(k + 1) % 3], dt,
                                   cfb, cnt, rate_max);
         __threadfence_block();
         named_arrive(BAR_EMPTY + par, nthr);
@@ -934,6 +953,52 @@ __global__ void __launch_bounds__(256, MINB) stage_kernel_ws(StageArgs a) {
     if (!a.persistent) break;
   }
   reduce_outputs(a, cnt, rate_max);
+}
+
+// Split form, second kernel: one thread per interior cell of the items
+// [item0, item1): the stage right-hand side the face kernel stored, then
+// rk_finish (the same arithmetic as the fused kernel).
+template <typename T, int DIM, bool FLAT>
+__global__ void __launch_bounds__(256) cell_kernel(StageArgs a) {
+  const double dt = stage_dt(a);
+  unsigned cnt[4] = {0u, 0u, 0u, 0u};
+  double rate_max = 0.0;
+  const int tx = a.tx, ty = a.ty, ntile = a.ntx * a.nty;
+  const long long per = (long long)tx * ty * a.nz;
+  const long long n = (long long)(a.item1 - a.item0) * per;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    const int item = a.item0 + (int)(t / per);
+    const int rem = (int)(t - (long long)(item - a.item0) * per);
+    const int k = rem / (tx * ty), c = rem - k * tx * ty;
+    const int i = c % tx, j = c / tx;
+    const int ord = item / ntile;
+    const int b = a.order[ord];
+    const int tile = item - ord * ntile;
+    const int bi = (tile % a.ntx) * tx + i, bj = (tile / a.ntx) * ty + j;
+    const int ci = (k * a.ny + bj) * a.nx + bi;
+    const int cg = ((k + a.gz) * a.Ny + (bj + a.gy)) * a.Nx + (bi + a.gx);
+    const LevelGeo geo = level_geo(a, a.blk[4 * b]);
+    const int I1 = a.blk[4 * b + 1] * a.nx + bi, I2 = a.blk[4 * b + 2] * a.ny + bj;
+    const unsigned cfb = a.nlev > 1 ? a.cf[b] : 0u;
+    const T* R = reinterpret_cast<const T*>(a.R) + (size_t)b * NV * a.nint + ci;
+    double rhs[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) rhs[v] = to_double(R[(size_t)v * a.nint]);
+    rk_finish<T, DIM, FLAT>(a, geo, b, ci, cg, I1, I2, bi, bj, k, rhs, dt, cfb, cnt, rate_max);
+  }
+  reduce_outputs(a, cnt, rate_max);
+}
+
+template <typename T, int DIM, bool FLAT>
+static cudaError_t launch_cells_t(const StageArgs& a, int grid, cudaStream_t st) {
+  cell_kernel<T, DIM, FLAT><<<grid, 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename T>
+static cudaError_t launch_cells_any(const StageArgs& a, int grid, cudaStream_t st) {
+  if (a.ndim == 3) return a.flat ? launch_cells_t<T, 3, true>(a, grid, st) : launch_cells_t<T, 3, false>(a, grid, st);
+  return a.flat ? launch_cells_t<T, 2, true>(a, grid, st) : launch_cells_t<T, 2, false>(a, grid, st);
 }
 
 // Coarse-fine flux correction: each listed coarse cell trades the coarse flux
@@ -1065,31 +1130,66 @@ static cudaError_t configure_all_t() {
   return e;
 }
 
+template <typename T, int DIM, bool FLAT>
+static cudaError_t launch_reflux_t(const StageArgs& a, cudaStream_t st);
+
 template <typename T, int DIM, bool FLAT, int MINB>
 static cudaError_t launch_stage_t(const StageArgs& a, int grid, int threads, size_t smem, cudaStream_t st) {
   cudaError_t e;
-  if (DIM == 3 && a.pwarps > 0) {
-    e = configure_ws_t<T, FLAT, MINB>();
-    if (e != cudaSuccess) return e;
-    stage_kernel_ws<T, FLAT, MINB><<<grid, threads, smem, st>>>(a);
-  } else {
+  if constexpr (DIM == 3 && MINB < 10) {
+    if (a.pwarps > 0) {
+      e = configure_ws_t<T, FLAT, MINB>();
+      if (e != cudaSuccess) return e;
+      stage_kernel_ws<T, FLAT, MINB><<<grid, threads, smem, st>>>(a);
+      e = cudaGetLastError();
+      if (e != cudaSuccess || a.nrcells == 0 || a.split) return e;
+      return launch_reflux_t<T, DIM, FLAT>(a, st);
+    }
+  }
+  {
     e = configure_stage_t<T, DIM, FLAT, MINB>();
     if (e != cudaSuccess) return e;
     stage_kernel<T, DIM, FLAT, MINB><<<grid, threads, smem, st>>>(a);
   }
   e = cudaGetLastError();
-  if (e != cudaSuccess || a.nrcells == 0) return e;
+  if (e != cudaSuccess || a.nrcells == 0 || a.split) return e;
+  return launch_reflux_t<T, DIM, FLAT>(a, st);
+}
+
+template <typename T, int DIM, bool FLAT>
+static cudaError_t launch_reflux_t(const StageArgs& a, cudaStream_t st) {
   int g = (a.nrcells + 127) / 128;
   reflux_kernel<T, DIM, FLAT><<<g, 128, 0, st>>>(a);
   return cudaGetLastError();
+}
+
+template <typename T>
+static cudaError_t launch_reflux_any(const StageArgs& a, cudaStream_t st) {
+  if (a.nrcells == 0) return cudaSuccess;
+  if (a.ndim == 3) return a.flat ? launch_reflux_t<T, 3, true>(a, st) : launch_reflux_t<T, 3, false>(a, st);
+  return a.flat ? launch_reflux_t<T, 2, true>(a, st) : launch_reflux_t<T, 2, false>(a, st);
 }
 
 // 3-D kernels exist with one or two resident CTAs per SM as the register
 // bound; 2-D grids use the one-CTA form.
 template <typename T>
 static cudaError_t launch_stage_any(const StageArgs& a, int grid, int threads, size_t smem, cudaStream_t st) {
+  if (a.split) {
+    if (a.ndim == 3) {
+      if (a.minb == 3)
+        return a.flat ? launch_stage_t<T, 3, true, 13>(a, grid, threads, smem, st)
+                      : launch_stage_t<T, 3, false, 13>(a, grid, threads, smem, st);
+      if (a.minb == 2)
+        return a.flat ? launch_stage_t<T, 3, true, 12>(a, grid, threads, smem, st)
+                      : launch_stage_t<T, 3, false, 12>(a, grid, threads, smem, st);
+      return a.flat ? launch_stage_t<T, 3, true, 11>(a, grid, threads, smem, st)
+                    : launch_stage_t<T, 3, false, 11>(a, grid, threads, smem, st);
+    }
+    return a.flat ? launch_stage_t<T, 2, true, 11>(a, grid, threads, smem, st)
+                  : launch_stage_t<T, 2, false, 11>(a, grid, threads, smem, st);
+  }
   if (a.ndim == 3) {
-    if (a.minb == 2)
+    if (a.minb >= 2)
       return a.flat ? launch_stage_t<T, 3, true, 2>(a, grid, threads, smem, st)
                     : launch_stage_t<T, 3, false, 2>(a, grid, threads, smem, st);
     return a.flat ? launch_stage_t<T, 3, true, 1>(a, grid, threads, smem, st)

@@ -59,7 +59,7 @@ def test_invalid_descriptions_are_rejected(bad):
 
 def test_status_strings():
     assert gb.status_string(0) == "ok"
-    assert gb.status_string(3) == "arena too small"
+    assert gb.status_string(3) == "arena too small or device allocation failed"
 
 
 def test_empty_and_inconsistent_block_lists_are_rejected():
