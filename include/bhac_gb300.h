@@ -70,7 +70,9 @@ typedef struct {
   int recon;             /* BHAC_RECON_* */
   int riemann;           /* BHAC_RIEMANN_* */
   int precision;         /* BHAC_PREC_FP64, or BHAC_PREC_MIXED: FP32 reconstruction,
-                            fluxes and sources summed into FP64 conserved state */
+                            fluxes and sources summed into FP64 conserved state;
+                            FP64 Newton inversion started from the FP32 previous
+                            primitives; a floored cell's D, S_i, tau rebuilt in FP32 */
   double gamma_ad;       /* ideal-gas index */
   double cfl;            /* Courant number */
   double ch, kappa;      /* GLM cleaning speed and damping rate */

@@ -227,13 +227,41 @@ void cell(const StageArgs& a, const HostState& h, int sb, int i, int j, int k, d
     Uu[v] = U[v] * N64(isg);
     Pg[v] = N64(Pd[(size_t)v * a.ncell]);
   }
-  const int st = con2prim_t<N64>(md, Uu, Pg, N64(rho_fl), N64(p_fl), a.c2p_gf, a.gam_fac, a.wmax, a.c2p_v2max,
+  // the mixed form starts Newton from the FP32 previous primitives and
+  // rebuilds a floored cell's D, S_i, tau in FP32 (as finish_cell does)
+  const bool mixed = std::is_same<T, N32>::value;
+  const float* crec32 =
+      (a.flat || !mixed) ? nullptr : h.tc32.data() + ((size_t)a.toff_c[L] + (size_t)I2 * N1 + I1) * CREC;
+  Met<N32> m32 = crec32 ? load_centre_metric<N32>(crec32) : flat_metric<N32>();
+  N64 Z0, v20;
+  if (mixed) {
+    const float* P3 = h.P32.data() + (size_t)sb * NV * a.ncell + cg;
+    N32 Pg32[NV];
+    for (int v = 0; v < NV; ++v) Pg32[v] = N32(P3[(size_t)v * a.ncell]);
+    N32 z, w;
+    c2p_guess<N32>(m32, Pg32, N32(a.gam_fac_f), z, w);
+    Z0 = N64((double)z.v);
+    v20 = N64((double)w.v);
+  } else {
+    c2p_guess<N64>(md, Pg, N64(a.gam_fac), Z0, v20);
+  }
+  const int st = con2prim_t<N64>(md, Uu, Pg, 1, Z0, v20, N64(rho_fl), N64(p_fl), a.c2p_gf, a.wmax, a.c2p_v2max,
                                  a.c2p_tol, a.c2p_maxit, Pn);
   if (st >= 2) {
-    Derived<N64> s;
-    derive(md, Pn, N64(a.gam_fac), s);
-    cons_of(Pn, s, Uu);
-    for (int v = 0; v < NV; ++v) U[v] = N64(sg) * Uu[v];
+    if (mixed) {
+      N32 P32[NV], Uc[NV];
+      for (int v = 0; v < NV; ++v) P32[v] = N32((float)Pn[v].v);
+      Derived<N32> s;
+      derive(m32, P32, N32(a.gam_fac_f), s);
+      cons_of(P32, s, Uc);
+      const N32 sg32 = N32(a.flat ? 1.0f : crec32[C_SG]);
+      for (int v = CD; v <= CTAU; ++v) U[v] = N64((double)(sg32 * Uc[v]).v);
+    } else {
+      Derived<N64> s;
+      derive(md, Pn, N64(a.gam_fac), s);
+      cons_of(Pn, s, Uu);
+      for (int v = 0; v < NV; ++v) U[v] = N64(sg) * Uu[v];
+    }
   }
   if (stage == 2) {
     N64 acg[3] = {N64(1.0), N64(1.0), N64(1.0)};

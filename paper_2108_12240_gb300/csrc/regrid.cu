@@ -147,7 +147,7 @@ __global__ void __launch_bounds__(256) transfer_kernel(StageArgs a, TransferArgs
     for (int v = 0; v < NV; ++v) Pin[(size_t)v * a.ncell] = Pg[v];
     const LevelGeo geo = level_geo(a, L);
     const int I1 = bc[0] * a.nx + loc[0], I2 = bc[1] * a.ny + loc[1];
-    finish_cell<T, DIM, FLAT>(a, geo, b, ci, cg, I1, I2, U, cnt, rate_max);
+    finish_cell<T, DIM, FLAT, false>(a, geo, b, ci, cg, I1, I2, U, cnt, rate_max);
   }
   reduce_outputs(a, cnt, rate_max);
 }

@@ -92,11 +92,25 @@ BHAC_HD T c2p_f1d(const C2PQ<T>& q, T gf, T v2max, T Z) {
   return Z - pr + T(0.5) * q.Bsq * (T(1.0) + v2) - T(0.5) * q.BS * q.BS / (Z * Z) - q.E;
 }
 
-// U undensitized; Pg the previous primitives; writes P; returns the status.
-// gf_d = (Gamma - 1)/Gamma and v2max_d = 1 - 1/W_max^2 come precomputed.
+// Newton starting point from the previous primitives Pg: Z = (rho + Gamma/(Gamma - 1) p) W^2
+// and v^2 = u^2 / W^2 with W^2 = 1 + u^2.
 template <typename T>
-BHAC_HD int con2prim_t(const Met<T>& m, const T* U, const T* Pg, T rho_fl, T p_fl, double gf_d,
-                       double gam_fac, double wmax_d, double v2max_d, double tol, int maxit, T* P) {
+BHAC_HD void c2p_guess(const Met<T>& m, const T* Pg, T gam_fac, T& Z0, T& v2) {
+  const T gu1 = m.g11 * Pg[U1] + m.g13 * Pg[U3];
+  const T gu2 = m.g22 * Pg[U2];
+  const T gu3 = m.g13 * Pg[U1] + m.g33 * Pg[U3];
+  const T usq = Pg[U1] * gu1 + Pg[U2] * gu2 + Pg[U3] * gu3;
+  Z0 = (Pg[RHO] + gam_fac * Pg[PRS]) * (T(1.0) + usq);
+  v2 = usq * rcp_t(T(1.0) + usq);
+}
+
+// U undensitized; (Z0g, v2g) the starting point (c2p_guess); Pg the previous
+// primitives, variable v at Pg[v ps], read only when every solver fails;
+// writes P; returns the status.  gf_d = (Gamma - 1)/Gamma and
+// v2max_d = 1 - 1/W_max^2 come precomputed.
+template <typename T>
+BHAC_HD int con2prim_t(const Met<T>& m, const T* U, const T* Pg, size_t ps, T Z0g, T v2g, T rho_fl, T p_fl,
+                       double gf_d, double wmax_d, double v2max_d, double tol, int maxit, T* P) {
   const T gf = T(gf_d);
   const T wmax = T(wmax_d);
   const T v2max = T(v2max_d);
@@ -119,14 +133,9 @@ BHAC_HD int con2prim_t(const Met<T>& m, const T* U, const T* Pg, T rho_fl, T p_f
   T Z = T(0.0), v2 = T(0.0);
   T W = T(0.0), sq = T(0.0);  // 1/sqrt(1 - v^2) and sqrt(1 - v^2) of the accepted solution
   if (fin && gt0_t(q.D) && gt0_t(q.E)) {
-    const T gu1 = m.g11 * Pg[U1] + m.g13 * Pg[U3];
-    const T gu2 = m.g22 * Pg[U2];
-    const T gu3 = m.g13 * Pg[U1] + m.g33 * Pg[U3];
-    const T usq = Pg[U1] * gu1 + Pg[U2] * gu2 + Pg[U3] * gu3;
-    const T Z0g = (Pg[RHO] + T(gam_fac) * Pg[PRS]) * (T(1.0) + usq);
     const T Z0 = (gt0_t(Z0g) && finite_t(Z0g)) ? Z0g : q.E;
     Z = Z0;
-    v2 = usq * rcp_t(T(1.0) + usq);
+    v2 = v2g;
     const T BS2 = q.BS * q.BS;
     for (int it = 0; it < maxit; ++it) {
       const T omv = T(1.0) - v2;
@@ -214,11 +223,11 @@ BHAC_HD int con2prim_t(const Met<T>& m, const T* U, const T* Pg, T rho_fl, T p_f
     P[U3] = c * (Su3 + bz * U[B3]);
   } else {
     status = 3;
-    P[RHO] = Pg[RHO];
-    P[PRS] = Pg[PRS];
-    P[U1] = Pg[U1];
-    P[U2] = Pg[U2];
-    P[U3] = Pg[U3];
+    P[RHO] = Pg[RHO * ps];
+    P[PRS] = Pg[PRS * ps];
+    P[U1] = Pg[U1 * ps];
+    P[U2] = Pg[U2 * ps];
+    P[U3] = Pg[U3 * ps];
   }
   P[B1] = U[B1];
   P[B2] = U[B2];
@@ -248,10 +257,11 @@ BHAC_HD int con2prim_t(const Met<T>& m, const T* U, const T* Pg, T rho_fl, T p_f
   return fl ? 2 : status;
 }
 
-static __device__ __forceinline__ int con2prim(const Met<double>& m, const double* U, const double* Pg, double rho_fl,
-                                            double p_fl, const StageArgs& a, double* P) {
-  return con2prim_t<double>(m, U, Pg, rho_fl, p_fl, a.c2p_gf, a.gam_fac, a.wmax, a.c2p_v2max, a.c2p_tol, a.c2p_maxit,
-                            P);
+static __device__ __forceinline__ int con2prim(const Met<double>& m, const double* U, const double* Pg, size_t ps,
+                                            double Z0, double v20, double rho_fl, double p_fl, const StageArgs& a,
+                                            double* P) {
+  return con2prim_t<double>(m, U, Pg, ps, Z0, v20, rho_fl, p_fl, a.c2p_gf, a.wmax, a.c2p_v2max, a.c2p_tol,
+                            a.c2p_maxit, P);
 }
 
 // CFL rate of one cell: sum over active d of c_d / dx_d, where c_d is the
@@ -486,32 +496,73 @@ __device__ __forceinline__ void to_register(const StageArgs& a, int b, int d, in
 }
 
 // Inversion, floors, outputs, counters and (stage 2) the CFL rate of a cell
-// whose stage conserved state U (densitized) is final.
-template <typename T, int DIM, bool FLAT>
+// whose stage conserved state U (densitized) is final.  The Newton iteration,
+// floors and CFL rate are FP64 in both forms.  In the mixed form (T = float)
+// the Newton starting point comes from the FP32 previous primitives (G32;
+// callers that hold their own FP64 starting point pass G32 = false) and a
+// floored cell's D, S_i, tau are rebuilt in FP32.
+template <typename T, int DIM, bool FLAT, bool G32 = (sizeof(T) == 4)>
 __device__ __forceinline__ void finish_cell(const StageArgs& a, const LevelGeo& geo, int b, int ci, int cg, int I1,
                                             int I2, double U[NV], unsigned cnt[4], double& rate_max) {
   const double* crec = FLAT ? nullptr : geo.tc + (size_t)(I2 * geo.N1 + I1) * CREC;
+  const float* crec32 = (FLAT || sizeof(T) == 8) ? nullptr : geo.tc32 + (size_t)(I2 * geo.N1 + I1) * CREC;
   const double sg = FLAT ? 1.0 : crec[C_SG];
   const double isg = FLAT ? 1.0 : crec[C_ISG];
   const double rho_fl = FLAT ? a.rho_fl_c : crec[C_RHOFL];
   const double p_fl = FLAT ? a.p_fl_c : crec[C_PFL];
   Met<double> md = FLAT ? flat_metric<double>() : load_centre_metric<double>(crec);
-  double Uu[NV], Pg[NV], Pn[NV];
+  Met<float> m32;
+  if (sizeof(T) == 4) m32 = FLAT ? flat_metric<float>() : load_centre_metric<float>(crec32);
+  double Uu[NV], Pn[NV];
   const double* Pd = a.P_in + (size_t)b * NV * a.ncell + cg;
 #pragma unroll
-  for (int v = 0; v < NV; ++v) {
-    Uu[v] = U[v] * isg;
-    Pg[v] = Pd[(size_t)v * a.ncell];
+  for (int v = 0; v < NV; ++v) Uu[v] = U[v] * isg;
+  int st;
+  if (G32) {
+    // mixed form: the Newton starting point from the FP32 previous primitives
+    // (a starting point needs no FP64); the FP64 ones are read only if every
+    // solver fails
+    const float* P3 = a.P32_in + (size_t)b * NV * a.ncell + cg;
+    float Pg32[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v)
+      Pg32[v] = (v == RHO || v == PRS || v == U1 || v == U2 || v == U3) ? P3[(size_t)v * a.ncell] : 0.0f;
+    float z0, w0;
+    c2p_guess<float>(m32, Pg32, a.gam_fac_f, z0, w0);
+    st = con2prim(md, Uu, Pd, (size_t)a.ncell, widen_f32(z0), widen_f32(w0), rho_fl, p_fl, a, Pn);
+  } else {
+    double Pg[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) Pg[v] = Pd[(size_t)v * a.ncell];
+    double z0, w0;
+    c2p_guess<double>(md, Pg, a.gam_fac, z0, w0);
+    st = con2prim(md, Uu, Pg, 1, z0, w0, rho_fl, p_fl, a, Pn);
   }
-  const int st = con2prim(md, Uu, Pg, rho_fl, p_fl, a, Pn);
   cnt[st] += 1u;
   a.status[(size_t)b * a.nint + ci] = (unsigned char)st;
-  if (st >= 2) {
-    Derived<double> s;
-    derive(md, Pn, a.gam_fac, s);
-    cons_of(Pn, s, Uu);
+  float P32[NV];
+  if (sizeof(T) == 4) {
 #pragma unroll
-    for (int v = 0; v < NV; ++v) U[v] = sg * Uu[v];
+    for (int v = 0; v < NV; ++v) P32[v] = narrow_f64(Pn[v]);
+  }
+  if (st >= 2) {
+    if (sizeof(T) == 4) {
+      // mixed form: the floored state's D, S_i, tau in FP32 (the field and psi
+      // are left as they are); FP64 form: every conserved variable in FP64
+      Derived<float> s;
+      derive(m32, P32, a.gam_fac_f, s);
+      float Uc[NV];
+      cons_of(P32, s, Uc);
+      const float sg32 = FLAT ? 1.0f : crec32[C_SG];
+#pragma unroll
+      for (int v = CD; v <= CTAU; ++v) U[v] = widen_f32(sg32 * Uc[v]);
+    } else {
+      Derived<double> s;
+      derive(md, Pn, a.gam_fac, s);
+      cons_of(Pn, s, Uu);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) U[v] = sg * Uu[v];
+    }
   }
   const size_t ub = (size_t)b * NV * a.nint + ci;
   double* Po = a.P_out + (size_t)b * NV * a.ncell + cg;
@@ -521,9 +572,9 @@ __device__ __forceinline__ void finish_cell(const StageArgs& a, const LevelGeo& 
     Po[(size_t)v * a.ncell] = Pn[v];
   }
   if (sizeof(T) == 4) {
-    float* P3 = a.P32_out + (size_t)b * NV * a.ncell + cg;
+    float* P3o = a.P32_out + (size_t)b * NV * a.ncell + cg;
 #pragma unroll
-    for (int v = 0; v < NV; ++v) P3[(size_t)v * a.ncell] = narrow_f64(Pn[v]);
+    for (int v = 0; v < NV; ++v) P3o[(size_t)v * a.ncell] = P32[v];
   }
   if (a.stage == 2) {
     double acg[3] = {1.0, 1.0, 1.0};

@@ -137,8 +137,12 @@ def test_backup_inversion_matches_oracle(gb, form):
     first step lands within rounding of the stopping threshold may take either
     of Newton's or the backup's answer, which agree to round-off: at most 1e-4
     of the cells may differ, and only between outcomes 0 and 1), conserved
-    state within 1e-12.  Mixed form: the backup is taken in the same share of
-    cells and the conserved state is within 1e-5."""
+    state within 1e-12.  Mixed form: its Newton iteration starts from the FP32
+    previous primitives, so cells whose FP64 starting point is already within
+    tol Z of the root (the near-stationary torus interior) need a second step
+    and go to the backup too: every cell the oracle sends to the backup takes
+    it (up to 1e-3 of the cells, at the threshold), and the conserved state is
+    within 1e-5."""
     g = pb.torus_3d(nroot=(4, 3, 2)).with_(c2p_maxit=1)
     P = pb.fm_torus_prims(g)
     s = gb.Solver(g, form)
@@ -159,7 +163,10 @@ def test_backup_inversion_matches_oracle(gb, form):
             assert pairs <= {(0, 1), (1, 0)}, pairs
             assert diff.sum() <= max(1, 1e-4 * ref_st.size), diff.sum()
         else:
-            assert abs(int((got_st == 1).sum()) - n1) <= 0.01 * ref_st.size
+            # floors report 2 whichever solver ran, so compare the unfloored cells
+            missed = (ref_st == 1) & (got_st != 1) & (got_st != 2)
+            assert missed.sum() <= max(1, 1e-3 * ref_st.size), missed.sum()
+            assert int((got_st == 1).sum()) >= n1 - 1e-3 * ref_st.size
     got, ref = s.cons(), o.cons()
     from tests.test_gpu_parity import assert_parity
     err = assert_parity(got, ref, TOL64 if form == "fp64" else TOLMIX, f"backup path ({form})", g)
