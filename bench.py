@@ -355,7 +355,7 @@ def e2e_form(gb, torch, g, P, form, steps, stream):
         s.host_fence()
 
     with torch.cuda.stream(stream):
-        run(1)  # untimed warm-up: first use of the scatter and gather kernels and the pinned buffers
+        run(1)  # untimed warm-up: first use of the load and gather kernels and the pinned buffers
     torch.cuda.synchronize()
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
     with torch.cuda.stream(stream):
@@ -364,7 +364,7 @@ def e2e_form(gb, torch, g, P, form, steps, stream):
         ev[1].record(stream)
     torch.cuda.synchronize()
     ms = ev[0].elapsed_time(ev[1])
-    launches = s.launches_per_step() + 4  # + scatter, init_cons, cfl, gather
+    launches = s.launches_per_step() + 2  # + the load (primitives, conserved state, CFL rate) and the gather
     s.close()
     return {"value": g.ncells * 2 * steps / (ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": nbytes,
             "d2h_bytes_per_step": nbytes, "ms_per_step": ms / steps, "kernels_per_step": launches}

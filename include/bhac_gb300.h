@@ -156,7 +156,10 @@ bhac_status bhac_fill_ghosts(bhac_ctx* ctx);
  *
  * Computes dt = cfl / max over interior cells of sum_d c_d/dx_d (c_d: largest of
  * the fast-magnetosonic speeds and the GLM speeds along d) into device memory;
- * also returns it through dt_host when non-NULL (synchronises the stream). */
+ * also returns it through dt_host when non-NULL (synchronises the stream).
+ * Right after a load (bhac_set_prims, bhac_set_prims_host_async), or a
+ * previous bhac_cfl_dt with no stage in between, the rate is already on the
+ * device and no kernel runs. */
 bhac_status bhac_cfl_dt(bhac_ctx* ctx, double* dt_host_or_null);
 
 /* Source: Sec. 2 (second-order time stepping of a finite-volume scheme with PPM
@@ -259,9 +262,10 @@ bhac_status bhac_regrid_transfer(const bhac_ctx* old_ctx, bhac_ctx* fresh_ctx);
  *
  * bhac_set_prims_host_async: copies interior primitives ([block][var][k][j][i],
  * FP64) from page-locked host memory into the input staging buffer on the
- * host-to-device copy stream, as soon as the previous load's scatter has
- * consumed that buffer; the context's stream then waits for the copy and
- * scatters and sets the conserved state as bhac_set_prims does.  Returns once
+ * host-to-device copy stream, as soon as the previous load has consumed that
+ * buffer; the context's stream then waits for the copy and loads it as
+ * bhac_set_prims does (one kernel: ghosted primitives, conserved state and
+ * the CFL rate of the loaded primitives).  Returns once
  * enqueued; `host_prims` must stay unchanged until a later bhac_host_fence()
  * has been followed by a synchronisation of the context's stream.
  *

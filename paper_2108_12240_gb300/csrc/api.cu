@@ -688,13 +688,15 @@ bhac_status bhac_set_prims(bhac_ctx* c, const double* prims, int on_device) {
   c->cur = 0;
   c->ucur = 0;
   StageArgs a = base_args(c);
-  cudaError_t e = launch_scatter_prims(a, src, c->P[0], c->P32[0], c->st);
-  if (e == cudaSuccess) e = launch_init_cons(a, c->P[0], c->U[0], c->st);
+  // one pass: ghosted primitives, conserved state and the CFL rate
+  cudaError_t e = cudaMemsetAsync(c->smax, 0, sizeof(unsigned long long), c->st);
+  if (e == cudaSuccess) e = launch_load(a, src, c->P[0], c->P32[0], c->U[0], c->st);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->d_status, 0, (size_t)c->nb * c->nint, c->st);
   if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(c->st);
   if (e != cudaSuccess) return BHAC_ERR_CUDA;
   c->prims_ok = true;
   c->cfl_ok = false;
+  c->cfl_fresh = true;
   c->faces_ok = false;
   c->pcur = 0;
   return BHAC_OK;
@@ -725,7 +727,7 @@ bhac_status bhac_set_prims_host_async(bhac_ctx* c, const double* host_prims) {
   if (!c->metric_ok) return BHAC_ERR_STATE;
   if (!page_locked(host_prims)) return BHAC_ERR_ARG;
   const size_t bytes = sizeof(double) * NV * (size_t)c->nb * c->nint;
-  // the copy starts once the previous load's scatter has consumed the staging buffer
+  // the copy starts once the previous load has consumed the staging buffer
   cudaError_t e = cudaStreamWaitEvent(c->cp_in, c->ev_scat, 0);
   if (e == cudaSuccess) e = cudaMemcpyAsync(c->scratch, host_prims, bytes, cudaMemcpyHostToDevice, c->cp_in);
   if (e == cudaSuccess) e = cudaEventRecord(c->ev_h2d, c->cp_in);
@@ -734,13 +736,16 @@ bhac_status bhac_set_prims_host_async(bhac_ctx* c, const double* host_prims) {
   c->cur = 0;
   c->ucur = 0;
   StageArgs a = base_args(c);
-  e = launch_scatter_prims(a, c->scratch, c->P[0], c->P32[0], c->st);
+  // one pass: ghosted primitives, conserved state and the CFL rate; then the
+  // staging buffer is free for the next load
+  e = cudaMemsetAsync(c->smax, 0, sizeof(unsigned long long), c->st);
+  if (e == cudaSuccess) e = launch_load(a, c->scratch, c->P[0], c->P32[0], c->U[0], c->st);
   if (e == cudaSuccess) e = cudaEventRecord(c->ev_scat, c->st);
-  if (e == cudaSuccess) e = launch_init_cons(a, c->P[0], c->U[0], c->st);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->d_status, 0, (size_t)c->nb * c->nint, c->st);
   if (e != cudaSuccess) return BHAC_ERR_CUDA;
   c->prims_ok = true;
   c->cfl_ok = false;
+  c->cfl_fresh = true;
   c->faces_ok = false;
   c->pcur = 0;
   return BHAC_OK;
@@ -785,10 +790,14 @@ bhac_status bhac_cfl_dt(bhac_ctx* c, double* dt_host) {
   NvtxRange range("bhac_cfl_dt");
   if (!c) return BHAC_ERR_ARG;
   if (!c->prims_ok) return BHAC_ERR_STATE;
-  if (cudaMemsetAsync(c->smax, 0, sizeof(unsigned long long), c->st) != cudaSuccess) return BHAC_ERR_CUDA;
-  StageArgs a = base_args(c);
-  a.P_in = c->P[c->cur];
-  if (launch_cfl(a, c->st) != cudaSuccess) return BHAC_ERR_CUDA;
+  if (!c->cfl_fresh) {
+    // (a load leaves the rate of the loaded primitives in smax already)
+    if (cudaMemsetAsync(c->smax, 0, sizeof(unsigned long long), c->st) != cudaSuccess) return BHAC_ERR_CUDA;
+    StageArgs a = base_args(c);
+    a.P_in = c->P[c->cur];
+    if (launch_cfl(a, c->st) != cudaSuccess) return BHAC_ERR_CUDA;
+    c->cfl_fresh = true;
+  }
   c->cfl_ok = true;
   if (dt_host) {
     unsigned long long bits = 0;
@@ -808,6 +817,7 @@ bhac_status bhac_stage(bhac_ctx* c, int stage, double dt) {
   if (!c->prims_ok) return BHAC_ERR_STATE;
   if (stage == 1 && !(dt > 0.0) && !c->cfl_ok) return BHAC_ERR_STATE;
   if (c->ct && !c->faces_ok) return BHAC_ERR_STATE;
+  c->cfl_fresh = false;  // the stage changes the primitives (stage 2 leaves their rate in smax)
   if (stage == 1 && c->d.imex && !c->ct) {
     // the IMEX first stage: the fluxes of stage 1 see psi of Y1
     StageArgs a = base_args(c);
@@ -964,6 +974,7 @@ bhac_status bhac_graph_capture(bhac_ctx* c, int nsteps) {
 bhac_status bhac_graph_launch(bhac_ctx* c) {
   if (!c) return BHAC_ERR_ARG;
   if (!c->graph) return BHAC_ERR_STATE;
+  c->cfl_fresh = false;
   return cuda_status(cudaGraphLaunch(c->graph, c->st));
 }
 
@@ -989,6 +1000,7 @@ bhac_status bhac_set_faces(bhac_ctx* c, const double* faces, int on_device) {
   if (e != cudaSuccess) return BHAC_ERR_CUDA;
   c->faces_ok = true;
   c->cfl_ok = false;
+  c->cfl_fresh = false;  // the cell field now comes from the faces
   return BHAC_OK;
 }
 

@@ -291,19 +291,6 @@ __device__ __forceinline__ void interior_coords(const StageArgs& a, long long t,
   cg = ((k + a.gz) * a.Ny + (j + a.gy)) * a.Nx + (i + a.gx);
 }
 
-__global__ void scatter_kernel(StageArgs a, const double* __restrict__ src, double* P, float* P32) {
-  const long long n = (long long)a.nblocks * a.nint;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
-    int b, ci, cg, i, j;
-    interior_coords(a, t, b, ci, cg, i, j);
-    for (int v = 0; v < NV; ++v) {
-      const double x = src[((size_t)b * NV + v) * a.nint + ci];
-      P[((size_t)b * NV + v) * a.ncell + cg] = x;
-      if (P32) P32[((size_t)b * NV + v) * a.ncell + cg] = (float)x;
-    }
-  }
-}
-
 __global__ void gather_kernel(StageArgs a, const double* __restrict__ P, double* dst) {
   const long long n = (long long)a.nblocks * a.nint;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
@@ -334,11 +321,6 @@ __global__ void init_cons_kernel(StageArgs a, const double* __restrict__ P, doub
     cons_of(Pc, s, Uc);
     for (int v = 0; v < NV; ++v) U[((size_t)b * NV + v) * a.nint + ci] = sg * Uc[v];
   }
-}
-
-cudaError_t launch_scatter_prims(const StageArgs& a, const double* src, double* P, float* P32, cudaStream_t st) {
-  scatter_kernel<<<grid_for((long long)a.nblocks * a.nint, 256), 256, 0, st>>>(a, src, P, P32);
-  return cudaGetLastError();
 }
 
 cudaError_t launch_gather_interior(const StageArgs& a, const double* P, double* dst, cudaStream_t st) {

@@ -43,6 +43,7 @@ struct bhac_ctx {
   int cur;       // primitive buffer holding the current state
   int ucur;      // conserved buffer holding the current state
   bool metric_ok, prims_ok, cfl_ok;
+  bool cfl_fresh;  // smax holds the CFL rate of the current primitives (set by loads and bhac_cfl_dt)
   // launch shape
   int tx, ty, threads, persistent, minb, pwarps;
   // refinement levels: metric-table record offsets per level

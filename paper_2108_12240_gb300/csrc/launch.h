@@ -19,6 +19,9 @@ constexpr int kTwoCtaSmem = 113 * 1024;
 cudaError_t launch_stage_fp64(const StageArgs& a, int grid, int threads, size_t smem, cudaStream_t st);
 cudaError_t launch_stage_mixed(const StageArgs& a, int grid, int threads, size_t smem, cudaStream_t st);
 cudaError_t launch_cfl(const StageArgs& a, cudaStream_t st);
+// one pass that loads interior primitives into the ghosted arrays, sets the
+// conserved state and reduces the CFL rate into a.smax_out
+cudaError_t launch_load(const StageArgs& a, const double* src, double* P, float* P32, double* U, cudaStream_t st);
 // split form: the cell kernel over a range of items, and the reflux pass
 cudaError_t launch_cells_fp64(const StageArgs& a, int grid, cudaStream_t st);
 cudaError_t launch_cells_mixed(const StageArgs& a, int grid, cudaStream_t st);
@@ -64,8 +67,7 @@ struct MetricArgs {
 };
 cudaError_t launch_metric_tables(const MetricArgs& m, cudaStream_t st);
 
-// interior <-> ghosted copies and the initial conserved state
-cudaError_t launch_scatter_prims(const StageArgs& a, const double* src, double* P, float* P32, cudaStream_t st);
+// interior <-> ghosted copies and the conserved state of loaded primitives
 cudaError_t launch_gather_interior(const StageArgs& a, const double* P, double* dst, cudaStream_t st);
 cudaError_t launch_init_cons(const StageArgs& a, const double* P, double* U, cudaStream_t st);
 
