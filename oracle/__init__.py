@@ -56,6 +56,7 @@ class OrParams(C.Structure):
         ("c2p_tol", C.c_double), ("c2p_maxit", C.c_int),
         ("rho_floor", C.c_double), ("rho_floor_pow", C.c_double), ("p_floor", C.c_double),
         ("p_floor_pow", C.c_double), ("w_max", C.c_double), ("ct", C.c_int), ("imex", C.c_int),
+        ("c2p_nk", C.c_int),
     ]
 
 
@@ -138,6 +139,7 @@ def params_of(grid) -> OrParams:
     p.w_max = grid.w_max
     p.ct = 1 if getattr(grid, "divb", "glm") == "ct" else 0
     p.imex = 1 if getattr(grid, "imex", False) else 0
+    p.c2p_nk = 1 if getattr(grid, "c2p", "newton") == "nk" else 0
     return p
 
 

@@ -337,10 +337,94 @@ static int finite9(const double* x) {
   return 1;
 }
 
+/* Momentum and energy residuals of the two-dimensional system in (Z, v^2):
+ *   F1 = (Z + B^2)^2 v^2 - (B.S)^2 (2 Z + B^2) / Z^2 - S^2,
+ *   F2 = Z - p + B^2 (1 + v^2)/2 - (B.S)^2 / (2 Z^2) - E. */
+static void c2p_residual(const c2p_in* q, double gf, double Z, double v2, double F[2]) {
+  double sq = sqrt(1.0 - v2);
+  double pr = gf * (Z * (1.0 - v2) - q->D * sq);
+  double BS2 = q->BS * q->BS;
+  F[0] = (Z + q->B2) * (Z + q->B2) * v2 - BS2 * (2.0 * Z + q->B2) / (Z * Z) - q->S2;
+  F[1] = Z - pr + 0.5 * q->B2 * (1.0 + v2) - 0.5 * BS2 / (Z * Z) - q->E;
+}
+
+/* One Jacobian-free Newton-Krylov step for the residuals above, at (Z, v^2).
+ * The system is scaled: rows by 1/(Z + B^2)^2 and 1/Z, the unknowns are
+ * (dZ / Z, dv^2).  The Newton equation J s = -F is solved by GMRES, whose
+ * Krylov space is the whole plane after two vectors, so two Arnoldi steps give
+ * its solution; each product of J with a unit vector u is the forward
+ * difference (G(x + eps u) - G(x)) / eps with eps = sqrt(machine epsilon),
+ * taken backwards when the forward point would leave 0 <= v^2 < 1.  Returns
+ * the step (dZ, dv^2). */
+static void c2p_nk_step(const c2p_in* q, double gf, double Z, double v2, double* dZ, double* dv2) {
+  const double eps = 1.4901161193847656e-08; /* 2^-26 */
+  double rs[2] = {1.0 / ((Z + q->B2) * (Z + q->B2)), 1.0 / Z};
+  double F[2], G0[2];
+  c2p_residual(q, gf, Z, v2, F);
+  G0[0] = rs[0] * F[0];
+  G0[1] = rs[1] * F[1];
+  double beta = sqrt(G0[0] * G0[0] + G0[1] * G0[1]);
+  *dZ = 0.0;
+  *dv2 = 0.0;
+  if (!(beta > 0.0)) return;
+  double V[2][2], Jv[2];
+  V[0][0] = -G0[0] / beta;
+  V[0][1] = -G0[1] / beta;
+  double H[2][2] = {{0.0, 0.0}, {0.0, 0.0}}; /* H[row][col] of the Arnoldi relation */
+  int m = 2;
+  for (int k = 0; k < 2; ++k) {
+    /* Jv = J V[k] by a one-sided difference */
+    double h = eps;
+    double w = v2 + h * V[k][1];
+    if (w < 0.0 || w >= 1.0) h = -eps;
+    double Fp[2];
+    c2p_residual(q, gf, Z + h * V[k][0] * Z, v2 + h * V[k][1], Fp);
+    Jv[0] = (rs[0] * Fp[0] - G0[0]) / h;
+    Jv[1] = (rs[1] * Fp[1] - G0[1]) / h;
+    /* modified Gram-Schmidt against the earlier basis vectors */
+    for (int i = 0; i <= k; ++i) {
+      H[i][k] = Jv[0] * V[i][0] + Jv[1] * V[i][1];
+      Jv[0] -= H[i][k] * V[i][0];
+      Jv[1] -= H[i][k] * V[i][1];
+    }
+    if (k == 0) {
+      double h21 = sqrt(Jv[0] * Jv[0] + Jv[1] * Jv[1]);
+      H[1][0] = h21;
+      if (!(h21 > 1e-14 * fabs(H[0][0]))) { /* V[0] spans an invariant direction */
+        m = 1;
+        break;
+      }
+      V[1][0] = Jv[0] / h21;
+      V[1][1] = Jv[1] / h21;
+    }
+  }
+  double y[2];
+  if (m == 1) {
+    y[0] = beta / H[0][0];
+    y[1] = 0.0;
+  } else {
+    /* least squares min |beta e1 - H y| for the 2 x 2 Hessenberg H (exact in
+     * the plane): one Givens rotation, then back substitution */
+    double r = sqrt(H[0][0] * H[0][0] + H[1][0] * H[1][0]);
+    double c = H[0][0] / r, sn = H[1][0] / r;
+    double R12 = c * H[0][1] + sn * H[1][1];
+    double R22 = -sn * H[0][1] + c * H[1][1];
+    double g0 = c * beta, g1 = -sn * beta;
+    y[1] = g1 / R22;
+    y[0] = (g0 - R12 * y[1]) / r;
+  }
+  double s0 = y[0] * V[0][0] + y[1] * (m == 2 ? V[1][0] : 0.0);
+  double s1 = y[0] * V[0][1] + y[1] * (m == 2 ? V[1][1] : 0.0);
+  *dZ = Z * s0;
+  *dv2 = s1;
+}
+
 /* Primary solver: two-dimensional Newton-Raphson in (Z, v^2) on the momentum
- * and energy equations (the "2D" scheme of Noble et al. 2006), started from
- * the previous primitives; stop when the step |dZ| <= tol Z (the iteration
- * converges quadratically, so that iterate is accurate to round-off).
+ * and energy equations (the "2D" scheme of Noble et al. 2006), or with
+ * p->c2p_nk the Jacobian-free Newton-Krylov step above in its place, started
+ * from the previous primitives; stop when the step |dZ| <= tol Z (the
+ * iteration converges quadratically, so that iterate is accurate to
+ * round-off).
  * Backup: bracketed bisection on Z of the one-dimensional energy residual.
  * Last resort: keep the previous primitives (status 3).  Floors last. */
 int or_con2prim(const or_params* p, const or_metric* m, const double U[OR_NV], const double Pg[OR_NV],
@@ -379,20 +463,25 @@ int or_con2prim(const or_params* p, const or_metric* m, const double U[OR_NV], c
     v2 = u2 / (1.0 + u2);
     if (!(Z > 0.0) || !isfinite(Z)) Z = q.E;
     for (int it = 0; it < p->c2p_maxit; ++it) {
-      double sq = sqrt(1.0 - v2);
-      double pr = gf * (Z * (1.0 - v2) - q.D * sq);
-      double BS2 = q.BS * q.BS;
-      double f1 = (Z + q.B2) * (Z + q.B2) * v2 - BS2 * (2.0 * Z + q.B2) / (Z * Z) - q.S2;
-      double f2 = Z - pr + 0.5 * q.B2 * (1.0 + v2) - 0.5 * BS2 / (Z * Z) - q.E;
-      double j11 = 2.0 * (Z + q.B2) * v2 + 2.0 * BS2 * (Z + q.B2) / (Z * Z * Z);
-      double j12 = (Z + q.B2) * (Z + q.B2);
-      double dpdZ = gf * (1.0 - v2);
-      double dpdv2 = gf * (-Z + 0.5 * q.D / sq);
-      double j21 = 1.0 - dpdZ + BS2 / (Z * Z * Z);
-      double j22 = -dpdv2 + 0.5 * q.B2;
-      double det = j11 * j22 - j12 * j21;
-      double dZ = (-f1 * j22 + f2 * j12) / det;
-      double dv2 = (-f2 * j11 + f1 * j21) / det;
+      double dZ, dv2;
+      if (p->c2p_nk) {
+        c2p_nk_step(&q, gf, Z, v2, &dZ, &dv2);
+      } else {
+        double sq = sqrt(1.0 - v2);
+        double pr = gf * (Z * (1.0 - v2) - q.D * sq);
+        double BS2 = q.BS * q.BS;
+        double f1 = (Z + q.B2) * (Z + q.B2) * v2 - BS2 * (2.0 * Z + q.B2) / (Z * Z) - q.S2;
+        double f2 = Z - pr + 0.5 * q.B2 * (1.0 + v2) - 0.5 * BS2 / (Z * Z) - q.E;
+        double j11 = 2.0 * (Z + q.B2) * v2 + 2.0 * BS2 * (Z + q.B2) / (Z * Z * Z);
+        double j12 = (Z + q.B2) * (Z + q.B2);
+        double dpdZ = gf * (1.0 - v2);
+        double dpdv2 = gf * (-Z + 0.5 * q.D / sq);
+        double j21 = 1.0 - dpdZ + BS2 / (Z * Z * Z);
+        double j22 = -dpdv2 + 0.5 * q.B2;
+        double det = j11 * j22 - j12 * j21;
+        dZ = (-f1 * j22 + f2 * j12) / det;
+        dv2 = (-f2 * j11 + f1 * j21) / det;
+      }
       double Zn = Z + dZ, v2n = v2 + dv2;
       if (!(Zn > 0.0)) Zn = 0.5 * Z;
       if (v2n < 0.0) v2n = 0.5 * v2;

@@ -69,6 +69,8 @@ typedef struct {
                             (uniform grids; psi is not evolved, ch and kappa are ignored) */
   int imex;              /* 0: the cleaning damping -alpha kappa psi is an explicit source;
                             1: it is the implicit part of IMEX-SSP2(2,2,2) */
+  int c2p_nk;            /* primary inversion: 0 Newton-Raphson with the analytic Jacobian,
+                            1 Jacobian-free Newton-Krylov (GMRES on difference quotients) */
 } or_params;
 
 /* Spatial metric at a point plus its first derivatives along the code

@@ -45,6 +45,7 @@ class Grid:
     w_max: float = 50.0
     divb: str = "glm"         # "glm" (cleaning) or "ct" (constrained transport, uniform grids)
     imex: bool = False        # cleaning damping as the implicit part of IMEX-SSP2(2,2,2)
+    c2p: str = "newton"       # primary inversion: "newton" (analytic Jacobian) or "nk" (Jacobian-free Newton-Krylov)
     ng: int = 3
     nlevels: int = 1
     blocks: np.ndarray = field(default=None, repr=False)  # (nb, 4) int32: level, ix, iy, iz
