@@ -632,6 +632,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="torus_3d_large")
     ap.add_argument("--form", default="both", choices=["both", "mixed", "fp64"])
+    ap.add_argument("--c2p", default="newton", choices=["newton", "nk"],
+                    help="primary inversion: analytic Newton (default) or Jacobian-free Newton-Krylov")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-ct", action="store_true", help="skip the constrained-transport form")
@@ -686,6 +688,9 @@ def main():
 
     g, desc = workload(args.workload)
     P = initial_prims(g)
+    if args.c2p != "newton":
+        g = g.with_(c2p=args.c2p)
+        desc += f"; {args.c2p} inversion"
     stream = torch.cuda.Stream()
     forms = ["mixed", "fp64"] if args.form == "both" else [args.form]
     ct_faces = None
@@ -739,7 +744,7 @@ def main():
         # FP64: 288 B per zone-stage; mixed: 252; constrained
         # transport adds the face fields read and written (3 x 8 B each way)
         bytes_alg = {"fp64": 288, "mixed": 252, "fp64_ct": 336}[form] * cells
-        traffic = recorded_traffic(args.workload, form, shape_key(r["launch_shape"]))
+        traffic = recorded_traffic(args.workload, form, shape_key(r["launch_shape"])) if args.c2p == "newton" else None
         fill = fill_roofline(g, form, r["fill_ms"], pk.get("hbm_gbs"))
         return {"bound": "alu", "achieved": ach64, "peak": alu["fp64_tflops"], "unit": "TFLOP/s",
                 "frac": ach64 / alu["fp64_tflops"], "traffic": traffic,

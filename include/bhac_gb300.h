@@ -54,6 +54,7 @@ enum { BHAC_RECON_PPM = 0, BHAC_RECON_MINMOD = 1 };
 enum { BHAC_RIEMANN_HLL = 0, BHAC_RIEMANN_TVDLF = 1 };
 enum { BHAC_PREC_FP64 = 0, BHAC_PREC_MIXED = 1 };
 enum { BHAC_DIVB_GLM = 0, BHAC_DIVB_CT = 1 };
+enum { BHAC_C2P_NEWTON = 0, BHAC_C2P_NK = 1 };
 
 /* Grid and scheme description, copied at init. */
 typedef struct {
@@ -90,6 +91,12 @@ typedef struct {
                             scheme (Pareschi & Russo 2005) whose explicit part is the SSP-RK2
                             step, so any kappa dt is stable (Sec. 2: implicit/explicit time
                             stepping for stiff sources).  Ignored with constrained transport. */
+  int c2p_solver;        /* primary conserved-to-primitive solver (Sec. 2: Newton-Raphson and
+                            Newton-Krylov solvers with backups): BHAC_C2P_NEWTON, 2-D
+                            Newton-Raphson with the analytic Jacobian; BHAC_C2P_NK,
+                            Jacobian-free Newton-Krylov (GMRES on difference quotients of the
+                            same residuals).  Both stop at |dZ| <= c2p_tol Z and share the
+                            bisection backup and the floors. */
 } bhac_grid_desc;
 
 /* One leaf block: refinement level and integer block coordinates at that level. */

@@ -46,6 +46,7 @@ class GridDesc(C.Structure):
         ("ch", C.c_double), ("kappa", C.c_double), ("c2p_tol", C.c_double), ("c2p_maxit", C.c_int),
         ("rho_floor", C.c_double), ("rho_floor_pow", C.c_double), ("p_floor", C.c_double),
         ("p_floor_pow", C.c_double), ("w_max", C.c_double), ("divb", C.c_int), ("imex", C.c_int),
+        ("c2p_solver", C.c_int),
     ]
 
 
@@ -329,6 +330,7 @@ def desc_of(grid, precision: str = "fp64") -> GridDesc:
     d.w_max = grid.w_max
     d.divb = 1 if getattr(grid, "divb", "glm") == "ct" else 0
     d.imex = 1 if getattr(grid, "imex", False) else 0
+    d.c2p_solver = {"newton": 0, "nk": 1}[getattr(grid, "c2p", "newton")]
     return d
 
 

@@ -57,6 +57,7 @@ bool valid_desc(const bhac_grid_desc* d, const bhac_block_desc* b, int nb) {
   if (d->divb < 0 || d->divb > 1) return false;
   if (d->divb == BHAC_DIVB_CT && (d->nlevels != 1 || d->precision != BHAC_PREC_FP64)) return false;
   if (d->imex < 0 || d->imex > 1) return false;
+  if (d->c2p_solver != BHAC_C2P_NEWTON && d->c2p_solver != BHAC_C2P_NK) return false;
   // the axis rule is for x2 (theta) only; phi must be periodic with an even cell count in 3-D
   for (int k = 0; k < 3; ++k)
     for (int s = 0; s < 2; ++s)
@@ -220,6 +221,7 @@ StageArgs base_args(const bhac_ctx* c) {
   a.c2p_maxit = d.c2p_maxit;
   a.wmax = d.w_max;
   a.imex = d.imex && !c->ct;
+  a.c2p_nk = d.c2p_solver == BHAC_C2P_NK;
   a.imex_g = 1.0 - 1.0 / sqrt(2.0);
   a.c2p_gf = (d.gamma_ad - 1.0) / d.gamma_ad;
   a.c2p_v2max = 1.0 - 1.0 / (d.w_max * d.w_max);

@@ -61,6 +61,7 @@ struct StageArgs {
   void* R;                   // that right-hand side, T per (block, var, interior cell)
   int item0, item1;          // (block, tile) items of this launch, in the visiting order
   int imex;                  // the cleaning damping is the implicit part of IMEX-SSP2(2,2,2)
+  int c2p_nk;                // primary inversion: Jacobian-free Newton-Krylov (else analytic Newton)
   double imex_g;             // its gamma = 1 - 1/sqrt(2)
   double wmax, rho_fl_c, p_fl_c;  // constant floors (flat coordinates)
   // state

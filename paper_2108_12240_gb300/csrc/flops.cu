@@ -246,7 +246,7 @@ void cell(const StageArgs& a, const HostState& h, int sb, int i, int j, int k, d
     c2p_guess<N64>(md, Pg, N64(a.gam_fac), Z0, v20);
   }
   const int st = con2prim_t<N64>(md, Uu, Pg, 1, Z0, v20, N64(rho_fl), N64(p_fl), a.c2p_gf, a.wmax, a.c2p_v2max,
-                                 a.c2p_tol, a.c2p_maxit, Pn);
+                                 a.c2p_tol, a.c2p_maxit, a.c2p_nk, Pn);
   if (st >= 2) {
     if (mixed) {
       N32 P32[NV], Uc[NV];

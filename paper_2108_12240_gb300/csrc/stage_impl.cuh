@@ -92,6 +92,102 @@ BHAC_HD T c2p_f1d(const C2PQ<T>& q, T gf, T v2max, T Z) {
   return Z - pr + T(0.5) * q.Bsq * (T(1.0) + v2) - T(0.5) * q.BS * q.BS / (Z * Z) - q.E;
 }
 
+// A product rounded on its own: the inversion's steps (dZ, dv^2) come out of
+// either solver as finished values, so the update Z + dZ is the same addition
+// whichever solver a kernel carries (no fused multiply-add across the choice).
+template <typename T>
+BHAC_HD T mul_rn(T a, T b) {
+  return a * b;
+}
+template <>
+BHAC_HD double mul_rn<double>(double a, double b) {
+#ifdef __CUDA_ARCH__
+  return __dmul_rn(a, b);
+#else
+  return a * b;
+#endif
+}
+
+// Momentum and energy residuals of the two-dimensional system in (Z, v^2):
+//   F1 = (Z + B^2)^2 v^2 - (B.S)^2 (2 Z + B^2) / Z^2 - S^2,
+//   F2 = Z - p + B^2 (1 + v^2)/2 - (B.S)^2 / (2 Z^2) - E.
+template <typename T>
+BHAC_HD void c2p_residual_t(const C2PQ<T>& q, T gf, T Z, T v2, T& F1, T& F2) {
+  const T omv = T(1.0) - v2;
+  const T sq = omv * rsqrt_t(omv);
+  const T pr = gf * (Z * omv - q.D * sq);
+  const T iZ = rcp_t(Z);
+  const T iZ2 = iZ * iZ;
+  const T BS2 = q.BS * q.BS;
+  const T ZB = Z + q.Bsq;
+  F1 = ZB * ZB * v2 - BS2 * (T(2.0) * Z + q.Bsq) * iZ2 - q.S2;
+  F2 = Z - pr + T(0.5) * q.Bsq * (T(1.0) + v2) - T(0.5) * BS2 * iZ2 - q.E;
+}
+
+// One Jacobian-free Newton-Krylov step at (Z, v^2): the system scaled by rows
+// 1/(Z + B^2)^2 and 1/Z, unknowns (dZ/Z, dv^2); GMRES, whose Krylov space is
+// the plane after two vectors, on products of the Jacobian with unit vectors
+// taken as forward differences with step 2^-26 (backward where the forward
+// point would leave 0 <= v^2 < 1).  Writes the step (dZ, dv^2).
+template <typename T>
+BHAC_HD void c2p_nk_step_t(const C2PQ<T>& q, T gf, T Z, T v2, T& dZ, T& dv2) {
+  const T eps = T(1.4901161193847656e-08), ieps = T(67108864.0);  // 2^-26, 2^26
+  const T ZB = Z + q.Bsq;
+  const T rs0 = rcp_t(ZB * ZB), rs1 = rcp_t(Z);
+  T F1, F2;
+  c2p_residual_t(q, gf, Z, v2, F1, F2);
+  const T G1 = rs0 * F1, G2 = rs1 * F2;
+  const T beta = sqrt_t(G1 * G1 + G2 * G2);
+  dZ = T(0.0);
+  dv2 = T(0.0);
+  if (!gt0_t(beta)) return;
+  const T ib = rcp_t(beta);
+  const T a1 = -G1 * ib, a2 = -G2 * ib;  // first basis vector
+  // J a by a one-sided difference
+  T sgn = T(1.0);
+  {
+    const T w = v2 + eps * a2;
+    if (lt0_x(w) || le_x(T(1.0), w)) sgn = T(-1.0);
+  }
+  T P1, P2;
+  c2p_residual_t(q, gf, Z + sgn * eps * a1 * Z, v2 + sgn * eps * a2, P1, P2);
+  T j1 = (rs0 * P1 - G1) * (sgn * ieps), j2 = (rs1 * P2 - G2) * (sgn * ieps);
+  const T h11 = j1 * a1 + j2 * a2;
+  j1 = j1 - h11 * a1;
+  j2 = j2 - h11 * a2;
+  const T h21 = sqrt_t(j1 * j1 + j2 * j2);
+  if (!lt_t(T(1e-14) * abs_t(h11), h21)) {  // a spans an invariant direction
+    const T y = beta * rcp_t(h11);
+    dZ = mul_rn(Z, y * a1);
+    dv2 = mul_rn(y, a2);
+    return;
+  }
+  const T i21 = rcp_t(h21);
+  const T b1 = j1 * i21, b2 = j2 * i21;  // second basis vector
+  sgn = T(1.0);
+  {
+    const T w = v2 + eps * b2;
+    if (lt0_x(w) || le_x(T(1.0), w)) sgn = T(-1.0);
+  }
+  c2p_residual_t(q, gf, Z + sgn * eps * b1 * Z, v2 + sgn * eps * b2, P1, P2);
+  T k1 = (rs0 * P1 - G1) * (sgn * ieps), k2 = (rs1 * P2 - G2) * (sgn * ieps);
+  const T h12 = k1 * a1 + k2 * a2;
+  k1 = k1 - h12 * a1;
+  k2 = k2 - h12 * a2;
+  const T h22 = k1 * b1 + k2 * b2;
+  // min |beta e1 - H y| for the 2 x 2 Hessenberg H: a Givens rotation, then
+  // back substitution
+  const T r = sqrt_t(h11 * h11 + h21 * h21);
+  const T ir = rcp_t(r);
+  const T c = h11 * ir, sn = h21 * ir;
+  const T R12 = c * h12 + sn * h22;
+  const T R22 = -sn * h12 + c * h22;
+  const T y1 = (-sn * beta) * rcp_t(R22);
+  const T y0 = (c * beta - R12 * y1) * ir;
+  dZ = mul_rn(Z, y0 * a1 + y1 * b1);
+  dv2 = mul_rn(y0, a2) + mul_rn(y1, b2);
+}
+
 // Newton starting point from the previous primitives Pg: Z = (rho + Gamma/(Gamma - 1) p) W^2
 // and v^2 = u^2 / W^2 with W^2 = 1 + u^2.
 template <typename T>
@@ -108,9 +204,12 @@ BHAC_HD void c2p_guess(const Met<T>& m, const T* Pg, T gam_fac, T& Z0, T& v2) {
 // primitives, variable v at Pg[v ps], read only when every solver fails;
 // writes P; returns the status.  gf_d = (Gamma - 1)/Gamma and
 // v2max_d = 1 - 1/W_max^2 come precomputed.
-template <typename T>
+// NKM: the primary solver, 0 analytic Newton, 1 Newton-Krylov, 2 chosen at run
+// time by nk (kernels that pick the solver at compile time carry no code of the
+// other one).
+template <typename T, int NKM = 2>
 BHAC_HD int con2prim_t(const Met<T>& m, const T* U, const T* Pg, size_t ps, T Z0g, T v2g, T rho_fl, T p_fl,
-                       double gf_d, double wmax_d, double v2max_d, double tol, int maxit, T* P) {
+                       double gf_d, double wmax_d, double v2max_d, double tol, int maxit, int nk, T* P) {
   const T gf = T(gf_d);
   const T wmax = T(wmax_d);
   const T v2max = T(v2max_d);
@@ -138,22 +237,27 @@ BHAC_HD int con2prim_t(const Met<T>& m, const T* U, const T* Pg, size_t ps, T Z0
     v2 = v2g;
     const T BS2 = q.BS * q.BS;
     for (int it = 0; it < maxit; ++it) {
-      const T omv = T(1.0) - v2;
-      const T isq = rsqrt_t(omv);
-      const T sq = omv * isq;
-      const T pr = gf * (Z * omv - q.D * sq);
-      const T iZ = rcp_t(Z);
-      const T iZ2 = iZ * iZ;
-      const T ZB = Z + q.Bsq;
-      const T f1 = ZB * ZB * v2 - BS2 * (T(2.0) * Z + q.Bsq) * iZ2 - q.S2;
-      const T f2 = Z - pr + T(0.5) * q.Bsq * (T(1.0) + v2) - T(0.5) * BS2 * iZ2 - q.E;
-      const T j11 = T(2.0) * ZB * v2 + T(2.0) * BS2 * ZB * iZ2 * iZ;
-      const T j12 = ZB * ZB;
-      const T j21 = T(1.0) - gf * omv + BS2 * iZ2 * iZ;
-      const T j22 = -gf * (-Z + T(0.5) * q.D * isq) + T(0.5) * q.Bsq;
-      const T idet = rcp_t(j11 * j22 - j12 * j21);
-      const T dZ = (-f1 * j22 + f2 * j12) * idet;
-      const T dv2 = (-f2 * j11 + f1 * j21) * idet;
+      T dZ, dv2;
+      if (NKM == 1 || (NKM == 2 && nk)) {
+        c2p_nk_step_t(q, gf, Z, v2, dZ, dv2);
+      } else {
+        const T omv = T(1.0) - v2;
+        const T isq = rsqrt_t(omv);
+        const T sq = omv * isq;
+        const T pr = gf * (Z * omv - q.D * sq);
+        const T iZ = rcp_t(Z);
+        const T iZ2 = iZ * iZ;
+        const T ZB = Z + q.Bsq;
+        const T f1 = ZB * ZB * v2 - BS2 * (T(2.0) * Z + q.Bsq) * iZ2 - q.S2;
+        const T f2 = Z - pr + T(0.5) * q.Bsq * (T(1.0) + v2) - T(0.5) * BS2 * iZ2 - q.E;
+        const T j11 = T(2.0) * ZB * v2 + T(2.0) * BS2 * ZB * iZ2 * iZ;
+        const T j12 = ZB * ZB;
+        const T j21 = T(1.0) - gf * omv + BS2 * iZ2 * iZ;
+        const T j22 = -gf * (-Z + T(0.5) * q.D * isq) + T(0.5) * q.Bsq;
+        const T idet = rcp_t(j11 * j22 - j12 * j21);
+        dZ = mul_rn(-f1 * j22 + f2 * j12, idet);
+        dv2 = mul_rn(-f2 * j11 + f1 * j21, idet);
+      }
       T Zn = Z + dZ, v2n = v2 + dv2;
       if (!gt0_t(Zn)) Zn = T(0.5) * Z;
       if (lt0_x(v2n)) v2n = T(0.5) * v2;
@@ -257,11 +361,12 @@ BHAC_HD int con2prim_t(const Met<T>& m, const T* U, const T* Pg, size_t ps, T Z0
   return fl ? 2 : status;
 }
 
+template <int NKM>
 static __device__ __forceinline__ int con2prim(const Met<double>& m, const double* U, const double* Pg, size_t ps,
                                             double Z0, double v20, double rho_fl, double p_fl, const StageArgs& a,
                                             double* P) {
-  return con2prim_t<double>(m, U, Pg, ps, Z0, v20, rho_fl, p_fl, a.c2p_gf, a.wmax, a.c2p_v2max, a.c2p_tol,
-                            a.c2p_maxit, P);
+  return con2prim_t<double, NKM>(m, U, Pg, ps, Z0, v20, rho_fl, p_fl, a.c2p_gf, a.wmax, a.c2p_v2max, a.c2p_tol,
+                                 a.c2p_maxit, a.c2p_nk, P);
 }
 
 // CFL rate of one cell: sum over active d of c_d / dx_d, where c_d is the
@@ -501,7 +606,7 @@ __device__ __forceinline__ void to_register(const StageArgs& a, int b, int d, in
 // the Newton starting point comes from the FP32 previous primitives (G32;
 // callers that hold their own FP64 starting point pass G32 = false) and a
 // floored cell's D, S_i, tau are rebuilt in FP32.
-template <typename T, int DIM, bool FLAT, bool G32 = (sizeof(T) == 4)>
+template <typename T, int DIM, bool FLAT, bool G32 = (sizeof(T) == 4), int NKM = 2>
 __device__ __forceinline__ void finish_cell(const StageArgs& a, const LevelGeo& geo, int b, int ci, int cg, int I1,
                                             int I2, double U[NV], unsigned cnt[4], double& rate_max) {
   const double* crec = FLAT ? nullptr : geo.tc + (size_t)(I2 * geo.N1 + I1) * CREC;
@@ -529,14 +634,14 @@ __device__ __forceinline__ void finish_cell(const StageArgs& a, const LevelGeo& 
       Pg32[v] = (v == RHO || v == PRS || v == U1 || v == U2 || v == U3) ? P3[(size_t)v * a.ncell] : 0.0f;
     float z0, w0;
     c2p_guess<float>(m32, Pg32, a.gam_fac_f, z0, w0);
-    st = con2prim(md, Uu, Pd, (size_t)a.ncell, widen_f32(z0), widen_f32(w0), rho_fl, p_fl, a, Pn);
+    st = con2prim<NKM>(md, Uu, Pd, (size_t)a.ncell, widen_f32(z0), widen_f32(w0), rho_fl, p_fl, a, Pn);
   } else {
     double Pg[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) Pg[v] = Pd[(size_t)v * a.ncell];
     double z0, w0;
     c2p_guess<double>(md, Pg, a.gam_fac, z0, w0);
-    st = con2prim(md, Uu, Pg, 1, z0, w0, rho_fl, p_fl, a, Pn);
+    st = con2prim<NKM>(md, Uu, Pg, 1, z0, w0, rho_fl, p_fl, a, Pn);
   }
   cnt[st] += 1u;
   a.status[(size_t)b * a.nint + ci] = (unsigned char)st;
@@ -606,7 +711,7 @@ __device__ __forceinline__ void reduce_outputs(const StageArgs& a, const unsigne
   }
 }
 
-template <typename T, int DIM, bool FLAT>
+template <typename T, int DIM, bool FLAT, int NKM = 2>
 __device__ __forceinline__ void rk_finish(const StageArgs& a, const LevelGeo& geo, int b, int ci, int cg, int I1, int I2,
                                           int bi, int bj, int k, const double rhs[NV], double dt, unsigned cfb,
                                           unsigned cnt[4], double& rate_max);
@@ -614,7 +719,7 @@ __device__ __forceinline__ void rk_finish(const StageArgs& a, const LevelGeo& ge
 // Divergence of the face fluxes staged in shared memory, sources, RK stage
 // combination and (unless the reflux pass owns the cell) the inversion of cell
 // c of plane k in the tile at (x0, y0) of block b.
-template <typename T, int DIM, bool FLAT, bool SPLIT>
+template <typename T, int DIM, bool FLAT, bool SPLIT, int NKM = 2>
 __device__ __forceinline__ void cell_update(const StageArgs& a, const LevelGeo& geo, const T* __restrict__ Pb, int b,
                                             int x0, int y0, int k, int c, const T* Fx, const T* Fy, const T* Fz0,
                                             const T* Fz1, double dt, unsigned cfb, unsigned cnt[4],
@@ -687,12 +792,12 @@ __device__ __forceinline__ void cell_update(const StageArgs& a, const LevelGeo& 
     for (int v = 0; v < NV; ++v) R[(size_t)v * a.nint] = sizeof(T) == 4 ? (T)narrow_f64(rhs[v]) : (T)rhs[v];
     return;
   }
-  rk_finish<T, DIM, FLAT>(a, geo, b, ci, cg, I1, I2, x0 + i, y0 + j, k, rhs, dt, cfb, cnt, rate_max);
+  rk_finish<T, DIM, FLAT, NKM>(a, geo, b, ci, cg, I1, I2, x0 + i, y0 + j, k, rhs, dt, cfb, cnt, rate_max);
 }
 
 // RK combination (and the IMEX damping), then the inversion, floors, outputs
 // and CFL rate of cell (bi, bj, k) of block b, given the stage right-hand side.
-template <typename T, int DIM, bool FLAT>
+template <typename T, int DIM, bool FLAT, int NKM>
 __device__ __forceinline__ void rk_finish(const StageArgs& a, const LevelGeo& geo, int b, int ci, int cg, int I1, int I2,
                                           int bi, int bj, int k, const double rhs[NV], double dt, unsigned cfb,
                                           unsigned cnt[4], double& rate_max) {
@@ -729,7 +834,7 @@ __device__ __forceinline__ void rk_finish(const StageArgs& a, const LevelGeo& ge
 #pragma unroll
     for (int v = 0; v < NV; ++v) a.Uout[ub + (size_t)v * a.nint] = U[v];
   } else {
-    finish_cell<T, DIM, FLAT>(a, geo, b, ci, cg, I1, I2, U, cnt, rate_max);
+    finish_cell<T, DIM, FLAT, (sizeof(T) == 4), NKM>(a, geo, b, ci, cg, I1, I2, U, cnt, rate_max);
   }
 }
 
@@ -751,6 +856,10 @@ __device__ __forceinline__ void rk_finish(const StageArgs& a, const LevelGeo& ge
 // the same numbers as a per-face reconstruction's.
 //
 // Shared memory (T): Fx, Fy, [Fz0, Fz1, EzR in 3-D], ExL, ExR, EyL, EyR.
+//
+// MINB: the register bound (resident CTAs per SM) in its last digit; + 10: the
+// face kernel of the split form (no inversion code); + 100: the Newton-Krylov
+// inversion in place of the analytic Newton step.
 // ----------------------------------------------------------------------------
 template <typename T, int DIM, bool FLAT, int MINB>
 __global__ void __launch_bounds__(256, MINB % 10) stage_kernel(StageArgs a) {
@@ -870,7 +979,8 @@ __global__ void __launch_bounds__(256, MINB % 10) stage_kernel(StageArgs a) {
       __syncthreads();
       // C: cell updates
       for (int c = threadIdx.x; c < sFz; c += blockDim.x)
-        cell_update<T, DIM, FLAT, (MINB >= 10)>(a, geo, Pb, b, x0, y0, k, c, Fx, Fy, Fz0, Fz1, dt, cfb, cnt, rate_max);
+        cell_update<T, DIM, FLAT, (MINB % 100 >= 10), (MINB >= 100 ? 1 : 0)>(a, geo, Pb, b, x0, y0, k, c, Fx, Fy, Fz0,
+                                                                          Fz1, dt, cfb, cnt, rate_max);
       __syncthreads();
       T* tmp = Fz0;
       Fz0 = Fz1;
@@ -1284,6 +1394,17 @@ static cudaError_t launch_stage_any(const StageArgs& a, int grid, int threads, s
     }
     return a.flat ? launch_stage_t<T, 2, true, 11>(a, grid, threads, smem, st)
                   : launch_stage_t<T, 2, false, 11>(a, grid, threads, smem, st);
+  }
+  if (a.c2p_nk && a.pwarps == 0) {  // the Newton-Krylov inversion compiled in
+    if (a.ndim == 3) {
+      if (a.minb >= 2)
+        return a.flat ? launch_stage_t<T, 3, true, 102>(a, grid, threads, smem, st)
+                      : launch_stage_t<T, 3, false, 102>(a, grid, threads, smem, st);
+      return a.flat ? launch_stage_t<T, 3, true, 101>(a, grid, threads, smem, st)
+                    : launch_stage_t<T, 3, false, 101>(a, grid, threads, smem, st);
+    }
+    return a.flat ? launch_stage_t<T, 2, true, 101>(a, grid, threads, smem, st)
+                  : launch_stage_t<T, 2, false, 101>(a, grid, threads, smem, st);
   }
   if (a.ndim == 3) {
     if (a.minb >= 2)

@@ -103,3 +103,17 @@ def test_imex_flag_is_validated():
     with pytest.raises(gb.BhacError) as e:
         gb.bhac_query_sizes(d, gb.blocks_of(g))
     assert e.value.status == 1
+
+
+def test_c2p_solver_is_validated():
+    """The primary inversion is BHAC_C2P_NEWTON (0) or BHAC_C2P_NK (1); the
+    Newton-Krylov choice sizes the same arena, another value is rejected."""
+    g = pb.shock_tube_2d(nblock=16, nroot=2)
+    n0 = gb.bhac_query_sizes(gb.desc_of(g), gb.blocks_of(g))
+    assert gb.bhac_query_sizes(gb.desc_of(g.with_(c2p="nk")), gb.blocks_of(g)) == n0
+    for bad in (-1, 2):
+        d = gb.desc_of(g)
+        d.c2p_solver = bad
+        with pytest.raises(gb.BhacError) as e:
+            gb.bhac_query_sizes(d, gb.blocks_of(g))
+        assert e.value.status == 1
