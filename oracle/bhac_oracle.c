@@ -8,8 +8,8 @@
  * It follows the method of the paper's Sec. 2 ("Code overview"): a
  * shock-capturing finite-volume scheme on a block grid with ghost cells,
  * covariant coordinates, a second-order two-stage time stepper, PPM (or
- * minmod) reconstruction, and a Newton conserved-to-primitive inversion with
- * backup strategies.  The concrete equations are the standard 3+1 ("Valencia")
+ * minmod) reconstruction, and a Newton (or Jacobian-free Newton-Krylov)
+ * conserved-to-primitive inversion with backup strategies.  The concrete equations are the standard 3+1 ("Valencia")
  * ideal GRMHD system with GLM divergence cleaning; each function names the
  * published form it writes out.  The code favours obviousness over speed:
  * metric quantities are re-evaluated at every point, nothing is fused.
