@@ -297,7 +297,7 @@ def fill_roofline(g, form: str, fill_ms: float, hbm_gbs):
     flag byte."""
     ghosts = g.nb * (int(np.prod([g.nx[d] + (2 * g.ng if d < g.ndim else 0) for d in range(3)]))
                      - int(np.prod(g.nx)))
-    fill_bytes = ghosts * (NVAR * (4 if form == "mixed" else 8) * 2 + 5)
+    fill_bytes = ghosts * (NVAR * (4 if form.startswith("mixed") else 8) * 2 + 5)
     gbs = fill_bytes / (fill_ms * 1e-3) / 1e9 if fill_ms > 0 else None
     return {"bound": "hbm", "achieved": gbs, "peak": hbm_gbs, "unit": "GB/s",
             "frac": gbs / hbm_gbs if (gbs and hbm_gbs) else None,
@@ -696,19 +696,19 @@ def main():
     ct_faces = None
     if args.form == "both" and not args.no_ct and g.nlevels == 1 and g.coords == "mks":
         # constrained transport beside the cleaning forms: the same torus with
-        # its loop field as face fields, FP64
+        # its loop field as face fields, both forms
         from problems import ct as pct
         ct_faces = pct.fm_torus_faces(g, P)
-        forms.append("fp64_ct")
+        forms += ["mixed_ct", "fp64_ct"]
     results = {}
     for form in forms:
         if dist:
             dist.barrier()
         torch.cuda.synchronize()
         with Clocks(local) as ck:
-            if form == "fp64_ct":
-                results[form] = time_form(gb, torch, g.with_(divb="ct"), P, "fp64", args.steps, args.warmup, stream,
-                                          faces=ct_faces)
+            if form.endswith("_ct"):
+                results[form] = time_form(gb, torch, g.with_(divb="ct"), P, form[:-3], args.steps, args.warmup,
+                                          stream, faces=ct_faces)
             else:
                 results[form] = time_form(gb, torch, g, P, form, args.steps, args.warmup, stream)
         results[form]["clocks"] = ck.summary()
@@ -743,12 +743,12 @@ def main():
         ach64 = fl["fp64_flops"] * cells / stage_s / 1e12
         # FP64: 288 B per zone-stage; mixed: 252; constrained
         # transport adds the face fields read and written (3 x 8 B each way)
-        bytes_alg = {"fp64": 288, "mixed": 252, "fp64_ct": 336}[form] * cells
+        bytes_alg = {"fp64": 288, "mixed": 252, "fp64_ct": 336, "mixed_ct": 300}[form] * cells
         traffic = recorded_traffic(args.workload, form, shape_key(r["launch_shape"])) if args.c2p == "newton" else None
         fill = fill_roofline(g, form, r["fill_ms"], pk.get("hbm_gbs"))
         return {"bound": "alu", "achieved": ach64, "peak": alu["fp64_tflops"], "unit": "TFLOP/s",
                 "frac": ach64 / alu["fp64_tflops"], "traffic": traffic,
-                "kernel": "ct_flux/ct_face/ct_cell kernels" if form == "fp64_ct" else "stage_kernel",
+                "kernel": "ct_flux/ct_face/ct_cell kernels" if form.endswith("_ct") else "stage_kernel",
                 "traffic_source": os.path.relpath(TRAFFIC_FILE, ROOT) if traffic else None,
                 "traffic_over_algorithmic": traffic / bytes_alg if traffic else None,
                 "stage_ms": r["stage_ms_mean"], "ghost_fill_ms": r["fill_ms"],

@@ -84,8 +84,10 @@ typedef struct {
                             W <= w_max; r = 1 in Cartesian coordinates */
   int divb;              /* BHAC_DIVB_GLM: GLM cleaning (psi evolved with ch, kappa);
                             BHAC_DIVB_CT: staggered-mesh constrained transport of face
-                            fields (uniform grids, nlevels = 1, FP64 form; psi stays 0,
-                            ch and kappa are ignored) */
+                            fields (uniform grids, nlevels = 1; psi stays 0, ch and
+                            kappa are ignored).  In the mixed form the face states and
+                            fluxes are FP32; the EMFs, the face update and the face
+                            field stay FP64, so div B stays at FP64 round-off */
   int imex;              /* 0: the cleaning damping -alpha kappa psi is an explicit source
                             of both stages; 1: it is the implicit part of the IMEX-SSP2(2,2,2)
                             scheme (Pareschi & Russo 2005) whose explicit part is the SSP-RK2

@@ -55,7 +55,7 @@ bool valid_desc(const bhac_grid_desc* d, const bhac_block_desc* b, int nb) {
   if (!(d->w_max > 1.0)) return false;
   // constrained transport: uniform grids in the FP64 form
   if (d->divb < 0 || d->divb > 1) return false;
-  if (d->divb == BHAC_DIVB_CT && (d->nlevels != 1 || d->precision != BHAC_PREC_FP64)) return false;
+  if (d->divb == BHAC_DIVB_CT && d->nlevels != 1) return false;
   if (d->imex < 0 || d->imex > 1) return false;
   if (d->c2p_solver != BHAC_C2P_NEWTON && d->c2p_solver != BHAC_C2P_NK) return false;
   // the axis rule is for x2 (theta) only; phi must be periodic with an even cell count in 3-D
@@ -381,6 +381,9 @@ CtArgs ct_args(const bhac_ctx* c) {
   t.te_c = c->te_c;
   t.te_f1 = c->te_f1;
   t.te_f2 = c->te_f2;
+  t.te_c32 = c->te_c32;
+  t.te_f1_32 = c->te_f1_32;
+  t.te_f2_32 = c->te_f2_32;
   t.axis_lo = c->d.bc[1][0] == BHAC_BC_AXIS;
   t.axis_hi = c->d.bc[1][1] == BHAC_BC_AXIS;
   return t;
@@ -398,6 +401,8 @@ bhac_status run_stage_ct(bhac_ctx* c, int stage, double dt) {
   a.dt_host = dt;
   a.P_in = c->P[in];
   a.P_out = c->P[out];
+  a.P32_in = c->P32[in];
+  a.P32_out = c->P32[out];
   if (stage == 1) {
     a.Un = c->U[c->ucur];
     a.U1 = nullptr;
@@ -409,7 +414,7 @@ bhac_status run_stage_ct(bhac_ctx* c, int stage, double dt) {
   }
   CtArgs t = ct_args(c);
   if (launch_ct_ring(c->ring_dst, c->ring_src, c->nring, c->phi[c->pcur], c->st) != cudaSuccess) return BHAC_ERR_CUDA;
-  if (launch_ct_stage(a, t, c->st) != cudaSuccess) return BHAC_ERR_CUDA;
+  if (launch_ct_stage(a, t, c->mixed, c->st) != cudaSuccess) return BHAC_ERR_CUDA;
   c->cur = out;
   c->ucur = 1 - c->ucur;
   c->pcur = 1 - c->pcur;
@@ -996,7 +1001,7 @@ bhac_status bhac_set_faces(bhac_ctx* c, const double* faces, int on_device) {
   CtArgs t = ct_args(c);
   cudaError_t e = launch_ct_copy_faces(a, c->ctg, src, c->phi[0], 1, c->st);
   // the cell field of the loaded primitives from the faces, then U
-  if (e == cudaSuccess) e = launch_ct_cell_field(a, t, c->P[c->cur], c->st);
+  if (e == cudaSuccess) e = launch_ct_cell_field(a, t, c->P[c->cur], c->mixed ? c->P32[c->cur] : nullptr, c->st);
   if (e == cudaSuccess) e = launch_init_cons(a, c->P[c->cur], c->U[c->ucur], c->st);
   if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(c->st);
   if (e != cudaSuccess) return BHAC_ERR_CUDA;

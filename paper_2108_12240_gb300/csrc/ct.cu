@@ -1,5 +1,9 @@
 // Staggered-mesh constrained transport (the div B control of the method's
-// Sec. 2) on uniform grids, FP64.
+// Sec. 2) on uniform grids, in the FP64 form or the mixed form (T = float: the
+// face states and fluxes in FP32 from the FP32 primitives, the fluxes stored,
+// the EMFs, the face update and the face field in FP64, so the discrete
+// divergence stays at FP64 round-off; the cell sources in FP32 and the
+// inversion as in the mixed stage kernel).
 //
 // Evolved field: Phi^d = sqrt(gamma) B^d at the centre of every face normal to
 // an active direction d.  A stage runs, after the usual ghost-cell fill:
@@ -127,57 +131,77 @@ __global__ void __launch_bounds__(256) ct_ring_kernel(const long long* __restric
     phi[dst[t]] = phi[src[t]];
 }
 
+__device__ __forceinline__ double to_t(double x, double) { return x; }
+__device__ __forceinline__ float to_t(double x, float) { return narrow_f64(x); }
+
 // Flux through face (D; i, j, k) of block b (D a compile-time direction, so
-// the states stay in registers), q its index among the direction's faces.
-template <int D, bool FLAT>
+// the states stay in registers), q its index among the direction's faces; T
+// the flux arithmetic (double: FP64 form; float: mixed form).
+template <typename T, int D, bool FLAT>
 __device__ __forceinline__ void ct_one_face(const StageArgs& a, const CtArgs& c, int b, int i, int j, int k,
                                             long long q) {
   const int G1 = a.blk[4 * b + 1] * a.nx + i, G2 = a.blk[4 * b + 2] * a.ny + j;
-  double F[NV];
+  T F[NV];
   const bool axis = !FLAT && D == 1 && ((G2 == 0 && c.axis_lo) || (G2 == a.N2g && c.axis_hi));
   if (axis) {
 #pragma unroll
-    for (int v = 0; v < NV; ++v) F[v] = 0.0;
+    for (int v = 0; v < NV; ++v) F[v] = T(0.0);
   } else {
     const int sd = D == 0 ? 1 : (D == 1 ? a.Nx : a.Nx * a.Ny);
     const int c0 = ((k + a.gz) * a.Ny + (j + a.gy)) * a.Nx + (i + a.gx);  // the cell above the face
-    const double* Pb = a.P_in + (size_t)b * NV * a.ncell;
-    double PL[NV], PR[NV];
+    const T* Pb = (sizeof(T) == 8 ? reinterpret_cast<const T*>(a.P_in) : reinterpret_cast<const T*>(a.P32_in)) +
+                  (size_t)b * NV * a.ncell;
+    T PL[NV], PR[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
-      const double* p = Pb + (size_t)v * a.ncell + c0;
+      const T* p = Pb + (size_t)v * a.ncell + c0;
       recon_var(a.recon, p[-3 * sd], p[-2 * sd], p[-sd], p[0], p[sd], p[2 * sd], PL[v], PR[v]);
     }
     positivity_fallback(a, Pb, sd, c0, PL, PR);
-    Met<double> m;
-    double acg = 1.0;
+    Met<T> m;
+    T acg = T(1.0);
     if (FLAT) {
-      m = flat_metric<double>();
+      m = flat_metric<T>();
     } else if (D == 0) {
-      const double* rec = c.te_f1 + ((size_t)(G2 + 1) * (a.N1g + 3) + (G1 + 1)) * FREC;
-      m = load_face_metric<double>(rec);
-      acg = rec[F_ACG];
+      const size_t r = ((size_t)(G2 + 1) * (a.N1g + 3) + (G1 + 1)) * FREC;
+      if (sizeof(T) == 8) {
+        m = load_face_metric<T>(c.te_f1 + r);
+        acg = T(c.te_f1[r + F_ACG]);
+      } else {
+        m = load_face_metric<T>(c.te_f1_32 + r);
+        acg = T(c.te_f1_32[r + F_ACG]);
+      }
     } else if (D == 1) {
-      const double* rec = c.te_f2 + ((size_t)(G2 + 1) * (a.N1g + 2) + (G1 + 1)) * FREC;
-      m = load_face_metric<double>(rec);
-      acg = rec[F_ACG];
+      const size_t r = ((size_t)(G2 + 1) * (a.N1g + 2) + (G1 + 1)) * FREC;
+      if (sizeof(T) == 8) {
+        m = load_face_metric<T>(c.te_f2 + r);
+        acg = T(c.te_f2[r + F_ACG]);
+      } else {
+        m = load_face_metric<T>(c.te_f2_32 + r);
+        acg = T(c.te_f2_32[r + F_ACG]);
+      }
     } else {
-      const double* rec = c.te_c + ((size_t)(G2 + 1) * (a.N1g + 2) + (G1 + 1)) * CREC;
-      m = load_centre_metric<double>(rec);
-      acg = rec[C_ACG3];
+      const size_t r = ((size_t)(G2 + 1) * (a.N1g + 2) + (G1 + 1)) * CREC;
+      if (sizeof(T) == 8) {
+        m = load_centre_metric<T>(c.te_c + r);
+        acg = T(c.te_c[r + C_ACG3]);
+      } else {
+        m = load_centre_metric<T>(c.te_c32 + r);
+        acg = T(c.te_c32[r + C_ACG3]);
+      }
     }
-    const double Bn = c.phi_in[(long long)b * c.g.nfb + ring_index(c.g, D, i, j, k)] / m.sg;
+    const T Bn = to_t(c.phi_in[(long long)b * c.g.nfb + ring_index(c.g, D, i, j, k)], T(0)) / m.sg;
     PL[B1 + D] = Bn;
     PR[B1 + D] = Bn;
-    riemann_flux(m, acg, PL, PR, D, a.riemann, a.gam, a.gam_fac, 0.0, F);
+    riemann_flux(m, acg, PL, PR, D, a.riemann, pick<T>(a.gam, a.gam_f), pick<T>(a.gam_fac, a.gam_fac_f), T(0.0), F);
   }
   const long long o = (long long)b * NV * c.g.nfb + NV * c.g.foff[D] + q;
 #pragma unroll
-  for (int v = 0; v < NV; ++v) c.xf[o + v * c.g.nfd[D]] = F[v];
+  for (int v = 0; v < NV; ++v) c.xf[o + v * c.g.nfd[D]] = to_double(F[v]);
 }
 
 // Fluxes through every face of every block and its ring, one thread per face.
-template <bool FLAT>
+template <typename T, bool FLAT>
 __global__ void __launch_bounds__(256) ct_flux_kernel(StageArgs a, CtArgs c) {
   const long long n = (long long)a.nblocks * c.g.nfb;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
@@ -190,11 +214,11 @@ __global__ void __launch_bounds__(256) ct_flux_kernel(StageArgs a, CtArgs c) {
     const int j = (int)((q / e0) % e1) - c.g.fo[d][1];
     const int k = (int)(q / ((long long)e0 * e1)) - c.g.fo[d][2];
     if (d == 0)
-      ct_one_face<0, FLAT>(a, c, b, i, j, k, q);
+      ct_one_face<T, 0, FLAT>(a, c, b, i, j, k, q);
     else if (d == 1)
-      ct_one_face<1, FLAT>(a, c, b, i, j, k, q);
+      ct_one_face<T, 1, FLAT>(a, c, b, i, j, k, q);
     else
-      ct_one_face<2, FLAT>(a, c, b, i, j, k, q);
+      ct_one_face<T, 2, FLAT>(a, c, b, i, j, k, q);
   }
 }
 
@@ -256,8 +280,10 @@ __global__ void __launch_bounds__(256) ct_face_kernel(StageArgs a, CtArgs c) {
 }
 
 // Flux divergence, sources, RK combination, the cell field from the updated
-// faces, then the stage kernel's inversion, floors, outputs and CFL rate.
-template <int DIM, bool FLAT>
+// faces, then the stage kernel's inversion, floors, outputs and CFL rate.  T:
+// the arithmetic of the sources (float in the mixed form, from the FP32
+// primitives and metric records).
+template <typename T, int DIM, bool FLAT>
 __global__ void __launch_bounds__(256) ct_cell_kernel(StageArgs a, CtArgs c) {
   const double dt = stage_dt(a);
   if (a.stage == 1 && blockIdx.x == 0 && threadIdx.x == 0) *a.dt_dev = dt;
@@ -281,18 +307,20 @@ __global__ void __launch_bounds__(256) ct_cell_kernel(StageArgs a, CtArgs c) {
       for (int v = 0; v < NV; ++v) rhs[v] += -(xf_at(c, b, d, v, ih, jh, kh) - xf_at(c, b, d, v, i, j, k)) / a.dxl0[d];
     }
     if (!FLAT) {
-      const double* crec = geo.tc + (size_t)(I2 * geo.N1 + I1) * CREC;
-      double Pc[NV], Uc[NV], S[NV];
+      const T* crec = (sizeof(T) == 8 ? reinterpret_cast<const T*>(geo.tc) : reinterpret_cast<const T*>(geo.tc32)) +
+                      (size_t)(I2 * geo.N1 + I1) * CREC;
+      const T* Pin = sizeof(T) == 8 ? reinterpret_cast<const T*>(a.P_in) : reinterpret_cast<const T*>(a.P32_in);
+      T Pc[NV], Uc[NV], S[NV];
 #pragma unroll
-      for (int v = 0; v < NV; ++v) Pc[v] = a.P_in[(size_t)b * NV * a.ncell + (size_t)v * a.ncell + cg];
-      const Met<double> m = load_centre_metric<double>(crec);
-      Derived<double> s;
-      derive(m, Pc, a.gam_fac, s);
+      for (int v = 0; v < NV; ++v) Pc[v] = Pin[(size_t)b * NV * a.ncell + (size_t)v * a.ncell + cg];
+      const Met<T> m = load_centre_metric<T>(crec);
+      Derived<T> s;
+      derive(m, Pc, pick<T>(a.gam_fac, a.gam_fac_f), s);
       cons_of(Pc, s, Uc);
-      sources_of(m, crec, Pc, s, Uc, 0.0, 0.0, S);
-      const double sg = crec[C_SG];
+      sources_of(m, crec, Pc, s, Uc, T(0.0), T(0.0), S);
+      const T sg = crec[C_SG];
 #pragma unroll
-      for (int v = 0; v < NV; ++v) rhs[v] += sg * S[v];
+      for (int v = 0; v < NV; ++v) rhs[v] += to_double(sg * S[v]);
     }
     const size_t ub = (size_t)b * NV * a.nint + ci;
     double U[NV];
@@ -308,14 +336,14 @@ __global__ void __launch_bounds__(256) ct_cell_kernel(StageArgs a, CtArgs c) {
       U[B1 + d] = 0.5 * (c.phi_out[lo] + c.phi_out[hi]);
     }
     U[PSI] = 0.0;
-    finish_cell<double, DIM, FLAT>(a, geo, b, ci, cg, I1, I2, U, cnt, rate_max);
+    finish_cell<T, DIM, FLAT>(a, geo, b, ci, cg, I1, I2, U, cnt, rate_max);
   }
   reduce_outputs(a, cnt, rate_max);
 }
 
 // The cell field of the loaded state from its faces.
 template <int DIM>
-__global__ void __launch_bounds__(256) ct_cell_field_kernel(StageArgs a, CtArgs c, double* P) {
+__global__ void __launch_bounds__(256) ct_cell_field_kernel(StageArgs a, CtArgs c, double* P, float* P32) {
   const long long n = (long long)a.nblocks * a.nint;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
     const int b = (int)(t / a.nint);
@@ -333,8 +361,10 @@ __global__ void __launch_bounds__(256) ct_cell_field_kernel(StageArgs a, CtArgs 
       const long long lo = (long long)b * c.g.nfb + ring_index(c.g, d, i, j, k);
       const long long hi = (long long)b * c.g.nfb + ring_index(c.g, d, i + (d == 0), j + (d == 1), k + (d == 2));
       Pc[(size_t)(B1 + d) * a.ncell] = 0.5 * (c.phi_in[lo] + c.phi_in[hi]) / sg;
+      if (P32) P32[(size_t)b * NV * a.ncell + cg + (size_t)(B1 + d) * a.ncell] = narrow_f64(Pc[(size_t)(B1 + d) * a.ncell]);
     }
     Pc[(size_t)PSI * a.ncell] = 0.0;
+    if (P32) P32[(size_t)b * NV * a.ncell + cg + (size_t)PSI * a.ncell] = 0.0f;
   }
 }
 
@@ -371,13 +401,20 @@ cudaError_t launch_ct_ring(const long long* dst, const long long* src, long long
   return cudaGetLastError();
 }
 
-cudaError_t launch_ct_stage(const StageArgs& a, const CtArgs& c, cudaStream_t st) {
+cudaError_t launch_ct_stage(const StageArgs& a, const CtArgs& c, bool mixed, cudaStream_t st) {
   const long long nf = (long long)a.nblocks * c.g.nfb, no = (long long)a.nblocks * c.g.nown_b,
                   nc = (long long)a.nblocks * a.nint;
-  if (a.flat)
-    ct_flux_kernel<true><<<grid_of(nf), 256, 0, st>>>(a, c);
-  else
-    ct_flux_kernel<false><<<grid_of(nf), 256, 0, st>>>(a, c);
+  if (mixed) {
+    if (a.flat)
+      ct_flux_kernel<float, true><<<grid_of(nf), 256, 0, st>>>(a, c);
+    else
+      ct_flux_kernel<float, false><<<grid_of(nf), 256, 0, st>>>(a, c);
+  } else {
+    if (a.flat)
+      ct_flux_kernel<double, true><<<grid_of(nf), 256, 0, st>>>(a, c);
+    else
+      ct_flux_kernel<double, false><<<grid_of(nf), 256, 0, st>>>(a, c);
+  }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (a.ndim == 3)
@@ -386,21 +423,30 @@ cudaError_t launch_ct_stage(const StageArgs& a, const CtArgs& c, cudaStream_t st
     ct_face_kernel<2><<<grid_of(no), 256, 0, st>>>(a, c);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  if (a.ndim == 3)
-    a.flat ? ct_cell_kernel<3, true><<<grid_of(nc), 256, 0, st>>>(a, c)
-           : ct_cell_kernel<3, false><<<grid_of(nc), 256, 0, st>>>(a, c);
-  else
-    a.flat ? ct_cell_kernel<2, true><<<grid_of(nc), 256, 0, st>>>(a, c)
-           : ct_cell_kernel<2, false><<<grid_of(nc), 256, 0, st>>>(a, c);
+  if (mixed) {
+    if (a.ndim == 3)
+      a.flat ? ct_cell_kernel<float, 3, true><<<grid_of(nc), 256, 0, st>>>(a, c)
+             : ct_cell_kernel<float, 3, false><<<grid_of(nc), 256, 0, st>>>(a, c);
+    else
+      a.flat ? ct_cell_kernel<float, 2, true><<<grid_of(nc), 256, 0, st>>>(a, c)
+             : ct_cell_kernel<float, 2, false><<<grid_of(nc), 256, 0, st>>>(a, c);
+  } else {
+    if (a.ndim == 3)
+      a.flat ? ct_cell_kernel<double, 3, true><<<grid_of(nc), 256, 0, st>>>(a, c)
+             : ct_cell_kernel<double, 3, false><<<grid_of(nc), 256, 0, st>>>(a, c);
+    else
+      a.flat ? ct_cell_kernel<double, 2, true><<<grid_of(nc), 256, 0, st>>>(a, c)
+             : ct_cell_kernel<double, 2, false><<<grid_of(nc), 256, 0, st>>>(a, c);
+  }
   return cudaGetLastError();
 }
 
-cudaError_t launch_ct_cell_field(const StageArgs& a, const CtArgs& c, double* P, cudaStream_t st) {
+cudaError_t launch_ct_cell_field(const StageArgs& a, const CtArgs& c, double* P, float* P32, cudaStream_t st) {
   const long long nc = (long long)a.nblocks * a.nint;
   if (a.ndim == 3)
-    ct_cell_field_kernel<3><<<grid_of(nc), 256, 0, st>>>(a, c, P);
+    ct_cell_field_kernel<3><<<grid_of(nc), 256, 0, st>>>(a, c, P, P32);
   else
-    ct_cell_field_kernel<2><<<grid_of(nc), 256, 0, st>>>(a, c, P);
+    ct_cell_field_kernel<2><<<grid_of(nc), 256, 0, st>>>(a, c, P, P32);
   return cudaGetLastError();
 }
 

@@ -39,13 +39,18 @@ struct CtArgs {
   const double* te_c;     // metric records on the grid extended by one cell each side in x1, x2
   const double* te_f1;
   const double* te_f2;
+  const float* te_c32;    // their FP32 copies (mixed form)
+  const float* te_f1_32;
+  const float* te_f2_32;
   int axis_lo, axis_hi;   // polar axis at the low / high x2 boundary
 };
 
 cudaError_t launch_ct_ring(const long long* dst, const long long* src, long long n, double* phi, cudaStream_t st);
-cudaError_t launch_ct_stage(const StageArgs& a, const CtArgs& c, cudaStream_t st);
-// B^d of the interior cells of P from the faces, psi = 0 (after a face load)
-cudaError_t launch_ct_cell_field(const StageArgs& a, const CtArgs& c, double* P, cudaStream_t st);
+// mixed: FP32 face fluxes and cell sources (the mixed form); else FP64
+cudaError_t launch_ct_stage(const StageArgs& a, const CtArgs& c, bool mixed, cudaStream_t st);
+// B^d of the interior cells of P (and of its FP32 copy P32 when not null) from
+// the faces, psi = 0 (after a face load)
+cudaError_t launch_ct_cell_field(const StageArgs& a, const CtArgs& c, double* P, float* P32, cudaStream_t st);
 // owned faces <-> the ring layout
 cudaError_t launch_ct_copy_faces(const StageArgs& a, const CtGeom& g, const double* src, double* dst, int to_ring,
                                  cudaStream_t st);

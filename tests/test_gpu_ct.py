@@ -123,8 +123,8 @@ def test_ct_keeps_the_divergence_at_round_off_over_many_steps(gb):
 
 def test_ct_call_order_and_forms(gb):
     """A step before the faces are loaded, and face calls on a cleaning-form
-    grid, are call-order errors; the mixed form and AMR grids with constrained
-    transport are rejected at init."""
+    grid, are call-order errors; AMR grids with constrained transport are
+    rejected at init."""
     g, P, F = _case("box2d")
     s = gb.Solver(g)
     s.set_prims(P)
@@ -136,6 +136,35 @@ def test_ct_call_order_and_forms(gb):
     with pytest.raises(gb.BhacError) as e:
         glm.set_faces(ct.random_potential_faces(g))
     assert e.value.status == 4
-    with pytest.raises(gb.BhacError) as e:
-        gb.Solver(g, "mixed")
-    assert e.value.status == 1
+
+
+@pytest.mark.parametrize("name", ["box2d", "box3d", "torus2d", "torus3d"])
+def test_ct_mixed_form_matches_oracle(gb, name):
+    """The mixed form of constrained transport (FP32 face states and fluxes,
+    FP64 EMFs, face update and face field) against the FP64 oracle: after one
+    step, conserved variables within the mixed form's per-step bar of 1e-5
+    (energy-scaled) and face fields within 1e-5 of the largest one; after two
+    more, every cell's discrete divergence still at FP64 round-off."""
+    from tests.test_gpu_parity import energy_scaled
+    g, P, F = _case(name)
+    F = _faces(g, F)
+    s = gb.Solver(g, "mixed")
+    s.set_prims(P)
+    s.set_faces(F)
+    o = oracle.Oracle(g)
+    o.set_prims(P)
+    o.set_faces(F)
+    dt = o.cfl_dt()
+    o.step(dt)
+    s.step(dt)
+    err = energy_scaled(s.cons(), o.cons(), g)
+    assert np.all(err <= 1e-5), err
+    fg, fo = s.faces(), o.faces()
+    scale = np.abs(fo).max()
+    assert np.abs(fg - fo).max() <= 1e-5 * scale
+    for _ in range(2):
+        s.step(0.0)
+    fg = s.faces()
+    dxmin = min((g.xmax[d] - g.xmin[d]) / (g.nroot[d] * g.nx[d]) for d in range(g.ndim))
+    assert np.abs(ct.face_divergence(g, fg)).max() <= 1e-12 * np.abs(fg).max() / dxmin
+    print(f"CT mixed {name}: energy-scaled error per conserved variable after a step {err.tolist()}")
