@@ -53,7 +53,7 @@ bool valid_desc(const bhac_grid_desc* d, const bhac_block_desc* b, int nb) {
   if (d->recon < 0 || d->recon > 1 || d->riemann < 0 || d->riemann > 1) return false;
   if (!(d->gamma_ad > 1.0) || !(d->cfl > 0.0) || !(d->ch > 0.0) || d->c2p_maxit < 1) return false;
   if (!(d->w_max > 1.0)) return false;
-  // constrained transport: uniform grids in the FP64 form
+  // constrained transport: uniform grids
   if (d->divb < 0 || d->divb > 1) return false;
   if (d->divb == BHAC_DIVB_CT && d->nlevels != 1) return false;
   if (d->imex < 0 || d->imex > 1) return false;

@@ -12,25 +12,22 @@ cudaError_t prepare_stage_fp64() { return configure_all_t<double>(); }
 cudaError_t launch_cells_fp64(const StageArgs& a, int grid, cudaStream_t st) { return launch_cells_any<double>(a, grid, st); }
 cudaError_t launch_reflux_fp64(const StageArgs& a, cudaStream_t st) { return launch_reflux_any<double>(a, st); }
 
-// grid for the per-cell reduction kernels: x over a block's interior cells, y
-// over blocks, about eight CTAs per SM in all, so that each thread takes many
-// cells and the warps' atomicMax on the one rate word stay few (one warp per
-// cell row would issue a million of them on the large torus, serialised at L2)
-static dim3 cell_grid(const StageArgs& a) {
+// grid for the per-cell reduction kernels: about eight CTAs per SM, so that
+// each thread takes many cells and the warps' atomicMax on the one rate word
+// stay few (one per 32 cells would be a million on the large torus, serialised
+// at L2)
+static int cell_grid(const StageArgs& a) {
   int dev = 0, nsm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  int gx = (a.nint + 255) / 256;
-  if (gx > 4) gx = 4;
-  if (gx < 1) gx = 1;
-  int gy = (8 * (nsm > 0 ? nsm : 1) + gx - 1) / gx;
-  if (gy > a.nblocks) gy = a.nblocks;
-  if (gy > 65535) gy = 65535;
-  return dim3(gx, gy < 1 ? 1 : gy, 1);
+  const long long n = (long long)a.nblocks * a.nint;
+  long long g = (n + 255) / 256;
+  if (g > 8LL * nsm) g = 8LL * nsm;
+  return g < 1 ? 1 : (int)g;
 }
 
 cudaError_t launch_cfl(const StageArgs& a, cudaStream_t st) {
-  const dim3 grid = cell_grid(a);
+  const int grid = cell_grid(a);
   if (a.ndim == 3) {
     if (a.flat) cfl_kernel<3, true><<<grid, 256, 0, st>>>(a);
     else cfl_kernel<3, false><<<grid, 256, 0, st>>>(a);
@@ -42,7 +39,7 @@ cudaError_t launch_cfl(const StageArgs& a, cudaStream_t st) {
 }
 
 cudaError_t launch_load(const StageArgs& a, const double* src, double* P, float* P32, double* U, cudaStream_t st) {
-  const dim3 grid = cell_grid(a);
+  const int grid = cell_grid(a);
   if (a.ndim == 3) {
     if (a.flat) load_kernel<3, true><<<grid, 256, 0, st>>>(a, src, P, P32, U);
     else load_kernel<3, false><<<grid, 256, 0, st>>>(a, src, P, P32, U);

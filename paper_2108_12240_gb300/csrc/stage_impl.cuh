@@ -1205,33 +1205,34 @@ __global__ void __launch_bounds__(128) reflux_kernel(StageArgs a) {
   reduce_outputs(a, cnt, rate_max);
 }
 
-// Stand-alone CFL rate reduction over interior cells (FP64 primitives).  Grid
-// y walks the blocks, grid x a block's interior cells (no 64-bit division per
-// cell).
+// Stand-alone CFL rate reduction over interior cells (FP64 primitives); a
+// grid-stride loop over (block, cell) with 32-bit index arithmetic (the
+// library's grids hold fewer than 2^31 interior cells).
 template <int DIM, bool FLAT>
 __global__ void __launch_bounds__(256) cfl_kernel(StageArgs a) {
   double rate_max = 0.0;
-  for (int b = blockIdx.y; b < a.nblocks; b += gridDim.y) {
+  const unsigned n = (unsigned)a.nblocks * (unsigned)a.nint;
+  for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+    const int b = (int)(t / (unsigned)a.nint);
+    const int ci = (int)(t - (unsigned)b * (unsigned)a.nint);
+    const int i = ci % a.nx, j = (ci / a.nx) % a.ny, k = ci / (a.nx * a.ny);
+    const int cg = ((k + a.gz) * a.Ny + (j + a.gy)) * a.Nx + (i + a.gx);
     const LevelGeo geo = level_geo(a, a.blk[4 * b]);
-    const double* Pb = a.P_in + (size_t)b * NV * a.ncell;
-    for (int ci = blockIdx.x * blockDim.x + threadIdx.x; ci < a.nint; ci += gridDim.x * blockDim.x) {
-      const int i = ci % a.nx, j = (ci / a.nx) % a.ny, k = ci / (a.nx * a.ny);
-      const int cg = ((k + a.gz) * a.Ny + (j + a.gy)) * a.Nx + (i + a.gx);
-      double P[NV];
+    double P[NV];
+    const double* Pd = a.P_in + (size_t)b * NV * a.ncell + cg;
 #pragma unroll
-      for (int v = 0; v < NV; ++v) P[v] = Pb[(size_t)v * a.ncell + cg];
-      Met<double> m = flat_metric<double>();
-      double acg[3] = {1.0, 1.0, 1.0};
-      if (!FLAT) {
-        const int I1 = a.blk[4 * b + 1] * a.nx + i, I2 = a.blk[4 * b + 2] * a.ny + j;
-        const double* crec = geo.tc + (size_t)(I2 * geo.N1 + I1) * CREC;
-        m = load_centre_metric<double>(crec);
-        acg[0] = crec[C_ACG1];
-        acg[1] = crec[C_ACG2];
-        acg[2] = crec[C_ACG3];
-      }
-      rate_max = fmax(rate_max, cfl_rate_t<double, DIM>(m, acg, P, a.gam, a.gam_fac, a.ch, geo.idx));
+    for (int v = 0; v < NV; ++v) P[v] = Pd[(size_t)v * a.ncell];
+    Met<double> m = flat_metric<double>();
+    double acg[3] = {1.0, 1.0, 1.0};
+    if (!FLAT) {
+      const int I1 = a.blk[4 * b + 1] * a.nx + i, I2 = a.blk[4 * b + 2] * a.ny + j;
+      const double* crec = geo.tc + (size_t)(I2 * geo.N1 + I1) * CREC;
+      m = load_centre_metric<double>(crec);
+      acg[0] = crec[C_ACG1];
+      acg[1] = crec[C_ACG2];
+      acg[2] = crec[C_ACG3];
     }
+    rate_max = fmax(rate_max, cfl_rate_t<double, DIM>(m, acg, P, a.gam, a.gam_fac, a.ch, geo.idx));
   }
   const double w = warp_max_d(rate_max);
   if ((threadIdx.x & 31u) == 0) atomicMax(a.smax_out, (unsigned long long)__double_as_longlong(w));
@@ -1241,42 +1242,43 @@ __global__ void __launch_bounds__(256) cfl_kernel(StageArgs a) {
 // FP64) go to the ghosted FP64 array P and (mixed form) its FP32 copy P32; the
 // densitized conserved state U follows from them, and the CFL rate of the
 // loaded primitives is reduced into smax_out (the same per-cell rate as
-// cfl_kernel's).
+// cfl_kernel's).  Same loop as cfl_kernel.
 template <int DIM, bool FLAT>
 __global__ void __launch_bounds__(256) load_kernel(StageArgs a, const double* __restrict__ src, double* P, float* P32,
                                                    double* U) {
   double rate_max = 0.0;
-  for (int b = blockIdx.y; b < a.nblocks; b += gridDim.y) {
+  const unsigned n = (unsigned)a.nblocks * (unsigned)a.nint;
+  for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+    const int b = (int)(t / (unsigned)a.nint);
+    const int ci = (int)(t - (unsigned)b * (unsigned)a.nint);
+    const int i = ci % a.nx, j = (ci / a.nx) % a.ny, k = ci / (a.nx * a.ny);
+    const int cg = ((k + a.gz) * a.Ny + (j + a.gy)) * a.Nx + (i + a.gx);
     const LevelGeo geo = level_geo(a, a.blk[4 * b]);
-    for (int ci = blockIdx.x * blockDim.x + threadIdx.x; ci < a.nint; ci += gridDim.x * blockDim.x) {
-      const int i = ci % a.nx, j = (ci / a.nx) % a.ny, k = ci / (a.nx * a.ny);
-      const int cg = ((k + a.gz) * a.Ny + (j + a.gy)) * a.Nx + (i + a.gx);
-      double Pc[NV], Uc[NV];
+    double Pc[NV], Uc[NV];
 #pragma unroll
-      for (int v = 0; v < NV; ++v) {
-        Pc[v] = src[((size_t)b * NV + v) * a.nint + ci];
-        P[((size_t)b * NV + v) * a.ncell + cg] = Pc[v];
-        if (P32) P32[((size_t)b * NV + v) * a.ncell + cg] = narrow_f64(Pc[v]);
-      }
-      Met<double> m = flat_metric<double>();
-      double sg = 1.0;
-      double acg[3] = {1.0, 1.0, 1.0};
-      if (!FLAT) {
-        const int I1 = a.blk[4 * b + 1] * a.nx + i, I2 = a.blk[4 * b + 2] * a.ny + j;
-        const double* rec = geo.tc + (size_t)(I2 * geo.N1 + I1) * CREC;
-        m = load_centre_metric<double>(rec);
-        sg = rec[C_SG];
-        acg[0] = rec[C_ACG1];
-        acg[1] = rec[C_ACG2];
-        acg[2] = rec[C_ACG3];
-      }
-      Derived<double> s;
-      derive(m, Pc, a.gam_fac, s);
-      cons_of(Pc, s, Uc);
-#pragma unroll
-      for (int v = 0; v < NV; ++v) U[((size_t)b * NV + v) * a.nint + ci] = sg * Uc[v];
-      rate_max = fmax(rate_max, cfl_rate_t<double, DIM>(m, acg, Pc, a.gam, a.gam_fac, a.ch, geo.idx));
+    for (int v = 0; v < NV; ++v) {
+      Pc[v] = src[((size_t)b * NV + v) * a.nint + ci];
+      P[((size_t)b * NV + v) * a.ncell + cg] = Pc[v];
+      if (P32) P32[((size_t)b * NV + v) * a.ncell + cg] = narrow_f64(Pc[v]);
     }
+    Met<double> m = flat_metric<double>();
+    double sg = 1.0;
+    double acg[3] = {1.0, 1.0, 1.0};
+    if (!FLAT) {
+      const int I1 = a.blk[4 * b + 1] * a.nx + i, I2 = a.blk[4 * b + 2] * a.ny + j;
+      const double* rec = geo.tc + (size_t)(I2 * geo.N1 + I1) * CREC;
+      m = load_centre_metric<double>(rec);
+      sg = rec[C_SG];
+      acg[0] = rec[C_ACG1];
+      acg[1] = rec[C_ACG2];
+      acg[2] = rec[C_ACG3];
+    }
+    Derived<double> s;
+    derive(m, Pc, a.gam_fac, s);
+    cons_of(Pc, s, Uc);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) U[((size_t)b * NV + v) * a.nint + ci] = sg * Uc[v];
+    rate_max = fmax(rate_max, cfl_rate_t<double, DIM>(m, acg, Pc, a.gam, a.gam_fac, a.ch, geo.idx));
   }
   const double w = warp_max_d(rate_max);
   if ((threadIdx.x & 31u) == 0) atomicMax(a.smax_out, (unsigned long long)__double_as_longlong(w));
