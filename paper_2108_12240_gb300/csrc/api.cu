@@ -56,6 +56,8 @@ bool valid_desc(const bhac_grid_desc* d, const bhac_block_desc* b, int nb) {
   // constrained transport: uniform grids
   if (d->divb < 0 || d->divb > 1) return false;
   if (d->divb == BHAC_DIVB_CT && d->nlevels != 1) return false;
+  // the face kernels' 32-bit indices: blocks x ring-extended faces < 2^31
+  if (d->divb == BHAC_DIVB_CT && (long long)nb * ct_geom(d).nfb >= (1LL << 31)) return false;
   if (d->imex < 0 || d->imex > 1) return false;
   if (d->c2p_solver != BHAC_C2P_NEWTON && d->c2p_solver != BHAC_C2P_NK) return false;
   // the axis rule is for x2 (theta) only; phi must be periodic with an even cell count in 3-D

@@ -203,16 +203,17 @@ __device__ __forceinline__ void ct_one_face(const StageArgs& a, const CtArgs& c,
 // Fluxes through every face of every block and its ring, one thread per face.
 template <typename T, bool FLAT>
 __global__ void __launch_bounds__(256) ct_flux_kernel(StageArgs a, CtArgs c) {
-  const long long n = (long long)a.nblocks * c.g.nfb;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
-    const int b = (int)(t / c.g.nfb);
-    const long long r = t - (long long)b * c.g.nfb;
+  // 32-bit index arithmetic: bhac_init_grid keeps blocks x ring-extended faces below 2^31
+  const unsigned n = (unsigned)a.nblocks * (unsigned)c.g.nfb;
+  for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+    const int b = (int)(t / (unsigned)c.g.nfb);
+    const int r = (int)(t - (unsigned)b * (unsigned)c.g.nfb);
     const int d = (c.g.ndim == 3 && r >= c.g.foff[2]) ? 2 : (r >= c.g.foff[1] ? 1 : 0);
-    const long long q = r - c.g.foff[d];
+    const int q = r - (int)c.g.foff[d];
     const int e0 = c.g.fe[d][0], e1 = c.g.fe[d][1];
-    const int i = (int)(q % e0) - c.g.fo[d][0];
-    const int j = (int)((q / e0) % e1) - c.g.fo[d][1];
-    const int k = (int)(q / ((long long)e0 * e1)) - c.g.fo[d][2];
+    const int i = q % e0 - c.g.fo[d][0];
+    const int j = (q / e0) % e1 - c.g.fo[d][1];
+    const int k = q / (e0 * e1) - c.g.fo[d][2];
     if (d == 0)
       ct_one_face<T, 0, FLAT>(a, c, b, i, j, k, q);
     else if (d == 1)
@@ -237,24 +238,24 @@ __device__ __forceinline__ double emf2(const CtArgs& c, int b, int i, int j, int
                  xf_at(c, b, 2, B1, i - 1, j, k));
 }
 
-__device__ __forceinline__ void owned_face(const CtGeom& g, long long r, int& d, int& i, int& j, int& k) {
+__device__ __forceinline__ void owned_face(const CtGeom& g, int r, int& d, int& i, int& j, int& k) {
   d = (g.ndim == 3 && r >= g.own_off[2]) ? 2 : (r >= g.own_off[1] ? 1 : 0);
-  const long long q = r - g.own_off[d];
+  const int q = r - (int)g.own_off[d];
   const int n0 = g.nx[0] + (d == 0), n1 = g.nx[1] + (d == 1);
-  i = (int)(q % n0);
-  j = (int)((q / n0) % n1);
-  k = (int)(q / ((long long)n0 * n1));
+  i = q % n0;
+  j = (q / n0) % n1;
+  k = q / (n0 * n1);
 }
 
 // d_t Phi = -curl E and the stage combination, one thread per owned face.
 template <int DIM>
 __global__ void __launch_bounds__(256) ct_face_kernel(StageArgs a, CtArgs c) {
   const double dt = stage_dt(a);
-  const long long n = (long long)a.nblocks * c.g.nown_b;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
-    const int b = (int)(t / c.g.nown_b);
+  const unsigned n = (unsigned)a.nblocks * (unsigned)c.g.nown_b;
+  for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+    const int b = (int)(t / (unsigned)c.g.nown_b);
     int d, i, j, k;
-    owned_face(c.g, t - (long long)b * c.g.nown_b, d, i, j, k);
+    owned_face(c.g, (int)(t - (unsigned)b * (unsigned)c.g.nown_b), d, i, j, k);
     const long long o = (long long)b * c.g.nfb + ring_index(c.g, d, i, j, k);
     const int G2 = a.blk[4 * b + 2] * a.ny + j;
     if (!a.flat && d == 1 && ((G2 == 0 && c.axis_lo) || (G2 == a.N2g && c.axis_hi))) {
@@ -263,14 +264,14 @@ __global__ void __launch_bounds__(256) ct_face_kernel(StageArgs a, CtArgs c) {
     }
     double R;
     if (d == 0) {
-      R = -(emf3(c, b, i, j + 1, k) - emf3(c, b, i, j, k)) / a.dxl0[1];
-      if (DIM == 3) R += (emf2(c, b, i, j, k + 1) - emf2(c, b, i, j, k)) / a.dxl0[2];
+      R = -(emf3(c, b, i, j + 1, k) - emf3(c, b, i, j, k)) * a.idx[1];
+      if (DIM == 3) R += (emf2(c, b, i, j, k + 1) - emf2(c, b, i, j, k)) * a.idx[2];
     } else if (d == 1) {
-      R = (emf3(c, b, i + 1, j, k) - emf3(c, b, i, j, k)) / a.dxl0[0];
-      if (DIM == 3) R -= (emf1(c, b, i, j, k + 1) - emf1(c, b, i, j, k)) / a.dxl0[2];
+      R = (emf3(c, b, i + 1, j, k) - emf3(c, b, i, j, k)) * a.idx[0];
+      if (DIM == 3) R -= (emf1(c, b, i, j, k + 1) - emf1(c, b, i, j, k)) * a.idx[2];
     } else {
-      R = -(emf2(c, b, i + 1, j, k) - emf2(c, b, i, j, k)) / a.dxl0[0] +
-          (emf1(c, b, i, j + 1, k) - emf1(c, b, i, j, k)) / a.dxl0[1];
+      R = -(emf2(c, b, i + 1, j, k) - emf2(c, b, i, j, k)) * a.idx[0] +
+          (emf1(c, b, i, j + 1, k) - emf1(c, b, i, j, k)) * a.idx[1];
     }
     if (a.stage == 1)
       c.phi_out[o] = c.phi_in[o] + dt * R;
@@ -291,10 +292,10 @@ __global__ void __launch_bounds__(256, 2) ct_cell_kernel(StageArgs a, CtArgs c) 
   unsigned cnt[4] = {0u, 0u, 0u, 0u};
   double rate_max = 0.0;
   const LevelGeo geo = level_geo(a, 0);
-  const long long n = (long long)a.nblocks * a.nint;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
-    const int b = (int)(t / a.nint);
-    const int ci = (int)(t - (long long)b * a.nint);
+  const unsigned n = (unsigned)a.nblocks * (unsigned)a.nint;
+  for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+    const int b = (int)(t / (unsigned)a.nint);
+    const int ci = (int)(t - (unsigned)b * (unsigned)a.nint);
     const int i = ci % a.nx, j = (ci / a.nx) % a.ny, k = ci / (a.nx * a.ny);
     const int cg = ((k + a.gz) * a.Ny + (j + a.gy)) * a.Nx + (i + a.gx);
     const int I1 = a.blk[4 * b + 1] * a.nx + i, I2 = a.blk[4 * b + 2] * a.ny + j;
@@ -305,7 +306,7 @@ __global__ void __launch_bounds__(256, 2) ct_cell_kernel(StageArgs a, CtArgs c) 
     for (int d = 0; d < DIM; ++d) {
       const int ih = i + (d == 0), jh = j + (d == 1), kh = k + (d == 2);
 #pragma unroll
-      for (int v = 0; v < NV; ++v) rhs[v] += -(xf_at(c, b, d, v, ih, jh, kh) - xf_at(c, b, d, v, i, j, k)) / a.dxl0[d];
+      for (int v = 0; v < NV; ++v) rhs[v] += -(xf_at(c, b, d, v, ih, jh, kh) - xf_at(c, b, d, v, i, j, k)) * a.idx[d];
     }
     if (!FLAT) {
       const T* crec = (sizeof(T) == 8 ? reinterpret_cast<const T*>(geo.tc) : reinterpret_cast<const T*>(geo.tc32)) +
@@ -375,7 +376,7 @@ __global__ void __launch_bounds__(256) ct_copy_kernel(int nblocks, CtGeom g, con
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
     const int b = (int)(t / g.nown_b);
     int d, i, j, k;
-    owned_face(g, t - (long long)b * g.nown_b, d, i, j, k);
+    owned_face(g, (int)(t - (long long)b * g.nown_b), d, i, j, k);
     const long long o = (long long)b * g.nfb + ring_index(g, d, i, j, k);
     if (to_ring)
       dst[o] = src[t];
