@@ -231,6 +231,7 @@ def time_form(gb, torch, g, P, form, steps, warmup, stream, count_flops=True, gr
            "fill_ms": fill_ms, "launch_shape": {"tx": shape[0], "ty": shape[1], "threads": shape[2],
                                                  "persistent": shape[3], "min_ctas": shape[4],
                                                  "producer_warps": shape[5] if len(shape) > 5 else 0,
+                                                 "z_parts": s.zsplit_in_force(),
                                                  "candidates_timed": len(tried)}}
     if graph_repeats > 0:
         if graph_steps <= 0:  # enough replays for about 50 ms per repeat

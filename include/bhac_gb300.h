@@ -360,6 +360,21 @@ bhac_status bhac_set_launch(bhac_ctx* ctx, int tx, int ty, int threads, int pers
  * returns BHAC_ERR_STATE while chunks > 0). */
 bhac_status bhac_set_split(bhac_ctx* ctx, int chunks);
 
+/* Z parts of the stage kernel's work items (3-D grids, the phased kernel):
+ * parts = p > 0 splits each (block, tile) column of cells into p runs of
+ * nz/p planes, each a work item of its own (every part recomputes the z faces
+ * at its bottom, the same numbers as the face carried up from below, so the
+ * results do not depend on p); parts = 0 (the default) lets the library
+ * choose: whole columns unless splitting fills the GPU's resident CTA slots
+ * markedly better (grids with few columns).  Source: the per-block update of
+ * Sec. 2; the paper's blocks are the work units, this only cuts them finer.
+ * BHAC_ERR_ARG: parts < 0, or parts > 0 on a 2-D grid or not dividing nz.
+ * bhac_zsplit_in_force returns the parts the last stage used (0 before any
+ * stage since the last launch-shape change; always 1 on 2-D grids, with the
+ * split form and with the warp-specialised kernel). */
+bhac_status bhac_set_zsplit(bhac_ctx* ctx, int parts);
+int bhac_zsplit_in_force(const bhac_ctx* ctx);
+
 /* Records `nsteps` steps with the device time step (bhac_step(ctx, 0.0)) into a
  * CUDA graph on the context's stream and instantiates it; bhac_graph_launch()
  * then replays all of them with one launch.  The stream must be a created

@@ -24,7 +24,8 @@ __all__ = [
     "bhac_status_string", "bhac_check_bit_ops", "bhac_launches_per_step", "bhac_get_prims_ghosted",
     "bhac_get_c2p_status", "bhac_set_cons", "bhac_set_prims_host_async", "bhac_get_prims_host_async",
     "bhac_host_fence", "bhac_measure_peaks", "bhac_set_faces", "bhac_get_faces",
-    "bhac_estimate", "bhac_regrid_plan", "bhac_regrid_transfer", "bhac_set_split",
+    "bhac_estimate", "bhac_regrid_plan", "bhac_regrid_transfer", "bhac_set_split", "bhac_set_zsplit",
+    "bhac_zsplit_in_force",
 ]
 
 NV = 9
@@ -87,6 +88,8 @@ def lib():
             "bhac_get_diagnostics": ([vp, C.POINTER(C.c_longlong)], i),
             "bhac_set_launch": ([vp, i, i, i, i, i, i], i),
             "bhac_set_split": ([vp, i], i),
+            "bhac_set_zsplit": ([vp, i], i),
+            "bhac_zsplit_in_force": ([vp], i),
             "bhac_count_flops": ([vp, d, i, C.c_uint, C.POINTER(d)], i),
             "bhac_graph_capture": ([vp, i], i),
             "bhac_graph_launch": ([vp], i),
@@ -243,6 +246,14 @@ def bhac_set_launch(ctx, tx=0, ty=0, threads=0, persistent=0, min_ctas=0, produc
 
 def bhac_set_split(ctx, chunks: int):
     return _check("bhac_set_split", lib().bhac_set_split(ctx, chunks))
+
+
+def bhac_set_zsplit(ctx, parts: int):
+    return _check("bhac_set_zsplit", lib().bhac_set_zsplit(ctx, parts))
+
+
+def bhac_zsplit_in_force(ctx) -> int:
+    return int(lib().bhac_zsplit_in_force(ctx))
 
 
 def bhac_count_flops(ctx, dt: float, nsamples: int = 2000, seed: int = 1):
@@ -524,6 +535,13 @@ class Solver:
     def set_split(self, chunks: int):
         """Split form of the stage in `chunks` chunks (0: the fused kernel)."""
         bhac_set_split(self.ctx, chunks)
+
+    def set_zsplit(self, parts: int):
+        """Z parts per (block, tile) work item (0: the library's choice)."""
+        bhac_set_zsplit(self.ctx, parts)
+
+    def zsplit_in_force(self) -> int:
+        return bhac_zsplit_in_force(self.ctx)
 
 
 # Fail loudly at import if the library cannot be loaded.

@@ -188,6 +188,7 @@ StageArgs base_args(const bhac_ctx* c) {
   a.nty = d.nx[1] / c->ty;
   a.nblocks = c->nb;
   a.nitems = c->nb * a.ntx * a.nty;
+  a.nzp = 1;
   a.item0 = 0;
   a.item1 = a.nitems;
   a.split = 0;
@@ -306,6 +307,39 @@ bhac_status ghost_fill(bhac_ctx* c, int buf, bool zero_smax) {
 
 namespace {
 
+// Z parts per (block, tile) column of the phased 3-D stage kernel.  A fixed
+// choice (bhac_set_zsplit) is used as given.  Otherwise: among the parts that
+// divide nz and leave at least 4 planes, the one that minimises the modelled
+// time, rounds of items over the resident CTA slots times the planes of an
+// item plus a quarter plane for the z faces it recomputes at its bottom.
+// Whole columns are kept unless splitting fills the GPU's slots markedly
+// better (small grids: 432 columns of 16^3 on 152 SMs).
+int choose_nzp(const bhac_ctx* c, const StageArgs& a, size_t smem) {
+  const int nz = c->d.nx[2];
+  if (c->zsplit > 0) return c->zsplit;
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const int per_sm = c->persistent ? c->persistent
+                                   : (c->mixed ? stage_occupancy_mixed(a, c->threads, smem)
+                                               : stage_occupancy_fp64(a, c->threads, smem));
+  const long long slots = (long long)(nsm > 0 ? nsm : 1) * (per_sm > 0 ? per_sm : 1);
+  const long long items = (long long)a.nitems;
+  int best = 1;
+  const double cost1 = (double)((items + slots - 1) / slots) * ((double)nz + 0.25);
+  double best_cost = cost1;
+  for (int p = 2; p <= nz; p *= 2) {
+    if (nz % p || nz / p < 4) break;
+    const long long n = items * p;
+    const double cost = (double)((n + slots - 1) / slots) * ((double)(nz / p) + 0.25);
+    if (cost < 0.95 * cost1 && cost < best_cost) {
+      best = p;
+      best_cost = cost;
+    }
+  }
+  return best;
+}
+
 bhac_status run_stage(bhac_ctx* c, int stage, double dt) {
   StageArgs a = base_args(c);
   const int in = c->cur, out = 1 - c->cur;
@@ -325,6 +359,15 @@ bhac_status run_stage(bhac_ctx* c, int stage, double dt) {
     a.Uout = c->U[1 - c->ucur];
   }
   const size_t smem = stage_smem(c, c->tx, c->ty, c->pwarps);
+  if (c->split <= 0 && c->pwarps == 0 && c->d.ndim == 3) {
+    // the phased kernel's items may be z parts of (block, tile) columns
+    if (c->nzp_eff <= 0) c->nzp_eff = choose_nzp(c, a, smem);
+    a.nzp = c->nzp_eff;
+    a.nitems *= a.nzp;
+    a.item1 = a.nitems;
+  } else {
+    c->nzp_eff = 1;  // whole columns (2-D grids, the split form, the warp-specialised kernel)
+  }
   int grid = a.nitems;
   if (c->persistent) {
     int dev = 0, nsm = 0;
@@ -500,6 +543,8 @@ bhac_status bhac_init_grid(bhac_ctx** out, const bhac_grid_desc* d, const bhac_b
   c->d_status = (unsigned char*)(c->arena + L.off_status);
   c->Rbuf = nullptr;
   c->split = 0;
+  c->zsplit = 0;
+  c->nzp_eff = 0;
   c->st2 = nullptr;
   c->ev_fork = c->ev_join2 = nullptr;
   for (int q = 0; q < 32; ++q) c->ev_chunk[q] = nullptr;
@@ -920,6 +965,7 @@ bhac_status bhac_set_launch(bhac_ctx* c, int tx, int ty, int threads, int persis
   c->ty = nty;
   c->threads = nth;
   c->persistent = persistent;
+  c->nzp_eff = 0;
   return BHAC_OK;
 }
 
@@ -945,8 +991,19 @@ bhac_status bhac_set_split(bhac_ctx* c, int chunks) {
     if (e != cudaSuccess) return BHAC_ERR_CUDA;
   }
   c->split = chunks;
+  c->nzp_eff = 0;
   return BHAC_OK;
 }
+
+bhac_status bhac_set_zsplit(bhac_ctx* c, int parts) {
+  if (!c || parts < 0) return BHAC_ERR_ARG;
+  if (parts > 0 && (c->d.ndim != 3 || c->d.nx[2] % parts)) return BHAC_ERR_ARG;
+  c->zsplit = parts;
+  c->nzp_eff = 0;
+  return BHAC_OK;
+}
+
+int bhac_zsplit_in_force(const bhac_ctx* c) { return c ? c->nzp_eff : -1; }
 
 bhac_status bhac_graph_capture(bhac_ctx* c, int nsteps) {
   if (!c || nsteps < 1) return BHAC_ERR_ARG;

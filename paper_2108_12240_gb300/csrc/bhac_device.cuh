@@ -41,6 +41,7 @@ struct StageArgs {
   int ncell, nint;       // ghosted / interior cells per block
   int tx, ty, ntx, nty;  // CTA column tile and tiles per block
   int nblocks, nitems;
+  int nzp;               // z parts per (block, tile) item of the phased 3-D kernel (1: whole columns)
   int persistent;
   int minb;              // register bound of the 3-D stage kernel: 1 or 2 CTAs per SM
   int pwarps;            // 3-D: warps that produce face fluxes while the others update cells (0: phased)

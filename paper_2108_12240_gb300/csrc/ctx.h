@@ -77,6 +77,9 @@ struct bhac_ctx {
   // split form: chunks of items, the face kernel on st and the cell kernel on
   // st2, chunk by chunk; R holds the stage right-hand side
   int split;
+  // z parts per (block, tile) item of the phased 3-D kernel: zsplit as set
+  // (0: chosen by the library), nzp_eff the count in force (0: not yet chosen)
+  int zsplit, nzp_eff;
   cudaStream_t st2;
   cudaEvent_t ev_chunk[32], ev_fork, ev_join2;
   double* Rbuf;

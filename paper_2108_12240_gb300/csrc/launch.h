@@ -19,6 +19,9 @@ constexpr int kTwoCtaSmem = 113 * 1024;
 cudaError_t launch_stage_fp64(const StageArgs& a, int grid, int threads, size_t smem, cudaStream_t st);
 cudaError_t launch_stage_mixed(const StageArgs& a, int grid, int threads, size_t smem, cudaStream_t st);
 cudaError_t launch_cfl(const StageArgs& a, cudaStream_t st);
+// resident CTAs per SM of the phased 3-D stage kernel these arguments select
+int stage_occupancy_fp64(const StageArgs& a, int threads, size_t smem);
+int stage_occupancy_mixed(const StageArgs& a, int threads, size_t smem);
 // one pass that loads interior primitives into the ghosted arrays, sets the
 // conserved state and reduces the CFL rate into a.smax_out
 cudaError_t launch_load(const StageArgs& a, const double* src, double* P, float* P32, double* U, cudaStream_t st);

@@ -50,4 +50,8 @@ cudaError_t launch_load(const StageArgs& a, const double* src, double* P, float*
   return cudaGetLastError();
 }
 
+int stage_occupancy_fp64(const StageArgs& a, int threads, size_t smem) {
+  return stage_occupancy_any<double>(a, threads, smem);
+}
+
 }  // namespace bhac

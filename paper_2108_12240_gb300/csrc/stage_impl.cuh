@@ -897,9 +897,12 @@ __global__ void __launch_bounds__(256, MINB % 10) stage_kernel(StageArgs a) {
       item = s_item;
     }
     if (item >= a.item1) break;
-    const int ord = item / ntile;
+    // item = (visiting-order block, tile, z part); a part runs planes [kbeg, kend)
+    const int zp = item % a.nzp, it2 = item / a.nzp;
+    const int ord = it2 / ntile;
     const int b = a.order[ord];
-    const int tile = item - ord * ntile;
+    const int tile = it2 - ord * ntile;
+    const int kbeg = zp * (a.nz / a.nzp), kend = kbeg + a.nz / a.nzp;
     const int x0 = (tile % a.ntx) * tx, y0 = (tile / a.ntx) * ty;
     const int L = a.blk[4 * b];
     const LevelGeo geo = level_geo(a, L);
@@ -911,12 +914,13 @@ __global__ void __launch_bounds__(256, MINB % 10) stage_kernel(StageArgs a) {
     T* Fz0 = Fza;
     T* Fz1 = Fzb;
     if (DIM == 3) {
-      // bottom face of plane 0 from the high edge of plane -1 and the low
-      // edge of plane 0; plane 0's high edge is kept for the face above it
+      // bottom face of plane kbeg from the high edge of plane kbeg - 1 and the
+      // low edge of plane kbeg; plane kbeg's high edge is kept for the face
+      // above it (the same arithmetic as the face carried up from below)
       for (int t = threadIdx.x; t < sFz; t += blockDim.x) {
         const int i = t % tx, j = t / tx;
         const int ig = i + x0 + a.gx, jg = j + y0 + a.gy;
-        const int c0 = (a.gz * a.Ny + jg) * a.Nx + ig;
+        const int c0 = ((kbeg + a.gz) * a.Ny + jg) * a.Nx + ig;
         T PL[NV], PR[NV], tmp[NV];
         if (axis_face<FLAT>(a, geo, 2, I2b + j)) {
 #pragma unroll
@@ -927,10 +931,10 @@ __global__ void __launch_bounds__(256, MINB % 10) stage_kernel(StageArgs a) {
           positivity_fallback(a, Pb, sz, c0, PL, PR);
           face_solve<T, FLAT>(a, geo, 2, I1b + i, I2b + j, PL, PR, Fz0 + t, sFz);
         }
-        if (regs) to_register(a, b, 2, 0, (j + y0) * a.nx + i + x0, Fz0 + t, sFz);
+        if (regs && kbeg == 0) to_register(a, b, 2, 0, (j + y0) * a.nx + i + x0, Fz0 + t, sFz);
       }
     }
-    for (int k = 0; k < a.nz; ++k) {
+    for (int k = kbeg; k < kend; ++k) {
       const int kg = k + a.gz;
       // R: edges (and the z face above plane k)
       for (int t = threadIdx.x; t < nzc + nex + ney; t += blockDim.x) {
@@ -1377,6 +1381,28 @@ static cudaError_t launch_reflux_any(const StageArgs& a, cudaStream_t st) {
   if (a.nrcells == 0) return cudaSuccess;
   if (a.ndim == 3) return a.flat ? launch_reflux_t<T, 3, true>(a, st) : launch_reflux_t<T, 3, false>(a, st);
   return a.flat ? launch_reflux_t<T, 2, true>(a, st) : launch_reflux_t<T, 2, false>(a, st);
+}
+
+// Resident CTAs per SM of the phased 3-D kernel that launch_stage_any would
+// launch for these arguments (non-split), at this CTA size and shared memory.
+template <typename T, bool FLAT, int MINB>
+static int occupancy_t(int threads, size_t smem) {
+  if (configure_stage_t<T, 3, FLAT, MINB>() != cudaSuccess) return 1;
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, stage_kernel<T, 3, FLAT, MINB>, threads, smem) != cudaSuccess) {
+    cudaGetLastError();
+    return 1;
+  }
+  return n > 0 ? n : 1;
+}
+
+template <typename T>
+static int stage_occupancy_any(const StageArgs& a, int threads, size_t smem) {
+  if (a.c2p_nk)
+    return a.minb >= 2 ? (a.flat ? occupancy_t<T, true, 102>(threads, smem) : occupancy_t<T, false, 102>(threads, smem))
+                       : (a.flat ? occupancy_t<T, true, 101>(threads, smem) : occupancy_t<T, false, 101>(threads, smem));
+  return a.minb >= 2 ? (a.flat ? occupancy_t<T, true, 2>(threads, smem) : occupancy_t<T, false, 2>(threads, smem))
+                     : (a.flat ? occupancy_t<T, true, 1>(threads, smem) : occupancy_t<T, false, 1>(threads, smem));
 }
 
 // 3-D kernels exist with one or two resident CTAs per SM as the register

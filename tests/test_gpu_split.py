@@ -105,3 +105,40 @@ def test_split_arguments_and_graph_capture(gb):
     with pytest.raises(gb.BhacError) as e:
         ct.set_split(2)
     assert e.value.status == 1
+
+
+@pytest.mark.parametrize("form", ["mixed", "fp64"])
+@pytest.mark.parametrize("name", ["torus3d", "amr", "box3d_imex"])
+def test_z_parts_are_the_whole_columns_bit_for_bit(gb, name, form):
+    """Work items cut into z parts (each recomputes the z faces at its bottom)
+    give the same bits as whole columns, for a fixed part count and for the
+    library's own choice; AMR grids exercise the coarse-fine face registers at
+    the block's z ends."""
+    g, P = _case(name)
+    outs = []
+    for parts in (1, 2, 4, 0):
+        s = gb.Solver(g, form)
+        s.set_launch(8, 8, 256, 2 if parts == 4 else 0, 0, 0)
+        s.set_zsplit(parts)
+        s.set_prims(P)
+        s.cfl_dt()
+        for _ in range(2):
+            s.step(0.0)
+        assert s.zsplit_in_force() == (parts if parts else s.zsplit_in_force()) >= 1
+        outs.append((parts, s.cons(), s.prims()))
+    for parts, c, p in outs[1:]:
+        assert np.array_equal(c, outs[0][1]), (name, form, parts)
+        assert np.array_equal(p, outs[0][2]), (name, form, parts)
+
+
+def test_z_parts_arguments(gb):
+    g, _ = _case("torus3d")
+    s = gb.Solver(g)
+    for bad in (-1, 3, 32):
+        with pytest.raises(gb.BhacError) as e:
+            s.set_zsplit(bad)
+        assert e.value.status == 1
+    two = gb.Solver(pb.torus_2d(nblock=16, nroot=(6, 4)))
+    with pytest.raises(gb.BhacError) as e:
+        two.set_zsplit(2)
+    assert e.value.status == 1
