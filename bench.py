@@ -177,6 +177,7 @@ def job_value(cells: int, world: int, ms_per_step: float) -> float:
 
 
 TUNE = True
+Z_PARTS = 0  # z parts per work item of the 3-D stage kernel (0: the library's choice)
 
 
 def time_form(gb, torch, g, P, form, steps, warmup, stream, count_flops=True, graph_repeats=3, graph_steps=1,
@@ -195,6 +196,8 @@ def time_form(gb, torch, g, P, form, steps, warmup, stream, count_flops=True, gr
         shape, tried = autotune.tune(s, P)  # launch shape for this grid and form (outside the timed region)
     else:
         shape, tried = autotune.cached_or_default(s), {}
+    if faces is None and g.ndim == 3:
+        s.set_zsplit(Z_PARTS)
     s.set_prims(P)
     if faces is not None:
         s.set_faces(faces)
@@ -309,7 +312,8 @@ def shape_key(ls) -> str:
     """Launch shape as recorded beside a traffic figure."""
     # the persistent schedule (which CTA takes which item) does not change the
     # per-launch DRAM bytes and is left out
-    return f"{ls['tx']}x{ls['ty']}/{ls['threads']}/minctas{ls['min_ctas']}/producers{ls['producer_warps']}"
+    return (f"{ls['tx']}x{ls['ty']}/{ls['threads']}/minctas{ls['min_ctas']}/producers{ls['producer_warps']}"
+            f"/zparts{ls.get('z_parts', 1)}")
 
 
 def recorded_traffic(workload_name, form, tile):
@@ -644,10 +648,13 @@ def main():
                     help="FORM tx,ty,threads,persistent,min_ctas,producers ...: four steps per shape, for ncu")
     ap.add_argument("--split-sweep", action="store_true",
                     help="fused stage kernel against the split form (face + cell kernels), one line")
+    ap.add_argument("--z-parts", type=int, default=0,
+                    help="z parts per work item of the 3-D stage kernel (0: the library's choice)")
     ap.add_argument("--no-tune", action="store_true", help="use the cached launch shape (or the default) without timing candidates")
     args = ap.parse_args()
-    global TUNE
+    global TUNE, Z_PARTS
     TUNE = not args.no_tune
+    Z_PARTS = args.z_parts
     if args.sweep_blocks:
         sweep_blocks(args)
         return

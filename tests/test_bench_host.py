@@ -21,9 +21,12 @@ def test_fingerprint_is_stable_and_hex():
 
 
 def test_shape_key_leaves_out_the_persistent_schedule():
-    ls = {"tx": 16, "ty": 16, "threads": 256, "persistent": 2, "min_ctas": 2, "producer_warps": 0}
-    assert bench.shape_key(ls) == "16x16/256/minctas2/producers0"
+    """The persistent schedule does not change a launch's bytes; the z parts
+    do (each part recomputes the z faces at its bottom)."""
+    ls = {"tx": 16, "ty": 16, "threads": 256, "persistent": 2, "min_ctas": 2, "producer_warps": 0, "z_parts": 1}
+    assert bench.shape_key(ls) == "16x16/256/minctas2/producers0/zparts1"
     assert bench.shape_key(dict(ls, persistent=0)) == bench.shape_key(ls)
+    assert bench.shape_key(dict(ls, z_parts=2)) != bench.shape_key(ls)
 
 
 @pytest.fixture
@@ -33,28 +36,28 @@ def record(tmp_path, monkeypatch):
         p.write_text("# header: with a colon\n"
                      f"sources_sha256: {sha}\n"
                      f"workload: {workload}\n"
-                     "traffic mixed 16x16/256/minctas2/producers0: 15887270768  (a) stage1 ...\n"
-                     "traffic fp64 16x16/256/minctas1/producers0: 13958643712  (a) stage1 ...\n")
+                     "traffic mixed 16x16/256/minctas2/producers0/zparts1: 15887270768  (a) stage1 ...\n"
+                     "traffic fp64 16x16/256/minctas1/producers0/zparts1: 13958643712  (a) stage1 ...\n")
         monkeypatch.setattr(bench, "TRAFFIC_FILE", str(p))
     return write
 
 
 def test_recorded_traffic_matches_sources_workload_form_and_shape(record):
     record(bench.kernel_fingerprint())
-    assert bench.recorded_traffic("torus_3d_large", "mixed", "16x16/256/minctas2/producers0") == 15887270768.0
-    assert bench.recorded_traffic("torus_3d_large", "fp64", "16x16/256/minctas1/producers0") == 13958643712.0
-    assert bench.recorded_traffic("torus_3d_large", "mixed", "16x16/256/minctas1/producers0") is None
-    assert bench.recorded_traffic("torus_3d", "mixed", "16x16/256/minctas2/producers0") is None
+    assert bench.recorded_traffic("torus_3d_large", "mixed", "16x16/256/minctas2/producers0/zparts1") == 15887270768.0
+    assert bench.recorded_traffic("torus_3d_large", "fp64", "16x16/256/minctas1/producers0/zparts1") == 13958643712.0
+    assert bench.recorded_traffic("torus_3d_large", "mixed", "16x16/256/minctas1/producers0/zparts1") is None
+    assert bench.recorded_traffic("torus_3d", "mixed", "16x16/256/minctas2/producers0/zparts1") is None
 
 
 def test_recorded_traffic_is_dropped_for_other_sources(record):
     record("0" * 64)
-    assert bench.recorded_traffic("torus_3d_large", "mixed", "16x16/256/minctas2/producers0") is None
+    assert bench.recorded_traffic("torus_3d_large", "mixed", "16x16/256/minctas2/producers0/zparts1") is None
 
 
 def test_recorded_traffic_without_a_record(monkeypatch, tmp_path):
     monkeypatch.setattr(bench, "TRAFFIC_FILE", str(tmp_path / "missing.txt"))
-    assert bench.recorded_traffic("torus_3d_large", "mixed", "16x16/256/minctas2/producers0") is None
+    assert bench.recorded_traffic("torus_3d_large", "mixed", "16x16/256/minctas2/producers0/zparts1") is None
 
 
 def test_fill_roofline_counts_ghost_cells_and_bytes():
