@@ -749,8 +749,10 @@ def main():
         stage_s = r["stage_ms_mean"] * 1e-3
         cells = g.ncells
         ach64 = fl["fp64_flops"] * cells / stage_s / 1e12
-        # FP64: 288 B per zone-stage; mixed: 252; constrained
-        # transport adds the face fields read and written (3 x 8 B each way)
+        # algorithmic bytes per zone-stage: FP64 288 (read P and U, write P and
+        # U, nine FP64 values each); mixed 252 (the FP32 primitive copy read in
+        # place of the FP64 one); constrained transport adds the face fields
+        # read and written (3 x 8 B each way)
         bytes_alg = {"fp64": 288, "mixed": 252, "fp64_ct": 336, "mixed_ct": 300}[form] * cells
         traffic = recorded_traffic(args.workload, form, shape_key(r["launch_shape"])) if args.c2p == "newton" else None
         fill = fill_roofline(g, form, r["fill_ms"], pk.get("hbm_gbs"))
