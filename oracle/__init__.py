@@ -104,6 +104,7 @@ def lib():
         L.or_face_count.restype = C.c_long
         L.or_set_faces.argtypes = [C.c_void_p, _DP]
         L.or_get_faces.argtypes = [C.c_void_p, _DP]
+        L.or_ct_ring_faces.argtypes = [C.c_void_p, C.c_int, _DP]
         _lib = L
     return _lib
 
@@ -284,6 +285,16 @@ class Oracle:
         out = np.zeros(self.L.or_face_count(self.ctx))
         self.L.or_get_faces(self.ctx, out)
         return out
+
+    def ring_faces(self, d):
+        """Phi^d over every block's faces and the ring one cell outside it
+        (filled from the owned faces), shape (nb, nz', ny', nx') with local
+        index -1 at position 0 across active directions."""
+        g = self.grid
+        ext = [g.nx[e] + (1 if e == d else (2 if e < g.ndim else 0)) for e in range(3)]
+        out = np.zeros(self.nb * ext[0] * ext[1] * ext[2])
+        self.L.or_ct_ring_faces(self.ctx, d, out)
+        return out.reshape(self.nb, ext[2], ext[1], ext[0])
 
     def estimate(self, eps=0.01):
         """Loehner's estimator on the density, maximum per block."""

@@ -1044,7 +1044,7 @@ double or_cfl_dt(or_ctx* c) {
   return c->p.cfl / smax;
 }
 
-/* ---- constrained transport (uniform grids) ---- */
+/* ---- constrained transport ---- */
 
 /* Staggered-mesh constrained transport: the field normal to each face is
  * evolved as Phi^d = sqrt(gamma) B^d at the face centre, by the induction
@@ -1061,7 +1061,14 @@ double or_cfl_dt(or_ctx* c) {
  * sqrt(gamma) B^d = (Phi^d_low + Phi^d_high) / 2.  A block owns its faces
  * 0..nx_d along d; the ring of faces one cell outside it across (needed by the
  * EMFs at the block's edges) is filled from the neighbours like ghost cells, so
- * both blocks sharing a face compute the same EMFs and keep the same value. */
+ * both blocks sharing a face compute the same EMFs and keep the same value.
+ * Across refinement levels a ring face takes the coarse face it lies on, or
+ * the mean of the two faces of the coarse cell it cuts, or the mean of the
+ * finer faces on it; the coarse flux through a face on a level boundary is the
+ * mean of the finer fluxes (as for the cell-centred variables), and an edge
+ * that a finer leaf touches takes the mean of the finer EMFs along it, so the
+ * coarse copy of such a face changes by the mean of the changes of the finer
+ * faces covering it, and every cell's divergence stays at round-off. */
 
 static size_t fcx(const or_ctx* c, int d, int b, int i, int j, int k) {
   const int* e = c->fe[d];
@@ -1075,66 +1082,120 @@ static size_t xfx(const or_ctx* c, int d, int b, int v, int i, int j, int k) {
   return ((((size_t)b * OR_NV + v) * e[2] + (k + o[2])) * e[1] + (j + o[1])) * e[0] + (i + o[0]);
 }
 
-/* Owner and local index of face (d; f local) of block b after the boundary
- * rules across it: periodic wrap, outflow / no-inflow copy of the nearest
- * face, polar axis mirror in theta (and phi + pi in 3-D).  Returns -1 if no
- * block owns it. */
-static int ct_face_source(const or_ctx* c, int d, int b, const int f[3], int lf[3]) {
-  const int* nx = c->p.nx;
-  long G[3], N[3];
-  for (int e = 0; e < 3; ++e) {
-    G[e] = (long)c->blk[4 * b + 1 + e] * nx[e] + f[e];
-    N[e] = (long)c->p.nroot[e] * nx[e];
-  }
-  for (int e = 0; e < c->p.ndim; ++e) {
-    if (e == d) continue;
-    for (int side = 0; side < 2; ++side) {
-      int out = side == 0 ? G[e] < 0 : G[e] >= N[e];
-      if (!out) continue;
-      int kind = c->p.bc[e][side];
-      if (kind == OR_BC_PERIODIC) {
-        G[e] = ((G[e] % N[e]) + N[e]) % N[e];
-      } else if (kind == OR_BC_OUTFLOW || kind == OR_BC_NOINFLOW) {
-        G[e] = side == 0 ? 0 : N[e] - 1;
-      } else if (kind == OR_BC_AXIS) {
-        G[e] = side == 0 ? -1 - G[e] : 2 * N[e] - 1 - G[e];
-        if (c->p.ndim == 3) G[2] = ((G[2] + N[2] / 2) % N[2] + N[2]) % N[2];
-      }
-    }
-  }
-  if (c->p.ndim == 3 && d != 2 && c->p.bc[2][0] == OR_BC_PERIODIC) G[2] = ((G[2] % N[2]) + N[2]) % N[2];
+/* cells along d at level L across the root domain */
+static long ncell_l(const or_ctx* c, int d, int L) {
+  return ((long)c->p.nroot[d] * c->p.nx[d]) << (d < c->p.ndim ? L : 0);
+}
+
+/* Level-L cell G (global index inside the root domain): 0 if a level-L leaf
+ * holds it, -1 if a coarser leaf covers it, +1 if finer leaves cover it. */
+static int cover_of(const or_ctx* c, int L, const long G[3]) {
   long bc[3];
-  for (int e = 0; e < 3; ++e) {
-    if (e == d) {
-      bc[e] = G[e] / nx[e];
-      if (bc[e] >= c->p.nroot[e]) bc[e] = c->p.nroot[e] - 1;
-      lf[e] = (int)(G[e] - bc[e] * nx[e]);
-    } else {
+  for (int d = 0; d < 3; ++d) bc[d] = G[d] / c->p.nx[d];
+  if (lut_get(c, L, bc) >= 0) return 0;
+  for (int Lc = L - 1; Lc >= 0; --Lc) {
+    for (int d = 0; d < 3; ++d) bc[d] = (d < c->p.ndim ? G[d] >> (L - Lc) : G[d]) / c->p.nx[d];
+    if (lut_get(c, Lc, bc) >= 0) return -1;
+  }
+  return 1;
+}
+
+/* Phi^d of face G at level L (a face index along d, cell indices across, inside
+ * the root domain): the face of the level-L leaf that holds it (the block above
+ * it along d, else the one below); where a coarser leaf covers it, the coarse
+ * face it lies on (even G_d) or the mean of the two faces of the coarse cell it
+ * cuts (odd G_d); where finer leaves cover it, the mean of the 2^(ndim-1)
+ * finer faces on it.  Only owned faces are read. */
+static double ct_face_value(const or_ctx* c, int d, int L, const long G[3]) {
+  const int* nx = c->p.nx;
+  const long Nd = ncell_l(c, d, L);
+  long bc[3];
+  int lf[3];
+  for (int e = 0; e < 3; ++e)
+    if (e != d) {
       bc[e] = G[e] / nx[e];
       lf[e] = (int)(G[e] % nx[e]);
     }
+  for (int above = 1; above >= 0; --above) {
+    const long cell = above ? G[d] : G[d] - 1;
+    if (cell < 0 || cell >= Nd) continue;
+    bc[d] = cell / nx[d];
+    lf[d] = (int)(G[d] - bc[d] * nx[d]);
+    const int b = lut_get(c, L, bc);
+    if (b >= 0) return c->fc[d][fcx(c, d, b, lf[0], lf[1], lf[2])];
   }
-  return lut_get(c, 0, bc);
+  long cell[3] = {G[0], G[1], G[2]};
+  if (cell[d] >= Nd) cell[d] = Nd - 1;
+  const int cov = cover_of(c, L, cell);
+  if (cov < 0 && L > 0) {
+    long H[3];
+    for (int e = 0; e < 3; ++e) H[e] = e < c->p.ndim ? G[e] >> 1 : G[e];
+    if (!(G[d] & 1)) return ct_face_value(c, d, L - 1, H);
+    long H1[3] = {H[0], H[1], H[2]};
+    H1[d] += 1;
+    return 0.5 * (ct_face_value(c, d, L - 1, H) + ct_face_value(c, d, L - 1, H1));
+  }
+  if (cov <= 0 || L + 1 >= c->p.nlevels) return 0.0; /* no leaf: an inconsistent grid */
+  int t[2], nt = 0;
+  for (int e = 0; e < c->p.ndim; ++e)
+    if (e != d) t[nt++] = e;
+  double s = 0.0;
+  for (int q = 0; q < (1 << nt); ++q) {
+    long F[3] = {G[0], G[1], G[2]};
+    F[d] = 2 * G[d];
+    for (int u = 0; u < nt; ++u) F[t[u]] = 2 * G[t[u]] + ((q >> u) & 1);
+    s += ct_face_value(c, d, L + 1, F);
+  }
+  return s / (1 << nt);
 }
 
+/* The ring faces of every block: the boundary rules across the face (periodic
+ * wrap, outflow / no-inflow copy of the nearest face, polar axis mirror in
+ * theta and phi + pi in 3-D), then the face's value at the block's level
+ * (zero where no face exists). */
 static void ct_fill_face_ring(or_ctx* c) {
+  const int* nx = c->p.nx;
 #pragma omp parallel for schedule(dynamic)
-  for (int b = 0; b < c->nb; ++b)
+  for (int b = 0; b < c->nb; ++b) {
+    const int L = c->blk[4 * b];
     for (int d = 0; d < c->p.ndim; ++d) {
       const int* e = c->fe[d];
       const int* o = c->fo[d];
+      long N[3];
+      for (int t = 0; t < 3; ++t) N[t] = ncell_l(c, t, L);
       for (int k = -o[2]; k < e[2] - o[2]; ++k)
         for (int j = -o[1]; j < e[1] - o[1]; ++j)
           for (int i = -o[0]; i < e[0] - o[0]; ++i) {
             int f[3] = {i, j, k}, ring = 0;
             for (int t = 0; t < 3; ++t)
-              if (t != d && (f[t] < 0 || f[t] >= c->p.nx[t])) ring = 1;
+              if (t != d && (f[t] < 0 || f[t] >= nx[t])) ring = 1;
             if (!ring) continue;
-            int lf[3];
-            int ob = ct_face_source(c, d, b, f, lf);
-            c->fc[d][fcx(c, d, b, i, j, k)] = ob >= 0 ? c->fc[d][fcx(c, d, ob, lf[0], lf[1], lf[2])] : 0.0;
+            long G[3];
+            for (int t = 0; t < 3; ++t) G[t] = (long)c->blk[4 * b + 1 + t] * nx[t] + f[t];
+            for (int t = 0; t < c->p.ndim; ++t) {
+              if (t == d) continue;
+              for (int side = 0; side < 2; ++side) {
+                int out = side == 0 ? G[t] < 0 : G[t] >= N[t];
+                if (!out) continue;
+                int kind = c->p.bc[t][side];
+                if (kind == OR_BC_PERIODIC) {
+                  G[t] = ((G[t] % N[t]) + N[t]) % N[t];
+                } else if (kind == OR_BC_OUTFLOW || kind == OR_BC_NOINFLOW) {
+                  G[t] = side == 0 ? 0 : N[t] - 1;
+                } else if (kind == OR_BC_AXIS) {
+                  G[t] = side == 0 ? -1 - G[t] : 2 * N[t] - 1 - G[t];
+                  if (c->p.ndim == 3) G[2] = ((G[2] + N[2] / 2) % N[2] + N[2]) % N[2];
+                }
+              }
+            }
+            if (c->p.ndim == 3 && d != 2 && c->p.bc[2][0] == OR_BC_PERIODIC) G[2] = ((G[2] % N[2]) + N[2]) % N[2];
+            int inside = 1;
+            for (int t = 0; t < 3; ++t)
+              if (G[t] < 0 || G[t] > N[t] || (t != d && G[t] == N[t])) inside = 0;
+            c->fc[d][fcx(c, d, b, i, j, k)] = inside ? ct_face_value(c, d, L, G) : 0.0;
           }
     }
+  }
 }
 
 /* Fluxes through every face of direction d of block b and its ring. */
@@ -1142,7 +1203,7 @@ static void ct_block_xfluxes(or_ctx* c, int b, int d) {
   int L = c->blk[4 * b];
   const int* e = c->fe[d];
   const int* o = c->fo[d];
-  long Nd = (long)c->p.nroot[d] * c->p.nx[d];
+  long Nd = ncell_l(c, d, L);
   for (int k = -o[2]; k < e[2] - o[2]; ++k)
     for (int j = -o[1]; j < e[1] - o[1]; ++j)
       for (int i = -o[0]; i < e[0] - o[0]; ++i) {
@@ -1191,6 +1252,73 @@ static double ct_emf2(const or_ctx* c, int b, int i, int j, int k) {
                  c->xf[2][xfx(c, 2, b, OR_B1, i, j, k)] - c->xf[2][xfx(c, 2, b, OR_B1, i - 1, j, k)]);
 }
 
+static double ct_emf_block(const or_ctx* c, int a, int b, int i, int j, int k) {
+  return a == 0 ? ct_emf1(c, b, i, j, k) : (a == 1 ? ct_emf2(c, b, i, j, k) : ct_emf3(c, b, i, j, k));
+}
+
+/* The level-L cell q (0..3) around the edge along a at G (a cell index along
+ * a, face indices across): across each active transverse direction the cell
+ * below (bit 0) or above (bit 1) the edge; periodic wrap; 0 where it leaves
+ * the root domain across another boundary. */
+static int ct_edge_cell(const or_ctx* c, int a, int L, const long G[3], int q, long C[3], int s[3]) {
+  int u = 0;
+  for (int e = 0; e < 3; ++e) {
+    C[e] = G[e];
+    s[e] = 0;
+    if (e == a || e >= c->p.ndim) continue;
+    s[e] = (q >> u++) & 1;
+    C[e] = G[e] - 1 + s[e];
+    const long N = ncell_l(c, e, L);
+    if (C[e] < 0 || C[e] >= N) {
+      if (c->p.bc[e][C[e] < 0 ? 0 : 1] != OR_BC_PERIODIC) return 0;
+      C[e] = ((C[e] % N) + N) % N;
+    }
+  }
+  return 1;
+}
+
+/* E_a (a = 0, 1, 2: E_1, E_2, E_3) at the edge of block b with local index
+ * (i, j, k) in the layout of ct_emf1/2/3: the block's own mean of four face
+ * fluxes, except where a finer leaf touches the edge.  There it is the mean
+ * of the finer EMFs along the edge (two segments when a is active, else one),
+ * each taken from a finer leaf holding a cell around that segment; then every
+ * coarse face around the edge changes by the mean of the changes of the finer
+ * faces covering it, and the coarse and fine copies of a face on a level
+ * boundary keep the same flux through it (EMF correction). */
+static double ct_emf(const or_ctx* c, int a, int b, int i, int j, int k) {
+  if (c->p.nlevels == 1) return ct_emf_block(c, a, b, i, j, k);
+  const int L = c->blk[4 * b];
+  const int* nx = c->p.nx;
+  const int loc[3] = {i, j, k};
+  long G[3], C[3];
+  int s[3];
+  for (int e = 0; e < 3; ++e) G[e] = (long)c->blk[4 * b + 1 + e] * nx[e] + loc[e];
+  int finer = 0;
+  for (int q = 0; q < 4 && !finer; ++q)
+    if (ct_edge_cell(c, a, L, G, q, C, s) && cover_of(c, L, C) > 0) finer = 1;
+  if (!finer || L + 1 >= c->p.nlevels) return ct_emf_block(c, a, b, i, j, k);
+  const int na = a < c->p.ndim ? 2 : 1;
+  double sum = 0.0;
+  int n = 0;
+  for (int t = 0; t < na; ++t) {
+    long F[3];
+    for (int e = 0; e < 3; ++e) F[e] = e >= c->p.ndim ? G[e] : 2 * G[e] + (e == a ? t : 0);
+    for (int q = 0; q < 4; ++q) {
+      if (!ct_edge_cell(c, a, L + 1, F, q, C, s)) continue;
+      long bc[3];
+      for (int e = 0; e < 3; ++e) bc[e] = C[e] / nx[e];
+      const int bf = lut_get(c, L + 1, bc);
+      if (bf < 0) continue;
+      int lf[3];
+      for (int e = 0; e < 3; ++e) lf[e] = (int)(C[e] - bc[e] * nx[e]) + (e != a && e < c->p.ndim && !s[e] ? 1 : 0);
+      sum += ct_emf_block(c, a, bf, lf[0], lf[1], lf[2]);
+      ++n;
+      break;
+    }
+  }
+  return n == na ? sum / na : ct_emf_block(c, a, b, i, j, k);
+}
+
 /* d_t Phi = -curl E on the owned faces of block b, then the stage combination
  * (stage 1: Phi1 = Phin + dt R; stage 2: Phi = Phin/2 + (Phi1 + dt R)/2).
  * Faces on the polar axis (sqrt(gamma) = 0) stay zero. */
@@ -1201,7 +1329,7 @@ static void ct_update_faces(or_ctx* c, int b, int stage, double dt) {
   double dx[3];
   for (int t = 0; t < 3; ++t) dx[t] = dxl(c, t, L);
   for (int d = 0; d < c->p.ndim; ++d) {
-    long Nd = (long)c->p.nroot[d] * nx[d];
+    long Nd = ncell_l(c, d, L);
     int n[3] = {nx[0], nx[1], nx[2]};
     n[d] += 1;
     for (int k = 0; k < n[2]; ++k)
@@ -1217,14 +1345,14 @@ static void ct_update_faces(or_ctx* c, int b, int stage, double dt) {
           }
           double R;
           if (d == 0) {
-            R = -(ct_emf3(c, b, i, j + 1, k) - ct_emf3(c, b, i, j, k)) / dx[1];
-            if (three) R += (ct_emf2(c, b, i, j, k + 1) - ct_emf2(c, b, i, j, k)) / dx[2];
+            R = -(ct_emf(c, 2, b, i, j + 1, k) - ct_emf(c, 2, b, i, j, k)) / dx[1];
+            if (three) R += (ct_emf(c, 1, b, i, j, k + 1) - ct_emf(c, 1, b, i, j, k)) / dx[2];
           } else if (d == 1) {
-            R = (ct_emf3(c, b, i + 1, j, k) - ct_emf3(c, b, i, j, k)) / dx[0];
-            if (three) R -= (ct_emf1(c, b, i, j, k + 1) - ct_emf1(c, b, i, j, k)) / dx[2];
+            R = (ct_emf(c, 2, b, i + 1, j, k) - ct_emf(c, 2, b, i, j, k)) / dx[0];
+            if (three) R -= (ct_emf(c, 0, b, i, j, k + 1) - ct_emf(c, 0, b, i, j, k)) / dx[2];
           } else {
-            R = -(ct_emf2(c, b, i + 1, j, k) - ct_emf2(c, b, i, j, k)) / dx[0] +
-                (ct_emf1(c, b, i, j + 1, k) - ct_emf1(c, b, i, j, k)) / dx[1];
+            R = -(ct_emf(c, 1, b, i + 1, j, k) - ct_emf(c, 1, b, i, j, k)) / dx[0] +
+                (ct_emf(c, 0, b, i, j + 1, k) - ct_emf(c, 0, b, i, j, k)) / dx[1];
           }
           if (stage == 1) {
             c->fcn[d][q] = c->fc[d][q];
@@ -1295,6 +1423,12 @@ void or_set_faces(or_ctx* c, const double* faces) {
 
 void or_get_faces(const or_ctx* c, double* faces) { ct_copy_faces((or_ctx*)c, faces, 0); }
 
+void or_ct_ring_faces(or_ctx* c, int d, double* out) {
+  ct_fill_face_ring(c);
+  size_t n = (size_t)c->nb * c->fe[d][0] * c->fe[d][1] * c->fe[d][2];
+  memcpy(out, c->fc[d], sizeof(double) * n);
+}
+
 /* ---- one Runge-Kutta stage ---- */
 
 static size_t fidx(const or_ctx* c, int d, int b, int v, int i, int j, int k) {
@@ -1338,6 +1472,12 @@ static void block_fluxes(or_ctx* c, int b, int d) {
         }
         for (int v = 0; v < OR_NV; ++v) c->flux[d][fidx(c, d, b, v, i, j, k)] = F[v];
       }
+}
+
+/* Flux of variable v through face (i, j, k) of direction d of block b: the
+ * face-flux arrays, or with constrained transport the ring-extended ones. */
+static double* flux_slot(or_ctx* c, int d, int b, int v, int i, int j, int k) {
+  return c->p.ct ? &c->xf[d][xfx(c, d, b, v, i, j, k)] : &c->flux[d][fidx(c, d, b, v, i, j, k)];
 }
 
 /* Coarse-fine flux correction: at a face where the neighbour is one level
@@ -1388,7 +1528,7 @@ static void reflux_block(or_ctx* c, int b) {
               li[d] = ffine;
               li[t1] = (int)(Gf[t1] % n[t1]);
               li[t2] = (int)(Gf[t2] % n[t2]);
-              for (int v = 0; v < OR_NV; ++v) acc[v] += c->flux[d][fidx(c, d, bf, v, li[0], li[1], li[2])];
+              for (int v = 0; v < OR_NV; ++v) acc[v] += *flux_slot(c, d, bf, v, li[0], li[1], li[2]);
               ++cnt;
             }
           if (cnt == 0) continue;
@@ -1396,7 +1536,7 @@ static void reflux_block(or_ctx* c, int b) {
           lc[d] = fcoarse;
           lc[t1] = a;
           lc[t2] = bb;
-          for (int v = 0; v < OR_NV; ++v) c->flux[d][fidx(c, d, b, v, lc[0], lc[1], lc[2])] = acc[v] / cnt;
+          for (int v = 0; v < OR_NV; ++v) *flux_slot(c, d, b, v, lc[0], lc[1], lc[2]) = acc[v] / cnt;
         }
     }
 }
@@ -1506,12 +1646,19 @@ void or_stage_blocks(or_ctx* c, int stage, double dt, int nsel, const int* sel) 
   if (c->p.imex && !c->p.ct && stage == 1) imex_first_stage_psi(c, dt);
   or_fill_ghosts(c);
   if (c->p.ct) {
-    /* constrained transport (uniform grids): ring faces, ring-extended fluxes,
-     * the face update, then the cells */
+    /* constrained transport: ring faces, ring-extended fluxes (of every block
+     * when levels differ: the corrections read the finer neighbours'), the
+     * coarse-fine flux correction, the face update with the EMF correction,
+     * then the cells */
     ct_fill_face_ring(c);
+    int allx = c->p.nlevels > 1;
 #pragma omp parallel for schedule(dynamic)
-    for (int q = 0; q < nsel; ++q)
-      for (int d = 0; d < c->p.ndim; ++d) ct_block_xfluxes(c, sel[q], d);
+    for (int q = 0; q < (allx ? c->nb : nsel); ++q)
+      for (int d = 0; d < c->p.ndim; ++d) ct_block_xfluxes(c, allx ? q : sel[q], d);
+    if (allx) {
+#pragma omp parallel for schedule(dynamic)
+      for (int q = 0; q < nsel; ++q) reflux_block(c, sel[q]);
+    }
     long long tot[4] = {0, 0, 0, 0};
 #pragma omp parallel
     {

@@ -118,7 +118,7 @@ void or_c2p_counts(const or_ctx* c, long long counts[4]);
 void or_c2p_status(const or_ctx* c, unsigned char* status);
 int or_ghosted_cells(const or_ctx* c);                    /* per block, with ghosts */
 
-/* ---- constrained transport (params.ct = 1, uniform grids) ----
+/* ---- constrained transport (params.ct = 1) ----
  * The evolved field is Phi^d = sqrt(gamma) B^d at the centre of each face
  * normal to an active direction d.  Owned faces of a block: index 0..nx_d
  * along d, the block's cells across; layout [block][d][k][j][i] over the
@@ -128,6 +128,11 @@ int or_ghosted_cells(const or_ctx* c);                    /* per block, with gho
 long or_face_count(const or_ctx* c);                      /* owned faces, all blocks */
 void or_set_faces(or_ctx* c, const double* faces);
 void or_get_faces(const or_ctx* c, double* faces);
+/* Fills the ring faces (the faces one cell outside each block, across) from
+ * the owned ones and copies Phi^d over every block's ring-extended face array,
+ * [block][k][j][i] with extents nx_e + 2 across in active directions e, nx_d + 1
+ * along d (the ring at local index -1 and nx_e); a test accessor. */
+void or_ct_ring_faces(or_ctx* c, int d, double* out);
 
 /* ---- AMR regridding ----
  * or_estimate: Loehner's error estimator on the density of every interior cell

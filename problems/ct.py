@@ -1,4 +1,4 @@
-"""Face-centred magnetic fields for constrained transport (uniform grids).
+"""Face-centred magnetic fields for constrained transport.
 
 The evolved field is Phi^d = sqrt(gamma) B^d at the centre of every face
 normal to an active direction d.  Layout of a face array (both the oracle's
@@ -9,7 +9,11 @@ A divergence-free start comes from a vector potential at cell edges:
   Phi^1 = d_2 A_3 - d_3 A_2,  Phi^2 = d_3 A_1 - d_1 A_3,  Phi^3 = d_1 A_2 - d_2 A_1
 by differences of the edge values (A_3 on edges along x3, A_1 along x1, A_2
 along x2), so the discrete divergence of every cell vanishes to round-off.
-These are set-ups and a diagnostic; the update arithmetic lives in the
+On a grid with refinement levels each block uses its own level's spacing.
+A potential component that does not depend on its own coordinate (A_1 free
+of x1, and so on) has exact edge integrals, so a coarse face on a level
+boundary then equals the mean of the finer faces covering it.
+These are set-ups and diagnostics; the update arithmetic lives in the
 oracle and in the library, not here."""
 from __future__ import annotations
 
@@ -55,7 +59,13 @@ def join_faces(grid: Grid, parts) -> np.ndarray:
 
 
 def _dx(grid):
-    return [(grid.xmax[d] - grid.xmin[d]) / (grid.nroot[d] * grid.nx[d]) for d in range(3)]
+    """Per direction, the spacing of every block at its level, shape (nb, 1, 1, 1)."""
+    lev = grid.blocks[:, 0].astype(np.int64)
+    out = []
+    for d in range(3):
+        scale = 2.0 ** lev if d < grid.ndim else np.ones(grid.nb)
+        out.append(((grid.xmax[d] - grid.xmin[d]) / (grid.nroot[d] * grid.nx[d]) / scale).reshape(-1, 1, 1, 1))
+    return out
 
 
 def _coords(grid, face_dims, centre_dims):
@@ -68,7 +78,7 @@ def _coords(grid, face_dims, centre_dims):
         n = grid.nx[d] + (1 if d in face_dims else 0)
         off = 0.0 if d in face_dims else 0.5
         g = grid.blocks[:, 1 + d].astype(np.int64)[:, None] * grid.nx[d] + np.arange(n)[None, :]
-        axes.append(grid.xmin[d] + (g + off) * dx[d])
+        axes.append(grid.xmin[d] + (g + off) * dx[d].reshape(-1, 1))
     nb = grid.nb
     X1 = axes[0][:, None, None, :]
     X2 = axes[1][:, None, :, None]
@@ -79,8 +89,7 @@ def _coords(grid, face_dims, centre_dims):
 
 def faces_from_potential(grid: Grid, A1=None, A2=None, A3=None) -> np.ndarray:
     """Phi from edge values of a vector potential (callables of (x1, x2, x3)
-    arrays; None for a zero component).  Uniform grids."""
-    assert grid.nlevels == 1
+    arrays; None for a zero component)."""
     dx = _dx(grid)
     three = grid.ndim == 3
 
@@ -172,3 +181,93 @@ def fm_torus_faces(grid: Grid, P: np.ndarray, r_in: float = 6.0, r_pmax: float =
         return scale * np.maximum(rho - 0.2, 0.0)
 
     return faces_from_potential(grid, A3=aphi)
+
+
+def own_potential_free(grid: Grid, seed: int = 7, amp: float = 0.5):
+    """A smooth random periodic potential whose component A_d does not depend
+    on x_d (exact edge integrals at every level): three callables or None."""
+    rng = np.random.default_rng(seed)
+
+    def comp(own):
+        modes = []
+        for _ in range(3):
+            kv = rng.integers(1, 3, size=3)
+            kv[own] = 0
+            if grid.ndim == 2:
+                kv[2] = 0
+            modes.append((kv, rng.uniform(0.2, 1.0), rng.uniform(0, 2 * np.pi)))
+
+        def f(x1, x2, x3):
+            out = np.zeros_like(x1)
+            for kv, a, ph in modes:
+                out += amp * a * np.sin(2 * np.pi * (kv[0] * x1 + kv[1] * x2 + kv[2] * x3) + ph) / (2 * np.pi)
+            return out
+        return f
+
+    if grid.ndim == 2:
+        return None, None, comp(2)
+    return comp(0), comp(1), comp(2)
+
+
+def _face_table(grid: Grid, faces):
+    """{(level, d, G1, G2, G3): Phi} over every block's owned faces (global
+    level indices: a face index along d, cell indices across)."""
+    out = {}
+    for d, p in enumerate(split_faces(grid, faces)):
+        nb, n3, n2, n1 = p.shape
+        k, j, i = np.meshgrid(np.arange(n3), np.arange(n2), np.arange(n1), indexing="ij")
+        for b in range(grid.nb):
+            lev, bx, by, bz = (int(v) for v in grid.blocks[b])
+            G1, G2, G3 = bx * grid.nx[0] + i, by * grid.nx[1] + j, bz * grid.nx[2] + k
+            for g1, g2, g3, v in zip(G1.ravel(), G2.ravel(), G3.ravel(), p[b].ravel()):
+                out[(lev, d, int(g1), int(g2), int(g3))] = float(v)
+    return out
+
+
+def level_face_mismatch(grid: Grid, faces) -> float:
+    """Largest |Phi of a coarse face - mean of the finer faces covering it| over
+    the faces that lie on a level boundary (0.0 on a uniform grid)."""
+    tab = _face_table(grid, faces)
+    worst = 0.0
+    for (lev, d, g1, g2, g3), v in tab.items():
+        G = [g1, g2, g3]
+        fine = []
+        trans = [e for e in range(grid.ndim) if e != d]
+        for q in range(1 << len(trans)):
+            F = [2 * G[e] if e < grid.ndim else G[e] for e in range(3)]
+            for u, e in enumerate(trans):
+                F[e] += (q >> u) & 1
+            key = (lev + 1, d, F[0], F[1], F[2])
+            if key in tab:
+                fine.append(tab[key])
+        if len(fine) == 1 << len(trans):
+            worst = max(worst, abs(v - sum(fine) / len(fine)))
+    return worst
+
+
+def plane_fluxes(grid: Grid, faces, d: int):
+    """Magnetic flux sum Phi^d * (face area) through each plane x_d = const at
+    the level-0 face positions (the finest faces available over each part of
+    the plane), as a list over the planes."""
+    tab = _face_table(grid, faces)
+    dx0 = [(grid.xmax[e] - grid.xmin[e]) / (grid.nroot[e] * grid.nx[e]) for e in range(3)]
+    N0 = grid.nroot[d] * grid.nx[d]
+    out = []
+    for G0 in range(N0):
+        total = 0.0
+        for (lev, dd, g1, g2, g3), v in tab.items():
+            G = (g1, g2, g3)
+            if dd != d or G[d] != G0 * 2 ** lev:
+                continue
+            # a face counts where no finer face covers it
+            trans = [e for e in range(grid.ndim) if e != d]
+            F = [2 * G[e] if e < grid.ndim else G[e] for e in range(3)]
+            if (lev + 1, d, F[0], F[1], F[2]) in tab:
+                continue
+            area = 1.0
+            for e in range(3):
+                if e != d:
+                    area *= dx0[e] / (2 ** lev if e < grid.ndim else 1)
+            total += v * area
+        out.append(total)
+    return out
