@@ -30,9 +30,35 @@ struct Layout {
   size_t off_P[2], off_P32[2], off_U[2], off_scratch, off_scratch_out, off_status, off_small;
   size_t off_nodes, off_ops, off_nodeval, off_cf, off_regoff, off_reg, off_rcells, off_rterms;
   size_t off_phi[2], off_xf, off_te_c, off_te_f1, off_te_f2, off_te_c32, off_te_f1_32, off_te_f2_32, off_ring[2];
+  size_t off_ringm[2], off_emf, off_xr[3], off_ef[2];
   size_t total;
   long long toff_c[MAXLEV], toff_f1[MAXLEV], toff_f2[MAXLEV];
+  long long teo_c[MAXLEV], teo_f1[MAXLEV], teo_f2[MAXLEV];
 };
+
+// The constrained-transport maps of a grid: the ring-face copies (every grid)
+// and, with refinement levels, the means and the coarse-fine corrections.
+struct CtMaps {
+  std::vector<long long> ring_dst, ring_src;
+  CtLevelMaps lv;
+  bool ok;
+};
+
+CtMaps build_ct_maps(const bhac_grid_desc* d, const bhac_block_desc* b, int nb) {
+  CtMaps m;
+  m.ok = true;
+  m.lv.ok = true;
+  if (d->divb != BHAC_DIVB_CT) return m;
+  if (d->nlevels == 1) {
+    m.ok = ct_ring_map(d, b, nb, ct_geom(d), m.ring_dst, m.ring_src);
+  } else {
+    m.lv = ct_level_maps(d, b, nb, ct_geom(d));
+    m.ok = m.lv.ok;
+    m.ring_dst.swap(m.lv.copy_dst);
+    m.ring_src.swap(m.lv.copy_src);
+  }
+  return m;
+}
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
@@ -53,11 +79,12 @@ bool valid_desc(const bhac_grid_desc* d, const bhac_block_desc* b, int nb) {
   if (d->recon < 0 || d->recon > 1 || d->riemann < 0 || d->riemann > 1) return false;
   if (!(d->gamma_ad > 1.0) || !(d->cfl > 0.0) || !(d->ch > 0.0) || d->c2p_maxit < 1) return false;
   if (!(d->w_max > 1.0)) return false;
-  // constrained transport: uniform grids
   if (d->divb < 0 || d->divb > 1) return false;
-  if (d->divb == BHAC_DIVB_CT && d->nlevels != 1) return false;
-  // the face kernels' 32-bit indices: blocks x ring-extended faces < 2^31
-  if (d->divb == BHAC_DIVB_CT && (long long)nb * ct_geom(d).nfb >= (1LL << 31)) return false;
+  // the face and edge kernels' 32-bit indices: blocks x ring-extended faces
+  // and blocks x edges < 2^31
+  if (d->divb == BHAC_DIVB_CT && ((long long)nb * ct_geom(d).nfb >= (1LL << 31) ||
+                                  (long long)nb * ct_geom(d).nEb >= (1LL << 31)))
+    return false;
   if (d->imex < 0 || d->imex > 1) return false;
   if (d->c2p_solver != BHAC_C2P_NEWTON && d->c2p_solver != BHAC_C2P_NK) return false;
   // the axis rule is for x2 (theta) only; phi must be periodic with an even cell count in 3-D
@@ -92,7 +119,7 @@ void geometry(const bhac_grid_desc* d, int g[3], int N[3], int& ncell, int& nint
   nslots = ncell - nint;
 }
 
-Layout layout(const bhac_grid_desc* d, int nb, const HostMaps& M, long long nring) {
+Layout layout(const bhac_grid_desc* d, int nb, const HostMaps& M, const CtMaps& C) {
   int g[3], N[3], ncell, nint, nslots;
   geometry(d, g, N, ncell, nint, nslots);
   const bool flat = d->coords == BHAC_COORDS_CART;
@@ -148,16 +175,34 @@ Layout layout(const bhac_grid_desc* d, int nb, const HostMaps& M, long long nrin
   const size_t nfaces = ct ? (size_t)nb * cg.nfb : 0;
   for (int s = 0; s < 2; ++s) L.off_phi[s] = take(sizeof(double) * nfaces);
   L.off_xf = take(sizeof(double) * NV * nfaces);
-  const size_t n1 = (size_t)d->nroot[0] * d->nx[0], n2 = (size_t)d->nroot[1] * d->nx[1];
-  const size_t ec = ct && !flat ? (n1 + 2) * (n2 + 2) : 0, ef1 = ct && !flat ? (n1 + 3) * (n2 + 2) : 0,
-               ef2 = ct && !flat ? (n1 + 2) * (n2 + 3) : 0;
+  size_t ec = 0, ef1 = 0, ef2 = 0;
+  for (int l = 0; l < MAXLEV; ++l) {
+    L.teo_c[l] = (long long)ec;
+    L.teo_f1[l] = (long long)ef1;
+    L.teo_f2[l] = (long long)ef2;
+    if (ct && !flat && l < d->nlevels) {
+      const size_t n1 = ((size_t)d->nroot[0] * d->nx[0]) << l, n2 = ((size_t)d->nroot[1] * d->nx[1]) << l;
+      ec += (n1 + 2) * (n2 + 2);
+      ef1 += (n1 + 3) * (n2 + 2);
+      ef2 += (n1 + 2) * (n2 + 3);
+    }
+  }
   L.off_te_c = take(sizeof(double) * CREC * ec);
   L.off_te_f1 = take(sizeof(double) * FREC * ef1);
   L.off_te_f2 = take(sizeof(double) * FREC * ef2);
   L.off_te_c32 = take(sizeof(float) * CREC * ec);
   L.off_te_f1_32 = take(sizeof(float) * FREC * ef1);
   L.off_te_f2_32 = take(sizeof(float) * FREC * ef2);
-  for (int s = 0; s < 2; ++s) L.off_ring[s] = take(sizeof(long long) * (ct ? (size_t)nring : 0));
+  for (int s = 0; s < 2; ++s) L.off_ring[s] = take(sizeof(long long) * C.ring_dst.size());
+  L.off_ringm[0] = take(sizeof(long long) * C.lv.mean_dst.size());
+  L.off_ringm[1] = take(sizeof(long long) * C.lv.mean_src.size());
+  const bool levels = ct && d->nlevels > 1;
+  L.off_emf = take(sizeof(double) * (levels ? (size_t)nb * cg.nEb : 0));
+  L.off_xr[0] = take(sizeof(long long) * C.lv.xr_dst.size());
+  L.off_xr[1] = take(sizeof(long long) * C.lv.xr_src.size());
+  L.off_xr[2] = take(sizeof(int) * C.lv.xr_d.size());
+  L.off_ef[0] = take(sizeof(long long) * C.lv.ef_dst.size());
+  L.off_ef[1] = take(sizeof(long long) * C.lv.ef_src.size());
   L.total = o;
   return L;
 }
@@ -429,8 +474,22 @@ CtArgs ct_args(const bhac_ctx* c) {
   t.te_c32 = c->te_c32;
   t.te_f1_32 = c->te_f1_32;
   t.te_f2_32 = c->te_f2_32;
+  for (int l = 0; l < MAXLEV; ++l) {
+    t.teo_c[l] = c->teo_c[l];
+    t.teo_f1[l] = c->teo_f1[l];
+    t.teo_f2[l] = c->teo_f2[l];
+  }
   t.axis_lo = c->d.bc[1][0] == BHAC_BC_AXIS;
   t.axis_hi = c->d.bc[1][1] == BHAC_BC_AXIS;
+  t.amr = c->d.nlevels > 1;
+  t.emf = c->emf;
+  t.xr_dst = c->xr_dst;
+  t.xr_src = c->xr_src;
+  t.xr_d = c->xr_d;
+  t.nxr = c->nxr;
+  t.ef_dst = c->ef_dst;
+  t.ef_src = c->ef_src;
+  t.nef = c->nef;
   return t;
 }
 
@@ -459,6 +518,8 @@ bhac_status run_stage_ct(bhac_ctx* c, int stage, double dt) {
   }
   CtArgs t = ct_args(c);
   if (launch_ct_ring(c->ring_dst, c->ring_src, c->nring, c->phi[c->pcur], c->st) != cudaSuccess) return BHAC_ERR_CUDA;
+  if (launch_ct_ring_mean(c->ringm_dst, c->ringm_src, c->nringm, c->phi[c->pcur], c->st) != cudaSuccess)
+    return BHAC_ERR_CUDA;
   if (launch_ct_stage(a, t, c->mixed, c->st) != cudaSuccess) return BHAC_ERR_CUDA;
   c->cur = out;
   c->ucur = 1 - c->ucur;
@@ -489,9 +550,9 @@ bhac_status bhac_query_sizes(const bhac_grid_desc* d, const bhac_block_desc* b, 
   geometry(d, g, N, ncell, nint, nslots);
   const HostMaps M = build_maps(d, b, nb, g, N, ncell);
   if (!M.ok) return BHAC_ERR_ARG;
-  std::vector<long long> rd, rs;
-  if (d->divb == BHAC_DIVB_CT && !ct_ring_map(d, b, nb, ct_geom(d), rd, rs)) return BHAC_ERR_ARG;
-  *out = layout(d, nb, M, (long long)rd.size()).total;
+  const CtMaps C = build_ct_maps(d, b, nb);
+  if (!C.ok) return BHAC_ERR_ARG;
+  *out = layout(d, nb, M, C).total;
   return BHAC_OK;
 }
 
@@ -502,9 +563,9 @@ bhac_status bhac_init_grid(bhac_ctx** out, const bhac_grid_desc* d, const bhac_b
   geometry(d, g, N, ncell, nint, nslots);
   const HostMaps M = build_maps(d, b, nb, g, N, ncell);
   if (!M.ok) return BHAC_ERR_ARG;  // a boundary rule or a level points at a missing block
-  std::vector<long long> ring_dst, ring_src;
-  if (d->divb == BHAC_DIVB_CT && !ct_ring_map(d, b, nb, ct_geom(d), ring_dst, ring_src)) return BHAC_ERR_ARG;
-  const Layout L = layout(d, nb, M, (long long)ring_dst.size());
+  const CtMaps C = build_ct_maps(d, b, nb);
+  if (!C.ok) return BHAC_ERR_ARG;  // a ring face or a correction points at a missing block
+  const Layout L = layout(d, nb, M, C);
   if (arena_bytes < L.total) return BHAC_ERR_NOMEM;
   bhac_ctx* c = new bhac_ctx();
   c->d = *d;
@@ -577,9 +638,25 @@ bhac_status bhac_init_grid(bhac_ctx** out, const bhac_grid_desc* d, const bhac_b
   c->te_c32 = (float*)(c->arena + L.off_te_c32);
   c->te_f1_32 = (float*)(c->arena + L.off_te_f1_32);
   c->te_f2_32 = (float*)(c->arena + L.off_te_f2_32);
+  for (int l = 0; l < MAXLEV; ++l) {
+    c->teo_c[l] = L.teo_c[l];
+    c->teo_f1[l] = L.teo_f1[l];
+    c->teo_f2[l] = L.teo_f2[l];
+  }
   c->ring_dst = (long long*)(c->arena + L.off_ring[0]);
   c->ring_src = (long long*)(c->arena + L.off_ring[1]);
-  c->nring = (long long)ring_dst.size();
+  c->nring = (long long)C.ring_dst.size();
+  c->ringm_dst = (long long*)(c->arena + L.off_ringm[0]);
+  c->ringm_src = (long long*)(c->arena + L.off_ringm[1]);
+  c->nringm = (long long)C.lv.mean_dst.size();
+  c->emf = (double*)(c->arena + L.off_emf);
+  c->xr_dst = (long long*)(c->arena + L.off_xr[0]);
+  c->xr_src = (long long*)(c->arena + L.off_xr[1]);
+  c->xr_d = (int*)(c->arena + L.off_xr[2]);
+  c->nxr = (long long)C.lv.xr_dst.size();
+  c->ef_dst = (long long*)(c->arena + L.off_ef[0]);
+  c->ef_src = (long long*)(c->arena + L.off_ef[1]);
+  c->nef = (long long)C.lv.ef_dst.size();
   c->cur = 0;
   c->ucur = 0;
   c->threads = 256;
@@ -644,8 +721,15 @@ bhac_status bhac_init_grid(bhac_ctx** out, const bhac_grid_desc* d, const bhac_b
   if (e == cudaSuccess) e = up(c->d_regoff, M.regoff.data(), sizeof(long long) * M.regoff.size());
   if (e == cudaSuccess) e = up(c->d_rcells, M.rcells.data(), sizeof(RefluxCell) * M.rcells.size());
   if (e == cudaSuccess) e = up(c->d_rterms, M.rterms.data(), sizeof(RefluxTerm) * M.rterms.size());
-  if (e == cudaSuccess) e = up(c->ring_dst, ring_dst.data(), sizeof(long long) * ring_dst.size());
-  if (e == cudaSuccess) e = up(c->ring_src, ring_src.data(), sizeof(long long) * ring_src.size());
+  if (e == cudaSuccess) e = up(c->ring_dst, C.ring_dst.data(), sizeof(long long) * C.ring_dst.size());
+  if (e == cudaSuccess) e = up(c->ring_src, C.ring_src.data(), sizeof(long long) * C.ring_src.size());
+  if (e == cudaSuccess) e = up(c->ringm_dst, C.lv.mean_dst.data(), sizeof(long long) * C.lv.mean_dst.size());
+  if (e == cudaSuccess) e = up(c->ringm_src, C.lv.mean_src.data(), sizeof(long long) * C.lv.mean_src.size());
+  if (e == cudaSuccess) e = up(c->xr_dst, C.lv.xr_dst.data(), sizeof(long long) * C.lv.xr_dst.size());
+  if (e == cudaSuccess) e = up(c->xr_src, C.lv.xr_src.data(), sizeof(long long) * C.lv.xr_src.size());
+  if (e == cudaSuccess) e = up(c->xr_d, C.lv.xr_d.data(), sizeof(int) * C.lv.xr_d.size());
+  if (e == cudaSuccess) e = up(c->ef_dst, C.lv.ef_dst.data(), sizeof(long long) * C.lv.ef_dst.size());
+  if (e == cudaSuccess) e = up(c->ef_src, C.lv.ef_src.data(), sizeof(long long) * C.lv.ef_src.size());
   if (e == cudaSuccess) e = cudaMemsetAsync(small, 0, 256, c->st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);  // the host maps die here
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->cp_in, cudaStreamNonBlocking);
@@ -698,31 +782,32 @@ bhac_status bhac_set_metric(bhac_ctx* c, int kind, double spin, double mass, con
     M.tab_f2_32 = c->tab_f2_32 + c->toff_f2[l] * FREC;
     if (launch_metric_tables(M, c->st) != cudaSuccess) return BHAC_ERR_CUDA;
   }
-  if (c->ct) {
-    // the same tables on the grid extended by one cell on each side in x1 and
-    // x2, for the faces around each block (a face beyond the polar axis sees
-    // the mirrored metric, which depends on sin^2 and cos^2 of theta only)
+  for (int l = 0; c->ct && l < c->d.nlevels; ++l) {
+    // the same tables of every level on its grid extended by one cell on each
+    // side in x1 and x2, for the faces around each block (a face beyond the
+    // polar axis sees the mirrored metric, which depends on sin^2 and cos^2 of
+    // theta only)
     MetricArgs M;
     M.coords = kind;
     M.spin = spin;
     M.mass = mass;
-    M.dx1 = (c->d.xmax[0] - c->d.xmin[0]) / c->N1g;
-    M.dx2 = (c->d.xmax[1] - c->d.xmin[1]) / c->N2g;
+    M.dx1 = (c->d.xmax[0] - c->d.xmin[0]) / (c->N1g << l);
+    M.dx2 = (c->d.xmax[1] - c->d.xmin[1]) / (c->N2g << l);
     M.x1min = c->d.xmin[0] - M.dx1;
     M.x2min = c->d.xmin[1] - M.dx2;
-    M.N1 = c->N1g + 2;
-    M.N2 = c->N2g + 2;
+    M.N1 = (c->N1g << l) + 2;
+    M.N2 = (c->N2g << l) + 2;
     M.axis_lo = M.axis_hi = 0;
     M.rho_floor = c->d.rho_floor;
     M.rho_pow = c->d.rho_floor_pow;
     M.p_floor = c->d.p_floor;
     M.p_pow = c->d.p_floor_pow;
-    M.tab_c = c->te_c;
-    M.tab_f1 = c->te_f1;
-    M.tab_f2 = c->te_f2;
-    M.tab_c32 = c->te_c32;
-    M.tab_f1_32 = c->te_f1_32;
-    M.tab_f2_32 = c->te_f2_32;
+    M.tab_c = c->te_c + c->teo_c[l] * CREC;
+    M.tab_f1 = c->te_f1 + c->teo_f1[l] * FREC;
+    M.tab_f2 = c->te_f2 + c->teo_f2[l] * FREC;
+    M.tab_c32 = c->te_c32 + c->teo_c[l] * CREC;
+    M.tab_f1_32 = c->te_f1_32 + c->teo_f1[l] * FREC;
+    M.tab_f2_32 = c->te_f2_32 + c->teo_f2[l] * FREC;
     if (launch_metric_tables(M, c->st) != cudaSuccess) return BHAC_ERR_CUDA;
   }
   c->metric_ok = true;
@@ -893,8 +978,11 @@ bhac_status bhac_launches_per_step(const bhac_ctx* c, int* out) {
   int per_fill = 1;  // the ghost gather
   for (size_t dep = 1; dep < c->depth_start.size(); ++dep)
     if (c->depth_start[dep] > c->depth_start[dep - 1]) ++per_fill;  // one cross-level node pass per depth
-  const int per_stage = c->ct ? per_fill + 4  // + ring copy, face fluxes, face update, cells
-                             : per_fill + 1 + (c->nrcells > 0 ? 1 : 0);   // + stage kernel (+ reflux)
+  // constrained transport: + ring copy, face fluxes, face update, cells; with
+  // refinement levels + ring means, flux correction, EMFs, EMF correction
+  const int levels = c->ct && c->d.nlevels > 1 ? 1 + (c->nxr > 0) + (c->nef > 0) : 0;
+  const int per_stage = c->ct ? per_fill + 4 + (c->nringm > 0) + levels
+                              : per_fill + 1 + (c->nrcells > 0 ? 1 : 0);  // + stage kernel (+ reflux)
   *out = 2 * per_stage + (c->d.imex && !c->ct ? 1 : 0);  // + the IMEX first-stage pass
   return BHAC_OK;
 }

@@ -23,6 +23,7 @@
 // the discrete divergence sum_d dPhi^d/dx_d of every cell stays at round-off.
 // psi is not evolved (zero), and no cleaning speed enters the fluxes.
 #include <algorithm>
+#include <unordered_map>
 
 #include "ct.h"
 #include "stage_impl.cuh"
@@ -53,6 +54,18 @@ CtGeom ct_geom(const bhac_grid_desc* d) {
   }
   g.nfb = off;
   g.nown_b = own;
+  long long eo = 0;
+  for (int a = 0; a < 3; ++a) {
+    const bool active = d->ndim == 3 || a == 2;
+    long long n = active ? 1 : 0;
+    for (int e = 0; e < 3; ++e) {
+      g.ee[a][e] = e == a ? d->nx[e] : d->nx[e] + (e < d->ndim ? 1 : 0);
+      n *= g.ee[a][e];
+    }
+    g.eoff[a] = eo;
+    eo += n;
+  }
+  g.nEb = eo;
   return g;
 }
 
@@ -116,6 +129,112 @@ bool ct_ring_map(const bhac_grid_desc* desc, const bhac_block_desc* blocks, int 
 
 namespace {
 
+// Leaf blocks by (level, block coordinates).
+struct LeafFinder {
+  std::unordered_map<unsigned long long, int> at;
+  static unsigned long long key(int L, long long x, long long y, long long z) {
+    return ((unsigned long long)L << 60) | ((unsigned long long)z << 40) | ((unsigned long long)y << 20) |
+           (unsigned long long)x;
+  }
+  int get(const bhac_grid_desc* d, int L, const long long bc[3]) const {
+    if (L < 0 || L >= d->nlevels) return -1;
+    for (int e = 0; e < 3; ++e) {
+      const long long n = (long long)d->nroot[e] << (e < d->ndim ? L : 0);
+      if (bc[e] < 0 || bc[e] >= n) return -1;
+    }
+    const auto it = at.find(key(L, bc[0], bc[1], bc[2]));
+    return it == at.end() ? -1 : it->second;
+  }
+};
+
+struct LevelCtx {
+  const bhac_grid_desc* d;
+  const CtGeom* g;
+  LeafFinder leaves;
+  long long ncell(int e, int L) const { return ((long long)d->nroot[e] * d->nx[e]) << (e < d->ndim ? L : 0); }
+  // 0: a level-L leaf holds cell G; -1: a coarser leaf covers it; +1: finer leaves do
+  int cover(int L, const long long G[3]) const {
+    long long bc[3];
+    for (int e = 0; e < 3; ++e) bc[e] = G[e] / d->nx[e];
+    if (leaves.get(d, L, bc) >= 0) return 0;
+    for (int Lc = L - 1; Lc >= 0; --Lc) {
+      for (int e = 0; e < 3; ++e) bc[e] = (e < d->ndim ? G[e] >> (L - Lc) : G[e]) / d->nx[e];
+      if (leaves.get(d, Lc, bc) >= 0) return -1;
+    }
+    return 1;
+  }
+  // Phi indices (ring layout, whole arena) whose mean is face G of direction dd
+  // at level L (a face index along dd, cell indices across, inside the domain):
+  // the face of the level-L leaf above it along dd, else below; the coarse face
+  // it lies on or the two faces of the coarse cell it cuts; the finer faces on
+  // it.  Returns the count (1, 2 or 4), 0 if the levels do not resolve it.
+  int face_sources(int dd, int L, const long long G[3], long long src[4]) const {
+    const long long Nd = ncell(dd, L);
+    long long bc[3];
+    int lf[3];
+    for (int e = 0; e < 3; ++e)
+      if (e != dd) {
+        bc[e] = G[e] / d->nx[e];
+        lf[e] = (int)(G[e] % d->nx[e]);
+      }
+    for (int above = 1; above >= 0; --above) {
+      const long long cell = above ? G[dd] : G[dd] - 1;
+      if (cell < 0 || cell >= Nd) continue;
+      bc[dd] = cell / d->nx[dd];
+      lf[dd] = (int)(G[dd] - bc[dd] * d->nx[dd]);
+      const int b = leaves.get(d, L, bc);
+      if (b >= 0) {
+        src[0] = (long long)b * g->nfb + ring_index_h(*g, dd, lf[0], lf[1], lf[2]);
+        return 1;
+      }
+    }
+    long long cell[3] = {G[0], G[1], G[2]};
+    if (cell[dd] >= Nd) cell[dd] = Nd - 1;
+    const int cov = cover(L, cell);
+    if (cov < 0 && L > 0) {
+      long long H[3], H1[3];
+      for (int e = 0; e < 3; ++e) H[e] = H1[e] = e < d->ndim ? G[e] >> 1 : G[e];
+      if (!(G[dd] & 1)) return face_sources(dd, L - 1, H, src) == 1 ? 1 : 0;
+      H1[dd] += 1;
+      long long s1[4];
+      if (face_sources(dd, L - 1, H, src) != 1 || face_sources(dd, L - 1, H1, s1) != 1) return 0;
+      src[1] = s1[0];
+      return 2;
+    }
+    if (cov <= 0 || L + 1 >= d->nlevels) return 0;
+    int t[2], nt = 0;
+    for (int e = 0; e < d->ndim; ++e)
+      if (e != dd) t[nt++] = e;
+    for (int q = 0; q < (1 << nt); ++q) {
+      long long F[3] = {G[0], G[1], G[2]}, s1[4];
+      F[dd] = 2 * G[dd];
+      for (int u = 0; u < nt; ++u) F[t[u]] = 2 * G[t[u]] + ((q >> u) & 1);
+      if (face_sources(dd, L + 1, F, s1) != 1) return 0;
+      src[q] = s1[0];
+    }
+    return 1 << nt;
+  }
+  // cell q (0..3) around the edge along a at G (level L): across each active
+  // transverse direction below (bit 0) or above (bit 1); periodic wrap; false
+  // where it leaves the domain across another boundary
+  bool edge_cell(int a, int L, const long long G[3], int q, long long C[3], int s[3]) const {
+    int u = 0;
+    for (int e = 0; e < 3; ++e) {
+      C[e] = G[e];
+      s[e] = 0;
+      if (e == a || e >= d->ndim) continue;
+      s[e] = (q >> u++) & 1;
+      C[e] = G[e] - 1 + s[e];
+      const long long N = ncell(e, L);
+      if (C[e] < 0 || C[e] >= N) {
+        if (d->bc[e][C[e] < 0 ? 0 : 1] != BHAC_BC_PERIODIC) return false;
+        C[e] = ((C[e] % N) + N) % N;
+      }
+    }
+    return true;
+  }
+};
+
 __device__ __forceinline__ long long ring_index(const CtGeom& g, int d, int i, int j, int k) {
   return g.foff[d] + ((long long)(k + g.fo[d][2]) * g.fe[d][1] + (j + g.fo[d][1])) * g.fe[d][0] + (i + g.fo[d][0]);
 }
@@ -131,6 +250,45 @@ __global__ void __launch_bounds__(256) ct_ring_kernel(const long long* __restric
     phi[dst[t]] = phi[src[t]];
 }
 
+__global__ void __launch_bounds__(256) ct_ring_mean_kernel(const long long* __restrict__ dst,
+                                                           const long long* __restrict__ src, long long n,
+                                                           double* phi) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    int m = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const long long o = src[4 * t + q];
+      if (o >= 0) {
+        s += phi[o];
+        ++m;
+      }
+    }
+    phi[dst[t]] = s / m;
+  }
+}
+
+// Coarse fluxes on level boundaries: the mean of the finer faces' fluxes, every variable.
+__global__ void __launch_bounds__(256) ct_reflux_kernel(CtArgs c) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < c.nxr;
+       t += (long long)gridDim.x * blockDim.x) {
+    const long long stride = c.g.nfd[c.xr_d[t]];
+    for (int v = 0; v < NV; ++v) {
+      double s = 0.0;
+      int m = 0;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const long long o = c.xr_src[4 * t + q];
+        if (o >= 0) {
+          s += c.xf[o + v * stride];
+          ++m;
+        }
+      }
+      c.xf[c.xr_dst[t] + v * stride] = s / m;
+    }
+  }
+}
+
 __device__ __forceinline__ double to_t(double x, double) { return x; }
 __device__ __forceinline__ float to_t(double x, float) { return narrow_f64(x); }
 
@@ -140,9 +298,11 @@ __device__ __forceinline__ float to_t(double x, float) { return narrow_f64(x); }
 template <typename T, int D, bool FLAT>
 __device__ __forceinline__ void ct_one_face(const StageArgs& a, const CtArgs& c, int b, int i, int j, int k,
                                             long long q) {
+  const int L = a.blk[4 * b];
   const int G1 = a.blk[4 * b + 1] * a.nx + i, G2 = a.blk[4 * b + 2] * a.ny + j;
+  const int N1 = a.N1l[L];
   T F[NV];
-  const bool axis = !FLAT && D == 1 && ((G2 == 0 && c.axis_lo) || (G2 == a.N2g && c.axis_hi));
+  const bool axis = !FLAT && D == 1 && ((G2 == 0 && c.axis_lo) || (G2 == a.N2l[L] && c.axis_hi));
   if (axis) {
 #pragma unroll
     for (int v = 0; v < NV; ++v) F[v] = T(0.0);
@@ -163,7 +323,7 @@ __device__ __forceinline__ void ct_one_face(const StageArgs& a, const CtArgs& c,
     if (FLAT) {
       m = flat_metric<T>();
     } else if (D == 0) {
-      const size_t r = ((size_t)(G2 + 1) * (a.N1g + 3) + (G1 + 1)) * FREC;
+      const size_t r = ((size_t)c.teo_f1[L] + (size_t)(G2 + 1) * (N1 + 3) + (G1 + 1)) * FREC;
       if (sizeof(T) == 8) {
         m = load_face_metric<T>(c.te_f1 + r);
         acg = T(c.te_f1[r + F_ACG]);
@@ -172,7 +332,7 @@ __device__ __forceinline__ void ct_one_face(const StageArgs& a, const CtArgs& c,
         acg = T(c.te_f1_32[r + F_ACG]);
       }
     } else if (D == 1) {
-      const size_t r = ((size_t)(G2 + 1) * (a.N1g + 2) + (G1 + 1)) * FREC;
+      const size_t r = ((size_t)c.teo_f2[L] + (size_t)(G2 + 1) * (N1 + 2) + (G1 + 1)) * FREC;
       if (sizeof(T) == 8) {
         m = load_face_metric<T>(c.te_f2 + r);
         acg = T(c.te_f2[r + F_ACG]);
@@ -181,7 +341,7 @@ __device__ __forceinline__ void ct_one_face(const StageArgs& a, const CtArgs& c,
         acg = T(c.te_f2_32[r + F_ACG]);
       }
     } else {
-      const size_t r = ((size_t)(G2 + 1) * (a.N1g + 2) + (G1 + 1)) * CREC;
+      const size_t r = ((size_t)c.teo_c[L] + (size_t)(G2 + 1) * (N1 + 2) + (G1 + 1)) * CREC;
       if (sizeof(T) == 8) {
         m = load_centre_metric<T>(c.te_c + r);
         acg = T(c.te_c[r + C_ACG3]);
@@ -280,6 +440,71 @@ __global__ void __launch_bounds__(256) ct_face_kernel(StageArgs a, CtArgs c) {
   }
 }
 
+// Every edge EMF of every block into c.emf (grids with refinement levels).
+__global__ void __launch_bounds__(256) ct_emf_kernel(StageArgs a, CtArgs c) {
+  const unsigned n = (unsigned)a.nblocks * (unsigned)c.g.nEb;
+  for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+    const int b = (int)(t / (unsigned)c.g.nEb);
+    const int r = (int)(t - (unsigned)b * (unsigned)c.g.nEb);
+    const int e = r >= c.g.eoff[2] ? 2 : (r >= c.g.eoff[1] ? 1 : 0);
+    const int q = r - (int)c.g.eoff[e];
+    const int i = q % c.g.ee[e][0], j = (q / c.g.ee[e][0]) % c.g.ee[e][1], k = q / (c.g.ee[e][0] * c.g.ee[e][1]);
+    c.emf[t] = e == 0 ? emf1(c, b, i, j, k) : (e == 1 ? emf2(c, b, i, j, k) : emf3(c, b, i, j, k));
+  }
+}
+
+// Edges that a finer leaf touches: the mean of the finer EMFs along them (the
+// finer entries are never corrected themselves, so the order does not matter).
+__global__ void __launch_bounds__(256) ct_emf_fix_kernel(CtArgs c) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < c.nef;
+       t += (long long)gridDim.x * blockDim.x) {
+    const long long s1 = c.ef_src[2 * t + 1];
+    const double e0 = c.emf[c.ef_src[2 * t]];
+    c.emf[c.ef_dst[t]] = s1 >= 0 ? (e0 + c.emf[s1]) / 2.0 : e0;
+  }
+}
+
+__device__ __forceinline__ double emf_at(const CtArgs& c, int b, int e, int i, int j, int k) {
+  return c.emf[(long long)b * c.g.nEb + c.g.eoff[e] + ((long long)k * c.g.ee[e][1] + j) * c.g.ee[e][0] + i];
+}
+
+// d_t Phi = -curl E from the stored (corrected) EMFs with the block's level
+// spacing, and the stage combination, one thread per owned face.
+template <int DIM>
+__global__ void __launch_bounds__(256) ct_face_level_kernel(StageArgs a, CtArgs c) {
+  const double dt = stage_dt(a);
+  const unsigned n = (unsigned)a.nblocks * (unsigned)c.g.nown_b;
+  for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+    const int b = (int)(t / (unsigned)c.g.nown_b);
+    int d, i, j, k;
+    owned_face(c.g, (int)(t - (unsigned)b * (unsigned)c.g.nown_b), d, i, j, k);
+    const long long o = (long long)b * c.g.nfb + ring_index(c.g, d, i, j, k);
+    const int L = a.blk[4 * b];
+    const int G2 = a.blk[4 * b + 2] * a.ny + j;
+    if (!a.flat && d == 1 && ((G2 == 0 && c.axis_lo) || (G2 == a.N2l[L] && c.axis_hi))) {
+      c.phi_out[o] = 0.0;  // sqrt(gamma) = 0 on the axis
+      continue;
+    }
+    const double s = (double)(1 << L);
+    const double ix = a.idx[0] * s, iy = a.idx[1] * s, iz = DIM == 3 ? a.idx[2] * s : a.idx[2];
+    double R;
+    if (d == 0) {
+      R = -(emf_at(c, b, 2, i, j + 1, k) - emf_at(c, b, 2, i, j, k)) * iy;
+      if (DIM == 3) R += (emf_at(c, b, 1, i, j, k + 1) - emf_at(c, b, 1, i, j, k)) * iz;
+    } else if (d == 1) {
+      R = (emf_at(c, b, 2, i + 1, j, k) - emf_at(c, b, 2, i, j, k)) * ix;
+      if (DIM == 3) R -= (emf_at(c, b, 0, i, j, k + 1) - emf_at(c, b, 0, i, j, k)) * iz;
+    } else {
+      R = -(emf_at(c, b, 1, i + 1, j, k) - emf_at(c, b, 1, i, j, k)) * ix +
+          (emf_at(c, b, 0, i, j + 1, k) - emf_at(c, b, 0, i, j, k)) * iy;
+    }
+    if (a.stage == 1)
+      c.phi_out[o] = c.phi_in[o] + dt * R;
+    else
+      c.phi_out[o] = 0.5 * c.phi_n[o] + 0.5 * (c.phi_in[o] + dt * R);
+  }
+}
+
 // Flux divergence, sources, RK combination, the cell field from the updated
 // faces, then the stage kernel's inversion, floors, outputs and CFL rate.  T:
 // the arithmetic of the sources (float in the mixed form, from the FP32
@@ -291,10 +516,10 @@ __global__ void __launch_bounds__(256, 2) ct_cell_kernel(StageArgs a, CtArgs c) 
   if (a.stage == 1 && blockIdx.x == 0 && threadIdx.x == 0) *a.dt_dev = dt;
   unsigned cnt[4] = {0u, 0u, 0u, 0u};
   double rate_max = 0.0;
-  const LevelGeo geo = level_geo(a, 0);
   const unsigned n = (unsigned)a.nblocks * (unsigned)a.nint;
   for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
     const int b = (int)(t / (unsigned)a.nint);
+    const LevelGeo geo = level_geo(a, a.blk[4 * b]);
     const int ci = (int)(t - (unsigned)b * (unsigned)a.nint);
     const int i = ci % a.nx, j = (ci / a.nx) % a.ny, k = ci / (a.nx * a.ny);
     const int cg = ((k + a.gz) * a.Ny + (j + a.gy)) * a.Nx + (i + a.gx);
@@ -306,7 +531,7 @@ __global__ void __launch_bounds__(256, 2) ct_cell_kernel(StageArgs a, CtArgs c) 
     for (int d = 0; d < DIM; ++d) {
       const int ih = i + (d == 0), jh = j + (d == 1), kh = k + (d == 2);
 #pragma unroll
-      for (int v = 0; v < NV; ++v) rhs[v] += -(xf_at(c, b, d, v, ih, jh, kh) - xf_at(c, b, d, v, i, j, k)) * a.idx[d];
+      for (int v = 0; v < NV; ++v) rhs[v] += -(xf_at(c, b, d, v, ih, jh, kh) - xf_at(c, b, d, v, i, j, k)) * geo.idx[d];
     }
     if (!FLAT) {
       const T* crec = (sizeof(T) == 8 ? reinterpret_cast<const T*>(geo.tc) : reinterpret_cast<const T*>(geo.tc32)) +
@@ -354,8 +579,9 @@ __global__ void __launch_bounds__(256) ct_cell_field_kernel(StageArgs a, CtArgs 
     const int cg = ((k + a.gz) * a.Ny + (j + a.gy)) * a.Nx + (i + a.gx);
     double sg = 1.0;
     if (!a.flat) {
+      const int L = a.blk[4 * b];
       const int I1 = a.blk[4 * b + 1] * a.nx + i, I2 = a.blk[4 * b + 2] * a.ny + j;
-      sg = a.tab_c[(size_t)(I2 * a.N1g + I1) * CREC + C_SG];
+      sg = a.tab_c[((size_t)a.toff_c[L] + (size_t)I2 * a.N1l[L] + I1) * CREC + C_SG];
     }
     double* Pc = P + (size_t)b * NV * a.ncell + cg;
 #pragma unroll
@@ -397,9 +623,175 @@ int grid_of(long long n) {
 
 }  // namespace
 
+CtLevelMaps ct_level_maps(const bhac_grid_desc* d, const bhac_block_desc* blocks, int nb, const CtGeom& g) {
+  CtLevelMaps M;
+  M.ok = false;
+  LevelCtx X;
+  X.d = d;
+  X.g = &g;
+  for (int b = 0; b < nb; ++b)
+    X.leaves.at[LeafFinder::key(blocks[b].level, blocks[b].ix, blocks[b].iy, blocks[b].iz)] = b;
+  const int* nx = d->nx;
+  // ring faces: the boundary rules across (at the block's level), then the sources
+  for (int b = 0; b < nb; ++b) {
+    const int L = blocks[b].level;
+    const long long bo[3] = {blocks[b].ix, blocks[b].iy, blocks[b].iz};
+    long long N[3];
+    for (int e = 0; e < 3; ++e) N[e] = X.ncell(e, L);
+    for (int dd = 0; dd < d->ndim; ++dd)
+      for (int k = -g.fo[dd][2]; k < g.fe[dd][2] - g.fo[dd][2]; ++k)
+        for (int j = -g.fo[dd][1]; j < g.fe[dd][1] - g.fo[dd][1]; ++j)
+          for (int i = -g.fo[dd][0]; i < g.fe[dd][0] - g.fo[dd][0]; ++i) {
+            const int f[3] = {i, j, k};
+            bool ring = false;
+            for (int e = 0; e < 3; ++e)
+              if (e != dd && (f[e] < 0 || f[e] >= nx[e])) ring = true;
+            if (!ring) continue;
+            long long G[3];
+            for (int e = 0; e < 3; ++e) G[e] = bo[e] * nx[e] + f[e];
+            for (int e = 0; e < d->ndim; ++e) {
+              if (e == dd) continue;
+              const int side = G[e] < 0 ? 0 : (G[e] >= N[e] ? 1 : -1);
+              if (side < 0) continue;
+              const int kind = d->bc[e][side];
+              if (kind == BHAC_BC_PERIODIC) {
+                G[e] = ((G[e] % N[e]) + N[e]) % N[e];
+              } else if (kind == BHAC_BC_OUTFLOW || kind == BHAC_BC_NOINFLOW) {
+                G[e] = side == 0 ? 0 : N[e] - 1;
+              } else {  // polar axis (x2): mirror, and phi + pi in 3-D
+                G[e] = side == 0 ? -1 - G[e] : 2 * N[e] - 1 - G[e];
+                if (d->ndim == 3) G[2] = ((G[2] + N[2] / 2) % N[2] + N[2]) % N[2];
+              }
+            }
+            if (d->ndim == 3 && dd != 2 && d->bc[2][0] == BHAC_BC_PERIODIC) G[2] = ((G[2] % N[2]) + N[2]) % N[2];
+            for (int e = 0; e < 3; ++e)
+              if (G[e] < 0 || G[e] > N[e] || (e != dd && G[e] == N[e])) return M;
+            long long src[4];
+            const int n = X.face_sources(dd, L, G, src);
+            if (n == 0) return M;
+            const long long dst = (long long)b * g.nfb + ring_index_h(g, dd, i, j, k);
+            if (n == 1) {
+              M.copy_dst.push_back(dst);
+              M.copy_src.push_back(src[0]);
+            } else {
+              M.mean_dst.push_back(dst);
+              for (int q = 0; q < 4; ++q) M.mean_src.push_back(q < n ? src[q] : -1);
+            }
+          }
+  }
+  // coarse fluxes on level boundaries: the mean of the finer ones (the finer
+  // faces in the order: first transverse direction (d + 1) % 3 outer, (d + 2) % 3 inner)
+  auto xf_index = [&](int b, int dd, int i, int j, int k) {
+    return (long long)b * NV * g.nfb + NV * g.foff[dd] + (ring_index_h(g, dd, i, j, k) - g.foff[dd]);
+  };
+  for (int b = 0; b < nb; ++b) {
+    const int L = blocks[b].level;
+    const long long bo[3] = {blocks[b].ix, blocks[b].iy, blocks[b].iz};
+    for (int dd = 0; dd < d->ndim; ++dd)
+      for (int side = 0; side < 2; ++side) {
+        long long nbc[3] = {bo[0], bo[1], bo[2]};
+        nbc[dd] += side == 0 ? -1 : 1;
+        const long long nbd = (long long)d->nroot[dd] << L;
+        if (nbc[dd] < 0 || nbc[dd] >= nbd) {
+          if (d->bc[dd][side] != BHAC_BC_PERIODIC) continue;
+          nbc[dd] = (nbc[dd] + nbd) % nbd;
+        }
+        if (X.leaves.get(d, L, nbc) >= 0) continue;
+        long long chb[3];
+        for (int e = 0; e < 3; ++e) chb[e] = e < d->ndim ? 2 * nbc[e] : nbc[e];
+        if (side == 0) chb[dd] += 1;
+        if (X.leaves.get(d, L + 1, chb) < 0) continue;
+        const int t1 = (dd + 1) % 3, t2 = (dd + 2) % 3;
+        const int fcoarse = side == 0 ? 0 : nx[dd], ffine = side == 0 ? nx[dd] : 0;
+        for (int a = 0; a < nx[t1]; ++a)
+          for (int bb = 0; bb < nx[t2]; ++bb) {
+            long long src[4] = {-1, -1, -1, -1};
+            int cnt = 0;
+            for (int s1 = 0; s1 < (t1 < d->ndim ? 2 : 1); ++s1)
+              for (int s2 = 0; s2 < (t2 < d->ndim ? 2 : 1); ++s2) {
+                const long long gc1 = bo[t1] * nx[t1] + a, gc2 = bo[t2] * nx[t2] + bb;
+                const long long Gf1 = t1 < d->ndim ? 2 * gc1 + s1 : gc1, Gf2 = t2 < d->ndim ? 2 * gc2 + s2 : gc2;
+                long long fb[3];
+                fb[dd] = chb[dd];
+                fb[t1] = Gf1 / nx[t1];
+                fb[t2] = Gf2 / nx[t2];
+                const int bf = X.leaves.get(d, L + 1, fb);
+                if (bf < 0) continue;
+                int li[3];
+                li[dd] = ffine;
+                li[t1] = (int)(Gf1 % nx[t1]);
+                li[t2] = (int)(Gf2 % nx[t2]);
+                src[cnt++] = xf_index(bf, dd, li[0], li[1], li[2]);
+              }
+            if (cnt == 0) continue;
+            int lc[3];
+            lc[dd] = fcoarse;
+            lc[t1] = a;
+            lc[t2] = bb;
+            M.xr_dst.push_back(xf_index(b, dd, lc[0], lc[1], lc[2]));
+            for (int q = 0; q < 4; ++q) M.xr_src.push_back(src[q]);
+            M.xr_d.push_back(dd);
+          }
+      }
+  }
+  // EMFs of edges that a finer leaf touches: the mean of the finer EMFs along them
+  for (int b = 0; b < nb; ++b) {
+    const int L = blocks[b].level;
+    const long long bo[3] = {blocks[b].ix, blocks[b].iy, blocks[b].iz};
+    for (int a = 0; a < 3; ++a) {
+      if (!(d->ndim == 3 || a == 2)) continue;
+      const int* ee = g.ee[a];
+      for (int k = 0; k < ee[2]; ++k)
+        for (int j = 0; j < ee[1]; ++j)
+          for (int i = 0; i < ee[0]; ++i) {
+            const int loc[3] = {i, j, k};
+            long long G[3], C[3];
+            int sgn[3];
+            for (int e = 0; e < 3; ++e) G[e] = bo[e] * nx[e] + loc[e];
+            bool finer = false;
+            for (int q = 0; q < 4 && !finer; ++q)
+              if (X.edge_cell(a, L, G, q, C, sgn) && X.cover(L, C) > 0) finer = true;
+            if (!finer || L + 1 >= d->nlevels) continue;
+            const int na = a < d->ndim ? 2 : 1;
+            long long src[2] = {-1, -1};
+            int n = 0;
+            for (int t = 0; t < na; ++t) {
+              long long F[3];
+              for (int e = 0; e < 3; ++e) F[e] = e >= d->ndim ? G[e] : 2 * G[e] + (e == a ? t : 0);
+              for (int q = 0; q < 4; ++q) {
+                if (!X.edge_cell(a, L + 1, F, q, C, sgn)) continue;
+                long long bc[3];
+                for (int e = 0; e < 3; ++e) bc[e] = C[e] / nx[e];
+                const int bf = X.leaves.get(d, L + 1, bc);
+                if (bf < 0) continue;
+                int lf[3];
+                for (int e = 0; e < 3; ++e)
+                  lf[e] = (int)(C[e] - bc[e] * nx[e]) + (e != a && e < d->ndim && !sgn[e] ? 1 : 0);
+                src[n++] = (long long)bf * g.nEb + g.eoff[a] + ((long long)lf[2] * g.ee[a][1] + lf[1]) * g.ee[a][0] + lf[0];
+                break;
+              }
+            }
+            if (n != na) continue;
+            M.ef_dst.push_back((long long)b * g.nEb + g.eoff[a] + ((long long)k * ee[1] + j) * ee[0] + i);
+            M.ef_src.push_back(src[0]);
+            M.ef_src.push_back(src[1]);
+          }
+    }
+  }
+  M.ok = true;
+  return M;
+}
+
 cudaError_t launch_ct_ring(const long long* dst, const long long* src, long long n, double* phi, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   ct_ring_kernel<<<grid_of(n), 256, 0, st>>>(dst, src, n, phi);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ct_ring_mean(const long long* dst, const long long* src, long long n, double* phi,
+                                cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  ct_ring_mean_kernel<<<grid_of(n), 256, 0, st>>>(dst, src, n, phi);
   return cudaGetLastError();
 }
 
@@ -419,10 +811,21 @@ cudaError_t launch_ct_stage(const StageArgs& a, const CtArgs& c, bool mixed, cud
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  if (a.ndim == 3)
+  if (c.amr) {
+    // refinement levels: coarse fluxes corrected, every EMF stored and the
+    // touched coarse ones corrected, then the face update from them
+    if (c.nxr > 0) ct_reflux_kernel<<<grid_of(c.nxr), 256, 0, st>>>(c);
+    ct_emf_kernel<<<grid_of((long long)a.nblocks * c.g.nEb), 256, 0, st>>>(a, c);
+    if (c.nef > 0) ct_emf_fix_kernel<<<grid_of(c.nef), 256, 0, st>>>(c);
+    if (a.ndim == 3)
+      ct_face_level_kernel<3><<<grid_of(no), 256, 0, st>>>(a, c);
+    else
+      ct_face_level_kernel<2><<<grid_of(no), 256, 0, st>>>(a, c);
+  } else if (a.ndim == 3) {
     ct_face_kernel<3><<<grid_of(no), 256, 0, st>>>(a, c);
-  else
+  } else {
     ct_face_kernel<2><<<grid_of(no), 256, 0, st>>>(a, c);
+  }
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (mixed) {

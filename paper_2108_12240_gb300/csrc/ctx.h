@@ -61,10 +61,12 @@ struct bhac_ctx {
   bhac::RefluxCell* d_rcells;
   bhac::RefluxTerm* d_rterms;
   int nrcells;
-  // constrained transport (uniform grids, FP64): face fields in ring layout
-  // (two buffers, pcur the current state's), ring-extended face fluxes, the
-  // metric records on the grid extended by one cell in x1 and x2, and the
-  // ring-face copy map
+  // constrained transport: face fields in ring layout (two buffers, pcur the
+  // current state's), ring-extended face fluxes, the metric records of every
+  // level on its grid extended by one cell in x1 and x2 (teo_*: each level's
+  // first record), and the ring-face maps (copies; means of 2 or 4 faces
+  // across levels); with refinement levels also the edge EMFs and the maps of
+  // the coarse-fine flux and EMF corrections
   bool ct, faces_ok;
   bhac::CtGeom ctg;
   double* phi[2];
@@ -72,8 +74,13 @@ struct bhac_ctx {
   double* xf;
   double *te_c, *te_f1, *te_f2;
   float *te_c32, *te_f1_32, *te_f2_32;
-  long long *ring_dst, *ring_src;
-  long long nring;
+  long long teo_c[bhac::MAXLEV], teo_f1[bhac::MAXLEV], teo_f2[bhac::MAXLEV];
+  long long *ring_dst, *ring_src, *ringm_dst, *ringm_src;
+  long long nring, nringm;
+  double* emf;
+  long long *xr_dst, *xr_src, *ef_dst, *ef_src;
+  int* xr_d;
+  long long nxr, nef;
   // split form: chunks of items, the face kernel on st and the cell kernel on
   // st2, chunk by chunk; R holds the stage right-hand side
   int split;

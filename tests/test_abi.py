@@ -4,6 +4,7 @@ invalid descriptions."""
 import os
 import re
 
+import numpy as np
 import pytest
 
 import paper_2108_12240_gb300 as gb
@@ -79,8 +80,11 @@ def test_empty_and_inconsistent_block_lists_are_rejected():
 
 def test_constrained_transport_descriptors():
     """Constrained transport adds the face fields, the ring-extended fluxes and
-    the ring map to the arena, in either form; it is limited to uniform grids
-    (AMR grids are rejected before any device work)."""
+    the ring map to the arena, in either form; with refinement levels also the
+    edge EMFs and the correction maps.  Its level maps need neighbouring
+    leaves (across faces, edges and corners) to differ by at most one level:
+    a grid that breaks that is rejected before any device work, although the
+    cleaning form accepts it."""
     g = pb.periodic_box(ndim=3, nblock=8, nroot=2)
     n_glm = gb.bhac_query_sizes(gb.desc_of(g), gb.blocks_of(g))
     n_ct = gb.bhac_query_sizes(gb.desc_of(g.with_(divb="ct")), gb.blocks_of(g))
@@ -88,9 +92,17 @@ def test_constrained_transport_descriptors():
     assert n_ct >= n_glm + 8 * faces * (2 + 9)
     n_ct_mixed = gb.bhac_query_sizes(gb.desc_of(g.with_(divb="ct"), "mixed"), gb.blocks_of(g))
     assert n_ct_mixed >= gb.bhac_query_sizes(gb.desc_of(g, "mixed"), gb.blocks_of(g)) + 8 * faces * (2 + 9)
-    amr = pb.amr_torus(root=(4, 2, 2), nblock=8).with_(divb="ct")
+    amr = pb.amr_torus(root=(4, 2, 2), nblock=8)
+    n_amr = gb.bhac_query_sizes(gb.desc_of(amr), gb.blocks_of(amr))
+    edges = amr.nb * 3 * 8 * 9 * 9
+    assert gb.bhac_query_sizes(gb.desc_of(amr.with_(divb="ct")), gb.blocks_of(amr)) >= n_amr + 8 * (
+        amr.nb * 3 * 9 * 10 * 10 * (2 + 9) + edges)
+    blocks = [(0, 1, 0, 0), (0, 0, 1, 0), (0, 1, 1, 0), (1, 0, 0, 0), (1, 1, 0, 0), (1, 0, 1, 0),
+              (2, 2, 2, 0), (2, 3, 2, 0), (2, 2, 3, 0), (2, 3, 3, 0)]  # level 2 next to level 0
+    jump = pb.periodic_box(ndim=2, nblock=8, nroot=2).with_(nlevels=3, blocks=np.asarray(blocks, dtype=np.int32))
+    assert gb.bhac_query_sizes(gb.desc_of(jump), gb.blocks_of(jump)) > 0
     with pytest.raises(gb.BhacError) as e:
-        gb.bhac_query_sizes(gb.desc_of(amr), gb.blocks_of(amr))
+        gb.bhac_query_sizes(gb.desc_of(jump.with_(divb="ct")), gb.blocks_of(jump))
     assert e.value.status == 1
 
 

@@ -6,7 +6,9 @@ several steps from the same seeded input: conserved variables within 1e-12
 largest face field; the GPU's faces keep every cell's discrete divergence at
 round-off.  Grids: periodic boxes in 2-D and 3-D with a random divergence-free
 field, the shock tube, and the torus in modified Kerr-Schild coordinates with
-the polar axis (2-D and 3-D)."""
+the polar axis (2-D and 3-D); across refinement levels two-level periodic
+boxes (2-D, 3-D) and the three-level torus, where the coarse faces on level
+boundaries also stay the mean of the finer faces covering them."""
 import numpy as np
 import pytest
 
@@ -41,6 +43,14 @@ def _case(name):
         g = pb.torus_2d(nblock=16, nroot=(6, 4)).with_(divb="ct")
         P = pb.fm_torus_prims(g)
         return g, P, ct.fm_torus_faces(g, P)
+    if name in ("amr_box2d", "amr_box3d"):
+        from tests.test_oracle_ct_amr import _amr_field, _box
+        g = _box(2 if name == "amr_box2d" else 3)
+        return g, pb.random_periodic_prims(g, jump=True), _amr_field(g)
+    if name == "amr_torus":
+        g = pb.amr_torus(root=(4, 2, 2), nblock=8).with_(divb="ct")
+        P = pb.fm_torus_prims(g)
+        return g, P, ct.fm_torus_faces(g, P)
     g = pb.torus_3d(nroot=(4, 3, 2)).with_(divb="ct")
     P = pb.fm_torus_prims(g)
     return g, P, ct.fm_torus_faces(g, P)
@@ -50,7 +60,13 @@ def _faces(g, F):
     return ct.random_potential_faces(g) if F is None else F
 
 
-@pytest.mark.parametrize("name", ["box2d", "box3d", "shock_tube", "torus2d", "torus3d"])
+def _dxmin(g):
+    """The finest cell width of the grid."""
+    return min((g.xmax[d] - g.xmin[d]) / (g.nroot[d] * g.nx[d]) for d in range(g.ndim)) / 2 ** (g.nlevels - 1)
+
+
+@pytest.mark.parametrize("name", ["box2d", "box3d", "shock_tube", "torus2d", "torus3d", "amr_box2d", "amr_box3d",
+                                  "amr_torus"])
 def test_ct_matches_oracle(gb, name):
     from tests.test_gpu_parity import energy_scaled
     g, P, F = _case(name)
@@ -76,15 +92,17 @@ def test_ct_matches_oracle(gb, name):
         scale = np.abs(fo).max()
         assert np.abs(fg - fo).max() <= TOL64 * scale, (step, np.abs(fg - fo).max() / scale)
         div = np.abs(ct.face_divergence(g, fg)).max()
-        dxmin = min((g.xmax[d] - g.xmin[d]) / (g.nroot[d] * g.nx[d]) for d in range(g.ndim))
-        assert div <= 1e-12 * scale / dxmin, div
+        assert div <= 1e-12 * scale / _dxmin(g), div
+        if g.nlevels > 1:
+            assert ct.level_face_mismatch(g, fg) <= 1e-13 * scale
     print(f"CT {name}: energy-scaled error per conserved variable after 3 steps {err.tolist()}")
 
 
-def test_ct_device_dt_and_graph_replay_are_bitwise_identical(gb):
+@pytest.mark.parametrize("name", ["torus2d", "amr_torus"])
+def test_ct_device_dt_and_graph_replay_are_bitwise_identical(gb, name):
     """Steps with the device time step, direct and replayed from a CUDA graph,
     give the same bits; the face buffers' roles return after every step."""
-    g, P, F = _case("torus2d")
+    g, P, F = _case(name)
     outs = []
     for mode in ("direct", "graph"):
         import torch
@@ -106,9 +124,10 @@ def test_ct_device_dt_and_graph_replay_are_bitwise_identical(gb):
     assert np.array_equal(outs[0][1], outs[1][1])
 
 
-def test_ct_keeps_the_divergence_at_round_off_over_many_steps(gb):
-    g, P, _ = _case("box3d")
-    F = ct.random_potential_faces(g)
+@pytest.mark.parametrize("name", ["box3d", "amr_box3d"])
+def test_ct_keeps_the_divergence_at_round_off_over_many_steps(gb, name):
+    g, P, F = _case(name)
+    F = _faces(g, F)
     s = gb.Solver(g)
     s.set_prims(P)
     s.set_faces(F)
@@ -117,14 +136,17 @@ def test_ct_keeps_the_divergence_at_round_off_over_many_steps(gb):
         s.step(0.0)
     fg = s.faces()
     assert np.abs(fg - F).max() > 0.1 * np.abs(F).max()
-    assert np.abs(ct.face_divergence(g, fg)).max() <= 1e-12 * np.abs(fg).max() * 16
+    assert np.abs(ct.face_divergence(g, fg)).max() <= 1e-12 * np.abs(fg).max() / _dxmin(g)
     assert np.all(s.prims()[:, 8] == 0.0)
+    if g.nlevels > 1:
+        assert ct.level_face_mismatch(g, fg) <= 1e-13 * np.abs(fg).max()
+        for d in range(g.ndim):
+            assert np.allclose(ct.plane_fluxes(g, fg, d), ct.plane_fluxes(g, F, d), rtol=0, atol=1e-12)
 
 
 def test_ct_call_order_and_forms(gb):
     """A step before the faces are loaded, and face calls on a cleaning-form
-    grid, are call-order errors; AMR grids with constrained transport are
-    rejected at init."""
+    grid, are call-order errors."""
     g, P, F = _case("box2d")
     s = gb.Solver(g)
     s.set_prims(P)
@@ -138,7 +160,7 @@ def test_ct_call_order_and_forms(gb):
     assert e.value.status == 4
 
 
-@pytest.mark.parametrize("name", ["box2d", "box3d", "torus2d", "torus3d"])
+@pytest.mark.parametrize("name", ["box2d", "box3d", "torus2d", "torus3d", "amr_box3d", "amr_torus"])
 def test_ct_mixed_form_matches_oracle(gb, name):
     """The mixed form of constrained transport (FP32 face states and fluxes,
     FP64 EMFs, face update and face field) against the FP64 oracle: after one
@@ -165,6 +187,7 @@ def test_ct_mixed_form_matches_oracle(gb, name):
     for _ in range(2):
         s.step(0.0)
     fg = s.faces()
-    dxmin = min((g.xmax[d] - g.xmin[d]) / (g.nroot[d] * g.nx[d]) for d in range(g.ndim))
-    assert np.abs(ct.face_divergence(g, fg)).max() <= 1e-12 * np.abs(fg).max() / dxmin
+    assert np.abs(ct.face_divergence(g, fg)).max() <= 1e-12 * np.abs(fg).max() / _dxmin(g)
+    if g.nlevels > 1:
+        assert ct.level_face_mismatch(g, fg) <= 1e-13 * np.abs(fg).max()
     print(f"CT mixed {name}: energy-scaled error per conserved variable after a step {err.tolist()}")
