@@ -702,7 +702,7 @@ def main():
     stream = torch.cuda.Stream()
     forms = ["mixed", "fp64"] if args.form == "both" else [args.form]
     ct_faces = None
-    if args.form == "both" and not args.no_ct and g.nlevels == 1 and g.coords == "mks":
+    if args.form == "both" and not args.no_ct and g.coords == "mks":
         # constrained transport beside the cleaning forms: the same torus with
         # its loop field as face fields, both forms
         from problems import ct as pct

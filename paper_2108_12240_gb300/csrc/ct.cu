@@ -745,6 +745,10 @@ CtLevelMaps ct_level_maps(const bhac_grid_desc* d, const bhac_block_desc* blocks
         for (int j = 0; j < ee[1]; ++j)
           for (int i = 0; i < ee[0]; ++i) {
             const int loc[3] = {i, j, k};
+            bool inner = true;  // all four cells around the edge are the block's own
+            for (int e = 0; e < d->ndim; ++e)
+              if (e != a && (loc[e] == 0 || loc[e] == nx[e])) inner = false;
+            if (inner) continue;
             long long G[3], C[3];
             int sgn[3];
             for (int e = 0; e < 3; ++e) G[e] = bo[e] * nx[e] + loc[e];
