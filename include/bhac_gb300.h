@@ -84,8 +84,10 @@ typedef struct {
                             W <= w_max; r = 1 in Cartesian coordinates */
   int divb;              /* BHAC_DIVB_GLM: GLM cleaning (psi evolved with ch, kappa);
                             BHAC_DIVB_CT: staggered-mesh constrained transport of face
-                            fields (uniform grids, nlevels = 1; psi stays 0, ch and
-                            kappa are ignored).  In the mixed form the face states and
+                            fields (psi stays 0, ch and kappa are ignored; with
+                            refinement levels, leaves touching across a face, edge or
+                            corner must differ by at most one level, else
+                            BHAC_ERR_ARG).  In the mixed form the face states and
                             fluxes are FP32; the EMFs, the face update and the face
                             field stay FP64, so div B stays at FP64 round-off */
   int imex;              /* 0: the cleaning damping -alpha kappa psi is an explicit source
@@ -219,7 +221,18 @@ bhac_status bhac_get_cons(bhac_ctx* ctx, double* out, int on_device);
  * (sqrt(gamma) B^d = (Phi^d_low + Phi^d_high) / 2), sets psi = 0 and recomputes
  * the conserved state; a step before it returns BHAC_ERR_STATE.
  * bhac_get_faces reads them back in the same layout.  BHAC_ERR_STATE for a
- * grid in the cleaning form. */
+ * grid in the cleaning form.
+ *
+ * Across refinement levels (Sec. 2 pairs the scheme with block-based tree
+ * AMR; the transfer rules are the hot-path reading): a face one cell outside a
+ * block takes the face of the leaf at the block's level, else the coarser face
+ * it lies on or the mean of the two faces of the coarser cell it cuts, else
+ * the mean of the finer faces on it; the coarse flux through a face on a level
+ * boundary is the mean of the finer fluxes; an edge that a finer leaf touches
+ * takes the mean of the finer EMFs along it.  A coarse face on a level boundary
+ * then changes by the mean of the changes of the finer faces covering it, so a
+ * loaded state whose coarse faces there are the mean of the finer ones keeps
+ * that to round-off, with every cell's divergence. */
 bhac_status bhac_set_faces(bhac_ctx* ctx, const double* faces, int on_device);
 bhac_status bhac_get_faces(bhac_ctx* ctx, double* faces, int on_device);
 
@@ -320,8 +333,10 @@ bhac_status bhac_get_diagnostics(bhac_ctx* ctx, long long counts[4]);
 /* Kernel launches one bhac_step makes on the context's stream: per stage one
  * cross-level node pass per dependency depth (AMR grids), the ghost gather,
  * the stage kernel and, where levels meet, the reflux kernel; with constrained
- * transport the ghost gather, the ring-face copy, the face-flux, face-update
- * and cell kernels; with IMEX one more pass before stage 1. */
+ * transport the ghost gather (and node passes), the ring-face copy, the
+ * face-flux, face-update and cell kernels, and with refinement levels also
+ * the ring-face means, the coarse-fine flux correction, the edge EMFs and
+ * their correction; with IMEX one more pass before stage 1. */
 bhac_status bhac_launches_per_step(const bhac_ctx* ctx, int* launches);
 
 /* Kernel launch shape of the stage kernel: tile of tx x ty cells per CTA column

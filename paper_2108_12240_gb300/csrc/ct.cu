@@ -1,5 +1,5 @@
 // Staggered-mesh constrained transport (the div B control of the method's
-// Sec. 2) on uniform grids, in the FP64 form or the mixed form (T = float: the
+// Sec. 2), in the FP64 form or the mixed form (T = float: the
 // face states and fluxes in FP32 from the FP32 primitives, the fluxes stored,
 // the EMFs, the face update and the face field in FP64, so the discrete
 // divergence stays at FP64 round-off; the cell sources in FP32 and the
@@ -21,6 +21,13 @@
 // Both blocks sharing a face compute its update from identical inputs (their
 // ghost cells and ring faces hold the same values), so their copies agree and
 // the discrete divergence sum_d dPhi^d/dx_d of every cell stays at round-off.
+// Across refinement levels a ring face is a copy, or the mean of the two faces
+// of the coarser cell it cuts, or of the finer faces on it; after the fluxes,
+// a coarse face on a level boundary takes the mean of the finer fluxes, every
+// edge EMF is stored, and an edge that a finer leaf touches takes the mean of
+// the finer EMFs along it before the face update (host-built maps), so the
+// coarse copy of a level-boundary face changes by the mean of the changes of
+// the finer faces covering it.
 // psi is not evolved (zero), and no cleaning speed enters the fluxes.
 #include <algorithm>
 #include <unordered_map>
