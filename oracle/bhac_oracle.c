@@ -1989,10 +1989,240 @@ int or_regrid_plan(const or_params* p, int nb, const int* blocks, const double* 
 
 /* Conservative transfer of the densitized state to a new leaf list, then the
  * inversion of every new cell. */
+/* ---- regridding with constrained transport: the face fields ---- */
+
+/* Phi^d of face F (level-L global index, a face index along d) held by an old
+ * level-L leaf: the block above it along d, else the one below, after the
+ * periodic wrap along d; 0 if no old level-L leaf holds it. */
+static int rg_old_face(const or_ctx* old, int d, int L, const long Fin[3], double* out) {
+  const int* nx = old->p.nx;
+  long F[3] = {Fin[0], Fin[1], Fin[2]};
+  const long Nd = ncell_l(old, d, L);
+  for (int above = 1; above >= 0; --above) {
+    long cell = above ? F[d] : F[d] - 1;
+    if (cell < 0 || cell >= Nd) {
+      if (old->p.bc[d][cell < 0 ? 0 : 1] != OR_BC_PERIODIC) continue;
+      cell = ((cell % Nd) + Nd) % Nd;
+    }
+    long bc[3];
+    int lf[3];
+    for (int e = 0; e < 3; ++e) {
+      long g = e == d ? cell : F[e];
+      bc[e] = g / nx[e];
+      lf[e] = (int)(g - bc[e] * nx[e]);
+    }
+    lf[d] += above ? 0 : 1;
+    int b = lut_get(old, L, bc);
+    if (b >= 0) {
+      *out = old->fc[d][fcx(old, d, b, lf[0], lf[1], lf[2])];
+      return 1;
+    }
+  }
+  return 0;
+}
+
+/* Solves the symmetric system M y = r (n unknowns, M positive semi-definite
+ * with the constants as its null space) with y_0 = 0, by Gaussian elimination
+ * on the remaining n - 1 equations. */
+static void rg_solve_fixed0(int n, double M[8][8], const double r[8], double y[8]) {
+  double a[8][9];
+  for (int i = 1; i < n; ++i) {
+    for (int j = 1; j < n; ++j) a[i - 1][j - 1] = M[i][j];
+    a[i - 1][n - 1] = r[i];
+  }
+  const int m = n - 1;
+  for (int col = 0; col < m; ++col) {
+    int piv = col;
+    for (int i = col + 1; i < m; ++i)
+      if (fabs(a[i][col]) > fabs(a[piv][col])) piv = i;
+    for (int j = 0; j <= m; ++j) {
+      double t = a[col][j];
+      a[col][j] = a[piv][j];
+      a[piv][j] = t;
+    }
+    for (int i = col + 1; i < m; ++i) {
+      double f = a[i][col] / a[col][col];
+      for (int j = col; j <= m; ++j) a[i][j] -= f * a[col][j];
+    }
+  }
+  y[0] = 0.0;
+  for (int i = m - 1; i >= 0; --i) {
+    double t = a[i][m];
+    for (int j = i + 1; j < m; ++j) t -= a[i][j] * y[j + 1];
+    y[i + 1] = t / a[i][i];
+  }
+}
+
+/* The face fields of new block b (level L) of c from the old grid (kind 0:
+ * kept as old block ob, 1: refined from old parent ob, 2: coarsened from its
+ * old children):
+ *  - kept: a copy;
+ *  - otherwise a face on the block's boundary held by an old leaf of level L
+ *    across it takes that leaf's value (the same face before the regrid);
+ *  - coarsened: the mean of the 2^(ndim-1) old finer faces on each face;
+ *  - refined, faces on the planes of the parent's faces: the parent face plus
+ *    +-1/4 of its minmod-limited differences to the neighbouring parent faces
+ *    across (within the parent block; at its edge the one difference there
+ *    is), so the finer faces keep the parent face's flux;
+ *  - refined, faces inside a parent cell: first the mean of the two outer
+ *    finer faces of that cell at the same position across, then the change of
+ *    least Euclidean norm that makes all 2^ndim finer cells of the parent cell
+ *    divergence-free (the outer faces already carry the parent cell's
+ *    divergence, zero). */
+static void rg_transfer_faces(const or_ctx* old, or_ctx* c, int b, int kind, int ob) {
+  const int* nx = c->p.nx;
+  const int nd = c->p.ndim;
+  const int L = c->blk[4 * b];
+  const long bo[3] = {c->blk[4 * b + 1], c->blk[4 * b + 2], c->blk[4 * b + 3]};
+  for (int d = 0; d < nd; ++d) {
+    int n[3] = {nx[0], nx[1], nx[2]};
+    n[d] += 1;
+    for (int k = 0; k < n[2]; ++k)
+      for (int j = 0; j < n[1]; ++j)
+        for (int i = 0; i < n[0]; ++i) {
+          const int f[3] = {i, j, k};
+          double *dst = &c->fc[d][fcx(c, d, b, i, j, k)], v;
+          if (kind == 0) {
+            *dst = old->fc[d][fcx(old, d, ob, i, j, k)];
+            continue;
+          }
+          long G[3];
+          for (int e = 0; e < 3; ++e) G[e] = bo[e] * nx[e] + f[e];
+          if ((f[d] == 0 || f[d] == nx[d]) && rg_old_face(old, d, L, G, &v)) {
+            *dst = v;
+            continue;
+          }
+          if (kind == 2) {
+            int t[2], nt = 0;
+            for (int e = 0; e < nd; ++e)
+              if (e != d) t[nt++] = e;
+            double sum = 0.0;
+            for (int q = 0; q < (1 << nt); ++q) {
+              long F[3] = {G[0], G[1], G[2]};
+              F[d] = 2 * G[d];
+              for (int u = 0; u < nt; ++u) F[t[u]] = 2 * G[t[u]] + ((q >> u) & 1);
+              double w = 0.0;
+              rg_old_face(old, d, L + 1, F, &w);
+              sum += w;
+            }
+            *dst = sum / (1 << nt);
+            continue;
+          }
+          if (G[d] & 1) continue; /* inside a parent cell: below */
+          int pl[3];
+          for (int e = 0; e < 3; ++e) pl[e] = (int)((e < nd ? G[e] >> 1 : G[e]) - (e < nd ? bo[e] >> 1 : bo[e]) * nx[e]);
+          const double Pc = old->fc[d][fcx(old, d, ob, pl[0], pl[1], pl[2])];
+          double val = Pc;
+          for (int e = 0; e < nd; ++e) {
+            if (e == d) continue;
+            int lo[3] = {pl[0], pl[1], pl[2]}, hi[3] = {pl[0], pl[1], pl[2]};
+            lo[e] -= 1;
+            hi[e] += 1;
+            double dl = 0.0, dh = 0.0;
+            int hl = pl[e] > 0, hh = pl[e] < nx[e] - 1;
+            if (hl) dl = Pc - old->fc[d][fcx(old, d, ob, lo[0], lo[1], lo[2])];
+            if (hh) dh = old->fc[d][fcx(old, d, ob, hi[0], hi[1], hi[2])] - Pc;
+            double slope = hl && hh ? minmod(dl, dh) : (hl ? dl : dh);
+            val += ((G[e] & 1) ? 0.25 : -0.25) * slope;
+          }
+          *dst = val;
+        }
+  }
+  if (kind != 1) return;
+  /* faces inside the parent cells */
+  double h[3];
+  for (int d = 0; d < 3; ++d) h[d] = dxl(c, d, L);
+  const int ncell = 1 << nd;
+  int ca[3] = {1, 1, 1};
+  for (int d = 0; d < nd; ++d) ca[d] = nx[d] / 2;
+  for (int pk = 0; pk < ca[2]; ++pk)
+    for (int pj = 0; pj < ca[1]; ++pj)
+      for (int pi = 0; pi < ca[0]; ++pi) {
+        const int base[3] = {2 * pi, 2 * pj, nd == 3 ? 2 * pk : 0};
+        /* unknowns: for each d, the faces at base_d + 1 of the cells a with a_d = 0 */
+        int nu = 0, ud[12], ua[12];
+        for (int d = 0; d < nd; ++d)
+          for (int a = 0; a < ncell; ++a)
+            if (!((a >> d) & 1)) {
+              ud[nu] = d;
+              ua[nu] = a;
+              ++nu;
+            }
+        double x0[12], A[8][12], r[8];
+        for (int q = 0; q < nu; ++q) {
+          const int d = ud[q], a = ua[q];
+          int lo[3], hi[3];
+          for (int e = 0; e < 3; ++e) lo[e] = hi[e] = base[e] + (e < nd ? (a >> e) & 1 : 0);
+          hi[d] = base[d] + 2; /* the outer high face of the cell above */
+          lo[d] = base[d];     /* the outer low face of the cell below */
+          x0[q] = 0.5 * (c->fc[d][fcx(c, d, b, lo[0], lo[1], lo[2])] + c->fc[d][fcx(c, d, b, hi[0], hi[1], hi[2])]);
+        }
+        for (int a = 0; a < ncell; ++a) {
+          for (int q = 0; q < nu; ++q) A[a][q] = 0.0;
+          r[a] = 0.0;
+        }
+        /* divergence of each finer cell with the first values */
+        for (int a = 0; a < ncell; ++a)
+          for (int d = 0; d < nd; ++d) {
+            int cl[3];
+            for (int e = 0; e < 3; ++e) cl[e] = base[e] + (e < nd ? (a >> e) & 1 : 0);
+            double lo, hi;
+            if (!((a >> d) & 1)) {
+              int lf[3] = {cl[0], cl[1], cl[2]};
+              lo = c->fc[d][fcx(c, d, b, lf[0], lf[1], lf[2])];
+              int q = 0;
+              while (!(ud[q] == d && ua[q] == a)) ++q;
+              hi = x0[q];
+              A[a][q] += 1.0 / h[d];
+            } else {
+              int hf[3] = {cl[0], cl[1], cl[2]};
+              hf[d] += 1;
+              hi = c->fc[d][fcx(c, d, b, hf[0], hf[1], hf[2])];
+              int q = 0;
+              while (!(ud[q] == d && ua[q] == (a & ~(1 << d)))) ++q;
+              lo = x0[q];
+              A[a][q] -= 1.0 / h[d];
+            }
+            r[a] += (hi - lo) / h[d];
+          }
+        /* least-norm change dx with A dx = -r: dx = -A^T y, (A A^T) y = r */
+        double M[8][8], y[8];
+        for (int p = 0; p < ncell; ++p)
+          for (int q = 0; q < ncell; ++q) {
+            M[p][q] = 0.0;
+            for (int u = 0; u < nu; ++u) M[p][q] += A[p][u] * A[q][u];
+          }
+        rg_solve_fixed0(ncell, M, r, y);
+        for (int q = 0; q < nu; ++q) {
+          double at_y = 0.0;
+          for (int a = 0; a < ncell; ++a) at_y += A[a][q] * y[a];
+          const int d = ud[q], a = ua[q];
+          int fl[3];
+          for (int e = 0; e < 3; ++e) fl[e] = base[e] + (e < nd ? (a >> e) & 1 : 0);
+          fl[d] = base[d] + 1;
+          c->fc[d][fcx(c, d, b, fl[0], fl[1], fl[2])] = x0[q] - at_y;
+        }
+      }
+}
+
 void or_regrid_transfer(const or_ctx* old, or_ctx* c) {
   const int* nx = c->p.nx;
   const int nd = c->p.ndim, nch = 1 << nd;
   long long cnt[4] = {0, 0, 0, 0};
+  if (c->p.ct) {
+    /* constrained transport: the face fields first (the cells' field is their mean) */
+    for (int b = 0; b < c->nb; ++b) {
+      int L = c->blk[4 * b];
+      long bc[3] = {c->blk[4 * b + 1], c->blk[4 * b + 2], c->blk[4 * b + 3]}, pb[3];
+      for (int k = 0; k < 3; ++k) pb[k] = k < nd ? bc[k] >> 1 : bc[k];
+      int ob = lut_get(old, L, bc), kind = 0;
+      if (ob < 0) {
+        ob = L > 0 ? lut_get(old, L - 1, pb) : -1;
+        kind = ob >= 0 ? 1 : 2;
+      }
+      rg_transfer_faces(old, c, b, kind, ob);
+    }
+  }
   for (int b = 0; b < c->nb; ++b) {
     int L = c->blk[4 * b];
     long bc[3] = {c->blk[4 * b + 1], c->blk[4 * b + 2], c->blk[4 * b + 3]};
@@ -2061,6 +2291,14 @@ void or_regrid_transfer(const or_ctx* old, or_ctx* c) {
               U[v] /= nch;
               Pg[v] /= nch;
             }
+          }
+          if (c->p.ct) {
+            for (int d = 0; d < nd; ++d) {
+              int hi[3] = {i, j, k};
+              hi[d] += 1;
+              U[OR_B1 + d] = 0.5 * (c->fc[d][fcx(c, d, b, i, j, k)] + c->fc[d][fcx(c, d, b, hi[0], hi[1], hi[2])]);
+            }
+            U[OR_PSI] = 0.0;
           }
           double x[3], Uu[OR_NV], Pn[OR_NV];
           or_metric m;

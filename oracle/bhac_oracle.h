@@ -151,7 +151,13 @@ void or_ct_ring_faces(or_ctx* c, int d, double* out);
  * minmod-limited slopes times +-1/4, slopes within the parent block only),
  * a coarsened one restricted (the mean of its 2^d children); then every cell
  * is inverted (guess: the parent's or the children's mean primitives) with
- * floors, as after a stage. */
+ * floors, as after a stage.  With constrained transport the face fields are
+ * transferred first (kept: copied; a face on a changed block's boundary held
+ * by an old leaf of the same level: that value; coarsened: the mean of the
+ * finer faces; refined: parent faces split with +-1/4 of their limited
+ * differences across, faces inside a parent cell from the least-norm
+ * divergence-free completion) and the cells' field is the mean of their
+ * faces.  Refinement needs nx even in the active directions. */
 void or_estimate(or_ctx* c, double eps, double* block_err);
 int or_regrid_plan(const or_params* p, int nb, const int* blocks, const double* block_err, double tol_refine,
                    double tol_coarsen, int max_level, int cap, int* new_blocks);
