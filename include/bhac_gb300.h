@@ -268,7 +268,19 @@ bhac_status bhac_get_faces(bhac_ctx* ctx, double* faces, int on_device);
  * inverted with floors (guess: the parent's or the children's mean
  * primitives) as after a stage.  Asynchronous on fresh's stream, which first
  * waits for the work enqueued on old's; `old` may be destroyed once fresh's
- * stream has passed the call.  Cleaning form only (BHAC_ERR_ARG otherwise). */
+ * stream has passed the call.  Both contexts use the same div B control.  With
+ * constrained transport (the loaded faces of `old` required, BHAC_ERR_STATE
+ * otherwise; nx even in every active direction, BHAC_ERR_ARG otherwise) the
+ * face fields go first: a kept block's are copied; a changed block's face on
+ * its boundary that an old leaf of the same level held keeps that value; a
+ * coarsened block's faces are the mean of the old finer faces on them; a
+ * refined block's faces on its parent's face planes are the parent face plus
+ * +-1/4 of its minmod-limited differences to the parent faces beside it
+ * (within the parent block, one-sided at its edge), keeping the parent face's
+ * flux, and the faces inside a parent cell are the mean of the two outer
+ * faces at the same place plus the least-norm change that makes the finer
+ * cells divergence-free; then the cells' field is the mean of their faces.
+ * Reading of the hot path (the paper names no transfer rule). */
 bhac_status bhac_estimate(bhac_ctx* ctx, double eps, double* block_err);
 bhac_status bhac_regrid_plan(const bhac_grid_desc* desc, const bhac_block_desc* blocks, int nblocks,
                              const double* block_err, double tol_refine, double tol_coarsen, int max_level,

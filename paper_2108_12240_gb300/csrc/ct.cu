@@ -76,9 +76,6 @@ CtGeom ct_geom(const bhac_grid_desc* d) {
   return g;
 }
 
-static long long ring_index_h(const CtGeom& g, int d, int i, int j, int k) {
-  return g.foff[d] + ((long long)(k + g.fo[d][2]) * g.fe[d][1] + (j + g.fo[d][1])) * g.fe[d][0] + (i + g.fo[d][0]);
-}
 
 bool ct_ring_map(const bhac_grid_desc* desc, const bhac_block_desc* blocks, int nb, const CtGeom& g,
                  std::vector<long long>& dst, std::vector<long long>& src) {
@@ -127,8 +124,8 @@ bool ct_ring_map(const bhac_grid_desc* desc, const bhac_block_desc* blocks, int 
             }
             const int o = lut[((size_t)ob[2] * nr[1] + ob[1]) * nr[0] + ob[0]];
             if (o < 0) return false;
-            dst.push_back((long long)b * g.nfb + ring_index_h(g, d, i, j, k));
-            src.push_back((long long)o * g.nfb + ring_index_h(g, d, lf[0], lf[1], lf[2]));
+            dst.push_back((long long)b * g.nfb + ring_index(g, d, i, j, k));
+            src.push_back((long long)o * g.nfb + ring_index(g, d, lf[0], lf[1], lf[2]));
           }
   }
   return true;
@@ -191,7 +188,7 @@ struct LevelCtx {
       lf[dd] = (int)(G[dd] - bc[dd] * d->nx[dd]);
       const int b = leaves.get(d, L, bc);
       if (b >= 0) {
-        src[0] = (long long)b * g->nfb + ring_index_h(*g, dd, lf[0], lf[1], lf[2]);
+        src[0] = (long long)b * g->nfb + ring_index(*g, dd, lf[0], lf[1], lf[2]);
         return 1;
       }
     }
@@ -242,9 +239,6 @@ struct LevelCtx {
   }
 };
 
-__device__ __forceinline__ long long ring_index(const CtGeom& g, int d, int i, int j, int k) {
-  return g.foff[d] + ((long long)(k + g.fo[d][2]) * g.fe[d][1] + (j + g.fo[d][1])) * g.fe[d][0] + (i + g.fo[d][0]);
-}
 
 // flux of variable v through face (d; i, j, k) of block b
 __device__ __forceinline__ double xf_at(const CtArgs& c, int b, int d, int v, int i, int j, int k) {
@@ -405,14 +399,6 @@ __device__ __forceinline__ double emf2(const CtArgs& c, int b, int i, int j, int
                  xf_at(c, b, 2, B1, i - 1, j, k));
 }
 
-__device__ __forceinline__ void owned_face(const CtGeom& g, int r, int& d, int& i, int& j, int& k) {
-  d = (g.ndim == 3 && r >= g.own_off[2]) ? 2 : (r >= g.own_off[1] ? 1 : 0);
-  const int q = r - (int)g.own_off[d];
-  const int n0 = g.nx[0] + (d == 0), n1 = g.nx[1] + (d == 1);
-  i = q % n0;
-  j = (q / n0) % n1;
-  k = q / (n0 * n1);
-}
 
 // d_t Phi = -curl E and the stage combination, one thread per owned face.
 template <int DIM>
@@ -676,7 +662,7 @@ CtLevelMaps ct_level_maps(const bhac_grid_desc* d, const bhac_block_desc* blocks
             long long src[4];
             const int n = X.face_sources(dd, L, G, src);
             if (n == 0) return M;
-            const long long dst = (long long)b * g.nfb + ring_index_h(g, dd, i, j, k);
+            const long long dst = (long long)b * g.nfb + ring_index(g, dd, i, j, k);
             if (n == 1) {
               M.copy_dst.push_back(dst);
               M.copy_src.push_back(src[0]);
@@ -689,7 +675,7 @@ CtLevelMaps ct_level_maps(const bhac_grid_desc* d, const bhac_block_desc* blocks
   // coarse fluxes on level boundaries: the mean of the finer ones (the finer
   // faces in the order: first transverse direction (d + 1) % 3 outer, (d + 2) % 3 inner)
   auto xf_index = [&](int b, int dd, int i, int j, int k) {
-    return (long long)b * NV * g.nfb + NV * g.foff[dd] + (ring_index_h(g, dd, i, j, k) - g.foff[dd]);
+    return (long long)b * NV * g.nfb + NV * g.foff[dd] + (ring_index(g, dd, i, j, k) - g.foff[dd]);
   };
   for (int b = 0; b < nb; ++b) {
     const int L = blocks[b].level;

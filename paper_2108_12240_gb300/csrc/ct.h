@@ -31,6 +31,23 @@ struct CtGeom {
 
 CtGeom ct_geom(const bhac_grid_desc* d);
 
+// Index of face (d; i, j, k) of a block in its ring-layout record (i, j, k
+// local: along d 0..nx_d, across -1..nx_e in active directions).
+__host__ __device__ __forceinline__ long long ring_index(const CtGeom& g, int d, int i, int j, int k) {
+  return g.foff[d] + ((long long)(k + g.fo[d][2]) * g.fe[d][1] + (j + g.fo[d][1])) * g.fe[d][0] + (i + g.fo[d][0]);
+}
+
+// Direction and local index of owned face r of a block (the public order:
+// d, then k, j, i with i fastest).
+__host__ __device__ __forceinline__ void owned_face(const CtGeom& g, int r, int& d, int& i, int& j, int& k) {
+  d = (g.ndim == 3 && r >= g.own_off[2]) ? 2 : (r >= g.own_off[1] ? 1 : 0);
+  const int q = r - (int)g.own_off[d];
+  const int n0 = g.nx[0] + (d == 0), n1 = g.nx[1] + (d == 1);
+  i = q % n0;
+  j = (q / n0) % n1;
+  k = q / (n0 * n1);
+}
+
 // Ring faces: for every block and ring slot, the Phi index it copies (a face
 // owned by the neighbour across, after the boundary rules).  Returns false if a
 // rule points at a missing block.

@@ -13,11 +13,27 @@
 // slopes (within the parent block; zero at its faces) times +-1/4; a new parent
 // takes the mean of its 2^d children.  Sums of sqrt(gamma) U dV are unchanged.
 // Every new cell is then inverted with floors, as after a stage.
+//
+// With constrained transport the face fields are transferred first: a kept
+// block's faces are copied; a changed block's face on its boundary that an old
+// leaf of the same level held keeps that value; a coarsened block's faces are
+// the mean of the old finer faces on them; a refined block's faces on the
+// planes of its parent's faces are the parent face plus +-1/4 of its
+// minmod-limited differences to the neighbouring parent faces across (within
+// the parent; one-sided at its edge), which keeps the parent face's flux, and
+// the faces inside a parent cell complete the 2^d finer cells divergence-free
+// with the least change from the mean of the two outer faces at the same
+// place: the change is -A^T y with A the finer cells' divergence operator and
+// y solving (A A^T) y = r (r the divergences before the change); A A^T is the
+// weighted Laplacian of the cube graph of the finer cells, whose eigenvectors
+// are the Walsh functions, so y comes in closed form.  The cells' field is
+// then the mean of their faces.
 #include <algorithm>
 #include <array>
 #include <map>
 #include <vector>
 
+#include "ct.h"
 #include "ctx.h"
 #include "stage_impl.cuh"
 
@@ -58,14 +74,159 @@ __global__ void __launch_bounds__(256) estimate_kernel(StageArgs a, const T* __r
 
 // Per new block: [0] kind (0 copy, 1 prolong, 2 restrict), [1] the old block
 // (copy, prolong), [2 + s] the old child whose offset bits along the active
-// dimensions are s (restrict).
-constexpr int kMapStride = 10;
+// dimensions are s (restrict), [10 + 2 d + side] the old leaf of the block's
+// level across its low (side 0) / high (side 1) face normal to d, or -1.
+constexpr int kMapStride = 16;
 
 struct TransferArgs {
   const int* map;
   const double* U_old;   // densitized, interior, old blocks
   const double* P_old;   // ghosted FP64 primitives of the old blocks
+  const double* phi;     // constrained transport: the new face fields (else null)
+  CtGeom g;
 };
+
+// The face fields of every new block except those inside refined parents'
+// cells, one thread per owned face.
+template <int DIM>
+__global__ void __launch_bounds__(256) face_transfer_kernel(StageArgs a, const int* __restrict__ map, CtGeom g,
+                                                           const double* __restrict__ phi_old, double* phi) {
+  const unsigned n = (unsigned)a.nblocks * (unsigned)g.nown_b;
+  for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+    const int b = (int)(t / (unsigned)g.nown_b);
+    int d, f[3];
+    owned_face(g, (int)(t - (unsigned)b * (unsigned)g.nown_b), d, f[0], f[1], f[2]);
+    const int* m = map + (size_t)b * kMapStride;
+    const int nxd[3] = {a.nx, a.ny, a.nz};
+    const int bc[3] = {a.blk[4 * b + 1], a.blk[4 * b + 2], a.blk[4 * b + 3]};
+    double* dst = phi + (long long)b * g.nfb + ring_index(g, d, f[0], f[1], f[2]);
+    if (m[0] == 0) {
+      *dst = phi_old[(long long)m[1] * g.nfb + ring_index(g, d, f[0], f[1], f[2])];
+      continue;
+    }
+    if (f[d] == 0 || f[d] == nxd[d]) {
+      const int across = m[10 + 2 * d + (f[d] == 0 ? 0 : 1)];
+      if (across >= 0) {
+        int o[3] = {f[0], f[1], f[2]};
+        o[d] = f[d] == 0 ? nxd[d] : 0;
+        *dst = phi_old[(long long)across * g.nfb + ring_index(g, d, o[0], o[1], o[2])];
+        continue;
+      }
+    }
+    int G[3];
+    for (int e = 0; e < 3; ++e) G[e] = bc[e] * nxd[e] + f[e];
+    if (m[0] == 2) {
+      // the mean of the old finer faces on it, first transverse direction the low bit
+      int tr[2], nt = 0;
+      for (int e = 0; e < DIM; ++e)
+        if (e != d) tr[nt++] = e;
+      double sum = 0.0;
+      for (int q = 0; q < (1 << nt); ++q) {
+        int F[3] = {G[0], G[1], G[2]}, lf[3], slot = 0;
+        F[d] = 2 * G[d];
+        for (int u = 0; u < nt; ++u) F[tr[u]] = 2 * G[tr[u]] + ((q >> u) & 1);
+        for (int e = 0; e < 3; ++e) {
+          if (e >= DIM) {
+            lf[e] = F[e] - bc[e] * nxd[e];
+            continue;
+          }
+          int off = (F[e] - 2 * bc[e] * nxd[e]) / nxd[e];
+          if (off > 1) off = 1;  // the child's high face
+          lf[e] = F[e] - (2 * bc[e] + off) * nxd[e];
+          slot |= off << e;
+        }
+        sum += phi_old[(long long)m[2 + slot] * g.nfb + ring_index(g, d, lf[0], lf[1], lf[2])];
+      }
+      *dst = sum / (1 << nt);
+      continue;
+    }
+    if (G[d] & 1) continue;  // inside a parent cell: the next kernel
+    int pl[3];
+    for (int e = 0; e < 3; ++e) pl[e] = e < DIM ? (G[e] >> 1) - (bc[e] >> 1) * nxd[e] : f[e];
+    const double* P = phi_old + (long long)m[1] * g.nfb;
+    const double pc = P[ring_index(g, d, pl[0], pl[1], pl[2])];
+    double val = pc;
+    for (int e = 0; e < DIM; ++e) {
+      if (e == d) continue;
+      int lo[3] = {pl[0], pl[1], pl[2]}, hi[3] = {pl[0], pl[1], pl[2]};
+      lo[e] -= 1;
+      hi[e] += 1;
+      const bool hl = pl[e] > 0, hh = pl[e] < nxd[e] - 1;
+      const double dl = hl ? pc - P[ring_index(g, d, lo[0], lo[1], lo[2])] : 0.0;
+      const double dh = hh ? P[ring_index(g, d, hi[0], hi[1], hi[2])] - pc : 0.0;
+      const double slope = hl && hh ? minmod_t(dl, dh) : (hl ? dl : dh);
+      val += ((G[e] & 1) ? 0.25 : -0.25) * slope;
+    }
+    *dst = val;
+  }
+}
+
+// The faces inside the parent cells of refined blocks: one thread per parent
+// cell (blocks of other kinds skip), the least-norm divergence-free completion.
+template <int DIM>
+__global__ void __launch_bounds__(256) face_interior_kernel(StageArgs a, const int* __restrict__ map, CtGeom g,
+                                                           double* phi) {
+  constexpr int NC = 1 << DIM;
+  const int hx = a.nx / 2, hy = a.ny / 2, hz = DIM == 3 ? a.nz / 2 : 1;
+  const unsigned per = (unsigned)hx * hy * hz;
+  const unsigned n = (unsigned)a.nblocks * per;
+  for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+    const int b = (int)(t / per);
+    if (map[(size_t)b * kMapStride] != 1) continue;
+    const int q = (int)(t - (unsigned)b * per);
+    const int base[3] = {2 * (q % hx), 2 * ((q / hx) % hy), DIM == 3 ? 2 * (q / (hx * hy)) : 0};
+    const int L = a.blk[4 * b];
+    double ih[3], w[3];
+    for (int d = 0; d < 3; ++d) {
+      ih[d] = d < DIM ? a.idx[d] * (double)(1 << L) : 0.0;
+      w[d] = ih[d] * ih[d];
+    }
+    double* P = phi + (long long)b * g.nfb;
+    // the first values: the mean of the two outer faces at the same place
+    double x0[DIM][NC], lo[DIM][NC], hi[DIM][NC];
+    for (int d = 0; d < DIM; ++d)
+      for (int c = 0; c < NC; ++c) {
+        int cl[3];
+        for (int e = 0; e < 3; ++e) cl[e] = base[e] + (e < DIM ? (c >> e) & 1 : 0);
+        int fl[3] = {cl[0], cl[1], cl[2]}, fh[3] = {cl[0], cl[1], cl[2]};
+        fl[d] = base[d];
+        fh[d] = base[d] + 2;
+        lo[d][c] = P[ring_index(g, d, fl[0], fl[1], fl[2])];
+        hi[d][c] = P[ring_index(g, d, fh[0], fh[1], fh[2])];
+        x0[d][c] = 0.5 * (lo[d][c] + hi[d][c]);  // used for c with bit d clear
+      }
+    // divergence of each finer cell with the first values
+    double r[NC];
+    for (int c = 0; c < NC; ++c) {
+      double s = 0.0;
+      for (int d = 0; d < DIM; ++d) {
+        const int c0 = c & ~(1 << d);
+        s += ((c >> d) & 1) ? (hi[d][c] - x0[d][c0]) * ih[d] : (x0[d][c0] - lo[d][c]) * ih[d];
+      }
+      r[c] = s;
+    }
+    // y = sum over the Walsh functions chi_s, s != 0, of <chi_s, r> / (NC lambda_s) chi_s,
+    // lambda_s = 2 sum_{d in s} 1/h_d^2
+    double y[NC];
+    for (int c = 0; c < NC; ++c) y[c] = 0.0;
+    for (int sw = 1; sw < NC; ++sw) {
+      double proj = 0.0, lam = 0.0;
+      for (int c = 0; c < NC; ++c) proj += (__popc(sw & c) & 1) ? -r[c] : r[c];
+      for (int d = 0; d < DIM; ++d)
+        if ((sw >> d) & 1) lam += 2.0 * w[d];
+      const double coef = proj / (NC * lam);
+      for (int c = 0; c < NC; ++c) y[c] += (__popc(sw & c) & 1) ? -coef : coef;
+    }
+    for (int d = 0; d < DIM; ++d)
+      for (int c = 0; c < NC; ++c) {
+        if ((c >> d) & 1) continue;
+        int fl[3];
+        for (int e = 0; e < 3; ++e) fl[e] = base[e] + (e < DIM ? (c >> e) & 1 : 0);
+        fl[d] = base[d] + 1;
+        P[ring_index(g, d, fl[0], fl[1], fl[2])] = x0[d][c] + (y[c | (1 << d)] - y[c]) * ih[d];
+      }
+  }
+}
 
 template <typename T, int DIM, bool FLAT>
 __global__ void __launch_bounds__(256) transfer_kernel(StageArgs a, TransferArgs r) {
@@ -141,6 +302,17 @@ __global__ void __launch_bounds__(256) transfer_kernel(StageArgs a, TransferArgs
         Pg[v] /= nch;
       }
     }
+    if (r.phi) {
+      // constrained transport: the cell field is the mean of the new faces
+      const double* P = r.phi + (long long)b * r.g.nfb;
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) {
+        int h[3] = {loc[0], loc[1], loc[2]};
+        h[d] += 1;
+        U[B1 + d] = 0.5 * (P[ring_index(r.g, d, loc[0], loc[1], loc[2])] + P[ring_index(r.g, d, h[0], h[1], h[2])]);
+      }
+      U[PSI] = 0.0;
+    }
     // the guess goes where finish_cell reads the previous primitives
     double* Pin = const_cast<double*>(a.P_in) + (size_t)b * NV * a.ncell + cg;
 #pragma unroll
@@ -152,15 +324,32 @@ __global__ void __launch_bounds__(256) transfer_kernel(StageArgs a, TransferArgs
   reduce_outputs(a, cnt, rate_max);
 }
 
-template <typename T>
-cudaError_t launch_transfer_t(const StageArgs& a, const TransferArgs& r, cudaStream_t st) {
+int transfer_grid(long long n) {
   int dev = 0, nsm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  const long long n = (long long)a.nblocks * a.nint;
   long long g = (n + 255) / 256;
   if (g > 32LL * nsm) g = 32LL * nsm;
-  const int grid = (int)(g < 1 ? 1 : g);
+  return (int)(g < 1 ? 1 : g);
+}
+
+cudaError_t launch_face_transfer(const StageArgs& a, const int* map, const CtGeom& g, const double* phi_old,
+                                 double* phi, cudaStream_t st) {
+  const long long nf = (long long)a.nblocks * g.nown_b;
+  const long long nc = (long long)a.nblocks * (a.nx / 2) * (a.ny / 2) * (a.ndim == 3 ? a.nz / 2 : 1);
+  if (a.ndim == 3) {
+    face_transfer_kernel<3><<<transfer_grid(nf), 256, 0, st>>>(a, map, g, phi_old, phi);
+    face_interior_kernel<3><<<transfer_grid(nc), 256, 0, st>>>(a, map, g, phi);
+  } else {
+    face_transfer_kernel<2><<<transfer_grid(nf), 256, 0, st>>>(a, map, g, phi_old, phi);
+    face_interior_kernel<2><<<transfer_grid(nc), 256, 0, st>>>(a, map, g, phi);
+  }
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_transfer_t(const StageArgs& a, const TransferArgs& r, cudaStream_t st) {
+  const int grid = transfer_grid((long long)a.nblocks * a.nint);
   if (a.ndim == 3)
     a.flat ? transfer_kernel<T, 3, true><<<grid, 256, 0, st>>>(a, r) : transfer_kernel<T, 3, false><<<grid, 256, 0, st>>>(a, r);
   else
@@ -409,12 +598,14 @@ extern "C" bhac_status bhac_regrid_plan(const bhac_grid_desc* d, const bhac_bloc
 extern "C" bhac_status bhac_regrid_transfer(const bhac_ctx* old, bhac_ctx* fresh) {
   if (!old || !fresh || old == fresh) return BHAC_ERR_ARG;
   const bhac_grid_desc &a = old->d, &b = fresh->d;
-  if (a.ndim != b.ndim || a.precision != b.precision || a.coords != b.coords || a.divb != BHAC_DIVB_GLM ||
-      b.divb != BHAC_DIVB_GLM)
+  if (a.ndim != b.ndim || a.precision != b.precision || a.coords != b.coords || a.divb != b.divb)
     return BHAC_ERR_ARG;
-  for (int k = 0; k < 3; ++k)
+  const bool ct = a.divb == BHAC_DIVB_CT;
+  for (int k = 0; k < 3; ++k) {
     if (a.nx[k] != b.nx[k] || a.nroot[k] != b.nroot[k]) return BHAC_ERR_ARG;
-  if (!old->prims_ok || !fresh->metric_ok) return BHAC_ERR_STATE;
+    if (ct && k < a.ndim && (a.nx[k] & 1)) return BHAC_ERR_ARG;  // parent cells split inside a block
+  }
+  if (!old->prims_ok || !fresh->metric_ok || (ct && !old->faces_ok)) return BHAC_ERR_STATE;
   // which old blocks feed each new one
   std::map<std::array<int, 4>, int> where;
   for (int n = 0; n < old->nb; ++n)
@@ -431,6 +622,19 @@ extern "C" bhac_status bhac_regrid_transfer(const bhac_ctx* old, bhac_ctx* fresh
       m[1] = it->second;
       continue;
     }
+    // the old leaves of this level across each face (periodic wrap)
+    for (int d = 0; d < nd; ++d)
+      for (int side = 0; side < 2; ++side) {
+        int q[3] = {c[0], c[1], c[2]};
+        const int nbd = b.nroot[d] << L;
+        q[d] += side ? 1 : -1;
+        if (q[d] < 0 || q[d] >= nbd) {
+          if (b.bc[d][side] != BHAC_BC_PERIODIC) continue;
+          q[d] = (q[d] + nbd) % nbd;
+        }
+        auto jt = where.find({L, q[0], q[1], q[2]});
+        if (jt != where.end()) m[10 + 2 * d + side] = jt->second;
+      }
     const int p[3] = {c[0] >> 1, c[1] >> 1, nd == 3 ? c[2] >> 1 : c[2]};
     if (L > 0 && (it = where.find({L - 1, p[0], p[1], p[2]})) != where.end()) {
       m[0] = 1;
@@ -467,12 +671,20 @@ extern "C" bhac_status bhac_regrid_transfer(const bhac_ctx* old, bhac_ctx* fresh
   r.map = d_map;
   r.U_old = old->U[old->ucur];
   r.P_old = old->P[old->cur];
-  e = fresh->mixed ? launch_transfer_t<float>(s, r, fresh->st) : launch_transfer_t<double>(s, r, fresh->st);
+  r.phi = ct ? fresh->phi[0] : nullptr;
+  r.g = fresh->ctg;
+  if (ct) e = launch_face_transfer(s, d_map, fresh->ctg, old->phi[old->pcur], fresh->phi[0], fresh->st);
+  if (e == cudaSuccess)
+    e = fresh->mixed ? launch_transfer_t<float>(s, r, fresh->st) : launch_transfer_t<double>(s, r, fresh->st);
   if (e == cudaSuccess) e = cudaMemsetAsync(fresh->work, 0, sizeof(unsigned int), fresh->st);
   if (e != cudaSuccess) return BHAC_ERR_CUDA;
   fresh->cur = 0;
   fresh->ucur = 0;
   fresh->prims_ok = true;
   fresh->cfl_ok = false;
+  if (ct) {
+    fresh->pcur = 0;
+    fresh->faces_ok = true;
+  }
   return BHAC_OK;
 }
