@@ -9,7 +9,8 @@ with the oracle on 64 blocks in eight 2x2x2 clusters spread over the torus
 body, both polar-axis rows, the inner and outer radial boundaries and the
 phi seam; the oracle recomputes stage 1 on every block within one block of
 a sampled one (through the axis by phi + pi, periodic in phi) and stage 2
-on the sampled blocks.  Error metric and bars as in test_gpu_parity: energy-
+on the sampled blocks.  The same for the constrained-transport forms the
+benchmark times beside them (face fields compared too).  Error metric and bars as in test_gpu_parity: energy-
 scaled per cell and conserved variable, 1e-12 (FP64 form) and 1e-5 (mixed
 form); the per-variable figures are printed (pytest -rP)."""
 import numpy as np
@@ -105,6 +106,48 @@ def test_bench_workload_at_bench_shape(gb, large, form):
     blocks = np.asarray(g.blocks)[sel]
     assert blocks[:, 2].min() == 0 and blocks[:, 2].max() == g.nroot[1] - 1  # both axis rows
     assert blocks[:, 1].min() == 0 and blocks[:, 1].max() == g.nroot[0] - 1  # both radial boundaries
+
+
+@pytest.mark.parametrize("form", ["fp64", "mixed"])
+def test_bench_workload_constrained_transport(gb, large, form):
+    """The benchmark's constrained-transport forms on the same 512x256x256
+    torus (the loop field as face fields): one GPU step against the oracle on
+    the same 64 sampled blocks (stage 1 on their neighbourhoods, whose ring
+    faces and ghost cells the sampled blocks read), conserved variables at the
+    bars above and the sampled blocks' face fields within 1e-12 (FP64) and
+    1e-5 (mixed) of the largest face field."""
+    import torch
+
+    from problems import ct
+    g, P = large
+    g = g.with_(divb="ct")
+    F = ct.fm_torus_faces(g, P)
+    s = gb.Solver(g, form)
+    s.set_prims(P)
+    s.set_faces(F)
+    dt = s.cfl_dt()
+    s.step(dt)
+    got, fgot = s.cons(), s.faces()
+    s.close()
+    del s
+    torch.cuda.empty_cache()
+    sel, hood = sampled_blocks(g)
+    o = oracle.Oracle(g)
+    o.set_prims(P)
+    o.set_faces(F)
+    assert o.cfl_dt() == pytest.approx(dt, rel=1e-13 if form == "fp64" else 1e-5)
+    o.stage(1, dt, blocks=hood)
+    o.stage(2, dt, blocks=sel)
+    ref, fref = o.cons(), o.faces()
+    assert np.all(np.isfinite(got[sel]))
+    err = energy_scaled(got[sel], ref[sel], g, sel)
+    print(f"512x256x256 torus, constrained transport, {form} form, 64 sampled blocks: "
+          f"energy-scaled error per conserved variable (D S1 S2 S3 tau B1 B2 B3 psi) {err.tolist()}")
+    assert np.all(err <= (TOL64 if form == "fp64" else TOLMIX)), err
+    scale = np.abs(F).max()
+    for d, (pg, pr) in enumerate(zip(ct.split_faces(g, fgot), ct.split_faces(g, fref))):
+        gap = np.abs(pg[sel] - pr[sel]).max() / scale
+        assert gap <= (TOL64 if form == "fp64" else TOLMIX), (d, gap)
 
 
 def test_launch_shapes_are_bitwise_identical_mixed(gb):
