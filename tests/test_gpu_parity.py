@@ -398,6 +398,39 @@ def test_launches_per_step(gb):
     assert n >= 2 * (1 + 1 + 1 + 1), n
 
 
+@pytest.mark.parametrize("name", ["torus_3d", "amr_torus", "torus_3d_ct", "amr_torus_ct", "box_imex"])
+def test_launch_count_is_the_kernels_a_step_runs(gb, name):
+    """bhac_launches_per_step (the bench's gpu_launches) equals the kernels the
+    profiler sees in one device-dt step (copies and memsets are not kernels)."""
+    import torch
+    from torch.autograd import DeviceType
+    from torch.profiler import ProfilerActivity, profile
+
+    from problems import ct
+    if name.startswith("amr"):
+        g = pb.amr_torus(root=(4, 2, 2), nblock=8)
+    elif name == "box_imex":
+        g = pb.periodic_box(ndim=3, nblock=8, nroot=2, kappa=50.0, imex=True)
+    else:
+        g = pb.torus_3d(nroot=(4, 3, 2))
+    P = pb.random_periodic_prims(g, jump=True) if name == "box_imex" else pb.fm_torus_prims(g)
+    if name.endswith("_ct"):
+        g = g.with_(divb="ct")
+    s = gb.Solver(g)
+    s.set_prims(P)
+    if name.endswith("_ct"):
+        s.set_faces(ct.fm_torus_faces(g, P))
+    s.cfl_dt()
+    s.step(0.0)
+    torch.cuda.synchronize()
+    with profile(activities=[ProfilerActivity.CUDA]) as prof:
+        s.step(0.0)
+        torch.cuda.synchronize()
+    kernels = [e.name for e in prof.events() if e.device_type == DeviceType.CUDA
+               and not e.name.startswith(("Memset", "Memcpy", "memset", "memcpy"))]
+    assert len(kernels) == s.launches_per_step(), (name, sorted(set(kernels)), len(kernels))
+
+
 @pytest.mark.parametrize("make", ["shock_tube", "torus_3d", "amr_torus"])
 def test_ghost_fill_matches_oracle(gb, make):
     """After one fill, every ghost cell equals the oracle's: same-level copies
