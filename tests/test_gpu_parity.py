@@ -423,9 +423,12 @@ def test_launch_count_is_the_kernels_a_step_runs(gb, name):
     s.cfl_dt()
     s.step(0.0)
     torch.cuda.synchronize()
-    with profile(activities=[ProfilerActivity.CUDA]) as prof:
-        s.step(0.0)
-        torch.cuda.synchronize()
+    # the profiler's first session in a process can come back without device
+    # events; the count is taken from the second
+    for _ in range(2):
+        with profile(activities=[ProfilerActivity.CUDA]) as prof:
+            s.step(0.0)
+            torch.cuda.synchronize()
     kernels = [e.name for e in prof.events() if e.device_type == DeviceType.CUDA
                and not e.name.startswith(("Memset", "Memcpy", "memset", "memcpy"))]
     assert len(kernels) == s.launches_per_step(), (name, sorted(set(kernels)), len(kernels))
