@@ -443,6 +443,17 @@ bhac_status bhac_count_flops(bhac_ctx* ctx, double dt, int nsamples, unsigned se
  * file-scope device array, so concurrent calls race on them. */
 bhac_status bhac_check_bit_ops(long long n, unsigned seed, long long out[11]);
 
+/* Self-check utility of the host-built constrained-transport maps (no device
+ * work; the paper has no counterpart): for a constrained-transport descriptor
+ * and its leaves, applies the ring-face maps bhac_init_grid would build to
+ * `owned` (host, every block's owned faces in the bhac_set_faces layout) and
+ * writes every block's ring-extended face arrays to `ring` (host): per block,
+ * per active d, extents nx_e + 2 across active directions (local index -1 at
+ * position 0) and nx_d + 1 along d, i fastest; zero where nothing maps.
+ * BHAC_ERR_ARG for an invalid descriptor or a grid the maps reject. */
+bhac_status bhac_ct_ring_faces_host(const bhac_grid_desc* desc, const bhac_block_desc* blocks, int nblocks,
+                                    const double* owned, double* ring);
+
 /* Measurement utility for the roofline (the paper has no counterpart): the
  * arithmetic throughput of the current device, each figure from one kernel that
  * keeps 8 CTAs of 256 threads per SM busy with 8 independent chains per

@@ -21,7 +21,7 @@ __all__ = [
     "bhac_query_sizes", "bhac_init_grid", "bhac_set_metric", "bhac_set_prims", "bhac_fill_ghosts",
     "bhac_cfl_dt", "bhac_step", "bhac_stage", "bhac_get_prims", "bhac_get_cons", "bhac_get_diagnostics",
     "bhac_set_launch", "bhac_count_flops", "bhac_graph_capture", "bhac_graph_launch", "bhac_cfl_dt_static", "bhac_destroy",
-    "bhac_status_string", "bhac_check_bit_ops", "bhac_launches_per_step", "bhac_get_prims_ghosted",
+    "bhac_status_string", "bhac_check_bit_ops", "bhac_ct_ring_faces_host", "bhac_launches_per_step", "bhac_get_prims_ghosted",
     "bhac_get_c2p_status", "bhac_set_cons", "bhac_set_prims_host_async", "bhac_get_prims_host_async",
     "bhac_host_fence", "bhac_measure_peaks", "bhac_set_faces", "bhac_get_faces",
     "bhac_estimate", "bhac_regrid_plan", "bhac_regrid_transfer", "bhac_set_split", "bhac_set_zsplit",
@@ -95,6 +95,7 @@ def lib():
             "bhac_graph_launch": ([vp], i),
             "bhac_cfl_dt_static": ([G, B, i, vp, vp, vp], i),
             "bhac_check_bit_ops": ([C.c_longlong, C.c_uint, C.POINTER(C.c_longlong)], i),
+            "bhac_ct_ring_faces_host": ([G, B, i, vp, vp], i),
             "bhac_launches_per_step": ([vp, C.POINTER(i)], i),
             "bhac_get_prims_ghosted": ([vp, vp, i], i),
             "bhac_get_c2p_status": ([vp, vp, i], i),
@@ -270,6 +271,26 @@ def bhac_check_bit_ops(n: int, seed: int = 1):
     out = (C.c_longlong * 11)()
     _check("bhac_check_bit_ops", lib().bhac_check_bit_ops(n, seed, out))
     return list(out)
+
+
+def bhac_ct_ring_faces_host(grid, owned):
+    """The library's ring-face maps applied on the host to the owned faces of
+    a constrained-transport grid: per active d, (nb, nz', ny', nx') arrays
+    with the ring one face outside each block (no device work)."""
+    d = desc_of(grid)
+    blocks = blocks_of(grid)
+    owned = np.ascontiguousarray(owned, dtype=np.float64)
+    ext = [[grid.nx[e] + (1 if e == dd else (2 if e < grid.ndim else 0)) for e in range(3)] for dd in range(grid.ndim)]
+    per = [int(np.prod(x)) for x in ext]
+    out = np.zeros(grid.nb * sum(per))
+    _check("bhac_ct_ring_faces_host", lib().bhac_ct_ring_faces_host(
+        C.byref(d), blocks, grid.nb, owned.ctypes.data_as(C.c_void_p), out.ctypes.data_as(C.c_void_p)))
+    blk = out.reshape(grid.nb, sum(per))
+    res, o = [], 0
+    for x, n in zip(ext, per):
+        res.append(blk[:, o:o + n].reshape(grid.nb, x[2], x[1], x[0]))
+        o += n
+    return res
 
 
 def bhac_measure_peaks(iters: int = 1 << 14, stream_ptr: int = 0):

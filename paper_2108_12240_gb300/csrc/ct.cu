@@ -779,6 +779,50 @@ CtLevelMaps ct_level_maps(const bhac_grid_desc* d, const bhac_block_desc* blocks
   return M;
 }
 
+}  // namespace bhac
+
+// Host self-check of the constrained-transport ring maps (test utility).
+extern "C" bhac_status bhac_ct_ring_faces_host(const bhac_grid_desc* d, const bhac_block_desc* b, int nb,
+                                               const double* owned, double* ring) {
+  using namespace bhac;
+  if (!d || !b || !owned || !ring || nb <= 0 || d->divb != BHAC_DIVB_CT || d->ndim < 2 || d->ndim > 3 ||
+      d->nlevels < 1 || d->nlevels > MAXLEV)
+    return BHAC_ERR_ARG;
+  const CtGeom g = ct_geom(d);
+  std::vector<long long> cd, cs, md, ms;
+  if (d->nlevels == 1) {
+    if (!ct_ring_map(d, b, nb, g, cd, cs)) return BHAC_ERR_ARG;
+  } else {
+    CtLevelMaps M = ct_level_maps(d, b, nb, g);
+    if (!M.ok) return BHAC_ERR_ARG;
+    cd.swap(M.copy_dst);
+    cs.swap(M.copy_src);
+    md.swap(M.mean_dst);
+    ms.swap(M.mean_src);
+  }
+  for (long long t = 0; t < (long long)nb * g.nfb; ++t) ring[t] = 0.0;
+  for (int q = 0; q < nb; ++q)
+    for (long long r = 0; r < g.nown_b; ++r) {
+      int dd, i, j, k;
+      owned_face(g, (int)r, dd, i, j, k);
+      ring[(long long)q * g.nfb + ring_index(g, dd, i, j, k)] = owned[(long long)q * g.nown_b + r];
+    }
+  for (size_t t = 0; t < cd.size(); ++t) ring[cd[t]] = ring[cs[t]];
+  for (size_t t = 0; t < md.size(); ++t) {
+    double s = 0.0;
+    int m = 0;
+    for (int q = 0; q < 4; ++q)
+      if (ms[4 * t + q] >= 0) {
+        s += ring[ms[4 * t + q]];
+        ++m;
+      }
+    ring[md[t]] = s / m;
+  }
+  return BHAC_OK;
+}
+
+namespace bhac {
+
 cudaError_t launch_ct_ring(const long long* dst, const long long* src, long long n, double* phi, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   ct_ring_kernel<<<grid_of(n), 256, 0, st>>>(dst, src, n, phi);
