@@ -66,7 +66,8 @@ typedef struct {
   int c2p_maxit;         /* Newton iteration cap */
   double rho_floor, rho_floor_pow, p_floor, p_floor_pow, w_max;
   int ct;                /* 0: GLM cleaning; 1: staggered-mesh constrained transport
-                            (uniform grids; psi is not evolved, ch and kappa are ignored) */
+                            (any level structure whose touching leaves differ by at most
+                            one level; psi is not evolved, ch and kappa are ignored) */
   int imex;              /* 0: the cleaning damping -alpha kappa psi is an explicit source;
                             1: it is the implicit part of IMEX-SSP2(2,2,2) */
   int c2p_nk;            /* primary inversion: 0 Newton-Raphson with the analytic Jacobian,

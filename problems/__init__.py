@@ -43,7 +43,7 @@ class Grid:
     p_floor: float = 1e-14
     p_floor_pow: float = 0.0
     w_max: float = 50.0
-    divb: str = "glm"         # "glm" (cleaning) or "ct" (constrained transport, uniform grids)
+    divb: str = "glm"         # "glm" (cleaning) or "ct" (staggered-mesh constrained transport)
     imex: bool = False        # cleaning damping as the implicit part of IMEX-SSP2(2,2,2)
     c2p: str = "newton"       # primary inversion: "newton" (analytic Jacobian) or "nk" (Jacobian-free Newton-Krylov)
     ng: int = 3
