@@ -619,6 +619,9 @@ int grid_of(long long n) {
 CtLevelMaps ct_level_maps(const bhac_grid_desc* d, const bhac_block_desc* blocks, int nb, const CtGeom& g) {
   CtLevelMaps M;
   M.ok = false;
+  // block coordinates enter the leaf keys as 20-bit fields
+  for (int e = 0; e < 3; ++e)
+    if (((long long)d->nroot[e] << (e < d->ndim ? d->nlevels - 1 : 0)) >= (1LL << 20)) return M;
   LevelCtx X;
   X.d = d;
   X.g = &g;
