@@ -228,3 +228,34 @@ def test_three_level_torus_keeps_the_field_divergence_free():
     top = g.nroot[1] * 2 ** g.blocks[:, 0] - 1
     assert np.all(p2[g.blocks[:, 2] == 0][:, :, 0, :] == 0.0)
     assert np.all(p2[g.blocks[:, 2] == top][:, :, -1, :] == 0.0)
+
+
+@pytest.mark.parametrize("ndim, divb", [(2, "ct"), (3, "ct"), (2, "glm"), (3, "glm")])
+def test_grid_entirely_at_level_one_is_the_uniform_finer_grid(ndim, divb):
+    """Every leaf at level 1 of a two-level description is the uniform grid
+    with twice the root blocks: the level-aware paths (spacings, global
+    indices, ring faces and boundary rules at the leaves' level, the EMFs)
+    must reproduce the uniform run bit for bit."""
+    n = 8
+    fine = pb.periodic_box(ndim=ndim, nblock=n, nroot=4).with_(divb=divb)
+    if ndim == 2:
+        blocks = [(1, i, j, 0) for j in range(4) for i in range(4)]
+    else:
+        blocks = [(1, i, j, k) for k in range(4) for j in range(4) for i in range(4)]
+    lev = pb.periodic_box(ndim=ndim, nblock=n, nroot=2).with_(
+        divb=divb, nlevels=2, blocks=np.asarray(blocks, dtype=np.int32))
+    # the same leaves in the same order, so the arrays line up block by block
+    assert np.array_equal(np.asarray(lev.blocks)[:, 1:], np.asarray(fine.blocks)[:, 1:])
+    P = pb.random_periodic_prims(fine, jump=False)
+    outs = []
+    for g in (fine, lev):
+        o = oracle.Oracle(g)
+        o.set_prims(P)
+        if divb == "ct":
+            o.set_faces(ct.random_potential_faces(fine))
+        for _ in range(3 if ndim == 2 else 1):
+            o.step(o.cfl_dt())
+        outs.append((o.cons(), o.faces() if divb == "ct" else None))
+    assert np.array_equal(outs[0][0], outs[1][0])
+    if divb == "ct":
+        assert np.array_equal(outs[0][1], outs[1][1])
