@@ -224,3 +224,32 @@ def test_ct_across_levels_scheme_variants(gb, name, variant):
     assert np.abs(fg - fo).max() <= TOL64 * scale
     assert np.abs(ct.face_divergence(g, fg)).max() <= 1e-12 * scale / _dxmin(g)
     assert ct.level_face_mismatch(g, fg) <= 1e-13 * scale
+
+
+@pytest.mark.parametrize("ndim, divb, form", [(2, "ct", "fp64"), (3, "ct", "fp64"), (3, "ct", "mixed"),
+                                              (3, "glm", "fp64")])
+def test_grid_entirely_at_level_one_is_the_uniform_finer_grid(gb, ndim, divb, form):
+    """The library's level paths (per-level spacings and tables, the level
+    maps of constrained transport with nothing to correct) on a grid whose
+    leaves are all at level 1 give the uniform finer grid's result (the
+    1/dx of level 1 is the uniform grid's exactly on this unit box)."""
+    n = 8
+    fine = pb.periodic_box(ndim=ndim, nblock=n, nroot=4).with_(divb=divb)
+    blocks = [(1, i, j, k) for k in range(4 if ndim == 3 else 1) for j in range(4) for i in range(4)]
+    lev = pb.periodic_box(ndim=ndim, nblock=n, nroot=2).with_(
+        divb=divb, nlevels=2, blocks=np.asarray(blocks, dtype=np.int32))
+    P = pb.random_periodic_prims(fine, jump=False)
+    outs = []
+    for g in (fine, lev):
+        s = gb.Solver(g, form)
+        s.set_prims(P)
+        if divb == "ct":
+            s.set_faces(ct.random_potential_faces(fine))
+        s.cfl_dt()
+        for _ in range(3):
+            s.step(0.0)
+        outs.append((s.cons(), s.faces() if divb == "ct" else None))
+    scale = np.abs(outs[0][0]).max()
+    assert np.abs(outs[0][0] - outs[1][0]).max() <= 1e-14 * scale
+    if divb == "ct":
+        assert np.abs(outs[0][1] - outs[1][1]).max() <= 1e-14 * np.abs(outs[0][1]).max()
