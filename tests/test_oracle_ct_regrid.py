@@ -137,3 +137,28 @@ def test_refining_and_coarsening_again_restores_the_faces(ndim):
     g1 = g.with_(blocks=_refine_root(g, _root(ndim, 1)))
     back = o.regridded(g1.blocks).regridded(g.blocks)
     assert np.abs(back.faces() - F).max() < 1e-14 * np.abs(F).max()
+
+
+def test_three_level_torus_regrid_keeps_the_field_divergence_free():
+    """The three-level torus (polar axis, phi + pi) regridded by its estimator's
+    plan, refinement and coarsening together: every cell's divergence at
+    round-off and the level boundaries consistent after the transfer and
+    after a step."""
+    g = pb.amr_torus(root=(4, 2, 2), nblock=8).with_(divb="ct")
+    P = pb.fm_torus_prims(g)
+    F = ct.fm_torus_faces(g, P)
+    o = oracle.Oracle(g)
+    o.set_prims(P)
+    o.set_faces(F)
+    new = o.regrid_plan(o.estimate(), 0.3, 0.05, 2)
+    old_levels = {tuple(b) for b in np.asarray(g.blocks)}
+    assert any(tuple(b) not in old_levels for b in new)
+    o2 = o.regridded(new)
+    g2 = o2.grid
+    scale = np.abs(F).max() * 64
+    for step in range(2):
+        F2 = o2.faces()
+        assert np.abs(ct.face_divergence(g2, F2)).max() < 1e-12 * scale, step
+        assert ct.level_face_mismatch(g2, F2) < 1e-14 * scale, step
+        assert np.all(np.isfinite(o2.cons()))
+        o2.step(o2.cfl_dt())
