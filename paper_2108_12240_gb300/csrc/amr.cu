@@ -89,12 +89,6 @@ struct Builder {
   }
 
   long long value_of(int L, const long long Gin[3]) {
-    const unsigned long long key = ((unsigned long long)L << 60) |
-                                   ((unsigned long long)(Gin[0] + 64) & 0xfffffULL) |
-                                   (((unsigned long long)(Gin[1] + 64) & 0xfffffULL) << 20) |
-                                   (((unsigned long long)(Gin[2] + 64) & 0xfffffULL) << 40);
-    auto it = memo.find(key);
-    if (it != memo.end()) return it->second;
     long long G[3] = {Gin[0], Gin[1], Gin[2]};
     unsigned fl = 0;
     long long res = 0;
@@ -106,44 +100,50 @@ struct Builder {
     for (int k = 0; k < 3; ++k) bc[k] = G[k] / d->nx[k];
     const int b = lookup(L, bc);
     if (b >= 0) {
+      // a cell of a leaf at this level (most ghost slots): no memo needed
       const long long li = G[0] % d->nx[0] + g[0], lj = G[1] % d->nx[1] + g[1], lk = G[2] % d->nx[2] + g[2];
-      res = op_cell((long long)b * ncell + (lk * N[1] + lj) * N[0] + li, fl);
-    } else {
-      bool coarse = false;
-      for (int Lc = L - 1; Lc >= 0 && !coarse; --Lc) {
-        long long bcc[3];
-        for (int k = 0; k < 3; ++k) bcc[k] = (k < d->ndim ? G[k] >> (L - Lc) : G[k]) / d->nx[k];
-        coarse = lookup(Lc, bcc) >= 0;
-      }
-      if (coarse && L > 0) {
-        long long C[3];
-        for (int k = 0; k < 3; ++k) C[k] = k < d->ndim ? G[k] >> 1 : G[k];
-        std::vector<long long> ops;
-        ops.push_back(value_of(L - 1, C));
-        unsigned parity = 0;
-        for (int k = 0; k < d->ndim; ++k) {
-          long long Cm[3] = {C[0], C[1], C[2]}, Cp[3] = {C[0], C[1], C[2]};
-          Cm[k] -= 1;
-          Cp[k] += 1;
-          ops.push_back(value_of(L - 1, Cm));
-          ops.push_back(value_of(L - 1, Cp));
-          if (G[k] & 1) parity |= 1u << k;
-        }
-        res = add_node(NODE_PROLONG, fl, parity, std::move(ops));
-      } else if (L + 1 < nlev) {
-        std::vector<long long> ops;
-        const int nch = 1 << d->ndim;
-        for (int ch = 0; ch < nch; ++ch) {
-          long long F[3] = {G[0], G[1], G[2]};
-          for (int k = 0; k < d->ndim; ++k) F[k] = 2 * G[k] + ((ch >> k) & 1);
-          ops.push_back(value_of(L + 1, F));
-        }
-        res = add_node(NODE_RESTRICT, fl, 0u, std::move(ops));
-      } else {
-        ok = false;  // nothing holds this cell
-      }
+      return op_cell((long long)b * ncell + (lk * N[1] + lj) * N[0] + li, fl);
     }
-    if (res & OP_NODE) memo[key] = res;  // cells are cheap to look up again
+    const unsigned long long key = ((unsigned long long)L << 60) |
+                                   ((unsigned long long)(Gin[0] + 64) & 0xfffffULL) |
+                                   (((unsigned long long)(Gin[1] + 64) & 0xfffffULL) << 20) |
+                                   (((unsigned long long)(Gin[2] + 64) & 0xfffffULL) << 40);
+    auto it = memo.find(key);
+    if (it != memo.end()) return it->second;
+    bool coarse = false;
+    for (int Lc = L - 1; Lc >= 0 && !coarse; --Lc) {
+      long long bcc[3];
+      for (int k = 0; k < 3; ++k) bcc[k] = (k < d->ndim ? G[k] >> (L - Lc) : G[k]) / d->nx[k];
+      coarse = lookup(Lc, bcc) >= 0;
+    }
+    if (coarse && L > 0) {
+      long long C[3];
+      for (int k = 0; k < 3; ++k) C[k] = k < d->ndim ? G[k] >> 1 : G[k];
+      std::vector<long long> ops;
+      ops.push_back(value_of(L - 1, C));
+      unsigned parity = 0;
+      for (int k = 0; k < d->ndim; ++k) {
+        long long Cm[3] = {C[0], C[1], C[2]}, Cp[3] = {C[0], C[1], C[2]};
+        Cm[k] -= 1;
+        Cp[k] += 1;
+        ops.push_back(value_of(L - 1, Cm));
+        ops.push_back(value_of(L - 1, Cp));
+        if (G[k] & 1) parity |= 1u << k;
+      }
+      res = add_node(NODE_PROLONG, fl, parity, std::move(ops));
+    } else if (L + 1 < nlev) {
+      std::vector<long long> ops;
+      const int nch = 1 << d->ndim;
+      for (int ch = 0; ch < nch; ++ch) {
+        long long F[3] = {G[0], G[1], G[2]};
+        for (int k = 0; k < d->ndim; ++k) F[k] = 2 * G[k] + ((ch >> k) & 1);
+        ops.push_back(value_of(L + 1, F));
+      }
+      res = add_node(NODE_RESTRICT, fl, 0u, std::move(ops));
+    } else {
+      ok = false;  // nothing holds this cell
+    }
+    if (res & OP_NODE) memo[key] = res;
     return res;
   }
 };

@@ -30,7 +30,6 @@
 // the finer faces covering it.
 // psi is not evolved (zero), and no cleaning speed enters the fluxes.
 #include <algorithm>
-#include <unordered_map>
 
 #include "ct.h"
 #include "stage_impl.cuh"
@@ -133,21 +132,30 @@ bool ct_ring_map(const bhac_grid_desc* desc, const bhac_block_desc* blocks, int 
 
 namespace {
 
-// Leaf blocks by (level, block coordinates).
+// Leaf blocks by (level, block coordinates): one dense table per level.
 struct LeafFinder {
-  std::unordered_map<unsigned long long, int> at;
-  static unsigned long long key(int L, long long x, long long y, long long z) {
-    return ((unsigned long long)L << 60) | ((unsigned long long)z << 40) | ((unsigned long long)y << 20) |
-           (unsigned long long)x;
+  std::vector<std::vector<int>> lut;
+  void build(const bhac_grid_desc* d, const bhac_block_desc* blocks, int nb) {
+    lut.resize(d->nlevels);
+    for (int L = 0; L < d->nlevels; ++L) {
+      size_t n = 1;
+      for (int e = 0; e < 3; ++e) n *= (size_t)d->nroot[e] << (e < d->ndim ? L : 0);
+      lut[L].assign(n, -1);
+    }
+    for (int b = 0; b < nb; ++b) {
+      const int L = blocks[b].level;
+      const size_t n0 = (size_t)d->nroot[0] << L, n1 = (size_t)d->nroot[1] << L;
+      lut[L][((size_t)blocks[b].iz * n1 + blocks[b].iy) * n0 + blocks[b].ix] = b;
+    }
   }
   int get(const bhac_grid_desc* d, int L, const long long bc[3]) const {
     if (L < 0 || L >= d->nlevels) return -1;
+    long long n[3];
     for (int e = 0; e < 3; ++e) {
-      const long long n = (long long)d->nroot[e] << (e < d->ndim ? L : 0);
-      if (bc[e] < 0 || bc[e] >= n) return -1;
+      n[e] = (long long)d->nroot[e] << (e < d->ndim ? L : 0);
+      if (bc[e] < 0 || bc[e] >= n[e]) return -1;
     }
-    const auto it = at.find(key(L, bc[0], bc[1], bc[2]));
-    return it == at.end() ? -1 : it->second;
+    return lut[L][(size_t)((bc[2] * n[1] + bc[1]) * n[0] + bc[0])];
   }
 };
 
@@ -619,14 +627,10 @@ int grid_of(long long n) {
 CtLevelMaps ct_level_maps(const bhac_grid_desc* d, const bhac_block_desc* blocks, int nb, const CtGeom& g) {
   CtLevelMaps M;
   M.ok = false;
-  // block coordinates enter the leaf keys as 20-bit fields
-  for (int e = 0; e < 3; ++e)
-    if (((long long)d->nroot[e] << (e < d->ndim ? d->nlevels - 1 : 0)) >= (1LL << 20)) return M;
   LevelCtx X;
   X.d = d;
   X.g = &g;
-  for (int b = 0; b < nb; ++b)
-    X.leaves.at[LeafFinder::key(blocks[b].level, blocks[b].ix, blocks[b].iy, blocks[b].iz)] = b;
+  X.leaves.build(d, blocks, nb);
   const int* nx = d->nx;
   // ring faces: the boundary rules across (at the block's level), then the sources
   for (int b = 0; b < nb; ++b) {
