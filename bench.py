@@ -597,6 +597,67 @@ def all_configs(args):
                           "state_mb_fp64": state_mb, "l2_resident": state_mb < 100, "forms": forms}), flush=True)
 
 
+def regrid_timing(args):
+    """One regrid of the 3-level AMR torus (4220 leaves of 16^3), mixed form,
+    cleaning and constrained transport: the device estimator, the host plan
+    (thresholds 0.3 / 0.05, max level 2), the new context (host maps, arena,
+    metric tables) and the device transfer, beside one step; one JSON line per
+    form of div B control (CUDA events on the context's stream for the device
+    parts, host wall time for the plan and the new context)."""
+    import torch
+
+    import paper_2108_12240_gb300 as gb
+    from problems import ct as pct
+
+    torch.cuda.set_device(0)
+    g0 = pb.amr_torus()
+    P = pb.fm_torus_prims(g0)
+    st = torch.cuda.Stream()
+
+    def ev():
+        return torch.cuda.Event(enable_timing=True)
+
+    for divb in ("glm", "ct"):
+        g = g0.with_(divb=divb)
+        s = gb.Solver(g, "mixed", stream=st)
+        s.set_prims(P)
+        if divb == "ct":
+            s.set_faces(pct.fm_torus_faces(g, P))
+        s.cfl_dt()
+        s.step(0.0)
+        torch.cuda.synchronize()
+        a, b = ev(), ev()
+        a.record(st)
+        s.step(0.0)
+        b.record(st)
+        torch.cuda.synchronize()
+        step_ms = a.elapsed_time(b)
+        a, b = ev(), ev()
+        a.record(st)
+        err = s.estimate()
+        b.record(st)
+        torch.cuda.synchronize()
+        est_ms = a.elapsed_time(b)
+        t0 = time.perf_counter()
+        new = gb.bhac_regrid_plan(gb.desc_of(g, "mixed"), gb.blocks_of(g), err, 0.3, 0.05, 2)
+        plan_s = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        fresh = gb.Solver(g.with_(blocks=new), "mixed", stream=st)
+        torch.cuda.synchronize()
+        init_s = time.perf_counter() - t0
+        a, b = ev(), ev()
+        a.record(st)
+        gb.bhac_regrid_transfer(s.ctx, fresh.ctx)
+        b.record(st)
+        torch.cuda.synchronize()
+        print(json.dumps({"divb": divb, "leaves": [g.nb, int(len(new))], "step_ms": step_ms, "estimate_ms": est_ms,
+                          "plan_s": plan_s, "new_context_s": init_s, "transfer_ms": a.elapsed_time(b)}), flush=True)
+        s.close()
+        fresh.close()
+        del s, fresh
+        torch.cuda.empty_cache()
+
+
 def sweep_blocks(args):
     """The 512x256x256 torus in several block shapes (8^3 to 32^3): zone-updates/s
     and FP64 roofline fraction per shape and form, one JSON line."""
@@ -643,6 +704,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-ct", action="store_true", help="skip the constrained-transport form")
     ap.add_argument("--sweep-blocks", action="store_true", help="block-shape roofline sweep instead of the bench line")
+    ap.add_argument("--regrid-timing", action="store_true", help="one regrid of the AMR torus, timed by part")
     ap.add_argument("--all-configs", action="store_true", help="every workload configuration, one line each")
     ap.add_argument("--shape-runs", nargs="+", metavar="FORM_OR_SHAPE",
                     help="FORM tx,ty,threads,persistent,min_ctas,producers ...: four steps per shape, for ncu")
@@ -657,6 +719,9 @@ def main():
     Z_PARTS = args.z_parts
     if args.sweep_blocks:
         sweep_blocks(args)
+        return
+    if args.regrid_timing:
+        regrid_timing(args)
         return
     if args.all_configs:
         all_configs(args)
