@@ -30,6 +30,7 @@
 // the finer faces covering it.
 // psi is not evolved (zero), and no cleaning speed enters the fluxes.
 #include <algorithm>
+#include <thread>
 
 #include "ct.h"
 #include "stage_impl.cuh"
@@ -632,8 +633,13 @@ CtLevelMaps ct_level_maps(const bhac_grid_desc* d, const bhac_block_desc* blocks
   X.g = &g;
   X.leaves.build(d, blocks, nb);
   const int* nx = d->nx;
-  // ring faces: the boundary rules across (at the block's level), then the sources
-  for (int b = 0; b < nb; ++b) {
+  // ring faces: the boundary rules across (at the block's level), then the
+  // sources; blocks in contiguous ranges on host threads, joined in order
+  struct RingOut {
+    std::vector<long long> copy_dst, copy_src, mean_dst, mean_src;
+    bool ok = true;
+  };
+  auto ring_block = [&](int b, RingOut& R) {
     const int L = blocks[b].level;
     const long long bo[3] = {blocks[b].ix, blocks[b].iy, blocks[b].iz};
     long long N[3];
@@ -665,19 +671,43 @@ CtLevelMaps ct_level_maps(const bhac_grid_desc* d, const bhac_block_desc* blocks
             }
             if (d->ndim == 3 && dd != 2 && d->bc[2][0] == BHAC_BC_PERIODIC) G[2] = ((G[2] % N[2]) + N[2]) % N[2];
             for (int e = 0; e < 3; ++e)
-              if (G[e] < 0 || G[e] > N[e] || (e != dd && G[e] == N[e])) return M;
+              if (G[e] < 0 || G[e] > N[e] || (e != dd && G[e] == N[e])) {
+                R.ok = false;
+                return;
+              }
             long long src[4];
             const int n = X.face_sources(dd, L, G, src);
-            if (n == 0) return M;
+            if (n == 0) {
+              R.ok = false;
+              return;
+            }
             const long long dst = (long long)b * g.nfb + ring_index(g, dd, i, j, k);
             if (n == 1) {
-              M.copy_dst.push_back(dst);
-              M.copy_src.push_back(src[0]);
+              R.copy_dst.push_back(dst);
+              R.copy_src.push_back(src[0]);
             } else {
-              M.mean_dst.push_back(dst);
-              for (int q = 0; q < 4; ++q) M.mean_src.push_back(q < n ? src[q] : -1);
+              R.mean_dst.push_back(dst);
+              for (int q = 0; q < 4; ++q) R.mean_src.push_back(q < n ? src[q] : -1);
             }
           }
+  };
+  {
+    const int nt = std::max(1, std::min(16, std::min(nb / 64, (int)std::thread::hardware_concurrency())));
+    std::vector<RingOut> part(nt);
+    std::vector<std::thread> pool;
+    for (int t = 0; t < nt; ++t)
+      pool.emplace_back([&, t] {
+        for (int b = (int)((long long)nb * t / nt); b < (int)((long long)nb * (t + 1) / nt) && part[t].ok; ++b)
+          ring_block(b, part[t]);
+      });
+    for (auto& th : pool) th.join();
+    for (const RingOut& R : part) {
+      if (!R.ok) return M;
+      M.copy_dst.insert(M.copy_dst.end(), R.copy_dst.begin(), R.copy_dst.end());
+      M.copy_src.insert(M.copy_src.end(), R.copy_src.begin(), R.copy_src.end());
+      M.mean_dst.insert(M.mean_dst.end(), R.mean_dst.begin(), R.mean_dst.end());
+      M.mean_src.insert(M.mean_src.end(), R.mean_src.begin(), R.mean_src.end());
+    }
   }
   // coarse fluxes on level boundaries: the mean of the finer ones (the finer
   // faces in the order: first transverse direction (d + 1) % 3 outer, (d + 2) % 3 inner)
