@@ -16,6 +16,8 @@ from tests.test_oracle_ct_amr import _amr_field, _box
 
 def _grids():
     yield "box2d", pb.periodic_box(ndim=2, nblock=8, nroot=2).with_(divb="ct")
+    yield "torus3d", pb.torus_3d(nroot=(4, 3, 2), nblock=(8, 8, 8)).with_(divb="ct")
+    yield "torus2d", pb.torus_2d(nblock=8, nroot=(4, 4)).with_(divb="ct")
     yield "amr_box2d", _box(2)
     yield "amr_box2d_outflow", _box(2, bc="outflow")
     yield "amr_box3d", _box(3)
